@@ -1,0 +1,241 @@
+"""Seeded synthetic inputs for CFNEB workloads.
+
+This module builds crystal structures and random draws only: lattices,
+vacancies, tilings, strains, seeded Gaussian displacements and request
+streams.  It holds none of the method's arithmetic (no cell filter, no
+interpolation, no forces) and serves the CUDA library, the oracle, the tests
+and the benchmark alike.
+
+Structures are (R, h): Cartesian positions (n, 3) and the lattice matrix h
+with the lattice vectors as rows.  All generators are deterministic for a
+given seed.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+
+_DATA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
+
+# ---------------------------------------------------------------------------
+# Lennard-Jones FCC
+# ---------------------------------------------------------------------------
+
+FCC_BASIS = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.0], [0.5, 0.0, 0.5], [0.0, 0.5, 0.5]])
+LJ_A = 1.5496  # FCC lattice constant (sigma units) used by the LJ workloads
+
+
+def fcc(a, n1, n2, n3):
+    """Conventional FCC supercell n1 x n2 x n3 (4 atoms per cell)."""
+    R = []
+    for i, j, k in itertools.product(range(n1), range(n2), range(n3)):
+        for b in FCC_BASIS:
+            R.append((np.array([i, j, k], dtype=np.float64) + b) * a)
+    h = np.diag([n1 * a, n2 * a, n3 * a]).astype(np.float64)
+    return np.array(R), h
+
+
+def _nearest_neighbour(R, h, i, exclude=()):
+    """Index of the atom nearest to atom i (minimum image; ties: lowest
+    index).  Used only to pick which atom hops."""
+    hinv = np.linalg.inv(h)
+    ds = (R - R[i]) @ hinv
+    ds -= np.round(ds)
+    d = np.linalg.norm(ds @ h, axis=1)
+    d[i] = np.inf
+    for e in exclude:
+        d[e] = np.inf
+    m = d.min()
+    return int(np.flatnonzero(np.isclose(d, m, rtol=0, atol=1e-9))[0])
+
+
+def lj_vacancy_hop(a=LJ_A, reps=(2, 2, 2), divacancy=False):
+    """Vacancy hop in FCC: atom 0 is removed; in the final state its nearest
+    neighbour (lowest index) sits on the vacant site.  With ``divacancy`` a
+    second neighbour of site 0 is removed too and the next neighbour hops.
+
+    Returns (R0, h, R1, h) with matched atom order.
+    """
+    R, h = fcc(a, *reps)
+    site = R[0].copy()
+    removed = [0]
+    if divacancy:
+        removed.append(_nearest_neighbour(R, h, 0))
+    hop = _nearest_neighbour(R, h, 0, exclude=removed)
+    keep = [i for i in range(len(R)) if i not in removed]
+    R0 = R[keep].copy()
+    R1 = R0.copy()
+    R1[keep.index(hop)] = site
+    return R0, h.copy(), R1, h.copy()
+
+
+def strained_cell(h, seed, amplitude=0.02):
+    """h (I + eps) with eps symmetric, entries uniform in [-amplitude, amplitude]."""
+    rng = np.random.default_rng(seed)
+    e = rng.uniform(-amplitude, amplitude, size=(3, 3))
+    e = np.triu(e) + np.triu(e, 1).T
+    return h @ (np.eye(3) + e)
+
+
+def affine(R, h_from, h_to):
+    """Positions carried along by a change of cell (same fractional coords)."""
+    return (R @ np.linalg.inv(h_from)) @ h_to
+
+
+# ---------------------------------------------------------------------------
+# Carbon: AB graphite and hexagonal diamond in one orthohexagonal setting
+# ---------------------------------------------------------------------------
+
+# in-plane fractional sites of a honeycomb layer in the (a, sqrt(3) a) cell
+_ALPHA = [(0.0, 0.0), (0.5, 0.5)]
+_BETA = [(0.5, 1.0 / 6.0), (0.0, 2.0 / 3.0)]
+_LAYER_A = [(0.0, 0.0), (0.5, 1.0 / 6.0), (0.5, 0.5), (0.0, 2.0 / 3.0)]
+_LAYER_B = [(0.5, 1.0 / 6.0), (0.0, 1.0 / 3.0), (0.0, 2.0 / 3.0), (0.5, 5.0 / 6.0)]
+
+
+def _is_alpha(xy):
+    return any(abs(xy[0] - p[0]) < 1e-9 and abs(xy[1] - p[1]) < 1e-9 for p in _ALPHA)
+
+
+def graphite_hexdiamond_cells(a_g=2.46, c_g=6.70, a_d=2.52, c_d=4.12, delta=1.0 / 16.0):
+    """8-atom orthohexagonal cells of AB graphite and hexagonal diamond with
+    matched atom order.
+
+    Graphite: layer A at z=0, layer B at z=1/2 (Bernal stacking).  Diamond
+    target of each atom: layer-A atoms keep their in-plane site; layer-B atoms
+    slide by (0, 1/3) (one bond length along the armchair direction) into
+    A registry; every layer buckles by +-delta (alpha sites up in the lower
+    layer, down in the upper one), which closes the interlayer bonds of
+    lonsdaleite.  Returns (s_g, h_g, s_d, h_d) with fractional coordinates.
+    """
+    s_g, s_d = [], []
+    for (x, y) in _LAYER_A:
+        s_g.append((x, y, 0.0))
+        s_d.append((x, y, delta if _is_alpha((x, y)) else -delta))
+    for (x, y) in _LAYER_B:
+        s_g.append((x, y, 0.5))
+        t = (x, (y + 1.0 / 3.0) % 1.0)
+        t = (t[0], 0.0 if abs(t[1] - 1.0) < 1e-12 else t[1])
+        s_d.append((t[0], t[1], 0.5 - delta if _is_alpha(t) else 0.5 + delta))
+    h_g = np.diag([a_g, math.sqrt(3.0) * a_g, c_g])
+    h_d = np.diag([a_d, math.sqrt(3.0) * a_d, c_d])
+    return np.array(s_g), h_g, np.array(s_d), h_d
+
+
+def tile(R, h, reps):
+    """Replicate a periodic structure reps = (n1, n2, n3) times."""
+    n1, n2, n3 = reps
+    out = []
+    for i, j, k in itertools.product(range(n1), range(n2), range(n3)):
+        shift = i * h[0] + j * h[1] + k * h[2]
+        out.append(R + shift)
+    return np.vstack(out), np.array([h[0] * n1, h[1] * n2, h[2] * n3])
+
+
+def tersoff_endpoint_cells():
+    """Relaxed 8-atom graphite and hexagonal-diamond cells (Tersoff 1988 C).
+
+    Stored in data/tersoff_c_endpoints_8atom.json; the file is written by
+    oracle/make_tersoff_endpoints.py, which relaxes the cells built by
+    graphite_hexdiamond_cells() with the FP64 CPU reference.
+    Returns (R_g, h_g, R_d, h_d).
+    """
+    with open(os.path.join(_DATA, "tersoff_c_endpoints_8atom.json")) as f:
+        d = json.load(f)
+    return (np.array(d["R_graphite"]), np.array(d["h_graphite"]),
+            np.array(d["R_hexdiamond"]), np.array(d["h_hexdiamond"]))
+
+
+def graphite_hexdiamond_path(reps):
+    """Endpoints of the graphite -> hexagonal-diamond band at a tiling."""
+    Rg, hg, Rd, hd = tersoff_endpoint_cells()
+    R0, h0 = tile(Rg, hg, reps)
+    R1, h1 = tile(Rd, hd, reps)
+    return R0, h0, R1, h1
+
+
+# ---------------------------------------------------------------------------
+# Random draws passed to both implementations
+# ---------------------------------------------------------------------------
+
+def interior_noise(seed, n_images, n_atoms, sigma):
+    """Gaussian displacements (n_images-2, n_atoms, 3), numpy PCG64 stream."""
+    rng = np.random.default_rng(seed)
+    return rng.normal(0.0, sigma, size=(n_images - 2, n_atoms, 3))
+
+
+# ---------------------------------------------------------------------------
+# Workloads (sizes of the benchmarked configurations)
+# ---------------------------------------------------------------------------
+
+def lj_vacancy_31():
+    """31-atom LJ FCC vacancy hop (2x2x2 conventional cells, a = 1.5496)."""
+    return dict(name="lj_fcc_vacancy_31", potential="lj", endpoints=lj_vacancy_hop(LJ_A, (2, 2, 2)),
+                n_images=7, k=1.0, climb=True, dt=0.01, fmax=1e-4, cell_filter=False,
+                precision="fp64")
+
+
+def tersoff_graphite_hexdiamond(reps=(6, 4, 3), n_images=9, seed=2510, jitter=0.01,
+                                precision="fp64"):
+    """Graphite -> hexagonal diamond, Tersoff C, cell filter on."""
+    R0, h0, R1, h1 = graphite_hexdiamond_path(reps)
+    n = len(R0)
+    return dict(name="tersoff_graphite_hexdiamond_%d" % n, potential="tersoff",
+                endpoints=(R0, h0, R1, h1), n_images=n_images, k=0.1, climb=True, dt=0.1,
+                fmax=0.05, cell_filter=True, precision=precision,
+                noise=interior_noise(seed, n_images, n, jitter) if jitter else None)
+
+
+TERSOFF_LARGE_REPS = (32, 24, 16)  # 8 * 32 * 24 * 16 = 98,304 atoms
+
+
+def near_cubic_factors(m):
+    """(n1, n2, n3) with n1 n2 n3 = m, as close to cubic as possible."""
+    best = None
+    for n1 in range(1, int(round(m ** (1 / 3))) + 2):
+        if m % n1:
+            continue
+        r = m // n1
+        for n2 in range(n1, int(math.isqrt(r)) + 1):
+            if r % n2:
+                continue
+            n3 = r // n2
+            key = max(n1, n2, n3) - min(n1, n2, n3)
+            if best is None or key < best[0]:
+                best = (key, (n1, n2, n3))
+    return best[1] if best else (1, 1, m)
+
+
+def lj_batch(seed=4, n_bands=64, n_lo=256, n_hi=32768, img_lo=5, img_hi=15, strain=0.02):
+    """Uneven LJ vacancy / divacancy bands with strained end cells."""
+    rng = np.random.default_rng(seed)
+    bands = []
+    for b in range(n_bands):
+        target = math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))
+        m = max(1, int(round(target / 4.0)))
+        reps = near_cubic_factors(m)
+        while min(reps) < 2:  # a vacancy hop needs at least 2 cells per side
+            m += 1
+            reps = near_cubic_factors(m)
+        div = bool(rng.integers(0, 2))
+        n_images = int(rng.integers(img_lo, img_hi + 1))
+        R0, h0, R1, h1 = lj_vacancy_hop(LJ_A, reps, divacancy=div)
+        h1s = strained_cell(h1, seed * 1000 + b, strain)
+        R1s = affine(R1, h1, h1s)
+        bands.append(dict(name="lj_%s_%d" % ("divac" if div else "vac", len(R0)),
+                          potential="lj", endpoints=(R0, h0, R1s, h1s), n_images=n_images,
+                          k=1.0, climb=True, dt=0.01, fmax=0.05, cell_filter=True))
+    return bands
+
+
+def poisson_arrivals(seed, rate, window):
+    """Arrival times of a Poisson process on [0, window)."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= window:
+            return np.array(out)
+        out.append(t)
