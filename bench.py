@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""CFNEB throughput benchmark (atom·steps/s on one GB300, or N replicas).
+
+A step is one pass of the whole relaxation path over the band: cell-filter
+map-back, cell-list build, Tersoff (or LJ) forces/energy/virial, cell-filter
+forces, NEB projection with the climbing image, and the FIRE move.
+atom·steps counts atoms x moving images x steps.
+
+Default workload: the graphite -> hexagonal-diamond Tersoff band tiled to
+98,304 atoms, 12 images (10 moving), mixed precision, rotation-free cell
+filter on, interior images jittered by 0.01 A (seeded).  Inputs are
+synthetic (cfneb_inputs).  The per-step working set (~0.3 GB of positions,
+forces, velocities, cell lists and neighbour lists) exceeds the 129 MB L2,
+so no flush is inserted between steps.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs its own band on its own GPU (weak scaling, no
+data-path collective); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atom·steps/s per GB300 (mixed vs plain FP64); served-band p50/p99 latency"
+UNIT = "atom·steps/s"
+
+WORKLOADS = {
+    "tersoff_graphite_hexdiamond_98304": dict(kind="tersoff", reps=(32, 24, 16), n_images=12,
+                                              precision="mixed", n_max=24),
+    "tersoff_graphite_hexdiamond_576": dict(kind="tersoff", reps=(6, 4, 3), n_images=9,
+                                            precision="fp64", n_max=9),
+}
+CPU_SAMPLE_REPS = (6, 4, 3)   # the 576-atom tile the large band is built from
+
+# algorithmic work per kernel launch: FLOPs for the force
+# kernels (useful arithmetic, transcendental functions counted as 1), bytes for
+# the memory-bound ones.  w = dict(pairs, triples, atoms, dof, ts)
+FLOP_MODELS = {
+    "tersoff_partials": lambda w: 65.0 * w["pairs"] + 89.0 * w["triples"],
+    "lj_force": lambda w: 40.0 * w["pairs"],
+}
+BYTE_MODELS = {
+    "tersoff_gather": lambda w: w["pairs"] * (8 + 6 * w["ts"]) + w["atoms"] * (8 + 3 * w["ts"]),
+    "bin_assign": lambda w: w["atoms"] * (7 * w["ts"] + 16),
+    "bin_scatter": lambda w: w["atoms"] * 16,
+    "bin_order": lambda w: w["atoms"] * (16 + 8 * w["ts"]),
+    "band_dots": lambda w: w["dof"] * 4 * w["ts"],
+    "neb_force": lambda w: w["dof"] * 6 * w["ts"],
+    "fire_update": lambda w: w["dof"] * 5 * w["ts"],
+}
+
+
+def fp32_peak_tflops(sm_mhz=2070.0):
+    """152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def band_inputs(wl, seed=2510):
+    import cfneb_inputs as ci
+    cfg = ci.tersoff_graphite_hexdiamond(reps=wl["reps"], n_images=wl["n_images"], seed=seed,
+                                         precision=wl["precision"])
+    return cfg
+
+
+def make_band(g, wl, cfg, stream, precision=None):
+    R0, h0, R1, h1 = cfg["endpoints"]
+    opt = g.default_options()
+    opt.k_spring = cfg["k"]
+    opt.climb = 1
+    prec = wl["precision"] if precision is None else precision
+    opt.precision = g.MIXED if prec == "mixed" else g.FP64
+    opt.dt = cfg["dt"]
+    opt.dt_max = 10 * cfg["dt"]
+    opt.maxstep = 0.2
+    opt.n_max = wl["n_max"]
+    cf = g.CellFilter(1, g.ROTFREE_B, 0.0, 0.0)
+    return g.create_band((R0, h0), (R1, h1), wl["n_images"], g.tersoff_potential(), cf, opt,
+                         stream=stream, noise=cfg["noise"])
+
+
+def time_steps(torch, band, stream, k, dist=None):
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start.record(stream)
+    band.step(k)
+    end.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    return start.elapsed_time(end)
+
+
+def cpu_oracle_rate(wl, seconds=12.0, steps=None, warmup=0):
+    """Oracle (FP64 CPU) atom·steps/s on the 576-atom tile of the same band."""
+    import oracle
+    import cfneb_inputs as ci
+    cfg = ci.tersoff_graphite_hexdiamond(reps=CPU_SAMPLE_REPS, n_images=wl["n_images"],
+                                         seed=2510)
+    R0, h0, R1, h1 = cfg["endpoints"]
+    band = oracle.make_band(oracle.Tersoff(), R0, h0, R1, h1, wl["n_images"], k=cfg["k"],
+                            climb=True, cell_filter=True,
+                            fire=oracle.Fire(dt=cfg["dt"], dt_max=10 * cfg["dt"]),
+                            noise=cfg["noise"])
+    for _ in range(warmup):
+        band.step(1)
+    n_done = 0
+    t0 = time.perf_counter()
+    while True:
+        band.step(1)
+        n_done += 1
+        el = time.perf_counter() - t0
+        if steps is not None and n_done >= steps:
+            break
+        if steps is None and el >= seconds:
+            break
+    n = len(R0)
+    moving = wl["n_images"] - 2
+    return {"value": n * moving * n_done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d-atom tile of the same graphite->hex-diamond Tersoff band, %d images "
+                      "(%d moving), %d FP64 steps in %.1f s, one thread; brute-force O(n^2) "
+                      "periodic neighbour search" % (n, wl["n_images"], moving, n_done, el),
+            "steps": n_done, "seconds": el}
+
+
+def run_reference(args, wl_name):
+    ws, rank, _ = dist_info()
+    if ws > 1 and rank != 0:
+        return 0
+    wl = WORKLOADS[wl_name]
+    res = cpu_oracle_rate(wl, steps=max(1, args.steps), warmup=args.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * res["seconds"] / res["steps"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl_name, "sample": res["sample"]},
+            "cpu_baseline": {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    source has not changed since (else None)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    ent = d.get(kernel)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_2510_16721_gb300", "csrc", ent["source"])
+    with open(src, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    if h != ent.get("source_sha256_16"):
+        return None
+    return ent.get("bytes_per_launch_full")
+
+
+def run_ours(args, wl_name):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_info()
+    dist = None
+    if ws > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist = td
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    import paper_2510_16721_gb300 as g
+    g.build()
+    g.lib()
+    wl = WORKLOADS[wl_name]
+    cfg = band_inputs(wl, seed=2510 + rank)
+    n = len(cfg["endpoints"][0])
+    moving = wl["n_images"] - 2
+    stream = torch.cuda.current_stream()
+    band = make_band(g, wl, cfg, stream)
+
+    # warm-up (also captures the CUDA graph)
+    band.step(args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = time_steps(torch, band, stream, args.steps, dist)
+    clk = clocks.stop()
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    path = band.get_path()
+    if not np.all(np.isfinite(path["energies"])):
+        raise RuntimeError("non-finite energies after the timed steps")
+    value = ws * n * moving * args.steps / (ms / 1e3)
+
+    # per-kernel times (events around each launch on the library's stream)
+    kp = max(5, min(args.steps, 50))
+    band.profile(True)
+    band.step(kp)
+    torch.cuda.synchronize()
+    prof = band.profile_read()
+    band.profile(False)
+    total = sum(v[0] for v in prof.values())
+    dom = max(prof.items(), key=lambda kv: kv[1][0])[0]
+    pairs, triples = band.get_work()
+    ts = 4 if wl["precision"] == "mixed" else 8
+    w = dict(pairs=pairs, triples=triples, atoms=n * moving, dof=(n + 3) * 3 * moving, ts=ts)
+    dom_ms = prof[dom][0] / max(1, prof[dom][1])
+    peaks, peak_src = measured_peaks()
+    if dom in FLOP_MODELS:
+        sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
+        achieved = FLOP_MODELS[dom](w) / (dom_ms * 1e-3) / 1e12
+        peak = fp32_peak_tflops(sm_max)
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x %.0f MHz" % sm_max}
+    else:
+        model = BYTE_MODELS.get(dom)
+        byts = model(w) if model else None
+        achieved = byts / (dom_ms * 1e-3) / 1e9 if byts else None
+        peak = peaks["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None,
+                "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % peak_src}
+    roof.update({"kernel": dom, "kernel_ms": dom_ms, "share": prof[dom][0] / total,
+                 "traffic": traffic_for(dom),
+                 "work_per_launch": {"pairs": pairs, "triples": triples, "atoms": n * moving}})
+    launches = band.launches_per_step() * args.steps
+    kernel_share = {k: round(v[0] / total, 4) for k, v in prof.items() if v[1]}
+    band.destroy()
+    del band
+
+    # end to end through the public API with host buffers: create (H2D of
+    # endpoints and jitter), K steps, path read back (D2H)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b2 = make_band(g, wl, cfg, stream)
+    b2.step(args.steps)
+    p2 = b2.get_path()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    b2.destroy()
+    h2d = 2 * n * 3 * 8 + 2 * 9 * 8 + (cfg["noise"].nbytes if cfg["noise"] is not None else 0)
+    d2h = p2["positions"].nbytes + p2["cells"].nbytes + p2["energies"].nbytes + 8
+    e2e = {"value": ws * n * moving * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+           "seconds": e2e_s, "includes": "band creation (allocation, endpoint upload, set-up "
+                                         "and endpoint evaluation), K steps, path download"}
+
+    # plain FP64 GPU path on the same workload (one band per launch)
+    fp64 = None
+    if not args.no_fp64:
+        b3 = make_band(g, wl, cfg, stream, precision="fp64")
+        k64 = max(3, args.steps // 4)
+        b3.step(min(3, args.warmup))
+        ms64 = time_steps(torch, b3, stream, k64)
+        fp64 = {"value": n * moving * k64 / (ms64 / 1e3), "unit": UNIT,
+                "ms_per_step": ms64 / k64, "steps": k64}
+        b3.destroy()
+
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline:
+        res = cpu_oracle_rate(wl, seconds=args.cpu_seconds)
+        cpu = {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 pair/three-body arithmetic, f64 reductions and 3x3 cell work"
+            if wl["precision"] == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": wl_name, "atoms": n, "images": wl["n_images"],
+                       "moving_images": moving, "precision": wl["precision"],
+                       "potential": "Tersoff 1988 C", "cell_filter": "rotation-free (B)",
+                       "l2": "working set > 129 MB L2, no flush", "graph": "CUDA graph per step",
+                       "parallelism": "replicas x%d" % ws},
+            "roofline": roof, "kernel_share": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk, "fp64_plain": fp64}
+    print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tersoff_graphite_hexdiamond_98304",
+                    choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args, args.workload)
+    return run_ours(args, args.workload)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

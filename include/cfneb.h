@@ -1,0 +1,230 @@
+/*
+ * cfneb.h -- C ABI of the GB300 (sm_103a) cell-filter nudged elastic band
+ * library.
+ *
+ * One relaxation step of a band of images (arXiv 2510.16721) is computed
+ * entirely by CUDA kernels of this library:
+ *   - cell filter, inverse map (Sec. II.C): B = X_lat / c, D = sqrt(B),
+ *     h = h0 D, R = R~ D;
+ *   - cell-list build over all periodic images of every atom (the per-atom
+ *     energy of Sec. II.B, Eq. U, depends on the neighbours of i in the
+ *     periodic crystal);
+ *   - Lennard-Jones or Tersoff energy, forces and virial
+ *     V = -1/2 sum_ij r^ij (x) f^ij (Sec. II.B, Eqs. V, V2);
+ *   - cell filter, forward map: atom rows F D^T and lattice rows
+ *     1/2 D^-T V D^-1 / c (Sec. II.C; the 1/2 makes the lattice force the
+ *     exact conjugate of B, whose increment is D dD^T + dD D^T);
+ *   - NEB force f_NEB = f_real(perp) + f_spring (Sec. II.A) with the upwind
+ *     tangent and climbing image the paper cites (Sec. I);
+ *   - FIRE update of the interior images (the optimiser is not named by the
+ *     paper, Sec. III);
+ *   - image insertion / deletion from the spacing of neighbouring images
+ *     (Sec. III).
+ *
+ * Conventions
+ *   - Every function returns an int status: 0 = CFNEB_OK, negative = error,
+ *     positive = informational.  cfneb_status_string() names it.
+ *   - Arrays passed in are caller owned, read during the call and copied;
+ *     arrays passed out are caller owned and filled during the call.  All
+ *     pointers in this header are HOST pointers.
+ *   - Positions are Cartesian, row-major n x 3 (double).  A cell is the 3x3
+ *     lattice matrix with the lattice vectors h1, h2, h3 as ROWS (Sec. II.B,
+ *     below Eq. epsilon), row-major.
+ *   - The image count N includes both endpoints; the endpoints never move.
+ *   - A band owns its device memory (allocated at creation, sized for
+ *     n_max images) and is bound to the CUDA stream given at creation: the
+ *     library orders its own work after the work already queued on that
+ *     stream, and work queued on it later runs after the library's.  A band
+ *     is not thread safe.
+ *   - Units: LJ in reduced units (eps, sigma); Tersoff in eV and Angstrom.
+ */
+#ifndef CFNEB_H
+#define CFNEB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define CFNEB_OK 0
+#define CFNEB_NOT_CONVERGED 1        /* cfneb_relax ran out of steps           */
+#define CFNEB_ERR_INVALID_ARG (-1)   /* NULL pointer, bad enum, bad size       */
+#define CFNEB_ERR_SHAPE_MISMATCH (-2)/* endpoints differ in atom count/types    */
+#define CFNEB_ERR_OUT_OF_MEMORY (-3) /* device allocation failed               */
+#define CFNEB_ERR_HBM_BUDGET (-4)    /* batch memory budget exceeded           */
+#define CFNEB_ERR_CUDA (-5)          /* a CUDA runtime call failed             */
+#define CFNEB_ERR_NONFINITE (-6)     /* NaN/Inf in forces, energies or state   */
+#define CFNEB_ERR_NOT_SPD (-7)       /* lattice coordinate B lost positivity   */
+#define CFNEB_ERR_NBR_OVERFLOW (-8)  /* more Tersoff neighbours than capacity  */
+#define CFNEB_ERR_TIMEOUT (-9)       /* a bounded device wait gave up          */
+#define CFNEB_ERR_STATE (-10)        /* call not valid in the current state    */
+
+/* ---- enums ------------------------------------------------------------- */
+#define CFNEB_LJ 0
+#define CFNEB_TERSOFF 1
+
+#define CFNEB_ROTFREE_B 0   /* lattice coordinate B = D D^T (Sec. II.C end)   */
+#define CFNEB_DEFGRAD_D 1   /* lattice coordinate D = h0^-1 h (Sec. II.C)     */
+
+#define CFNEB_FP64 0        /* all arithmetic in double                       */
+#define CFNEB_MIXED 1       /* FP32 pair/three-body arithmetic and vectors;
+                               FP64 energies, reductions and 3x3 cell work    */
+
+/* ---- structures -------------------------------------------------------- */
+typedef struct cfneb_band cfneb_band;   /* opaque, owned by the library */
+
+typedef struct {
+    int32_t n_atoms;
+    const int32_t *types;     /* n_atoms species ids, or NULL; one species  */
+    const double *positions;  /* n_atoms x 3, Cartesian, row-major          */
+    double cell[9];           /* rows = lattice vectors h1, h2, h3          */
+} cfneb_structure;
+
+typedef struct {
+    int32_t kind;             /* CFNEB_LJ or CFNEB_TERSOFF                   */
+    /* Lennard-Jones: phi = 4 eps [(sigma/r)^12 - (sigma/r)^6], cut at rc,
+       minus phi(rc) when shift_energy != 0                                  */
+    double eps, sigma, rc;
+    int32_t shift_energy;
+    /* Tersoff (1988 form, lambda3 = 0): A, B, lambda1, lambda2, beta, n, c,
+       d, h, R, D.  All zero selects Tersoff's 1988 carbon parameters.       */
+    double tersoff[11];
+} cfneb_potential;
+
+typedef struct {
+    int32_t enabled;          /* 0: fixed cell (h = h0 for every image)      */
+    int32_t variant;          /* CFNEB_ROTFREE_B (default) or CFNEB_DEFGRAD_D */
+    double cell_factor;       /* c in X_lat = c B; <= 0 selects n_atoms      */
+    double pressure;          /* external pressure P: H = U + P Omega        */
+} cfneb_cell_filter;
+
+typedef struct {
+    double k_spring;          /* spring constant (energy / length^2)         */
+    int32_t climb;            /* climbing image on from the first step       */
+    int32_t precision;        /* CFNEB_FP64 or CFNEB_MIXED                   */
+    double dt, dt_max, maxstep; /* FIRE: initial/maximum step, per-row clamp */
+    const double *interior_noise; /* (n_images-2) x n_atoms x 3 displacements
+                                     added to the interior images' R~ after
+                                     linear interpolation, or NULL           */
+    int32_t adaptive;         /* spacing-driven insertion / deletion          */
+    int32_t n_min, n_max;     /* image-count bounds; n_max is the capacity   */
+    int32_t k_ref, cooldown;  /* refinement check every k_ref steps, at least
+                                 cooldown steps after the previous change    */
+    double alpha_ins, alpha_del; /* insert if l_s > alpha_ins mean(l); delete
+                                 if l_(j-1) + l_j < alpha_del mean(l)        */
+    double bin_scale;         /* cell-list bin width / cutoff (>= 1, or 0.5);
+                                 0 selects the tuned default                 */
+} cfneb_options;
+
+/* Fill *opt with the defaults: k 0.1, climb on, FP64, FIRE dt 0.1,
+ * dt_max 1.0, maxstep 0.2, no noise, adaptive off, n_min 3, n_max = the
+ * image count given at creation, k_ref 10, cooldown 20, alpha_ins 1.5,
+ * alpha_del 0.5, bin_scale 0 (tuned).  Returns CFNEB_OK. */
+int cfneb_default_options(cfneb_options *opt);
+
+/* Create a band between two endpoint structures (Sec. III: the cell filter
+ * turns each image into generalised coordinates before forces are taken).
+ *   h0 = cell of `initial`; each endpoint is mapped to X = (R~, c B) with
+ *   R~ = s h0 and B = D D^T, D = h0^-1 h (Sec. II.C); the final endpoint's
+ *   fractional coordinates are unwrapped to the nearest periodic image of
+ *   the initial ones; interior images are the linear interpolation of X
+ *   plus `interior_noise`.  Endpoint energies are evaluated once.
+ * n_images >= 3.  cuda_stream is a cudaStream_t (NULL = legacy default).
+ * On success *out owns the band; destroy it with cfneb_destroy_band.
+ * Errors: INVALID_ARG, SHAPE_MISMATCH, OUT_OF_MEMORY, CUDA, NOT_SPD. */
+int cfneb_create_band(const cfneb_structure *initial, const cfneb_structure *final,
+                      int32_t n_images, const cfneb_potential *potential,
+                      const cfneb_cell_filter *cell_filter, const cfneb_options *options,
+                      void *cuda_stream, cfneb_band **out);
+
+/* Run n_steps relaxation steps (map-back, cell list, forces, cell filter,
+ * NEB projection, FIRE).  Queued on the band's stream; returns without
+ * waiting unless adaptive refinement needs a host decision.  A step whose
+ * f_NEB already meets the tolerance of the last cfneb_relax call moves
+ * nothing.  Errors raised on the device surface at the next synchronising
+ * call (relax, get_path, get_state). */
+int cfneb_step(cfneb_band *band, int32_t n_steps);
+
+/* Iterate until fmax = max row norm of f_NEB over the interior images
+ * (atom rows and the 3 lattice rows) is below `fmax`, or max_steps steps
+ * were taken.  *steps_done = steps taken by this call; *converged = 1 if
+ * the tolerance was met.  Returns CFNEB_OK, CFNEB_NOT_CONVERGED or an
+ * error.  Synchronises with the device every few steps. */
+int cfneb_relax(cfneb_band *band, double fmax, int64_t max_steps, int64_t *steps_done,
+                int32_t *converged);
+
+/* Insert the linear midpoint of images after_index and after_index + 1
+ * (0 <= after_index < N - 1, N < n_max).  Resets FIRE.  Endpoints are left
+ * bit-identical. */
+int cfneb_insert_image(cfneb_band *band, int32_t after_index);
+
+/* Delete interior image `index` (0 < index < N - 1, N > n_min).  Resets
+ * FIRE. */
+int cfneb_delete_image(cfneb_band *band, int32_t index);
+
+/* Copy the current path to the host.  Any output pointer may be NULL.
+ *   *n_images  = N
+ *   positions  = N x n_atoms x 3 Cartesian positions (R = R~ D)
+ *   cells      = N x 9 cells h = h0 D
+ *   energies   = N energies (U + P Omega)
+ *   fmax       = largest f_NEB row norm at the last step (0 before any step)
+ * Synchronises. */
+int cfneb_get_path(const cfneb_band *band, int32_t *n_images, double *positions,
+                   double *cells, double *energies, double *fmax);
+
+/* Copy the full state to the host (checkpoints, parity checks).  Any
+ * pointer may be NULL.  Rows per image: n_atoms + 3.
+ *   X       = N x (n+3) x 3 generalised coordinates (R~ rows, then c B)
+ *   F       = N x (n+3) x 3 generalised forces of the last evaluation
+ *   Fneb    = N x (n+3) x 3 NEB forces of the last step (endpoints 0)
+ *   virials = N x 9 virials V (row-major V_mn)
+ *   fire    = 4 doubles: dt, alpha, steps with positive power, steps taken
+ *   climbing_index = index of the climbing image of the last step (-1 none)
+ * Synchronises. */
+int cfneb_get_state(const cfneb_band *band, double *X, double *F, double *Fneb,
+                    double *virials, double *fire, int32_t *climbing_index);
+
+/* Release the band and its device memory. */
+int cfneb_destroy_band(cfneb_band *band);
+
+/* Single-point evaluation of `count` structures (any cells, any sizes):
+ * energies[count], forces[sum n_i x 3] (Cartesian, structures back to
+ * back), virials[count x 9].  Same kernels as a relaxation step (cell list
+ * and force kernels).  Output pointers may be NULL.  Synchronises. */
+int cfneb_evaluate(const cfneb_structure *structures, int32_t count,
+                   const cfneb_potential *potential, int32_t precision, void *cuda_stream,
+                   double *energies, double *forces, double *virials);
+
+/* Per-kernel timing.  With profiling on, each kernel launch of
+ * cfneb_step is bracketed by CUDA events on the band's internal stream
+ * (the stream the kernels run on; graphs are not used while profiling).
+ * cfneb_profile_read returns the summed event time (ms) and launch count of
+ * kernel `kernel_id` since profiling was switched on; cfneb_kernel_name
+ * names ids 0 .. cfneb_kernel_count()-1. */
+int cfneb_profile(cfneb_band *band, int32_t enable);
+int cfneb_profile_read(cfneb_band *band, int32_t kernel_id, double *total_ms,
+                       int64_t *launches);
+int32_t cfneb_kernel_count(void);
+const char *cfneb_kernel_name(int32_t kernel_id);
+
+/* Work counters of the last evaluation of the interior images, summed over
+ * them: *pairs = neighbour entries (i, j, shift) inside the cutoff,
+ * *triples = ordered pairs of distinct neighbour entries of one atom (the
+ * three-body terms of Tersoff; 0 for LJ).  Used to turn kernel times into
+ * arithmetic rates.  Synchronises. */
+int cfneb_get_work(const cfneb_band *band, double *pairs, double *triples);
+
+/* Number of kernel launches one cfneb_step makes for this band (for
+ * launch accounting). */
+int cfneb_launches_per_step(const cfneb_band *band, int32_t *launches);
+
+/* Human-readable name of a status code. */
+const char *cfneb_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CFNEB_H */

@@ -14,8 +14,8 @@ numpy primitives (matrix products, ``eigh``) as the only library steps:
   D^-T V D^-1 (Sec. II.C);
 * NEB -- f_NEB = f_real(perp) + f_spring (Sec. II.A) with the improved (upwind)
   tangent and the climbing image that Sec. I cites;
-* FIRE -- the optimiser (the paper uses "existing ASE optimizers", Sec. III,
-  without naming one);
+* FIRE -- the optimiser (Sec. III relies on standard optimisers of the
+  host package without naming one);
 * adaptive refinement -- images inserted or removed from the spacing of the
   images in configuration space after NEB iterations (Sec. III).
 

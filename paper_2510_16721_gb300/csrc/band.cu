@@ -1,0 +1,484 @@
+// Per-image reduction, cell-filter lattice force, NEB projection and FIRE.
+//
+// k_image_finalize  sums the force kernel's tile partials (FP64, slot order)
+//                   into E and V, adds the external pressure (H = U + P Omega,
+//                   V - P Omega I) and writes the three lattice rows of the
+//                   generalised force: (1/c) 1/2 D^-T V_sym D^-1 for the
+//                   rotation-free filter, (1/c) D^-T V for the deformation
+//                   gradient (Sec. II.C).
+// k_band_dots       per row tile: |dX+|^2, |dX-|^2, dX+.dX-, F.dX+, F.dX- in
+//                   FP64 (dX+ = X_{i+1} - X_i, dX- = X_i - X_{i-1}).
+// k_dots_reduce     sums those tile partials per image (one warp per image).
+// k_neb_coef        per band: climbing image, upwind tangent weights and the
+//                   two coefficients with f_NEB = F + a dX+ + b dX-.  Since
+//                   tau = w+ dX+ + w- dX-, |tau| and F.tau follow from the five
+//                   dots, and the projection f - (f.t)t + k(|dX+|-|dX-|) t
+//                   (Sec. II.A; climbing image f - 2 (f.t) t) becomes two
+//                   scalars per image.
+// k_neb_force       writes f_NEB and per-tile FIRE sums F.v, F.F, v.v and the
+//                   largest row norm (fmax).
+// k_fire_scalars    per band: convergence test, FIRE decision (Bitzek et al.
+//                   2006, band-global power P = F.v) and the new dt, alpha.
+// k_fire_update     v <- cv v + cf F; v += dt F; dX = dt v clamped per row to
+//                   maxstep; X += dX (interior images only).
+#include "common.cuh"
+
+namespace cfneb {
+
+template <typename T>
+__global__ void k_image_finalize(const ImgRef *imgs, BandDev *bands) {
+    ImgRef r = imgs[blockIdx.x];
+    BandDev &b = bands[r.band];
+    const BandParams *bp = b.bp;
+    ImgScalars &sc = b.sc[r.img];
+    const double *part = b.atom_part + (size_t)r.img * b.atpi * NPART;
+    double s[12];
+    for (int k = 0; k < 12; ++k) {
+        double v = 0.0;
+        for (int t = threadIdx.x; t < b.atpi; t += 32) v += part[(size_t)t * NPART + k];
+        s[k] = warp_sum(v);
+    }
+    if (threadIdx.x != 0) return;
+    sc.pairs = s[10];
+    sc.triples = s[11];
+    double U = s[0];
+    double V[9];
+    for (int k = 0; k < 9; ++k) V[k] = s[1 + k];
+    double E = U;
+    if (bp->pressure != 0.0) {
+        E += bp->pressure * sc.omega;
+        for (int a = 0; a < 3; ++a) V[4 * a] -= bp->pressure * sc.omega;
+    }
+    sc.U = U;
+    sc.E = E;
+    for (int k = 0; k < 9; ++k) sc.V[k] = V[k];
+    double Phi[9];
+    if (!bp->filter) {
+        for (int k = 0; k < 9; ++k) Phi[k] = 0.0;
+    } else {
+        const double *Di = sc.Dinv;
+        double DiT[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) DiT[3 * i + j] = Di[3 * j + i];
+        double tmp[9];
+        if (bp->variant == 0) {
+            double Vs[9];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) Vs[3 * i + j] = 0.5 * (V[3 * i + j] + V[3 * j + i]);
+            matmul3(DiT, Vs, tmp);
+            matmul3(tmp, Di, Phi);
+            for (int k = 0; k < 9; ++k) Phi[k] *= 0.5 / bp->c;
+        } else {
+            matmul3(DiT, V, Phi);
+            for (int k = 0; k < 9; ++k) Phi[k] /= bp->c;
+        }
+    }
+    T *F = (T *)b.F + ((size_t)r.img * b.rows + b.n) * 3;
+    for (int k = 0; k < 9; ++k) F[k] = (T)Phi[k];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_band_dots(const Tile *tiles, BandDev *bands) {
+    Tile tl = tiles[blockIdx.x];
+    BandDev &b = bands[tl.band];
+    const int row = tl.t * TILE + threadIdx.x;
+    double acc[5] = {0, 0, 0, 0, 0};
+    if (row < b.rows) {
+        const size_t stride = (size_t)b.rows * 3;
+        const T *x0 = (const T *)b.X + tl.img * stride + (size_t)row * 3;
+        const T *xm = x0 - stride, *xp = x0 + stride;
+        const T *f = (const T *)b.F + tl.img * stride + (size_t)row * 3;
+        for (int c = 0; c < 3; ++c) {
+            double a = (double)x0[c];
+            double dp = (double)xp[c] - a, dm = a - (double)xm[c], fc = (double)f[c];
+            acc[0] += dp * dp;
+            acc[1] += dm * dm;
+            acc[2] += dp * dm;
+            acc[3] += fc * dp;
+            acc[4] += fc * dm;
+        }
+    }
+    double tot[5];
+    block_sum<5>(acc, tot);
+    if (threadIdx.x == 0) {
+        double *part = b.row_part + ((size_t)tl.img * b.rtpi + tl.t) * NPART;
+        for (int k = 0; k < 5; ++k) part[k] = tot[k];
+    }
+}
+
+// one warp per image: sum the row-tile partials k = 0..K-1 into dst
+__global__ void k_dots_reduce(const ImgRef *imgs, BandDev *bands) {
+    ImgRef r = imgs[blockIdx.x];
+    BandDev &b = bands[r.band];
+    const double *part = b.row_part + (size_t)r.img * b.rtpi * NPART;
+    double s[5];
+    for (int k = 0; k < 5; ++k) {
+        double v = 0.0;
+        for (int t = threadIdx.x; t < b.rtpi; t += 32) v += part[(size_t)t * NPART + k];
+        s[k] = warp_sum(v);
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 5; ++k) b.sc[r.img].dots[k] = s[k];
+}
+
+// one block (one thread per image) per band
+__global__ void k_neb_coef(const int *band_ids, BandDev *bands) {
+    BandDev &b = bands[band_ids[blockIdx.x]];
+    BandParams *bp = b.bp;
+    const int N = bp->N;
+    __shared__ int s_ci;
+    if (threadIdx.x == 0) {
+        int ci = -1;
+        if (bp->climb) {
+            double best = 0.0;
+            for (int i = 1; i < N - 1; ++i)
+                if (ci < 0 || b.sc[i].E > best) {
+                    best = b.sc[i].E;
+                    ci = i;
+                }
+        }
+        s_ci = ci;
+        bp->ci = ci;
+    }
+    __syncthreads();
+    for (int i = 1 + threadIdx.x; i < N - 1; i += blockDim.x) {
+        const ImgScalars &sc = b.sc[i];
+        const double Em = b.sc[i - 1].E, E0 = sc.E, Ep = b.sc[i + 1].E;
+        double wp, wm;
+        if (Ep > E0 && E0 > Em) {
+            wp = 1.0; wm = 0.0;
+        } else if (Ep < E0 && E0 < Em) {
+            wp = 0.0; wm = 1.0;
+        } else {
+            const double a = fabs(Ep - E0), c = fabs(Em - E0);
+            const double dmax = fmax(a, c), dmin = fmin(a, c);
+            if (dmax == 0.0) {
+                wp = 1.0; wm = 1.0;
+            } else if (Ep > Em) {
+                wp = dmax; wm = dmin;
+            } else {
+                wp = dmin; wm = dmax;
+            }
+        }
+        const double pp = sc.dots[0], mm = sc.dots[1], pm = sc.dots[2];
+        const double fp = sc.dots[3], fm = sc.dots[4];
+        const double tt = wp * wp * pp + 2.0 * wp * wm * pm + wm * wm * mm;
+        const double tn = sqrt(tt);
+        const double ft = (wp * fp + wm * fm) / tn;  // F . tau_hat
+        double gamma;
+        if (i == s_ci) {
+            gamma = -2.0 * ft;
+        } else {
+            gamma = bp->k * (sqrt(pp) - sqrt(mm)) - ft;
+        }
+        b.sc[i].coef[0] = gamma * wp / tn;
+        b.sc[i].coef[1] = gamma * wm / tn;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_neb_force(const Tile *tiles, BandDev *bands) {
+    Tile tl = tiles[blockIdx.x];
+    BandDev &b = bands[tl.band];
+    const int row = tl.t * TILE + threadIdx.x;
+    double acc[4] = {0, 0, 0, 0};
+    if (row < b.rows) {
+        const ImgScalars &sc = b.sc[tl.img];
+        const T ca = (T)sc.coef[0], cb = (T)sc.coef[1];
+        const size_t stride = (size_t)b.rows * 3;
+        const size_t o = tl.img * stride + (size_t)row * 3;
+        const T *x0 = (const T *)b.X + o;
+        const T *xm = x0 - stride, *xp = x0 + stride;
+        const T *f = (const T *)b.F + o;
+        const T *v = (const T *)b.v + o;
+        T *fn = (T *)b.Fneb + o;
+        T fv = 0, ff = 0, vv = 0;
+        for (int c = 0; c < 3; ++c) {
+            const T a = x0[c];
+            const T g = f[c] + ca * (xp[c] - a) + cb * (a - xm[c]);
+            fn[c] = g;
+            fv += g * v[c];
+            ff += g * g;
+            vv += v[c] * v[c];
+        }
+        acc[0] = (double)fv;
+        acc[1] = (double)ff;
+        acc[2] = (double)vv;
+        acc[3] = (double)ff;  // row norm^2 for fmax
+    }
+    double tot[3];
+    double three[3] = {acc[0], acc[1], acc[2]};
+    block_sum<3>(three, tot);
+    // block max of the row norms
+    __shared__ double smax[TILE / 32];
+    double m = warp_max(acc[3]);
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mx = 0.0;
+        for (int q = 0; q < TILE / 32; ++q) mx = fmax(mx, smax[q]);
+        double *part = b.row_part + ((size_t)tl.img * b.rtpi + tl.t) * NPART;
+        part[5] = tot[0];
+        part[6] = tot[1];
+        part[7] = tot[2];
+        part[8] = mx;
+    }
+}
+
+// one block per band; warps sum the per-image tile partials, thread 0 runs
+// the FIRE logic
+__global__ void k_fire_scalars(const int *band_ids, BandDev *bands) {
+    BandDev &b = bands[band_ids[blockIdx.x]];
+    BandParams *bp = b.bp;
+    const int N = bp->N;
+    __shared__ double s_img[64][4];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double tot[4] = {0, 0, 0, 0};
+    // images 1..N-2 in fixed groups of nw
+    for (int g0 = 1; g0 < N - 1; g0 += nw) {
+        const int i = g0 + w;
+        if (i < N - 1) {
+            const double *part = b.row_part + (size_t)i * b.rtpi * NPART;
+            double v[4] = {0, 0, 0, 0};
+            for (int t = lane; t < b.rtpi; t += 32) {
+                v[0] += part[(size_t)t * NPART + 5];
+                v[1] += part[(size_t)t * NPART + 6];
+                v[2] += part[(size_t)t * NPART + 7];
+                v[3] = fmax(v[3], part[(size_t)t * NPART + 8]);
+            }
+            v[0] = warp_sum(v[0]);
+            v[1] = warp_sum(v[1]);
+            v[2] = warp_sum(v[2]);
+            v[3] = warp_max(v[3]);
+            if (lane == 0)
+                for (int k = 0; k < 4; ++k) s_img[w][k] = v[k];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < nw && g0 + q < N - 1; ++q) {
+                tot[0] += s_img[q][0];
+                tot[1] += s_img[q][1];
+                tot[2] += s_img[q][2];
+                tot[3] = fmax(tot[3], s_img[q][3]);
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    const double P = tot[0], FF = tot[1], VV = tot[2];
+    const double fmax_ = sqrt(tot[3]);
+    bp->P = P;
+    bp->FF = FF;
+    bp->VV = VV;
+    bp->fmax = fmax_;
+    if (!isfinite(P) || !isfinite(FF) || !isfinite(VV)) {
+        atomicOr(&bp->status, ST_NONFINITE);
+    }
+    bp->converged = (bp->status == 0 && bp->ftol >= 0.0 && fmax_ < bp->ftol) ? 1 : 0;
+    if (bp->status != 0 || bp->converged || bp->steps >= bp->move_limit) {
+        bp->move = 0;
+        bp->cv = 0.0;
+        bp->cf = 0.0;
+        return;
+    }
+    bp->move = 1;
+    // FIRE (Bitzek et al. 2006): N_min 5, f_inc 1.1, f_dec 0.5, alpha0 0.1,
+    // f_alpha 0.99; the first move after a reset skips the power test
+    double cv = 1.0, cf = 0.0;
+    if (!bp->fresh) {
+        if (P > 0.0) {
+            if (FF > 0.0) {
+                cv = 1.0 - bp->alpha;
+                cf = bp->alpha * sqrt(VV) / sqrt(FF);
+            }
+            if (bp->npos > 5) {
+                bp->dt = fmin(bp->dt * 1.1, bp->dt_max);
+                bp->alpha *= 0.99;
+            }
+            bp->npos += 1;
+        } else {
+            cv = 0.0;
+            cf = 0.0;
+            bp->alpha = 0.1;
+            bp->dt *= 0.5;
+            bp->npos = 0;
+        }
+    }
+    bp->fresh = 0;
+    bp->cv = cv;
+    bp->cf = cf;
+    bp->steps += 1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_fire_update(const Tile *tiles, BandDev *bands) {
+    Tile tl = tiles[blockIdx.x];
+    BandDev &b = bands[tl.band];
+    const BandParams *bp = b.bp;
+    if (!bp->move) return;
+    const int row = tl.t * TILE + threadIdx.x;
+    if (row >= b.rows) return;
+    const size_t o = (tl.img * (size_t)b.rows + row) * 3;
+    T *x = (T *)b.X + o;
+    T *v = (T *)b.v + o;
+    const T *f = (const T *)b.Fneb + o;
+    const T cv = (T)bp->cv, cf = (T)bp->cf, dt = (T)bp->dt;
+    T dx[3];
+    T n2 = 0;
+    for (int c = 0; c < 3; ++c) {
+        T vc = cv * v[c] + cf * f[c];
+        vc += dt * f[c];
+        v[c] = vc;
+        dx[c] = dt * vc;
+        n2 += dx[c] * dx[c];
+    }
+    const T ms = (T)bp->maxstep;
+    if (n2 > ms * ms) {
+        const T s = ms / sqrt(n2);
+        for (int c = 0; c < 3; ++c) dx[c] *= s;
+    }
+    for (int c = 0; c < 3; ++c) x[c] += dx[c];
+}
+
+// X_img <- 1/2 (X_{img-1} + X_{img+1}) (image insertion; all rows)
+template <typename T>
+__global__ void k_midpoint(BandDev *band, int img) {
+    BandDev &b = *band;
+    const size_t stride = (size_t)b.rows * 3;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < stride;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const T *xm = (const T *)b.X + (img - 1) * stride;
+        const T *xp = (const T *)b.X + (img + 1) * stride;
+        ((T *)b.X)[img * stride + e] = (T)0.5 * (xm[e] + xp[e]);
+    }
+}
+
+// Band set-up (Sec. II.C and Sec. III): endpoints to generalised
+// coordinates and linear interpolation.  s = R h^-1 for each endpoint; the
+// final endpoint's s is shifted by whole lattice vectors to the periodic
+// image nearest the initial one; R~ = s h0; lattice rows c B with
+// B = D D^T, D = h0^-1 h (or c D).  With the filter off the final
+// Cartesian positions are kept and the cell stays h0.  Image k gets
+// X_0 + k/(N-1) (X_{N-1} - X_0), plus the caller's displacements on the
+// interior atom rows.  Everything in FP64, stored as T.
+template <typename T>
+__global__ void k_setup(const double *R0, const double *R1, const double *noise, int N,
+                        BandDev *band, const double *h1) {
+    BandDev &b = *band;
+    const BandParams *bp = b.bp;
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = b.n;
+    if (row > n) return;
+    const size_t stride = (size_t)b.rows * 3;
+    double h1inv[9];
+    inv3(h1, h1inv);
+    if (row < n) {
+        double s0[3], s1[3], a0[3], a1[3];
+        for (int a = 0; a < 3; ++a) {
+            s0[a] = R0[3 * row] * bp->h0inv[a] + R0[3 * row + 1] * bp->h0inv[3 + a] +
+                    R0[3 * row + 2] * bp->h0inv[6 + a];
+            s1[a] = R1[3 * row] * h1inv[a] + R1[3 * row + 1] * h1inv[3 + a] +
+                    R1[3 * row + 2] * h1inv[6 + a];
+            s1[a] -= rint(s1[a] - s0[a]);
+        }
+        const double *g1 = bp->filter ? bp->h0 : h1;
+        for (int c = 0; c < 3; ++c) {
+            a0[c] = s0[0] * bp->h0[c] + s0[1] * bp->h0[3 + c] + s0[2] * bp->h0[6 + c];
+            a1[c] = s1[0] * g1[c] + s1[1] * g1[3 + c] + s1[2] * g1[6 + c];
+        }
+        for (int k = 0; k < N; ++k) {
+            const double t = (double)k / (double)(N - 1);
+            T *x = (T *)b.X + k * stride + (size_t)row * 3;
+            for (int c = 0; c < 3; ++c) {
+                double v = a0[c] + t * (a1[c] - a0[c]);
+                if (noise && k > 0 && k < N - 1) v += noise[((size_t)(k - 1) * n + row) * 3 + c];
+                x[c] = (T)v;
+            }
+        }
+    } else {
+        double D0[9], D1[9], L0[9], L1[9];
+        matmul3(bp->h0inv, bp->h0, D0);
+        matmul3(bp->h0inv, bp->filter ? h1 : bp->h0, D1);
+        if (bp->variant == 0) {
+            double t0[9], t1[9];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    t0[3 * i + j] = D0[3 * j + i];
+                    t1[3 * i + j] = D1[3 * j + i];
+                }
+            matmul3(D0, t0, L0);
+            matmul3(D1, t1, L1);
+        } else {
+            for (int k = 0; k < 9; ++k) { L0[k] = D0[k]; L1[k] = D1[k]; }
+        }
+        for (int k = 0; k < N; ++k) {
+            const double t = (double)k / (double)(N - 1);
+            T *x = (T *)b.X + k * stride + (size_t)n * 3;
+            for (int e = 0; e < 9; ++e) {
+                double a = bp->c * L0[e], c = bp->c * L1[e];
+                x[e] = (T)(a + t * (c - a));
+            }
+        }
+    }
+}
+
+// ---- launchers -------------------------------------------------------------
+
+template <typename T>
+void launch_setup(const double *R0, const double *R1, const double *noise, int n, int N,
+                  BandDev *band, cudaStream_t s, const double *h1) {
+    k_setup<T><<<(n + 1 + 127) / 128, 128, 0, s>>>(R0, R1, noise, N, band, h1);
+}
+
+template <typename T>
+void launch_image_finalize(const ImgRef *imgs, int count, BandDev *bands, cudaStream_t s) {
+    if (count <= 0) return;
+    k_image_finalize<T><<<count, 32, 0, s>>>(imgs, bands);
+}
+template <typename T>
+void launch_band_dots(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    k_band_dots<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
+}
+void launch_dots_reduce(const ImgRef *imgs, int count, BandDev *bands, cudaStream_t s) {
+    if (count <= 0) return;
+    k_dots_reduce<<<count, 32, 0, s>>>(imgs, bands);
+}
+void launch_neb_coef(const int *band_ids, int nbands, BandDev *bands, cudaStream_t s) {
+    if (nbands <= 0) return;
+    k_neb_coef<<<nbands, 32, 0, s>>>(band_ids, bands);
+}
+template <typename T>
+void launch_neb_force(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    k_neb_force<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
+}
+void launch_fire_scalars(const int *band_ids, int nbands, BandDev *bands, cudaStream_t s) {
+    if (nbands <= 0) return;
+    k_fire_scalars<<<nbands, 256, 0, s>>>(band_ids, bands);
+}
+template <typename T>
+void launch_fire_update(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    k_fire_update<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
+}
+template <typename T>
+void launch_midpoint(BandDev *band, int img, int rows, cudaStream_t s) {
+    int blocks = (rows * 3 + 255) / 256;
+    blocks = blocks > 1024 ? 1024 : blocks;
+    k_midpoint<T><<<blocks, 256, 0, s>>>(band, img);
+}
+
+#define CFNEB_INST(T)                                                                       \
+    template void launch_image_finalize<T>(const ImgRef *, int, BandDev *, cudaStream_t);   \
+    template void launch_band_dots<T>(const Tile *, int, BandDev *, cudaStream_t);          \
+    template void launch_neb_force<T>(const Tile *, int, BandDev *, cudaStream_t);          \
+    template void launch_fire_update<T>(const Tile *, int, BandDev *, cudaStream_t);        \
+    template void launch_midpoint<T>(BandDev *, int, int, cudaStream_t);                  \
+    template void launch_setup<T>(const double *, const double *, const double *, int, int, \
+                                  BandDev *, cudaStream_t, const double *);
+CFNEB_INST(float)
+CFNEB_INST(double)
+#undef CFNEB_INST
+
+}  // namespace cfneb

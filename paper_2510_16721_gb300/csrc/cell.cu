@@ -1,0 +1,389 @@
+// Cell filter inverse map and cell-list build.
+//
+// Map-back (Sec. II.C): the lattice rows of X hold c B; B = X_lat / c is
+// symmetrised and D = B^(1/2) taken with a cyclic Jacobi eigen-solve in FP64
+// (rotation-free variant), or D = X_lat / c (deformation-gradient variant).
+// Then h = h0 D, and the bin geometry of the image is derived from the
+// perpendicular widths of h.
+//
+// Cell list: atoms are binned in fractional space (s = R~ h0^-1, which is
+// also R h^-1 since R = R~ D and h = h0 D), wrapped into [0, 1).  The bin
+// edge vectors bv_a = h_a / nb_a are rounded to T, and each atom stores its
+// Cartesian offset from the centre of its bin, sum_a (b_a + 1/2) bv_a, in T.
+// A pair vector is then (off_j - off_i) + sum_a (delta_a bv_a + t_a dh_a),
+// where delta is the unwrapped bin offset of the neighbour bin, t its
+// periodic shift and dh_a = h_a - nb_a bv_a the (tiny) difference between a
+// lattice vector and nb_a rounded bin vectors.  For |delta| <= 1 in an
+// orthorhombic cell every term is exact in FP32, so the only roundings are
+// those of the two small offsets and of the final sums: pair vectors keep
+// ~6e-8 A absolute accuracy whatever the cell size.  Enumerating delta over
+// [-m_a, m_a] with m_a = ceil(rc / bin width) visits every periodic image
+// of every atom within rc exactly once, also when rc exceeds half the cell
+// width (no minimum-image assumption; the neighbourhoods of Sec. II.B are
+// periodic).
+//
+// Determinism: atoms are counted into bins with integer atomics, then each
+// bin's atoms are ordered by atom index, so the slot order (and every
+// summation order downstream) is the same on every run.
+#include "common.cuh"
+
+namespace cfneb {
+
+// ---- 3x3 symmetric square root (cyclic Jacobi, FP64) --------------------
+
+// Returns false if B is not positive definite.
+__device__ bool sym_sqrt3(const double *Bin, double *S) {
+    double a[3][3], q[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            a[i][j] = 0.5 * (Bin[3 * i + j] + Bin[3 * j + i]);
+            q[i][j] = (i == j) ? 1.0 : 0.0;
+        }
+    for (int sweep = 0; sweep < 32; ++sweep) {
+        double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+        double diag = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+        if (off <= 1e-34 * diag) break;
+        for (int p = 0; p < 2; ++p)
+            for (int r = p + 1; r < 3; ++r) {
+                double apr = a[p][r];
+                if (apr == 0.0) continue;
+                // rotation angle that annihilates a[p][r]
+                double theta = (a[r][r] - a[p][p]) / (2.0 * apr);
+                double t = (theta >= 0.0 ? 1.0 : -1.0) /
+                           (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < 3; ++k) {  // A <- A J (columns p, r)
+                    double akp = a[k][p], akr = a[k][r];
+                    a[k][p] = c * akp - s * akr;
+                    a[k][r] = s * akp + c * akr;
+                }
+                for (int k = 0; k < 3; ++k) {  // A <- J^T A (rows p, r)
+                    double apk = a[p][k], ark = a[r][k];
+                    a[p][k] = c * apk - s * ark;
+                    a[r][k] = s * apk + c * ark;
+                }
+                for (int k = 0; k < 3; ++k) {  // Q <- Q J
+                    double qkp = q[k][p], qkr = q[k][r];
+                    q[k][p] = c * qkp - s * qkr;
+                    q[k][r] = s * qkp + c * qkr;
+                }
+            }
+    }
+    double w[3] = {a[0][0], a[1][1], a[2][2]};
+    bool ok = (w[0] > 0.0) && (w[1] > 0.0) && (w[2] > 0.0);
+    for (int i = 0; i < 3; ++i) w[i] = ok ? sqrt(w[i]) : 1.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            S[3 * i + j] = q[i][0] * w[0] * q[j][0] + q[i][1] * w[1] * q[j][1] +
+                           q[i][2] * w[2] * q[j][2];
+    return ok;
+}
+
+template <typename T>
+__global__ void k_mapback(const ImgRef *imgs, int count, BandDev *bands) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    ImgRef r = imgs[k];
+    BandDev &b = bands[r.band];
+    BandParams *bp = b.bp;
+    ImgScalars &sc = b.sc[r.img];
+    const T *Xl = (const T *)b.X + ((size_t)r.img * b.rows + b.n) * 3;
+    double D[9];
+    bool ok = true;
+    if (!bp->filter) {
+        for (int i = 0; i < 9; ++i) D[i] = (i % 4 == 0) ? 1.0 : 0.0;
+    } else {
+        double L[9];
+        for (int i = 0; i < 9; ++i) L[i] = (double)Xl[i] / bp->c;
+        if (bp->variant == 0) {
+            ok = sym_sqrt3(L, D);
+        } else {
+            for (int i = 0; i < 9; ++i) D[i] = L[i];
+            ok = det3(D) > 0.0;
+        }
+    }
+    if (!ok) {
+        atomicOr(&bp->status, ST_NOT_SPD);
+        for (int i = 0; i < 9; ++i) D[i] = (i % 4 == 0) ? 1.0 : 0.0;
+    }
+    double h[9];
+    matmul3(bp->h0, D, h);
+    for (int i = 0; i < 9; ++i) {
+        sc.D[i] = D[i];
+        sc.h[i] = h[i];
+    }
+    inv3(D, sc.Dinv);
+    inv3(h, sc.hinv);
+    double omega = fabs(det3(h));
+    sc.omega = omega;
+    // perpendicular widths w_a = Omega / |h_b x h_c|
+    double w[3];
+    for (int a = 0; a < 3; ++a) {
+        const double *u = h + 3 * ((a + 1) % 3), *v = h + 3 * ((a + 2) % 3);
+        double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2],
+               cz = u[0] * v[1] - u[1] * v[0];
+        w[a] = omega / sqrt(cx * cx + cy * cy + cz * cz);
+    }
+    int nb[3];
+    for (int a = 0; a < 3; ++a) {
+        double q = floor(w[a] / bp->bin_w);
+        nb[a] = q < 1.0 ? 1 : (q > 1024.0 ? 1024 : (int)q);
+    }
+    // keep within the bin capacity: coarser bins are always correct
+    while ((long long)nb[0] * nb[1] * nb[2] > b.nbins_cap) {
+        int a = (nb[0] >= nb[1] && nb[0] >= nb[2]) ? 0 : (nb[1] >= nb[2] ? 1 : 2);
+        nb[a] -= 1;
+    }
+    // bin vectors on a grid of q = 2^(e - 19), 2^e >= max |h_a / nb_a|: every
+    // sum of three products delta_a bv_a (|delta| <= 7) is then exact in
+    // FP32; dh = h - nb bv carries the (sub-1e-4 A) quantisation to the
+    // periodic wrap
+    double bmax = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) bmax = fmax(bmax, fabs(h[3 * a + c] / nb[a]));
+    const double q = ldexp(1.0, ilogb(bmax) + 1 - 19);
+    for (int a = 0; a < 3; ++a) {
+        double bw = w[a] / nb[a];
+        int m = (int)ceil(bp->rc / bw);
+        sc.m[a] = m < 1 ? 1 : (m > MAX_STENCIL ? MAX_STENCIL : m);
+        sc.nb[a] = nb[a];
+        for (int c = 0; c < 3; ++c) {
+            const double v = q * rint(h[3 * a + c] / nb[a] / q);
+            sc.bv[3 * a + c] = v;
+            sc.dh[3 * a + c] = h[3 * a + c] - nb[a] * v;
+        }
+    }
+    sc.nbins = nb[0] * nb[1] * nb[2];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_bin_assign(const Tile *tiles, BandDev *bands) {
+    using T4 = typename Vec4<T>::type;
+    Tile tl = tiles[blockIdx.x];
+    BandDev &b = bands[tl.band];
+    int i = tl.t * TILE + threadIdx.x;
+    if (i >= b.n) return;
+    const ImgScalars &sc = b.sc[tl.img];
+    const BandParams *bp = b.bp;
+    const T *Xi = (const T *)b.X + ((size_t)tl.img * b.rows + i) * 3;
+    double rt[3] = {(double)Xi[0], (double)Xi[1], (double)Xi[2]};
+    double s[3];
+    int bi[3];
+    for (int a = 0; a < 3; ++a) {
+        s[a] = rt[0] * bp->h0inv[a] + rt[1] * bp->h0inv[3 + a] + rt[2] * bp->h0inv[6 + a];
+        s[a] -= floor(s[a]);
+        if (s[a] >= 1.0) s[a] = 0.0;
+        int q = (int)(s[a] * sc.nb[a]);
+        bi[a] = q >= sc.nb[a] ? sc.nb[a] - 1 : q;
+    }
+    int lin = (bi[0] * sc.nb[1] + bi[1]) * sc.nb[2] + bi[2];
+    // offset from the bin centre: R (wrapped) - sum_a (b_a + 1/2) bv_a
+    double off[3];
+    for (int c = 0; c < 3; ++c) {
+        const double R = s[0] * sc.h[c] + s[1] * sc.h[3 + c] + s[2] * sc.h[6 + c];
+        const double ctr = (bi[0] + 0.5) * sc.bv[c] + (bi[1] + 0.5) * sc.bv[3 + c] +
+                           (bi[2] + 0.5) * sc.bv[6 + c];
+        off[c] = R - ctr;
+    }
+    size_t ai = (size_t)tl.img * b.n + i;
+    int rank = atomicAdd(&b.bin_count[(size_t)tl.img * b.nbins_cap + lin], 1);
+    b.atom_bin[ai] = lin;
+    b.atom_rank[ai] = rank;
+    T4 o, lo;
+    o.x = (T)off[0];
+    o.y = (T)off[1];
+    o.z = (T)off[2];
+    o.w = (T)0;
+    lo.x = (T)(off[0] - (double)o.x);
+    lo.y = (T)(off[1] - (double)o.y);
+    lo.z = (T)(off[2] - (double)o.z);
+    lo.w = (T)0;
+    ((T4 *)b.atom_off)[ai] = o;
+    ((T4 *)b.atom_off_lo)[ai] = lo;
+}
+
+// Exclusive scan of the bin counts, in three passes over SCAN_TILE-bin
+// tiles: tile sums, a scan of the tile sums per image, and a block-wide scan
+// of each tile offset by its tile prefix.  Integer arithmetic: exact and
+// deterministic.  Counts are reset to zero for the next build.
+constexpr int SCAN_TILE = 1024;
+
+__device__ inline int block_excl_scan_1024(int v, int *total) {
+    __shared__ int wsum[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int s = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        wsum[lane] = s;  // inclusive scan of the warp sums
+    }
+    __syncthreads();
+    const int before = (w > 0) ? wsum[w - 1] : 0;
+    *total = wsum[31];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(256) k_bin_tilesum(const ImgRef *imgs, BandDev *bands) {
+    ImgRef r = imgs[blockIdx.y];
+    BandDev &b = bands[r.band];
+    const int nb = b.sc[r.img].nbins;
+    const int t0 = blockIdx.x * SCAN_TILE;
+    if (t0 >= nb) return;
+    const int *cnt = b.bin_count + (size_t)r.img * b.nbins_cap;
+    int s = 0;
+    for (int k = threadIdx.x; k < SCAN_TILE && t0 + k < nb; k += blockDim.x) s += cnt[t0 + k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ int ws[8];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += ws[q];
+        b.bin_tsum[(size_t)r.img * b.tsum_cap + blockIdx.x] = tot;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_bin_tilescan(const ImgRef *imgs, BandDev *bands) {
+    ImgRef r = imgs[blockIdx.x];
+    BandDev &b = bands[r.band];
+    const int nt = (b.sc[r.img].nbins + SCAN_TILE - 1) / SCAN_TILE;
+    int *ts = b.bin_tsum + (size_t)r.img * b.tsum_cap;
+    int carry = 0;
+    for (int base = 0; base < nt; base += 1024) {
+        const int k = base + threadIdx.x;
+        const int v = k < nt ? ts[k] : 0;
+        int tot;
+        const int ex = block_excl_scan_1024(v, &tot);
+        if (k < nt) ts[k] = carry + ex;
+        carry += tot;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_bin_scanfill(const ImgRef *imgs, BandDev *bands) {
+    ImgRef r = imgs[blockIdx.y];
+    BandDev &b = bands[r.band];
+    const int nb = b.sc[r.img].nbins;
+    const int t0 = blockIdx.x * SCAN_TILE;
+    if (t0 >= nb) return;
+    int *cnt = b.bin_count + (size_t)r.img * b.nbins_cap;
+    int *start = b.bin_start + (size_t)r.img * (b.nbins_cap + 1);
+    const int bin = t0 + threadIdx.x;
+    const int v = bin < nb ? cnt[bin] : 0;
+    int tot;
+    const int ex = block_excl_scan_1024(v, &tot);
+    const int off = b.bin_tsum[(size_t)r.img * b.tsum_cap + blockIdx.x];
+    if (bin < nb) {
+        start[bin] = off + ex;
+        cnt[bin] = 0;
+        if (bin == nb - 1) start[nb] = off + ex + v;
+    }
+}
+
+__global__ void __launch_bounds__(TILE) k_bin_scatter(const Tile *tiles, BandDev *bands) {
+    Tile tl = tiles[blockIdx.x];
+    BandDev &b = bands[tl.band];
+    int i = tl.t * TILE + threadIdx.x;
+    if (i >= b.n) return;
+    size_t ai = (size_t)tl.img * b.n + i;
+    const int *start = b.bin_start + (size_t)tl.img * (b.nbins_cap + 1);
+    b.slot_unsorted[(size_t)tl.img * b.n + start[b.atom_bin[ai]] + b.atom_rank[ai]] = i;
+}
+
+// One thread per bin: order the bin's atoms by atom index and write the
+// sorted slot arrays.
+template <typename T>
+__global__ void k_bin_order(const ImgRef *imgs, BandDev *bands) {
+    using T4 = typename Vec4<T>::type;
+    ImgRef r = imgs[blockIdx.y];
+    BandDev &b = bands[r.band];
+    int bin = blockIdx.x * blockDim.x + threadIdx.x;
+    if (bin >= b.sc[r.img].nbins) return;
+    const int *start = b.bin_start + (size_t)r.img * (b.nbins_cap + 1);
+    size_t base = (size_t)r.img * b.n;
+    int s0 = start[bin], s1 = start[bin + 1];
+    const int *un = b.slot_unsorted + base;
+    for (int p = s0; p < s1; ++p) {
+        int idx = un[p];
+        int rk = 0;
+        for (int q = s0; q < s1; ++q) rk += (un[q] < idx);
+        int dst = s0 + rk;
+        b.slot_atom[base + dst] = idx;
+        b.slot_bin[base + dst] = bin;
+        b.atom_slot[base + idx] = dst;
+        ((T4 *)b.slot_off)[base + dst] = ((const T4 *)b.atom_off)[base + idx];
+        ((T4 *)b.slot_off_lo)[base + dst] = ((const T4 *)b.atom_off_lo)[base + idx];
+    }
+}
+
+// Cartesian positions R = R~ D (FP64) of the listed images, for output.
+template <typename T>
+__global__ void k_cartesian(const ImgRef *imgs, BandDev *bands) {
+    ImgRef r = imgs[blockIdx.y];
+    BandDev &b = bands[r.band];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.n) return;
+    const ImgScalars &sc = b.sc[r.img];
+    const T *Xi = (const T *)b.X + ((size_t)r.img * b.rows + i) * 3;
+    double x[3] = {(double)Xi[0], (double)Xi[1], (double)Xi[2]};
+    double *o = b.cart + ((size_t)r.img * b.n + i) * 3;
+    for (int c = 0; c < 3; ++c) o[c] = x[0] * sc.D[c] + x[1] * sc.D[3 + c] + x[2] * sc.D[6 + c];
+}
+
+// ---- launchers -------------------------------------------------------------
+
+template <typename T>
+void launch_mapback(const ImgRef *imgs, int count, BandDev *bands, cudaStream_t s) {
+    if (count <= 0) return;
+    k_mapback<T><<<(count + 31) / 32, 32, 0, s>>>(imgs, count, bands);
+}
+template <typename T>
+void launch_bin_assign(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    k_bin_assign<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
+}
+void launch_bin_scan(const ImgRef *imgs, int count, int max_bins, BandDev *bands,
+                     cudaStream_t s, int part) {
+    if (count <= 0 || max_bins <= 0) return;
+    dim3 grid((max_bins + SCAN_TILE - 1) / SCAN_TILE, count);
+    if (part == 0) k_bin_tilesum<<<grid, 256, 0, s>>>(imgs, bands);
+    else if (part == 1) k_bin_tilescan<<<count, 1024, 0, s>>>(imgs, bands);
+    else k_bin_scanfill<<<grid, 1024, 0, s>>>(imgs, bands);
+}
+void launch_bin_scatter(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    k_bin_scatter<<<ntiles, TILE, 0, s>>>(tiles, bands);
+}
+template <typename T>
+void launch_bin_order(const ImgRef *imgs, int count, int max_bins, BandDev *bands,
+                      cudaStream_t s) {
+    if (count <= 0 || max_bins <= 0) return;
+    dim3 grid((max_bins + 127) / 128, count);
+    k_bin_order<T><<<grid, 128, 0, s>>>(imgs, bands);
+}
+template <typename T>
+void launch_cartesian(const ImgRef *imgs, int count, int max_n, BandDev *bands, cudaStream_t s) {
+    if (count <= 0 || max_n <= 0) return;
+    dim3 grid((max_n + 127) / 128, count);
+    k_cartesian<T><<<grid, 128, 0, s>>>(imgs, bands);
+}
+
+#define CFNEB_INST(T)                                                                     \
+    template void launch_mapback<T>(const ImgRef *, int, BandDev *, cudaStream_t);       \
+    template void launch_bin_assign<T>(const Tile *, int, BandDev *, cudaStream_t);      \
+    template void launch_bin_order<T>(const ImgRef *, int, int, BandDev *, cudaStream_t); \
+    template void launch_cartesian<T>(const ImgRef *, int, int, BandDev *, cudaStream_t);
+CFNEB_INST(float)
+CFNEB_INST(double)
+#undef CFNEB_INST
+
+}  // namespace cfneb

@@ -1,0 +1,238 @@
+// Shared device-side data layout of the CFNEB library.
+//
+// A band of N images of n atoms lives in HBM as image-major arrays:
+//   X, F, Fneb, v : [ncap][n+3][3] of T   (T = double for CFNEB_FP64,
+//                                           float for CFNEB_MIXED)
+// rows 0..n-1 are atoms (R~ and the forces conjugate to it), rows n..n+2 the
+// lattice coordinate c B (Sec. II.C: the (n+3) "atoms" of the cell filter).
+// Per-image FP64 scalars (energy, virial, D, h, bin geometry) sit in
+// ImgScalars[ncap]; per-band constants and FIRE state in BandParams.
+//
+// Kernels are launched over tile tables: each tile is (band, image, t) and
+// covers rows [t*TILE, (t+1)*TILE) of that image, so any mix of bands of
+// different sizes runs in one launch.  Partial sums of a tile land in a
+// fixed slot (image, t) of its band, and every reduction sums the slots of a
+// band in slot order: results do not depend on which other bands share the
+// launch.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cfneb {
+
+constexpr int TILE = 128;           // rows per tile = threads per block
+constexpr int MAXN_TERSOFF = 12;    // Tersoff neighbour capacity per atom
+constexpr int NPART = 12;           // doubles per tile partial record
+constexpr int MAX_STENCIL = 7;      // |delta| <= 7 bins per axis
+
+// device status bits (BandParams::status)
+enum : int {
+    ST_NOT_SPD = 1,
+    ST_NBR_OVERFLOW = 2,
+    ST_NONFINITE = 4,
+};
+
+struct ImgScalars {
+    double E;            // energy (U + P Omega)
+    double U;            // potential energy
+    double V[9];         // virial, V_eff = V - P Omega I
+    double D[9];         // deformation gradient (symmetric root of B)
+    double Dinv[9];
+    double h[9];         // current cell h = h0 D (rows = lattice vectors)
+    double hinv[9];
+    double bv[9];        // bin edge vectors, row a = h_a / nb_a rounded to T
+    double dh[9];        // wrap correction, row a = h_a - nb_a bv_a
+    double omega;        // |det h|
+    double dots[5];      // |dX+|^2, |dX-|^2, dX+.dX-, F.dX+, F.dX-
+    double coef[2];      // f_NEB = F + coef[0] dX+ + coef[1] dX-
+    double pairs;        // neighbour entries inside the cutoff (last evaluation)
+    double triples;      // ordered neighbour pairs (j, k != j) of the atoms (Tersoff)
+    int nb[3];           // bins per axis
+    int m[3];            // stencil half width per axis
+    int nbins;
+    int pad;
+};
+
+struct BandParams {
+    // constants of the band
+    double h0[9], h0inv[9];
+    double c;            // cell factor: X_lat = c B
+    double pressure;
+    double k;            // spring constant
+    double dt0, dt_max, maxstep;
+    double rc;           // potential cutoff
+    double bin_w;        // target bin width
+    double ftol;         // convergence tolerance (< 0: never converged)
+    double pot[12];      // LJ: eps, sigma, rc, phi(rc) or 0; Tersoff: A, B,
+                         // lambda1, lambda2, beta, n, c, d, h, R, D
+    int filter, variant, climb, n;
+    int N;               // current image count
+    int kind;
+    // FIRE state
+    double dt, alpha;
+    int npos, fresh;
+    // outputs of the last step
+    double P, FF, VV, fmax;
+    double cv, cf;       // velocity mixing of the step
+    long long steps;     // FIRE moves taken
+    long long move_limit;// no move once steps reaches this
+    int ci;              // climbing image (-1: none)
+    int converged;       // fmax < ftol at the last evaluation
+    int move;            // the last step moved the images
+    int status;
+};
+
+struct BandDev {
+    int n, rows, ncap, nbins_cap;
+    int atpi, rtpi;      // atom tiles / row tiles per image
+    void *X, *F, *Fneb, *v;
+    ImgScalars *sc;
+    BandParams *bp;
+    // cell list (image-major)
+    int *bin_count;      // [ncap][nbins_cap]
+    int *bin_start;      // [ncap][nbins_cap + 1]
+    int *bin_tsum;       // [ncap][tsum_cap] scan tile sums / prefixes
+    int tsum_cap;
+    int *atom_bin, *atom_rank, *slot_unsorted, *slot_atom, *slot_bin, *atom_slot;  // [ncap][n]
+    void *atom_off, *slot_off;   // [ncap][n] x 4 T (x, y, z, pad): offsets, leading part
+    void *atom_off_lo, *slot_off_lo;  // [ncap][n] x 4 T: offset - leading part
+    // Tersoff per-slot neighbour data
+    int *nbr_cnt;        // [ncap][n]
+    int *nbr_slot;       // [ncap][MAXN][n]
+    int *nbr_code;       // [ncap][MAXN][n]
+    void *nbr_P;         // [ncap][3*MAXN][n] of T
+    // partial sums
+    double *atom_part;   // [ncap][atpi][NPART]
+    double *row_part;    // [ncap][rtpi][NPART]
+    // Cartesian output scratch [ncap][n][3] doubles (get_path)
+    double *cart;
+};
+
+struct Tile {
+    int band, img, t, pad;
+};
+
+struct ImgRef {
+    int band, img;
+};
+
+struct LJParams {
+    double eps, sigma, rc, ephi_c;   // ephi_c = phi(rc) if shifted, else 0
+};
+
+struct TersoffParams {
+    double A, B, lambda1, lambda2, beta, n, c, d, h, R, D;
+};
+
+// ---- small helpers ------------------------------------------------------
+
+__host__ __device__ inline double det3(const double *m) {
+    return m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
+           m[2] * (m[3] * m[7] - m[4] * m[6]);
+}
+
+__host__ __device__ inline void inv3(const double *m, double *o) {
+    double d = det3(m);
+    double id = 1.0 / d;
+    o[0] = (m[4] * m[8] - m[5] * m[7]) * id;
+    o[1] = (m[2] * m[7] - m[1] * m[8]) * id;
+    o[2] = (m[1] * m[5] - m[2] * m[4]) * id;
+    o[3] = (m[5] * m[6] - m[3] * m[8]) * id;
+    o[4] = (m[0] * m[8] - m[2] * m[6]) * id;
+    o[5] = (m[2] * m[3] - m[0] * m[5]) * id;
+    o[6] = (m[3] * m[7] - m[4] * m[6]) * id;
+    o[7] = (m[1] * m[6] - m[0] * m[7]) * id;
+    o[8] = (m[0] * m[4] - m[1] * m[3]) * id;
+}
+
+__host__ __device__ inline void matmul3(const double *a, const double *b, double *o) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            o[3 * i + j] = a[3 * i] * b[j] + a[3 * i + 1] * b[3 + j] + a[3 * i + 2] * b[6 + j];
+}
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4_32a; };
+
+// packed stencil offset: 5 bits per axis, biased by 16
+__host__ __device__ inline int pack_code(int d0, int d1, int d2) {
+    return (d0 + 16) | ((d1 + 16) << 5) | ((d2 + 16) << 10);
+}
+__host__ __device__ inline int neg_code(int code) {
+    int d0 = (code & 31) - 16, d1 = ((code >> 5) & 31) - 16, d2 = ((code >> 10) & 31) - 16;
+    return pack_code(-d0, -d1, -d2);
+}
+
+// deterministic warp sum (fixed butterfly)
+__device__ inline double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ inline double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Sum K per-thread values over a TILE-thread block in FP64 (fixed order);
+// thread 0 of the block receives the totals in out[0..K-1].
+template <int K>
+__device__ inline void block_sum(double (&v)[K], double *out) {
+    __shared__ double red[TILE / 32][K > 0 ? K : 1];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double s = warp_sum(v[k]);
+        if (lane == 0) red[w][k] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double s = 0.0;
+            for (int q = 0; q < TILE / 32; ++q) s += red[q][k];
+            out[k] = s;
+        }
+    }
+    __syncthreads();  // red[] may be reused by a later call
+}
+
+// ---- launchers (defined in the kernel translation units) ---------------
+
+template <typename T>
+void launch_mapback(const ImgRef *imgs, int count, BandDev *bands, cudaStream_t s);
+template <typename T>
+void launch_bin_assign(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
+// part 0: tile sums, 1: scan of the tile sums, 2: final per-bin scan
+void launch_bin_scan(const ImgRef *imgs, int count, int max_bins, BandDev *bands,
+                     cudaStream_t s, int part);
+void launch_bin_scatter(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
+template <typename T>
+void launch_bin_order(const ImgRef *imgs, int count, int max_bins, BandDev *bands,
+                      cudaStream_t s);
+template <typename T>
+void launch_lj(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
+template <typename T>
+void launch_tersoff_partials(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
+template <typename T>
+void launch_tersoff_gather(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
+template <typename T>
+void launch_image_finalize(const ImgRef *imgs, int count, BandDev *bands, cudaStream_t s);
+template <typename T>
+void launch_band_dots(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
+void launch_dots_reduce(const ImgRef *imgs, int count, BandDev *bands, cudaStream_t s);
+void launch_neb_coef(const int *band_ids, int nbands, BandDev *bands, cudaStream_t s);
+template <typename T>
+void launch_neb_force(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
+void launch_fire_scalars(const int *band_ids, int nbands, BandDev *bands, cudaStream_t s);
+template <typename T>
+void launch_fire_update(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
+template <typename T>
+void launch_cartesian(const ImgRef *imgs, int count, int max_n, BandDev *bands, cudaStream_t s);
+template <typename T>
+void launch_midpoint(BandDev *band, int img, int rows, cudaStream_t s);
+template <typename T>
+void launch_setup(const double *R0, const double *R1, const double *noise, int n, int N,
+                  BandDev *band, cudaStream_t s, const double *h1);
+
+}  // namespace cfneb

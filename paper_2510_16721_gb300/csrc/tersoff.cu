@@ -1,0 +1,380 @@
+// Tersoff (1988 form, lambda3 = 0) energy, forces and virial.
+//
+//   U_i = 1/2 sum_j fC(r_ij) [A e^{-l1 r_ij} - b_ij B e^{-l2 r_ij}]
+//   b_ij = (1 + (beta zeta_ij)^n)^(-1/2n),
+//   zeta_ij = sum_{k != j} fC(r_ik) g(cos theta_ijk)
+//
+// Two kernels, both one thread per atom in cell-list slot order:
+//
+// 1. k_ters_partials: collects the neighbour entries (j, periodic shift)
+//    of atom i inside R + D from the cell list, and computes the site energy
+//    U_i and every partial P_ij = dU_i/dr^ij (Sec. II.B, Eq. U: U_i is a
+//    function of the r^ij of i's neighbours).  It also accumulates the
+//    virial in its per-site form V_mn = -sum_i sum_j P_ij,n r^ij_m (first
+//    line of the derivation of Eq. V2), which needs no pair forces.
+// 2. k_ters_gather: F_i = sum_j f^ij with f^ij = P_ij - P_ji (Sec. II.B),
+//    where P_ji is read from j's list at the entry that points back to i
+//    under the opposite shift.  No atomics: each atom sums its own terms in
+//    list order, so the result is deterministic.
+//
+// The angular function is evaluated as g = 1 + c^2 u^2 / (d^2 (d^2 + u^2)),
+// u = h - cos theta: algebraically Tersoff's 1 + c^2/d^2 - c^2/(d^2 + u^2),
+// but free of the cancellation between two ~8e7 terms that would cost FP32
+// four digits.
+//
+// Distances are carried to twice the working precision.  With n < 1 the
+// bond-order derivative grows like zeta^(n-1) when a neighbour nears R + D,
+// so forces there respond to a distance error d like d^0.46: ~1e-4 eV/A for
+// the 1e-7 A that an FP32 pair vector near 2 A can hold.  Each atom's
+// offset is stored as a leading FP32 part plus the FP32 remainder; a pair
+// vector is formed as (o_j - o_i) + c with Knuth's two-sum keeping the
+// rounding errors (c, the displacement between bin centres, is exact by
+// construction), and s = r - R follows from r^2 - R^2 with FMA-exact
+// squares.  Directions and angles use the leading part; every radial
+// function (f_C, f_R, f_A and derivatives) uses s, accurate to ~1e-12 A.
+// exp(-l r) is evaluated as exp(-l R) exp(-l s).  The cutoff function is
+// written without cancellation: with a = pi (D - s) / 4D and
+// b = pi (D + s) / 4D (a + b = pi/2), 1/2 - 1/2 sin(pi s / 2D) = sin^2 a and
+// its derivative -(pi/4D) cos(pi s / 2D) = -(pi/2D) sin a sin b; D - s and
+// D + s are formed exactly (two-term D), so f_C keeps full relative accuracy
+// even where it is 1e-8 (a neighbour at the outer edge, where the bond-order
+// derivative amplifies any absolute error).
+#include "common.cuh"
+
+namespace cfneb {
+
+template <typename T> struct M;
+template <> struct M<float> {
+    static __device__ float ex(float x) { return expf(x); }
+    static __device__ float lg(float x) { return logf(x); }
+    static __device__ float l1p(float x) { return log1pf(x); }
+    static __device__ float sq(float x) { return sqrtf(x); }
+    static __device__ float sn(float x) { return sinf(x); }
+};
+template <> struct M<double> {
+    static __device__ double ex(double x) { return exp(x); }
+    static __device__ double lg(double x) { return log(x); }
+    static __device__ double l1p(double x) { return log1p(x); }
+    static __device__ double sq(double x) { return sqrt(x); }
+    static __device__ double sn(double x) { return sin(x); }
+};
+
+template <typename T>
+struct TP {  // Tersoff constants in T
+    T A, B, l1, l2, beta, n, c2, d2, h, R, D, Rhi, pi_2D, pi_4D, inv2n;
+    T AeR, BeR;        // A exp(-l1 R), B exp(-l2 R)
+    T R2hi, R2lo;      // R^2 as a two-term sum
+    T Dlo;             // D - (T)D
+    __device__ void load(const TersoffParams &p) {
+        A = (T)p.A; B = (T)p.B; l1 = (T)p.lambda1; l2 = (T)p.lambda2; beta = (T)p.beta;
+        n = (T)p.n; c2 = (T)(p.c * p.c); d2 = (T)(p.d * p.d); h = (T)p.h; R = (T)p.R;
+        D = (T)p.D; Rhi = (T)(p.R + p.D);
+        pi_2D = (T)(0.5 * 3.14159265358979323846 / p.D);
+        pi_4D = (T)(0.25 * 3.14159265358979323846 / p.D);
+        inv2n = (T)(0.5 / p.n);
+        AeR = (T)(p.A * exp(-p.lambda1 * p.R));
+        BeR = (T)(p.B * exp(-p.lambda2 * p.R));
+        R2hi = (T)(p.R * p.R);
+        R2lo = (T)(p.R * p.R - (double)R2hi);
+        Dlo = (T)(p.D - (double)D);
+    }
+};
+
+__device__ inline float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ inline double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ inline float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ inline double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ inline float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ inline double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+
+// Knuth's two-sum: s + e == a + b exactly
+template <typename T>
+__device__ inline void two_sum(T a, T b, T &s, T &e) {
+    s = add_rn(a, b);
+    const T bb = sub_rn(s, a);
+    e = add_rn(sub_rn(a, sub_rn(s, bb)), sub_rn(b, bb));
+}
+
+// Dekker's fast two-sum (|a| >= |b|): s + e == a + b exactly
+template <typename T>
+__device__ inline void fast_two_sum(T a, T b, T &s, T &e) {
+    s = add_rn(a, b);
+    e = sub_rn(b, sub_rn(s, a));
+}
+
+// r and s = r - R for the pair vector (x + xl, y + yl, z + zl), leading
+// parts x, y, z and small remainders xl, yl, zl
+template <typename T>
+__device__ inline void dist_s(const TP<T> &q, T x, T y, T z, T xl, T yl, T zl, T &r, T &s) {
+    const T px = mul_rn(x, x), py = mul_rn(y, y), pz = mul_rn(z, z);
+    const T ex = fma(x, x, -px) + (T)2 * x * xl, ey = fma(y, y, -py) + (T)2 * y * yl,
+            ez = fma(z, z, -pz) + (T)2 * z * zl;
+    T s1, e1, s2, e2;
+    two_sum(px, py, s1, e1);
+    two_sum(s1, pz, s2, e2);
+    const T lo = add_rn(add_rn(add_rn(ex, ey), ez), add_rn(e1, e2));
+    // s2 - R^2 is exact when r^2 lies within a factor 2 of R^2
+    const T d = add_rn(sub_rn(s2, q.R2hi), sub_rn(lo, q.R2lo));
+    r = M<T>::sq(add_rn(s2, lo));
+    s = d / (r + q.R);
+}
+
+// cutoff function and derivative from s = r - R (see the header comment)
+template <typename T>
+__device__ inline void cutoff(const TP<T> &q, T s, T &fc, T &dfc) {
+    const T u = sub_rn(q.D, s) + q.Dlo;  // D - s
+    const T v = add_rn(q.D, s) + q.Dlo;  // D + s
+    if (v <= (T)0) { fc = (T)1; dfc = (T)0; return; }
+    if (u <= (T)0) { fc = (T)0; dfc = (T)0; return; }
+    const T sa = M<T>::sn(q.pi_4D * u), sb = M<T>::sn(q.pi_4D * v);
+    fc = sa * sa;
+    dfc = -q.pi_2D * sa * sb;
+}
+
+template <typename T>
+__device__ inline void gfun(const TP<T> &q, T cs, T &g, T &dg) {
+    T u = q.h - cs;
+    T den = q.d2 + u * u;
+    g = (T)1 + q.c2 * u * u / (q.d2 * den);
+    dg = -(T)2 * q.c2 * u / (den * den);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_ters_partials(const Tile *tiles, BandDev *bands) {
+    using T4 = typename Vec4<T>::type;
+    Tile tl = tiles[blockIdx.x];
+    BandDev &b = bands[tl.band];
+    const ImgScalars &sc = b.sc[tl.img];
+    __shared__ T s_bv[9], s_dh[9];
+    __shared__ int s_nb[3], s_m[3];
+    if (threadIdx.x < 9) {
+        s_bv[threadIdx.x] = (T)sc.bv[threadIdx.x];
+        s_dh[threadIdx.x] = (T)sc.dh[threadIdx.x];
+    }
+    if (threadIdx.x < 3) {
+        s_nb[threadIdx.x] = sc.nb[threadIdx.x];
+        s_m[threadIdx.x] = sc.m[threadIdx.x];
+    }
+    __syncthreads();
+    TP<T> q;
+    q.load(*(const TersoffParams *)b.bp->pot);
+    const int n = b.n;
+    const int t = tl.t * TILE + threadIdx.x;
+    const size_t base = (size_t)tl.img * n;
+    const T4 *off = (const T4 *)b.slot_off + base;
+    const T4 *offl = (const T4 *)b.slot_off_lo + base;
+    const int *start = b.bin_start + (size_t)tl.img * (b.nbins_cap + 1);
+    int *nslot = b.nbr_slot + (size_t)tl.img * MAXN_TERSOFF * n;
+    int *ncode = b.nbr_code + (size_t)tl.img * MAXN_TERSOFF * n;
+    T *nP = (T *)b.nbr_P + (size_t)tl.img * 3 * MAXN_TERSOFF * n;
+    const T rc2_screen = q.Rhi * q.Rhi * (T)1.00001;
+
+    T rx[MAXN_TERSOFF], ry[MAXN_TERSOFF], rz[MAXN_TERSOFF], rd[MAXN_TERSOFF];
+    T sr[MAXN_TERSOFF];  // r - R
+    T fc[MAXN_TERSOFF], dfc[MAXN_TERSOFF];
+    T Px[MAXN_TERSOFF], Py[MAXN_TERSOFF], Pz[MAXN_TERSOFF];
+    int cnt = 0, total = 0;
+    T U = 0;
+    T vir[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (t < n) {
+        const int bin = b.slot_bin[base + t];
+        const int nb1 = s_nb[1], nb2 = s_nb[2];
+        const int b0 = bin / (nb1 * nb2), b1 = (bin / nb2) % nb1, b2 = bin % nb2;
+        const T4 oi = off[t];
+        const T4 oil = offl[t];
+        for (int d0 = -s_m[0]; d0 <= s_m[0]; ++d0) {
+            const int u0 = b0 + d0;
+            int w0 = u0 % s_nb[0];
+            w0 += (w0 < 0) ? s_nb[0] : 0;
+            const int t0 = (u0 - w0) / s_nb[0];
+            for (int d1 = -s_m[1]; d1 <= s_m[1]; ++d1) {
+                const int u1 = b1 + d1;
+                int w1 = u1 % nb1;
+                w1 += (w1 < 0) ? nb1 : 0;
+                const int t1 = (u1 - w1) / nb1;
+                for (int d2 = -s_m[2]; d2 <= s_m[2]; ++d2) {
+                    const int u2 = b2 + d2;
+                    int w2 = u2 % nb2;
+                    w2 += (w2 < 0) ? nb2 : 0;
+                    const int t2 = (u2 - w2) / nb2;
+                    const int w = (w0 * nb1 + w1) * nb2 + w2;
+                    // bin-centre displacement: exact (quantised bin vectors)
+                    const T cx = d0 * s_bv[0] + d1 * s_bv[3] + d2 * s_bv[6];
+                    const T cy = d0 * s_bv[1] + d1 * s_bv[4] + d2 * s_bv[7];
+                    const T cz = d0 * s_bv[2] + d1 * s_bv[5] + d2 * s_bv[8];
+                    // periodic-wrap remainder (tiny)
+                    const T wx = t0 * s_dh[0] + t1 * s_dh[3] + t2 * s_dh[6];
+                    const T wy = t0 * s_dh[1] + t1 * s_dh[4] + t2 * s_dh[7];
+                    const T wz = t0 * s_dh[2] + t1 * s_dh[5] + t2 * s_dh[8];
+                    const T ux0 = (cx + wx) - oi.x, uy0 = (cy + wy) - oi.y,
+                            uz0 = (cz + wz) - oi.z;
+                    const int q1 = start[w + 1];
+                    for (int qs = start[w]; qs < q1; ++qs) {
+                        const T4 oj = off[qs];
+                        const T ux = oj.x + ux0, uy = oj.y + uy0, uz = oj.z + uz0;
+                        if (ux * ux + uy * uy + uz * uz >= rc2_screen) continue;
+                        const T4 ojl = offl[qs];
+                        T x, y, z, ex1, ey1, ez1, ex2, ey2, ez2;
+                        two_sum(oj.x, -oi.x, x, ex1);
+                        two_sum(oj.y, -oi.y, y, ey1);
+                        two_sum(oj.z, -oi.z, z, ez1);
+                        two_sum(x, cx, x, ex2);
+                        two_sum(y, cy, y, ey2);
+                        two_sum(z, cz, z, ez2);
+                        T xl = ((ojl.x - oil.x) + wx) + (ex1 + ex2);
+                        T yl = ((ojl.y - oil.y) + wy) + (ey1 + ey2);
+                        T zl = ((ojl.z - oil.z) + wz) + (ez1 + ez2);
+                        // renormalise: the leading part (used for directions)
+                        // takes the wrap remainder, the low part keeps the rest
+                        fast_two_sum(x, xl, x, xl);
+                        fast_two_sum(y, yl, y, yl);
+                        fast_two_sum(z, zl, z, zl);
+                        T r, s;
+                        dist_s(q, x, y, z, xl, yl, zl, r, s);
+                        if (sub_rn(s, q.D) < q.Dlo && r > (T)0) {
+                            if (cnt < MAXN_TERSOFF) {
+                                rx[cnt] = x; ry[cnt] = y; rz[cnt] = z;
+                                rd[cnt] = r;
+                                sr[cnt] = s;
+                                nslot[(size_t)cnt * n + t] = qs;
+                                ncode[(size_t)cnt * n + t] = pack_code(d0, d1, d2);
+                                ++cnt;
+                            }
+                            ++total;
+                        }
+                    }
+                }
+            }
+        }
+        b.nbr_cnt[base + t] = cnt;
+        if (total > MAXN_TERSOFF) atomicOr(&b.bp->status, ST_NBR_OVERFLOW);
+        for (int j = 0; j < cnt; ++j) {
+            cutoff(q, sr[j], fc[j], dfc[j]);
+            Px[j] = Py[j] = Pz[j] = (T)0;
+        }
+        for (int j = 0; j < cnt; ++j) {
+            // zeta_ij and the bond order
+            T zeta = 0;
+            for (int k = 0; k < cnt; ++k) {
+                if (k == j) continue;
+                T cs = (rx[j] * rx[k] + ry[j] * ry[k] + rz[j] * rz[k]) / (rd[j] * rd[k]);
+                T g, dg;
+                gfun(q, cs, g, dg);
+                zeta += fc[k] * g;
+            }
+            T bij = (T)1, dbij = (T)0;
+            if (zeta > (T)0) {
+                T x = M<T>::ex(q.n * M<T>::lg(q.beta * zeta));
+                bij = M<T>::ex(-q.inv2n * M<T>::l1p(x));
+                dbij = (T)(-0.5) * bij * x / (((T)1 + x) * zeta);
+            }
+            const T fr = q.AeR * M<T>::ex(-q.l1 * sr[j]);
+            const T fa = -q.BeR * M<T>::ex(-q.l2 * sr[j]);
+            const T dfr = -q.l1 * fr, dfa = -q.l2 * fa;
+            U += (T)0.5 * fc[j] * (fr + bij * fa);
+            const T radial =
+                (T)0.5 * (dfc[j] * (fr + bij * fa) + fc[j] * (dfr + bij * dfa)) / rd[j];
+            Px[j] += radial * rx[j];
+            Py[j] += radial * ry[j];
+            Pz[j] += radial * rz[j];
+            const T pref = (T)0.5 * fc[j] * fa * dbij;
+            if (pref == (T)0) continue;
+            for (int k = 0; k < cnt; ++k) {
+                if (k == j) continue;
+                const T ijk = (T)1 / (rd[j] * rd[k]);
+                const T cs = (rx[j] * rx[k] + ry[j] * ry[k] + rz[j] * rz[k]) * ijk;
+                T g, dg;
+                gfun(q, cs, g, dg);
+                // d cos / d r^ij and d cos / d r^ik
+                const T aj = cs / (rd[j] * rd[j]), ak = cs / (rd[k] * rd[k]);
+                const T sj = pref * fc[k] * dg;
+                Px[j] += sj * (rx[k] * ijk - aj * rx[j]);
+                Py[j] += sj * (ry[k] * ijk - aj * ry[j]);
+                Pz[j] += sj * (rz[k] * ijk - aj * rz[j]);
+                const T rk = pref * dfc[k] * g / rd[k];
+                const T sk = pref * fc[k] * dg;
+                Px[k] += rk * rx[k] + sk * (rx[j] * ijk - ak * rx[k]);
+                Py[k] += rk * ry[k] + sk * (ry[j] * ijk - ak * ry[k]);
+                Pz[k] += rk * rz[k] + sk * (rz[j] * ijk - ak * rz[k]);
+            }
+        }
+        for (int j = 0; j < cnt; ++j) {
+            nP[(size_t)(3 * j + 0) * n + t] = Px[j];
+            nP[(size_t)(3 * j + 1) * n + t] = Py[j];
+            nP[(size_t)(3 * j + 2) * n + t] = Pz[j];
+            // V_mn -= r_m P_n
+            vir[0] -= rx[j] * Px[j]; vir[1] -= rx[j] * Py[j]; vir[2] -= rx[j] * Pz[j];
+            vir[3] -= ry[j] * Px[j]; vir[4] -= ry[j] * Py[j]; vir[5] -= ry[j] * Pz[j];
+            vir[6] -= rz[j] * Px[j]; vir[7] -= rz[j] * Py[j]; vir[8] -= rz[j] * Pz[j];
+        }
+    }
+    double acc[12];
+    acc[0] = (double)U;
+    for (int k = 0; k < 9; ++k) acc[1 + k] = (double)vir[k];
+    acc[10] = (double)cnt;
+    acc[11] = (double)(cnt * (cnt - 1));
+    double tot[12];
+    block_sum<12>(acc, tot);
+    if (threadIdx.x == 0) {
+        double *part = b.atom_part + ((size_t)tl.img * b.atpi + tl.t) * NPART;
+        for (int k = 0; k < 12; ++k) part[k] = tot[k];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_ters_gather(const Tile *tiles, BandDev *bands) {
+    Tile tl = tiles[blockIdx.x];
+    BandDev &b = bands[tl.band];
+    const int n = b.n;
+    const int t = tl.t * TILE + threadIdx.x;
+    if (t >= n) return;
+    const ImgScalars &sc = b.sc[tl.img];
+    const size_t base = (size_t)tl.img * n;
+    const int *nslot = b.nbr_slot + (size_t)tl.img * MAXN_TERSOFF * n;
+    const int *ncode = b.nbr_code + (size_t)tl.img * MAXN_TERSOFF * n;
+    const int *ncnt = b.nbr_cnt + base;
+    const T *nP = (const T *)b.nbr_P + (size_t)tl.img * 3 * MAXN_TERSOFF * n;
+    T fx = 0, fy = 0, fz = 0;
+    const int cnt = ncnt[t];
+    for (int k = 0; k < cnt; ++k) {
+        fx += nP[(size_t)(3 * k + 0) * n + t];
+        fy += nP[(size_t)(3 * k + 1) * n + t];
+        fz += nP[(size_t)(3 * k + 2) * n + t];
+        const int qs = nslot[(size_t)k * n + t];
+        const int back = neg_code(ncode[(size_t)k * n + t]);
+        const int cq = ncnt[qs];
+        for (int k2 = 0; k2 < cq; ++k2) {
+            if (nslot[(size_t)k2 * n + qs] == t && ncode[(size_t)k2 * n + qs] == back) {
+                fx -= nP[(size_t)(3 * k2 + 0) * n + qs];
+                fy -= nP[(size_t)(3 * k2 + 1) * n + qs];
+                fz -= nP[(size_t)(3 * k2 + 2) * n + qs];
+                break;
+            }
+        }
+    }
+    const T g0 = fx * (T)sc.D[0] + fy * (T)sc.D[1] + fz * (T)sc.D[2];
+    const T g1 = fx * (T)sc.D[3] + fy * (T)sc.D[4] + fz * (T)sc.D[5];
+    const T g2 = fx * (T)sc.D[6] + fy * (T)sc.D[7] + fz * (T)sc.D[8];
+    const int atom = b.slot_atom[base + t];
+    T *F = (T *)b.F + ((size_t)tl.img * b.rows + atom) * 3;
+    F[0] = g0;
+    F[1] = g1;
+    F[2] = g2;
+}
+
+template <typename T>
+void launch_tersoff_partials(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    k_ters_partials<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
+}
+template <typename T>
+void launch_tersoff_gather(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    k_ters_gather<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
+}
+template void launch_tersoff_partials<float>(const Tile *, int, BandDev *, cudaStream_t);
+template void launch_tersoff_partials<double>(const Tile *, int, BandDev *, cudaStream_t);
+template void launch_tersoff_gather<float>(const Tile *, int, BandDev *, cudaStream_t);
+template void launch_tersoff_gather<double>(const Tile *, int, BandDev *, cudaStream_t);
+
+}  // namespace cfneb
