@@ -168,7 +168,9 @@ int cfneb_delete_image(cfneb_band *band, int32_t index);
  *   *n_images  = N
  *   positions  = N x n_atoms x 3 Cartesian positions (R = R~ D)
  *   cells      = N x 9 cells h = h0 D
- *   energies   = N energies (U + P Omega)
+ *   energies   = N energies (U + P Omega) of these positions and cells,
+ *                from an FP64 energy pass (on either precision): barriers
+ *                read from them carry FP64 totals
  *   fmax       = largest f_NEB row norm at the last step (0 before any step)
  * Synchronises. */
 int cfneb_get_path(const cfneb_band *band, int32_t *n_images, double *positions,
@@ -191,8 +193,9 @@ int cfneb_destroy_band(cfneb_band *band);
 
 /* Single-point evaluation of `count` structures (any cells, any sizes):
  * energies[count], forces[sum n_i x 3] (Cartesian, structures back to
- * back), virials[count x 9].  Same kernels as a relaxation step (cell list
- * and force kernels).  Output pointers may be NULL.  Synchronises. */
+ * back), virials[count x 9].  Forces and virials come from the kernels of a
+ * relaxation step in the requested precision; energies from the FP64
+ * energy pass.  Output pointers may be NULL.  Synchronises. */
 int cfneb_evaluate(const cfneb_structure *structures, int32_t count,
                    const cfneb_potential *potential, int32_t precision, void *cuda_stream,
                    double *energies, double *forces, double *virials);

@@ -33,8 +33,9 @@ enum : int {
 };
 
 struct ImgScalars {
-    double E;            // energy (U + P Omega)
+    double E;            // energy (U + P Omega) of the last step's evaluation
     double U;            // potential energy
+    double E64;          // FP64 energy (U + P Omega) for reporting
     double V[9];         // virial, V_eff = V - P Omega I
     double D[9];         // deformation gradient (symmetric root of B)
     double Dinv[9];
@@ -227,6 +228,9 @@ void launch_neb_force(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_
 void launch_fire_scalars(const int *band_ids, int nbands, BandDev *bands, cudaStream_t s);
 template <typename T>
 void launch_fire_update(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
+template <typename T>
+void launch_energy64(const Tile *tiles, int ntiles, const ImgRef *imgs, int nimg, BandDev *bands,
+                     cudaStream_t s);
 template <typename T>
 void launch_cartesian(const ImgRef *imgs, int count, int max_n, BandDev *bands, cudaStream_t s);
 template <typename T>

@@ -1,0 +1,153 @@
+// FP64 total energies for reporting (paths, barriers, single points).
+//
+// The per-step force kernels of the mixed path evaluate per-atom energies in
+// FP32; that is enough to order neighbouring images for the upwind tangent
+// and to pick the climbing image, but a total over ~1e5 atoms carries errors
+// of ~1e-2 eV (in a perfect crystal every atom makes the same rounding
+// error).  Reported energies therefore come from these kernels, which redo
+// the energy -- and only the energy -- in FP64 from the cell list of the
+// configuration being reported: pair vectors from the two-term offsets (exact
+// positions), bin displacements and wrap corrections in FP64, then the
+// Lennard-Jones or Tersoff energy of Sec. II.B's per-atom split summed over
+// atoms in FP64.  Used by cfneb_get_path and cfneb_evaluate, never inside a
+// relaxation step.
+#include "common.cuh"
+
+namespace cfneb {
+
+template <typename T>
+__device__ inline void pair_vec64(const typename Vec4<T>::type &oi, const typename Vec4<T>::type &oil,
+                                  const typename Vec4<T>::type &oj, const typename Vec4<T>::type &ojl,
+                                  const double *c, double *r) {
+    r[0] = ((double)oj.x + (double)ojl.x) - ((double)oi.x + (double)oil.x) + c[0];
+    r[1] = ((double)oj.y + (double)ojl.y) - ((double)oi.y + (double)oil.y) + c[1];
+    r[2] = ((double)oj.z + (double)ojl.z) - ((double)oi.z + (double)oil.z) + c[2];
+}
+
+// Walk the stencil of slot t and call f(r[3]) for every neighbour entry
+// within rc (periodic images included, the atom itself excluded).
+template <typename T, typename Fn>
+__device__ inline void for_neighbours64(const BandDev &b, int img, int t, const ImgScalars &sc,
+                                        double rc2, Fn f) {
+    using T4 = typename Vec4<T>::type;
+    const size_t base = (size_t)img * b.n;
+    const T4 *off = (const T4 *)b.slot_off + base;
+    const T4 *offl = (const T4 *)b.slot_off_lo + base;
+    const int *start = b.bin_start + (size_t)img * (b.nbins_cap + 1);
+    const int bin = b.slot_bin[base + t];
+    const int nb0 = sc.nb[0], nb1 = sc.nb[1], nb2 = sc.nb[2];
+    const int b0 = bin / (nb1 * nb2), b1 = (bin / nb2) % nb1, b2 = bin % nb2;
+    const T4 oi = off[t], oil = offl[t];
+    for (int d0 = -sc.m[0]; d0 <= sc.m[0]; ++d0) {
+        const int u0 = b0 + d0;
+        int w0 = u0 % nb0;
+        w0 += (w0 < 0) ? nb0 : 0;
+        const int t0 = (u0 - w0) / nb0;
+        for (int d1 = -sc.m[1]; d1 <= sc.m[1]; ++d1) {
+            const int u1 = b1 + d1;
+            int w1 = u1 % nb1;
+            w1 += (w1 < 0) ? nb1 : 0;
+            const int t1 = (u1 - w1) / nb1;
+            for (int d2 = -sc.m[2]; d2 <= sc.m[2]; ++d2) {
+                const int u2 = b2 + d2;
+                int w2 = u2 % nb2;
+                w2 += (w2 < 0) ? nb2 : 0;
+                const int t2 = (u2 - w2) / nb2;
+                const int w = (w0 * nb1 + w1) * nb2 + w2;
+                double c[3];
+                for (int k = 0; k < 3; ++k)
+                    c[k] = d0 * sc.bv[k] + d1 * sc.bv[3 + k] + d2 * sc.bv[6 + k] +
+                           t0 * sc.dh[k] + t1 * sc.dh[3 + k] + t2 * sc.dh[6 + k];
+                const int q1 = start[w + 1];
+                for (int q = start[w]; q < q1; ++q) {
+                    double r[3];
+                    pair_vec64<T>(oi, oil, off[q], offl[q], c, r);
+                    const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+                    if (r2 < rc2 && r2 > 0.0) f(r, r2);
+                }
+            }
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_energy64(const Tile *tiles, BandDev *bands) {
+    Tile tl = tiles[blockIdx.x];
+    BandDev &b = bands[tl.band];
+    const ImgScalars &sc = b.sc[tl.img];
+    const BandParams *bp = b.bp;
+    const int t = tl.t * TILE + threadIdx.x;
+    double U = 0.0;
+    if (t < b.n) {
+        if (bp->kind == 0) {
+            const LJParams p = *(const LJParams *)bp->pot;
+            const double s2 = p.sigma * p.sigma;
+            for_neighbours64<T>(b, tl.img, t, sc, p.rc * p.rc, [&](const double *r, double r2) {
+                const double sr6 = s2 * s2 * s2 / (r2 * r2 * r2);
+                U += 0.5 * (4.0 * p.eps * (sr6 * sr6 - sr6) - p.ephi_c);
+            });
+        } else {
+            const TersoffParams p = *(const TersoffParams *)bp->pot;
+            const double rc = p.R + p.D;
+            double rx[MAXN_TERSOFF], ry[MAXN_TERSOFF], rz[MAXN_TERSOFF], rd[MAXN_TERSOFF];
+            int cnt = 0;
+            for_neighbours64<T>(b, tl.img, t, sc, rc * rc, [&](const double *r, double r2) {
+                if (cnt < MAXN_TERSOFF) {
+                    rx[cnt] = r[0];
+                    ry[cnt] = r[1];
+                    rz[cnt] = r[2];
+                    rd[cnt] = sqrt(r2);
+                    ++cnt;
+                }
+            });
+            const double pi = 3.14159265358979323846;
+            const double c2 = p.c * p.c, d2 = p.d * p.d;
+            for (int j = 0; j < cnt; ++j) {
+                double zeta = 0.0;
+                for (int k = 0; k < cnt; ++k) {
+                    if (k == j) continue;
+                    const double cs = (rx[j] * rx[k] + ry[j] * ry[k] + rz[j] * rz[k]) /
+                                      (rd[j] * rd[k]);
+                    const double u = p.h - cs;
+                    const double g = 1.0 + c2 * u * u / (d2 * (d2 + u * u));
+                    const double sk = rd[k] - p.R;
+                    const double fck = sk <= -p.D ? 1.0 : (sk >= p.D ? 0.0 : pow(sin(0.25 * pi * (p.D - sk) / p.D), 2.0));
+                    zeta += fck * g;
+                }
+                const double b_ = zeta > 0.0 ? pow(1.0 + pow(p.beta * zeta, p.n), -0.5 / p.n) : 1.0;
+                const double sj = rd[j] - p.R;
+                const double fcj = sj <= -p.D ? 1.0 : (sj >= p.D ? 0.0 : pow(sin(0.25 * pi * (p.D - sj) / p.D), 2.0));
+                U += 0.5 * fcj * (p.A * exp(-p.lambda1 * rd[j]) - b_ * p.B * exp(-p.lambda2 * rd[j]));
+            }
+        }
+    }
+    double acc[1] = {U};
+    double tot[1];
+    block_sum<1>(acc, tot);
+    if (threadIdx.x == 0) b.atom_part[((size_t)tl.img * b.atpi + tl.t) * NPART] = tot[0];
+}
+
+// one warp per image: E64 = sum of the tile energies (+ P Omega)
+__global__ void k_energy_finalize(const ImgRef *imgs, BandDev *bands) {
+    ImgRef r = imgs[blockIdx.x];
+    BandDev &b = bands[r.band];
+    const double *part = b.atom_part + (size_t)r.img * b.atpi * NPART;
+    double v = 0.0;
+    for (int t = threadIdx.x; t < b.atpi; t += 32) v += part[(size_t)t * NPART];
+    v = warp_sum(v);
+    if (threadIdx.x == 0) b.sc[r.img].E64 = v + b.bp->pressure * b.sc[r.img].omega;
+}
+
+template <typename T>
+void launch_energy64(const Tile *tiles, int ntiles, const ImgRef *imgs, int nimg, BandDev *bands,
+                     cudaStream_t s) {
+    if (ntiles <= 0 || nimg <= 0) return;
+    k_energy64<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
+    k_energy_finalize<<<nimg, 32, 0, s>>>(imgs, bands);
+}
+template void launch_energy64<float>(const Tile *, int, const ImgRef *, int, BandDev *,
+                                     cudaStream_t);
+template void launch_energy64<double>(const Tile *, int, const ImgRef *, int, BandDev *,
+                                      cudaStream_t);
+
+}  // namespace cfneb

@@ -202,7 +202,7 @@ struct Launcher {
 
 template <typename T>
 void enqueue_eval(cfneb_band *b, Launcher &L, const ImgRef *imgs, int nimg, const Tile *atiles,
-                  int natiles) {
+                  int natiles, bool forces = true) {
     BandDev *d = b->d_self;
     cudaStream_t s = b->s;
     L.pre(K_MAPBACK); launch_mapback<T>(imgs, nimg, d, s); L.post(K_MAPBACK);
@@ -213,6 +213,10 @@ void enqueue_eval(cfneb_band *b, Launcher &L, const ImgRef *imgs, int nimg, cons
     L.pre(K_BIN_SCANFILL); launch_bin_scan(imgs, nimg, nbc, d, s, 2); L.post(K_BIN_SCANFILL);
     L.pre(K_BIN_SCATTER); launch_bin_scatter(atiles, natiles, d, s); L.post(K_BIN_SCATTER);
     L.pre(K_BIN_ORDER); launch_bin_order<T>(imgs, nimg, b->dv.nbins_cap, d, s); L.post(K_BIN_ORDER);
+    if (!forces) {
+        launch_energy64<T>(atiles, natiles, imgs, nimg, d, s);
+        return;
+    }
     if (b->kind == CFNEB_LJ) {
         L.pre(K_LJ); launch_lj<T>(atiles, natiles, d, s); L.post(K_LJ);
     } else {
@@ -312,6 +316,33 @@ void eval_images(cfneb_band *b, const std::vector<int> &imgs) {
     else
         enqueue_eval<double>(b, L, b->d_scratch_imgs, (int)im.size(), b->d_scratch_tiles,
                              (int)at.size());
+    b->prof = prof;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(b->s));
+}
+
+// FP64 energies (ImgScalars::E64) of the images' current coordinates:
+// map-back, cell list and the FP64 energy kernel, no forces
+void refine_energies(cfneb_band *b, int first, int count) {
+    std::vector<ImgRef> im;
+    std::vector<Tile> at;
+    for (int i = first; i < first + count; ++i) {
+        im.push_back({0, i});
+        for (int t = 0; t < b->dv.atpi; ++t) at.push_back({0, i, t, 0});
+    }
+    CK(cudaMemcpyAsync(b->d_scratch_imgs, im.data(), im.size() * sizeof(ImgRef),
+                       cudaMemcpyHostToDevice, b->s));
+    CK(cudaMemcpyAsync(b->d_scratch_tiles, at.data(), at.size() * sizeof(Tile),
+                       cudaMemcpyHostToDevice, b->s));
+    Launcher L{b};
+    bool prof = b->prof;
+    b->prof = false;
+    if (b->precision == CFNEB_MIXED)
+        enqueue_eval<float>(b, L, b->d_scratch_imgs, (int)im.size(), b->d_scratch_tiles,
+                            (int)at.size(), false);
+    else
+        enqueue_eval<double>(b, L, b->d_scratch_imgs, (int)im.size(), b->d_scratch_tiles,
+                             (int)at.size(), false);
     b->prof = prof;
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(b->s));
@@ -820,19 +851,14 @@ int cfneb_get_path(const cfneb_band *cb, int32_t *n_images, double *positions, d
     try {
         enter(b);
         if (n_images) *n_images = b->N;
-        std::vector<ImgRef> im;
-        for (int i = 0; i < b->N; ++i) im.push_back({0, i});
-        CK(cudaMemcpyAsync(b->d_scratch_imgs, im.data(), im.size() * sizeof(ImgRef),
-                           cudaMemcpyHostToDevice, b->s));
-        if (positions || cells) {
-            // map the current X back to Cartesian (D from B, R = R~ D)
-            if (b->precision == CFNEB_MIXED) {
-                launch_mapback<float>(b->d_scratch_imgs, b->N, b->d_self, b->s);
+        if (positions || cells || energies) {
+            // FP64 energies of the current images (map-back, cell list, energy),
+            // then Cartesian positions R = R~ D from the same map-back
+            refine_energies(b, 0, b->N);
+            if (b->precision == CFNEB_MIXED)
                 launch_cartesian<float>(b->d_scratch_imgs, b->N, b->n, b->d_self, b->s);
-            } else {
-                launch_mapback<double>(b->d_scratch_imgs, b->N, b->d_self, b->s);
+            else
                 launch_cartesian<double>(b->d_scratch_imgs, b->N, b->n, b->d_self, b->s);
-            }
             CK(cudaGetLastError());
         }
         std::vector<ImgScalars> sc(b->N);
@@ -844,7 +870,7 @@ int cfneb_get_path(const cfneb_band *cb, int32_t *n_images, double *positions, d
         read_params(b);
         for (int i = 0; i < b->N; ++i) {
             if (cells) std::memcpy(cells + 9 * i, sc[i].h, 9 * sizeof(double));
-            if (energies) energies[i] = sc[i].E;
+            if (energies) energies[i] = sc[i].E64;
         }
         if (fmax) *fmax = b->h_bp->fmax;
         leave(b);
@@ -929,14 +955,16 @@ int cfneb_evaluate(const cfneb_structure *structures, int32_t count,
         if (st != CFNEB_OK) return st;
         try {
             enter(b);
-            // the endpoints were evaluated at creation: image 0 is S
+            // the endpoints were evaluated at creation: image 0 is S; its
+            // reported energy is the FP64 one
+            refine_energies(b, 0, 1);
             std::vector<ImgScalars> sc(1);
             CK(cudaMemcpyAsync(sc.data(), b->dv.sc, sizeof(ImgScalars), cudaMemcpyDeviceToHost,
                                b->s));
             std::vector<char> tmp((size_t)b->dv.rows * 3 * b->ts);
             CK(cudaMemcpyAsync(tmp.data(), b->dv.F, tmp.size(), cudaMemcpyDeviceToHost, b->s));
             CK(cudaStreamSynchronize(b->s));
-            if (energies) energies[k] = sc[0].E;
+            if (energies) energies[k] = sc[0].E64;
             if (virials) std::memcpy(virials + 9 * k, sc[0].V, 9 * sizeof(double));
             if (forces) {
                 for (int i = 0; i < S.n_atoms * 3; ++i)
