@@ -222,23 +222,27 @@ def run_reference(args, wl_name):
 
 
 def traffic_for(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel
-    source has not changed since (else None)."""
+    """DRAM bytes per launch of `kernel` from the committed ncu summaries
+    (profiles/*.md rows "| kernel | source.cu | sha256_16 | bytes |"), or
+    None when the kernel's source changed since the capture."""
+    import glob
     import hashlib
-    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
-    if not os.path.exists(p):
-        return None
-    with open(p) as f:
-        d = json.load(f)
-    ent = d.get(kernel)
-    if not ent:
-        return None
-    src = os.path.join(ROOT, "paper_2510_16721_gb300", "csrc", ent["source"])
-    with open(src, "rb") as f:
-        h = hashlib.sha256(f.read()).hexdigest()[:16]
-    if h != ent.get("source_sha256_16"):
-        return None
-    return ent.get("bytes_per_launch_full")
+    for md in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(md) as f:
+            for line in f:
+                cells = [c.strip() for c in line.strip().strip("|").split("|")]
+                if len(cells) != 4 or cells[0] != kernel or not cells[1].endswith(".cu"):
+                    continue
+                src = os.path.join(ROOT, "paper_2510_16721_gb300", "csrc", cells[1])
+                with open(src, "rb") as s:
+                    h = hashlib.sha256(s.read()).hexdigest()[:16]
+                if h != cells[2]:
+                    return None
+                try:
+                    return float(cells[3])
+                except ValueError:
+                    return None
+    return None
 
 
 def run_ours(args, wl_name):
