@@ -223,6 +223,38 @@ int cfneb_get_work(const cfneb_band *band, double *pairs, double *triples);
  * launch accounting). */
 int cfneb_launches_per_step(const cfneb_band *band, int32_t *launches);
 
+/* ---- evaluation without device allocation --------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot call cudaMalloc: code running while a CUDA graph is captured on its
+ * stream, allocators that own all of a process's device memory (a caching
+ * pool or a fixed arena), services that must not allocate once serving.
+ *
+ * Lennard-Jones energy, forces and virial (FP64, the same kernels and
+ * results as cfneb_evaluate with CFNEB_FP64) of one periodic structure of
+ * n_atoms <= CFNEB_NOALLOC_MAX_ATOMS atoms.  Scratch memory is one
+ * file-scope device array of about 8.5 MB, present on every GPU that loads
+ * the library until the process exits; nothing is allocated or freed.
+ *   d_positions  DEVICE pointer, n_atoms x 3 Cartesian positions (caller owned)
+ *   cell         HOST pointer, 9 doubles, rows = lattice vectors
+ *   eps, sigma, rc, shift_energy: as in cfneb_potential
+ *   d_energy     DEVICE pointer to 1 double, or NULL
+ *   d_forces     DEVICE pointer to n_atoms x 3 doubles, or NULL
+ *   d_virial     DEVICE pointer to 9 doubles, or NULL
+ *   cuda_stream  the stream the work is queued on (NULL = legacy default)
+ * Returns without waiting; the outputs are valid once the stream reaches
+ * this point.  n_atoms above the maximum, a NULL position or cell pointer,
+ * or a singular cell return CFNEB_ERR_INVALID_ARG before any GPU work.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Every
+ * call shares the one array and leaves its contents behind (the counts that
+ * must start at zero are cleared by each call), so calls that overlap on the
+ * GPU -- other streams, or unsynchronised host threads -- race. */
+#define CFNEB_NOALLOC_MAX_ATOMS 32768
+int cfneb_lj_evaluate_noalloc(const double *d_positions, int32_t n_atoms, const double *cell,
+                              double eps, double sigma, double rc, int32_t shift_energy,
+                              double *d_energy, double *d_forces, double *d_virial,
+                              void *cuda_stream);
+
 /* Human-readable name of a status code. */
 const char *cfneb_status_string(int status);
 

@@ -43,7 +43,7 @@ EXPORTS = [
     "cfneb_insert_image", "cfneb_delete_image", "cfneb_get_path", "cfneb_get_state",
     "cfneb_destroy_band", "cfneb_evaluate", "cfneb_profile", "cfneb_profile_read",
     "cfneb_kernel_count", "cfneb_kernel_name", "cfneb_launches_per_step",
-    "cfneb_status_string", "cfneb_get_work",
+    "cfneb_status_string", "cfneb_get_work", "cfneb_lj_evaluate_noalloc",
 ]
 
 
@@ -113,6 +113,8 @@ def lib():
             "cfneb_launches_per_step": ([vp, P(i32)], ctypes.c_int),
             "cfneb_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "cfneb_get_work": ([vp, dp, dp], ctypes.c_int),
+            "cfneb_lj_evaluate_noalloc": ([vp, i32, dp, dbl, dbl, dbl, i32, vp, vp, vp, vp],
+                                          ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -304,6 +306,19 @@ def create_band(initial, final, n_images, potential, cell_filter=None, options=N
     _check(st, "cfneb_create_band")
     n_max = max(int(n_images), int(opt.n_max))
     return Band(h.value, A.n_atoms, n_max)
+
+
+NOALLOC_MAX_ATOMS = 32768
+
+
+def lj_evaluate_noalloc(d_positions, n_atoms, cell, eps, sigma, rc, shift_energy, d_energy,
+                        d_forces, d_virial, stream=None):
+    """cfneb_lj_evaluate_noalloc: device pointers (ints) in and out, host cell."""
+    c = np.ascontiguousarray(cell, dtype=np.float64).reshape(9)
+    return lib().cfneb_lj_evaluate_noalloc(d_positions, int(n_atoms), _dptr(c), float(eps),
+                                           float(sigma), float(rc), int(shift_energy),
+                                           d_energy, d_forces, d_virial,
+                                           _stream_handle(stream))
 
 
 def evaluate(structures, potential, precision=FP64, stream=None):

@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcfneb.so")
-SOURCES = ["cell.cu", "lj.cu", "tersoff.cu", "band.cu", "energy64.cu", "engine.cu"]
+SOURCES = ["cell.cu", "lj.cu", "tersoff.cu", "band.cu", "energy64.cu", "engine.cu",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]
