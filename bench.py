@@ -38,6 +38,9 @@ WORKLOADS = {
                                               precision="mixed", n_max=24),
     "tersoff_graphite_hexdiamond_576": dict(kind="tersoff", reps=(6, 4, 3), n_images=9,
                                             precision="fp64", n_max=9),
+    # 64 LJ vacancy / divacancy bands, 256..32768 atoms log-uniform, 5..15
+    # images, +-2% end strain, cell filter on, one batch (one launch per kernel)
+    "lj_batch64": dict(kind="lj_batch", n_bands=64, precision="mixed"),
 }
 CPU_SAMPLE_REPS = (6, 4, 3)   # the 576-atom tile the large band is built from
 
@@ -376,6 +379,175 @@ def run_ours(args, wl_name):
     return 0
 
 
+def make_lj_band(g, bc, precision, stream):
+    R0, h0, R1, h1 = bc["endpoints"]
+    opt = g.default_options()
+    opt.k_spring = bc["k"]
+    opt.climb = 1
+    opt.precision = precision
+    opt.dt = bc["dt"]
+    opt.dt_max = 10 * bc["dt"]
+    opt.maxstep = 0.2
+    opt.n_max = bc["n_images"]
+    opt.bin_scale = 0.0
+    cf = g.CellFilter(1, g.ROTFREE_B, 0.0, 0.0)
+    return g.create_band((R0, h0), (R1, h1), bc["n_images"], g.lj_potential(), cf, opt,
+                         stream=stream)
+
+
+def cpu_oracle_lj_rate(bcs, seconds):
+    """Oracle atom·steps/s on the smallest band of the batch (one thread)."""
+    import oracle
+    bc = min(bcs, key=lambda c: len(c["endpoints"][0]))
+    R0, h0, R1, h1 = bc["endpoints"]
+    band = oracle.make_band(oracle.LJ(), R0, h0, R1, h1, bc["n_images"], k=bc["k"], climb=True,
+                            cell_filter=True, fire=oracle.Fire(dt=bc["dt"]))
+    n_done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds or n_done == 0:
+        band.step(1)
+        n_done += 1
+    el = time.perf_counter() - t0
+    n, m = len(R0), bc["n_images"] - 2
+    return {"value": n * m * n_done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "smallest band of the batch (%d atoms, %d moving images), %d FP64 steps in "
+                      "%.1f s, one thread" % (n, m, n_done, el)}
+
+
+def run_batch(args):
+    import numpy as np
+    import torch
+    import cfneb_inputs as ci
+    ws, rank, local = dist_info()
+    dist = None
+    if ws > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl")
+        dist = td
+    torch.cuda.set_device(local)
+    import paper_2510_16721_gb300 as g
+    g.build()
+    wl = WORKLOADS[args.workload]
+    bcs = ci.lj_batch(seed=4 + rank, n_bands=wl["n_bands"])
+    stream = torch.cuda.current_stream()
+    work = sum(len(c["endpoints"][0]) * (c["n_images"] - 2) for c in bcs)
+    t_create = time.perf_counter()
+    bands = [make_lj_band(g, c, g.MIXED, stream) for c in bcs]
+    bt = g.Batch(g.MIXED, stream=stream)
+    for b in bands:
+        bt.add(b)
+    t_create = time.perf_counter() - t_create
+    bt.autotune(4)
+    bt.step(args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = time_steps(torch, bt, stream, args.steps, dist)
+    clk = clocks.stop()
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * work * args.steps / (ms / 1e3)
+    st = bt.status()
+    assert all(s["status"] == 0 for s in st)
+    # per-kernel profile
+    kp = max(5, min(args.steps, 20))
+    bt.profile(True)
+    bt.step(kp)
+    prof = bt.profile_read()
+    bt.profile(False)
+    total = sum(v[0] for v in prof.values())
+    dom = max(prof.items(), key=lambda kv: kv[1][0])[0]
+    pairs = sum(b.get_work()[0] for b in bands)
+    dom_ms = prof[dom][0] / max(1, prof[dom][1])
+    w = dict(pairs=pairs, triples=0.0, atoms=work, dof=sum(
+        (len(c["endpoints"][0]) + 3) * 3 * (c["n_images"] - 2) for c in bcs), ts=4)
+    peaks, peak_src = measured_peaks()
+    if dom in FLOP_MODELS:
+        sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
+        ach = FLOP_MODELS[dom](w) / (dom_ms * 1e-3) / 1e12
+        peak = fp32_peak_tflops(sm_max)
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x %.0f MHz" % sm_max}
+    else:
+        byts = BYTE_MODELS[dom](w) if dom in BYTE_MODELS else None
+        ach = byts / (dom_ms * 1e-3) / 1e9 if byts else None
+        peak = peaks["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak if ach else None,
+                "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % peak_src}
+    roof.update({"kernel": dom, "kernel_ms": dom_ms, "share": prof[dom][0] / total,
+                 "traffic": traffic_for(dom), "work_per_launch": {"pairs": pairs, "atoms": work}})
+    launches = None
+    bt.destroy()
+    for b in bands:
+        b.destroy()
+    # plain FP64, one band per launch: every band stepped on its own
+    k64 = max(3, args.steps // 5)
+    b64 = [make_lj_band(g, c, g.FP64, stream) for c in bcs]
+    for b in b64:
+        b.step(2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for b in b64:
+        b.step(k64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    fp64 = {"value": work * k64 / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64 / k64,
+            "steps": k64, "mode": "FP64, one band per launch (each band's own graph)"}
+    for b in b64:
+        b.destroy()
+    # end to end: create from host arrays, K batch steps, every path read back
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b2 = [make_lj_band(g, c, g.MIXED, stream) for c in bcs]
+    bt2 = g.Batch(g.MIXED, stream=stream)
+    for b in b2:
+        bt2.add(b)
+    bt2.step(args.steps)
+    d2h = 0
+    for b in b2:
+        p = b.get_path()
+        d2h += p["positions"].nbytes + p["cells"].nbytes + p["energies"].nbytes + 8
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    h2d = sum(2 * len(c["endpoints"][0]) * 3 * 8 + 18 * 8 for c in bcs)
+    bt2.destroy()
+    for b in b2:
+        b.destroy()
+    e2e = {"value": ws * work * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+           "seconds": e2e_s, "includes": "creation of all bands, K batch steps, all paths read"}
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+        return 0
+    cpu = None if args.no_cpu_baseline else cpu_oracle_lj_rate(bcs, args.cpu_seconds)
+    sizes = [len(c["endpoints"][0]) for c in bcs]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 pair arithmetic, f64 reductions and 3x3 cell work", "data": "synthetic",
+            "config": {"workload": args.workload, "bands": len(bcs), "atoms_min": min(sizes),
+                       "atoms_max": max(sizes), "atom_images_per_step": work,
+                       "precision": "mixed", "potential": "LJ rc 2.5",
+                       "cell_filter": "rotation-free (B)", "bin_width": "autotuned per class",
+                       "l2": "working set > 129 MB L2, no flush",
+                       "graph": "one CUDA graph per batch step",
+                       "parallelism": "replicas x%d" % ws},
+            "roofline": roof, "kernel_share": {k: round(v[0] / total, 4)
+                                               for k, v in prof.items() if v[1]},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 16 * args.steps, "clocks": clk,
+            "fp64_plain": fp64, "create_s": t_create}
+    print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -391,7 +563,11 @@ def main():
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
+        if WORKLOADS[args.workload]["kind"] == "lj_batch":
+            args.workload = "tersoff_graphite_hexdiamond_98304"
         return run_reference(args, args.workload)
+    if WORKLOADS[args.workload]["kind"] == "lj_batch":
+        return run_batch(args)
     return run_ours(args, args.workload)
 
 

@@ -200,6 +200,112 @@ int cfneb_evaluate(const cfneb_structure *structures, int32_t count,
                    const cfneb_potential *potential, int32_t precision, void *cuda_stream,
                    double *energies, double *forces, double *virials);
 
+/* ---- batches: many bands, one launch per kernel --------------------------
+ * A batch steps all its member bands together: every kernel of a step is
+ * launched once over the tiles of all members (uneven atom and image counts
+ * mixed), the whole step is one captured CUDA graph, and each band keeps its
+ * own FIRE state, convergence test and refinement.  Results of a band do not
+ * depend on the other members (reductions use fixed per-band slots).
+ * Members must share the precision; LJ and Tersoff bands may be mixed.
+ * While a band is a member its work is queued on the batch's stream; the
+ * band calls above stay valid on it.  The batch does not own its bands. */
+typedef struct cfneb_batch cfneb_batch;
+
+/* Create an empty batch.  budget_bytes bounds the summed device memory of
+ * the members (0 = unbounded).  cuda_stream as in cfneb_create_band. */
+int cfneb_batch_create(int32_t precision, uint64_t budget_bytes, void *cuda_stream,
+                       cfneb_batch **out);
+
+/* Add a band (CFNEB_ERR_HBM_BUDGET if it does not fit the budget,
+ * CFNEB_ERR_INVALID_ARG if the precision differs or it is already in a
+ * batch). */
+int cfneb_batch_add(cfneb_batch *batch, cfneb_band *band);
+
+/* Remove a band; it returns to its own stream.  The band is not destroyed. */
+int cfneb_batch_remove(cfneb_batch *batch, cfneb_band *band);
+
+/* n_steps steps of every member (members that converged under the last
+ * cfneb_batch_relax or spent their move budget do not move). */
+int cfneb_batch_step(cfneb_batch *batch, int32_t n_steps);
+
+/* Relax every member until its fmax < tol or it made max_steps moves
+ * (counted per band from this call).  *n_converged = members converged.
+ * Synchronises every few steps. */
+int cfneb_batch_relax(cfneb_batch *batch, double fmax, int64_t max_steps, int32_t *n_converged);
+
+/* Per-member state, members in the order they were added (removed ones
+ * skipped): moves taken, converged flag, fmax of the last step, status
+ * (0 or a CFNEB_ERR code).  Arrays of length >= the member count; any may
+ * be NULL.  *count = member count.  Synchronises. */
+int cfneb_batch_status(cfneb_batch *batch, int32_t *count, int64_t *steps, int32_t *converged,
+                       double *fmax, int32_t *status);
+
+/* Device memory of a band, and of a batch's members against its budget. */
+int cfneb_band_bytes(const cfneb_band *band, uint64_t *bytes);
+int cfneb_batch_bytes(const cfneb_batch *batch, uint64_t *used, uint64_t *budget);
+
+/* Per-kernel CUDA-event timing of batch steps (as cfneb_profile). */
+int cfneb_batch_profile(cfneb_batch *batch, int32_t enable);
+int cfneb_batch_profile_read(cfneb_batch *batch, int32_t kernel_id, double *total_ms,
+                             int64_t *launches);
+
+/* Release the batch (members are removed, not destroyed). */
+int cfneb_batch_destroy(cfneb_batch *batch);
+
+/* ---- serving: continuous batching of band requests ------------------------
+ * A server keeps one batch on the GPU.  Requests (two endpoints and band
+ * options) are submitted with an arrival time on the server's clock (seconds
+ * since cfneb_server_create).  cfneb_server_run admits arrived requests in
+ * arrival order as the device-memory budget allows (a request that does not
+ * fit waits), steps every resident band together, and retires a band as soon
+ * as it converges (fmax < its tolerance), spends its move budget or fails;
+ * retired bands free their memory for the next admissions, so new bands join
+ * while others are mid-relaxation.  Latency = retirement - arrival. */
+typedef struct cfneb_server cfneb_server;
+
+int cfneb_server_create(int32_t precision, uint64_t budget_bytes, void *cuda_stream,
+                        cfneb_server **out);
+
+/* Queue a request; inputs are copied.  *id receives its id (0, 1, ...). */
+int cfneb_server_submit(cfneb_server *server, const cfneb_structure *initial,
+                        const cfneb_structure *final, int32_t n_images,
+                        const cfneb_potential *potential, const cfneb_cell_filter *cell_filter,
+                        const cfneb_options *options, double fmax, int64_t max_steps,
+                        double arrival_s, int64_t *id);
+
+/* Serve until every submitted request is retired or the server clock passes
+ * until_s.  Returns CFNEB_OK, or CFNEB_NOT_CONVERGED if requests remain. */
+int cfneb_server_run(cfneb_server *server, double until_s);
+
+/* Result of a request: *state 0 queued, 1 running, 2 retired; latency in
+ * seconds; moves; converged flag; barrier = max E - E(initial) from FP64
+ * energies; status of the band (0 or a CFNEB_ERR code). */
+int cfneb_server_result(cfneb_server *server, int64_t id, int32_t *state, double *latency_s,
+                        int64_t *steps, int32_t *converged, double *barrier, int32_t *status);
+
+/* Latency percentiles over retired requests, retired count, and the served
+ * throughput in atom-steps/s (moving images x atoms x moves of every
+ * retired request, over the server clock). */
+int cfneb_server_stats(cfneb_server *server, double *p50_s, double *p99_s, int64_t *retired,
+                       double *atom_steps_per_s);
+
+int cfneb_server_destroy(cfneb_server *server);
+
+/* ---- autotuning of the cell-list bin shape ------------------------------
+ * Times `steps` force evaluations of the band (no moves: the state is left
+ * as it was) for each candidate bin width (0.5, 0.75, 1.0, 1.3 x cutoff),
+ * keeps the fastest for the band and caches it for its class (potential,
+ * precision, atom count and density buckets).  Bands created later with
+ * options.bin_scale = 0 in a cached class start with the cached width.
+ * Bands created with bin_scale = 0 reserve bins for the finest candidate;
+ * untuned classes start at 0.5 (LJ) or 1.0 (Tersoff).
+ * *best_scale receives the chosen width / cutoff.  Synchronises. */
+int cfneb_autotune(cfneb_band *band, int32_t steps, double *best_scale);
+
+/* Autotune one member per class and apply the result to every member of
+ * that class.  Synchronises. */
+int cfneb_batch_autotune(cfneb_batch *batch, int32_t steps);
+
 /* Per-kernel timing.  With profiling on, each kernel launch of
  * cfneb_step is bracketed by CUDA events on the band's internal stream
  * (the stream the kernels run on; graphs are not used while profiling).

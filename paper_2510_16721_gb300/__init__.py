@@ -44,6 +44,11 @@ EXPORTS = [
     "cfneb_destroy_band", "cfneb_evaluate", "cfneb_profile", "cfneb_profile_read",
     "cfneb_kernel_count", "cfneb_kernel_name", "cfneb_launches_per_step",
     "cfneb_status_string", "cfneb_get_work", "cfneb_lj_evaluate_noalloc",
+    "cfneb_band_bytes", "cfneb_batch_create", "cfneb_batch_add", "cfneb_batch_remove",
+    "cfneb_batch_step", "cfneb_batch_relax", "cfneb_batch_status", "cfneb_batch_bytes",
+    "cfneb_batch_profile", "cfneb_batch_profile_read", "cfneb_batch_destroy",
+    "cfneb_autotune", "cfneb_batch_autotune", "cfneb_server_create", "cfneb_server_submit",
+    "cfneb_server_run", "cfneb_server_result", "cfneb_server_stats", "cfneb_server_destroy",
 ]
 
 
@@ -115,6 +120,28 @@ def lib():
             "cfneb_get_work": ([vp, dp, dp], ctypes.c_int),
             "cfneb_lj_evaluate_noalloc": ([vp, i32, dp, dbl, dbl, dbl, i32, vp, vp, vp, vp],
                                           ctypes.c_int),
+            "cfneb_band_bytes": ([vp, P(ctypes.c_uint64)], ctypes.c_int),
+            "cfneb_batch_create": ([i32, ctypes.c_uint64, vp, P(vp)], ctypes.c_int),
+            "cfneb_batch_add": ([vp, vp], ctypes.c_int),
+            "cfneb_batch_remove": ([vp, vp], ctypes.c_int),
+            "cfneb_batch_step": ([vp, i32], ctypes.c_int),
+            "cfneb_batch_relax": ([vp, dbl, i64, P(i32)], ctypes.c_int),
+            "cfneb_batch_status": ([vp, P(i32), P(i64), P(i32), dp, P(i32)], ctypes.c_int),
+            "cfneb_batch_bytes": ([vp, P(ctypes.c_uint64), P(ctypes.c_uint64)], ctypes.c_int),
+            "cfneb_batch_profile": ([vp, i32], ctypes.c_int),
+            "cfneb_batch_profile_read": ([vp, i32, dp, P(i64)], ctypes.c_int),
+            "cfneb_batch_destroy": ([vp], ctypes.c_int),
+            "cfneb_autotune": ([vp, i32, dp], ctypes.c_int),
+            "cfneb_batch_autotune": ([vp, i32], ctypes.c_int),
+            "cfneb_server_create": ([i32, ctypes.c_uint64, vp, P(vp)], ctypes.c_int),
+            "cfneb_server_submit": ([vp, P(Structure), P(Structure), i32, P(Potential),
+                                     P(CellFilter), P(Options), dbl, i64, dbl, P(i64)],
+                                    ctypes.c_int),
+            "cfneb_server_run": ([vp, dbl], ctypes.c_int),
+            "cfneb_server_result": ([vp, i64, P(i32), dp, P(i64), P(i32), dp, P(i32)],
+                                    ctypes.c_int),
+            "cfneb_server_stats": ([vp, dp, dp, P(i64), dp], ctypes.c_int),
+            "cfneb_server_destroy": ([vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -268,6 +295,17 @@ class Band:
         _check(lib().cfneb_get_work(self._h, ctypes.byref(p), ctypes.byref(t)), "cfneb_get_work")
         return float(p.value), float(t.value)
 
+    def autotune(self, steps=5):
+        """cfneb_autotune: returns the chosen bin width / cutoff."""
+        best = ctypes.c_double(0.0)
+        _check(lib().cfneb_autotune(self._h, int(steps), ctypes.byref(best)), "cfneb_autotune")
+        return float(best.value)
+
+    def bytes(self):
+        b = ctypes.c_uint64(0)
+        _check(lib().cfneb_band_bytes(self._h, ctypes.byref(b)), "cfneb_band_bytes")
+        return int(b.value)
+
     def launches_per_step(self):
         n = ctypes.c_int32(0)
         _check(lib().cfneb_launches_per_step(self._h, ctypes.byref(n)), "cfneb_launches_per_step")
@@ -306,6 +344,154 @@ def create_band(initial, final, n_images, potential, cell_filter=None, options=N
     _check(st, "cfneb_create_band")
     n_max = max(int(n_images), int(opt.n_max))
     return Band(h.value, A.n_atoms, n_max)
+
+
+class Batch:
+    """Many bands stepped together (wraps cfneb_batch*); does not own them."""
+
+    def __init__(self, precision=FP64, budget_bytes=0, stream=None):
+        h = ctypes.c_void_p(0)
+        _check(lib().cfneb_batch_create(int(precision), int(budget_bytes),
+                                        _stream_handle(stream), ctypes.byref(h)),
+               "cfneb_batch_create")
+        self._h = h
+        self.members = []
+
+    def add(self, band):
+        st = lib().cfneb_batch_add(self._h, band.handle)
+        _check(st, "cfneb_batch_add")
+        self.members.append(band)
+        return st
+
+    def try_add(self, band):
+        """Add if the budget allows; returns True on success."""
+        st = lib().cfneb_batch_add(self._h, band.handle)
+        if st == ERR_HBM_BUDGET:
+            return False
+        _check(st, "cfneb_batch_add")
+        self.members.append(band)
+        return True
+
+    def remove(self, band):
+        _check(lib().cfneb_batch_remove(self._h, band.handle), "cfneb_batch_remove")
+        self.members.remove(band)
+
+    def step(self, n_steps=1):
+        return _check(lib().cfneb_batch_step(self._h, int(n_steps)), "cfneb_batch_step")
+
+    def relax(self, fmax, max_steps):
+        nc = ctypes.c_int32(0)
+        st = lib().cfneb_batch_relax(self._h, float(fmax), int(max_steps), ctypes.byref(nc))
+        _check(st, "cfneb_batch_relax", allow=(OK, NOT_CONVERGED))
+        return int(nc.value)
+
+    def status(self):
+        n = len(self.members)
+        steps = (ctypes.c_int64 * max(n, 1))()
+        conv = (ctypes.c_int32 * max(n, 1))()
+        fm = np.zeros(max(n, 1))
+        stt = (ctypes.c_int32 * max(n, 1))()
+        cnt = ctypes.c_int32(0)
+        _check(lib().cfneb_batch_status(self._h, ctypes.byref(cnt), steps, conv, _dptr(fm), stt),
+               "cfneb_batch_status")
+        return [dict(steps=int(steps[i]), converged=bool(conv[i]), fmax=float(fm[i]),
+                     status=int(stt[i])) for i in range(cnt.value)]
+
+    def autotune(self, steps=5):
+        return _check(lib().cfneb_batch_autotune(self._h, int(steps)), "cfneb_batch_autotune")
+
+    def bytes(self):
+        u = ctypes.c_uint64(0)
+        b = ctypes.c_uint64(0)
+        _check(lib().cfneb_batch_bytes(self._h, ctypes.byref(u), ctypes.byref(b)),
+               "cfneb_batch_bytes")
+        return int(u.value), int(b.value)
+
+    def profile(self, enable=True):
+        return _check(lib().cfneb_batch_profile(self._h, int(bool(enable))), "cfneb_batch_profile")
+
+    def profile_read(self):
+        out = {}
+        for k in range(lib().cfneb_kernel_count()):
+            ms = ctypes.c_double(0.0)
+            cnt = ctypes.c_int64(0)
+            _check(lib().cfneb_batch_profile_read(self._h, k, ctypes.byref(ms),
+                                                  ctypes.byref(cnt)), "cfneb_batch_profile_read")
+            out[lib().cfneb_kernel_name(k).decode()] = (float(ms.value), int(cnt.value))
+        return out
+
+    def destroy(self):
+        if self._h is not None and self._h.value:
+            _check(lib().cfneb_batch_destroy(self._h), "cfneb_batch_destroy")
+            self._h = ctypes.c_void_p(0)
+            self.members = []
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop (wraps cfneb_server*)."""
+
+    def __init__(self, precision=FP64, budget_bytes=0, stream=None):
+        h = ctypes.c_void_p(0)
+        _check(lib().cfneb_server_create(int(precision), int(budget_bytes),
+                                         _stream_handle(stream), ctypes.byref(h)),
+               "cfneb_server_create")
+        self._h = h
+
+    def submit(self, initial, final, n_images, potential, cell_filter, options, fmax, max_steps,
+               arrival_s):
+        keep = []
+        A = make_structure(initial[0], initial[1], keep)
+        B = make_structure(final[0], final[1], keep)
+        rid = ctypes.c_int64(-1)
+        _check(lib().cfneb_server_submit(self._h, ctypes.byref(A), ctypes.byref(B),
+                                         int(n_images), ctypes.byref(potential),
+                                         ctypes.byref(cell_filter), ctypes.byref(options),
+                                         float(fmax), int(max_steps), float(arrival_s),
+                                         ctypes.byref(rid)), "cfneb_server_submit")
+        return int(rid.value)
+
+    def run(self, until_s):
+        st = lib().cfneb_server_run(self._h, float(until_s))
+        _check(st, "cfneb_server_run", allow=(OK, NOT_CONVERGED))
+        return st == OK
+
+    def result(self, rid):
+        state, conv, stt = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+        lat, bar = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        steps = ctypes.c_int64(0)
+        _check(lib().cfneb_server_result(self._h, int(rid), ctypes.byref(state),
+                                         ctypes.byref(lat), ctypes.byref(steps),
+                                         ctypes.byref(conv), ctypes.byref(bar),
+                                         ctypes.byref(stt)), "cfneb_server_result")
+        return dict(state=int(state.value), latency_s=float(lat.value), steps=int(steps.value),
+                    converged=bool(conv.value), barrier=float(bar.value),
+                    status=int(stt.value))
+
+    def stats(self):
+        p50, p99, thr = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_double(0.0)
+        n = ctypes.c_int64(0)
+        _check(lib().cfneb_server_stats(self._h, ctypes.byref(p50), ctypes.byref(p99),
+                                        ctypes.byref(n), ctypes.byref(thr)),
+               "cfneb_server_stats")
+        return dict(p50_s=float(p50.value), p99_s=float(p99.value), retired=int(n.value),
+                    atom_steps_per_s=float(thr.value))
+
+    def destroy(self):
+        if self._h is not None and self._h.value:
+            _check(lib().cfneb_server_destroy(self._h), "cfneb_server_destroy")
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 NOALLOC_MAX_ATOMS = 32768

@@ -422,7 +422,26 @@ __global__ void k_setup(const double *R0, const double *R1, const double *noise,
     }
 }
 
+// per band: moves, converged, status, fmax, climbing image, N (batch polling)
+__global__ void k_gather_status(BandDev *bands, int nb, double *out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nb) return;
+    const BandParams *bp = bands[k].bp;
+    double *o = out + 6 * (size_t)k;
+    o[0] = (double)bp->steps;
+    o[1] = (double)bp->converged;
+    o[2] = (double)bp->status;
+    o[3] = bp->fmax;
+    o[4] = (double)bp->ci;
+    o[5] = (double)bp->N;
+}
+
 // ---- launchers -------------------------------------------------------------
+
+void launch_gather_status(BandDev *bands, int nb, double *out, cudaStream_t s) {
+    if (nb <= 0) return;
+    k_gather_status<<<(nb + 127) / 128, 128, 0, s>>>(bands, nb, out);
+}
 
 template <typename T>
 void launch_setup(const double *R0, const double *R1, const double *noise, int n, int N,

@@ -235,6 +235,7 @@ template <typename T>
 void launch_cartesian(const ImgRef *imgs, int count, int max_n, BandDev *bands, cudaStream_t s);
 template <typename T>
 void launch_midpoint(BandDev *band, int img, int rows, cudaStream_t s);
+void launch_gather_status(BandDev *bands, int nb, double *out, cudaStream_t s);
 template <typename T>
 void launch_setup(const double *R0, const double *R1, const double *noise, int n, int N,
                   BandDev *band, cudaStream_t s, const double *h1);

@@ -12,10 +12,16 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <deque>
+#include <thread>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/cfneb.h"
@@ -53,12 +59,27 @@ const char *kKernelNames[K_COUNT] = {
 const double kTersoff1988C[11] = {1393.6, 346.74, 3.4879, 2.2119, 1.5724e-7, 0.72751,
                                   38049.0, 4.3484, -0.57058, 1.95, 0.15};
 
-struct DevBuf {
-    void *p = nullptr;
-    size_t bytes = 0;
-};
+// bin width candidates (x cutoff) of the autotuner; the first is the finest
+const double kTuneScales[4] = {0.5, 0.75, 1.0, 1.3};
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, double> g_tune;  // class -> bin width / rc
+
+// untuned default per potential (measured on GB300: LJ at FCC density is
+// fastest with half-cutoff bins, carbon Tersoff with cutoff-wide bins)
+double tuned_scale(const std::tuple<int, int, int, int> &key) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+    return std::get<0>(key) == CFNEB_LJ ? 0.5 : 1.0;
+}
 
 }  // namespace
+
+struct cfneb_batch;
+namespace {
+void batch_mark_dirty(cfneb_batch *bt);
+}
 
 // One band: its device buffers and host-side configuration.
 struct cfneb_band {
@@ -73,6 +94,9 @@ struct cfneb_band {
     size_t bytes = 0;
     long long last_change = 0;
     long long last_check = -1;
+    long long move_limit = 1LL << 62;  // host copy of BandParams::move_limit
+    double rc = 0.0;             // potential cutoff
+    std::tuple<int, int, int, int> tune_key{};
     double ftol = -1.0;
     // stream ordering
     cudaStream_t user = nullptr, s = nullptr;
@@ -95,6 +119,9 @@ struct cfneb_band {
     std::vector<cudaEvent_t> prof_ev;
     // pinned host mirror of BandParams
     BandParams *h_bp = nullptr;
+    // batch membership: while a member, s is the batch's stream
+    cfneb_batch *batch = nullptr;
+    cudaStream_t own_s = nullptr;
 };
 
 namespace {
@@ -115,6 +142,7 @@ void *dalloc(cfneb_band *b, size_t bytes) {
 void free_band(cfneb_band *b) {
     if (!b) return;
     if (b->s) cudaStreamSynchronize(b->s);
+    if (b->own_s) b->s = b->own_s;
     for (void *p : b->allocs) cudaFree(p);
     b->allocs.clear();
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
@@ -179,119 +207,191 @@ void build_tables(cfneb_band *b) {
                            cudaMemcpyHostToDevice, b->s));
     CK(cudaStreamSynchronize(b->s));  // host vectors go out of scope
     b->graph_dirty = true;
+    if (b->batch) batch_mark_dirty(b->batch);
 }
 
 // ---- kernel sequences ------------------------------------------------------
 
+// Kernel launches of one step (or one evaluation) over a set of images, possibly
+// of many bands: the tables index into an array of BandDev.
+struct LaunchSet {
+    BandDev *d_bands = nullptr;
+    cudaStream_t s = nullptr;
+    const ImgRef *imgs = nullptr;
+    int nimg = 0;
+    const Tile *atiles = nullptr;        // atom tiles of every listed image
+    int n_atiles = 0;
+    const Tile *atiles_lj = nullptr;     // the LJ bands' atom tiles
+    int n_lj = 0;
+    const Tile *atiles_ters = nullptr;   // the Tersoff bands' atom tiles
+    int n_ters = 0;
+    const Tile *rtiles = nullptr;        // row tiles
+    int n_rtiles = 0;
+    const int *band_ids = nullptr;
+    int nbands = 0;
+    int max_bins = 0;                    // largest nbins_cap among the bands
+};
+
+// optional CUDA-event bracketing of every launch (profiling)
 struct Launcher {
-    cfneb_band *b;
+    bool prof = false;
+    std::vector<cudaEvent_t> *ev = nullptr;
+    cudaStream_t s = nullptr;
     int k = 0;
-    void pre(int id) {
-        if (b->prof) CK(cudaEventRecord(b->prof_ev[2 * k], b->s));
-        (void)id;
+    std::vector<int> ids;
+    void pre(int) {
+        if (prof) CK(cudaEventRecord((*ev)[2 * k], s));
     }
     void post(int id) {
-        if (b->prof) {
-            CK(cudaEventRecord(b->prof_ev[2 * k + 1], b->s));
+        if (prof) {
+            CK(cudaEventRecord((*ev)[2 * k + 1], s));
             ids.push_back(id);
             ++k;
         }
     }
-    std::vector<int> ids;
 };
+
+template <typename T>
+void enqueue_eval_set(const LaunchSet &ls, Launcher &L, bool forces = true) {
+    BandDev *d = ls.d_bands;
+    cudaStream_t s = ls.s;
+    L.pre(K_MAPBACK); launch_mapback<T>(ls.imgs, ls.nimg, d, s); L.post(K_MAPBACK);
+    L.pre(K_BIN_ASSIGN); launch_bin_assign<T>(ls.atiles, ls.n_atiles, d, s); L.post(K_BIN_ASSIGN);
+    L.pre(K_BIN_TILESUM); launch_bin_scan(ls.imgs, ls.nimg, ls.max_bins, d, s, 0); L.post(K_BIN_TILESUM);
+    L.pre(K_BIN_TILESCAN); launch_bin_scan(ls.imgs, ls.nimg, ls.max_bins, d, s, 1); L.post(K_BIN_TILESCAN);
+    L.pre(K_BIN_SCANFILL); launch_bin_scan(ls.imgs, ls.nimg, ls.max_bins, d, s, 2); L.post(K_BIN_SCANFILL);
+    L.pre(K_BIN_SCATTER); launch_bin_scatter(ls.atiles, ls.n_atiles, d, s); L.post(K_BIN_SCATTER);
+    L.pre(K_BIN_ORDER); launch_bin_order<T>(ls.imgs, ls.nimg, ls.max_bins, d, s); L.post(K_BIN_ORDER);
+    if (!forces) {
+        launch_energy64<T>(ls.atiles, ls.n_atiles, ls.imgs, ls.nimg, d, s);
+        return;
+    }
+    if (ls.n_lj) {
+        L.pre(K_LJ); launch_lj<T>(ls.atiles_lj, ls.n_lj, d, s); L.post(K_LJ);
+    }
+    if (ls.n_ters) {
+        L.pre(K_TERS_PARTIALS); launch_tersoff_partials<T>(ls.atiles_ters, ls.n_ters, d, s);
+        L.post(K_TERS_PARTIALS);
+        L.pre(K_TERS_GATHER); launch_tersoff_gather<T>(ls.atiles_ters, ls.n_ters, d, s);
+        L.post(K_TERS_GATHER);
+    }
+    L.pre(K_IMAGE_FINALIZE); launch_image_finalize<T>(ls.imgs, ls.nimg, d, s); L.post(K_IMAGE_FINALIZE);
+}
+
+template <typename T>
+void enqueue_step_set(const LaunchSet &ls, Launcher &L) {
+    BandDev *d = ls.d_bands;
+    cudaStream_t s = ls.s;
+    enqueue_eval_set<T>(ls, L);
+    L.pre(K_BAND_DOTS); launch_band_dots<T>(ls.rtiles, ls.n_rtiles, d, s); L.post(K_BAND_DOTS);
+    L.pre(K_DOTS_REDUCE); launch_dots_reduce(ls.imgs, ls.nimg, d, s); L.post(K_DOTS_REDUCE);
+    L.pre(K_NEB_COEF); launch_neb_coef(ls.band_ids, ls.nbands, d, s); L.post(K_NEB_COEF);
+    L.pre(K_NEB_FORCE); launch_neb_force<T>(ls.rtiles, ls.n_rtiles, d, s); L.post(K_NEB_FORCE);
+    L.pre(K_FIRE_SCALARS); launch_fire_scalars(ls.band_ids, ls.nbands, d, s); L.post(K_FIRE_SCALARS);
+    L.pre(K_FIRE_UPDATE); launch_fire_update<T>(ls.rtiles, ls.n_rtiles, d, s);
+    L.post(K_FIRE_UPDATE);
+}
+
+int launches_in_set(const LaunchSet &ls) {
+    return 7 + (ls.n_lj ? 1 : 0) + (ls.n_ters ? 2 : 0) + 1 + 6;
+}
+
+LaunchSet band_set(cfneb_band *b, const ImgRef *imgs, int nimg, const Tile *atiles, int nat) {
+    LaunchSet ls;
+    ls.d_bands = b->d_self;
+    ls.s = b->s;
+    ls.imgs = imgs;
+    ls.nimg = nimg;
+    ls.atiles = atiles;
+    ls.n_atiles = nat;
+    if (b->kind == CFNEB_LJ) {
+        ls.atiles_lj = atiles;
+        ls.n_lj = nat;
+    } else {
+        ls.atiles_ters = atiles;
+        ls.n_ters = nat;
+    }
+    ls.rtiles = b->d_rtiles;
+    ls.n_rtiles = b->n_rtiles;
+    ls.band_ids = b->d_band_ids;
+    ls.nbands = 1;
+    ls.max_bins = b->dv.nbins_cap;
+    return ls;
+}
+
+LaunchSet band_step_set(cfneb_band *b) {
+    return band_set(b, b->d_imgs, b->n_imgs, b->d_atiles, b->n_atiles);
+}
 
 template <typename T>
 void enqueue_eval(cfneb_band *b, Launcher &L, const ImgRef *imgs, int nimg, const Tile *atiles,
                   int natiles, bool forces = true) {
-    BandDev *d = b->d_self;
-    cudaStream_t s = b->s;
-    L.pre(K_MAPBACK); launch_mapback<T>(imgs, nimg, d, s); L.post(K_MAPBACK);
-    L.pre(K_BIN_ASSIGN); launch_bin_assign<T>(atiles, natiles, d, s); L.post(K_BIN_ASSIGN);
-    const int nbc = b->dv.nbins_cap;
-    L.pre(K_BIN_TILESUM); launch_bin_scan(imgs, nimg, nbc, d, s, 0); L.post(K_BIN_TILESUM);
-    L.pre(K_BIN_TILESCAN); launch_bin_scan(imgs, nimg, nbc, d, s, 1); L.post(K_BIN_TILESCAN);
-    L.pre(K_BIN_SCANFILL); launch_bin_scan(imgs, nimg, nbc, d, s, 2); L.post(K_BIN_SCANFILL);
-    L.pre(K_BIN_SCATTER); launch_bin_scatter(atiles, natiles, d, s); L.post(K_BIN_SCATTER);
-    L.pre(K_BIN_ORDER); launch_bin_order<T>(imgs, nimg, b->dv.nbins_cap, d, s); L.post(K_BIN_ORDER);
-    if (!forces) {
-        launch_energy64<T>(atiles, natiles, imgs, nimg, d, s);
-        return;
-    }
-    if (b->kind == CFNEB_LJ) {
-        L.pre(K_LJ); launch_lj<T>(atiles, natiles, d, s); L.post(K_LJ);
-    } else {
-        L.pre(K_TERS_PARTIALS); launch_tersoff_partials<T>(atiles, natiles, d, s);
-        L.post(K_TERS_PARTIALS);
-        L.pre(K_TERS_GATHER); launch_tersoff_gather<T>(atiles, natiles, d, s);
-        L.post(K_TERS_GATHER);
-    }
-    L.pre(K_IMAGE_FINALIZE); launch_image_finalize<T>(imgs, nimg, d, s); L.post(K_IMAGE_FINALIZE);
-}
-
-template <typename T>
-void enqueue_step(cfneb_band *b, Launcher &L) {
-    BandDev *d = b->d_self;
-    cudaStream_t s = b->s;
-    enqueue_eval<T>(b, L, b->d_imgs, b->n_imgs, b->d_atiles, b->n_atiles);
-    L.pre(K_BAND_DOTS); launch_band_dots<T>(b->d_rtiles, b->n_rtiles, d, s); L.post(K_BAND_DOTS);
-    L.pre(K_DOTS_REDUCE); launch_dots_reduce(b->d_imgs, b->n_imgs, d, s); L.post(K_DOTS_REDUCE);
-    L.pre(K_NEB_COEF); launch_neb_coef(b->d_band_ids, 1, d, s); L.post(K_NEB_COEF);
-    L.pre(K_NEB_FORCE); launch_neb_force<T>(b->d_rtiles, b->n_rtiles, d, s); L.post(K_NEB_FORCE);
-    L.pre(K_FIRE_SCALARS); launch_fire_scalars(b->d_band_ids, 1, d, s); L.post(K_FIRE_SCALARS);
-    L.pre(K_FIRE_UPDATE); launch_fire_update<T>(b->d_rtiles, b->n_rtiles, d, s);
-    L.post(K_FIRE_UPDATE);
+    enqueue_eval_set<T>(band_set(b, imgs, nimg, atiles, natiles), L, forces);
 }
 
 int launches_per_step(const cfneb_band *b) {
-    return 7 + (b->kind == CFNEB_LJ ? 1 : 2) + 1 + 6;
+    return launches_in_set(band_set(const_cast<cfneb_band *>(b), nullptr, 1, nullptr, 1));
 }
 
-void run_step_sequence(cfneb_band *b) {
-    Launcher L{b};
-    if (b->precision == CFNEB_MIXED) enqueue_step<float>(b, L);
-    else enqueue_step<double>(b, L);
+// run the launches of `ls` once with events around each launch and add the
+// times to (ms, n)
+template <typename F>
+void profiled(cudaStream_t s, std::vector<cudaEvent_t> &ev, double *ms, long long *n, F enq) {
+    Launcher L;
+    L.prof = true;
+    L.ev = &ev;
+    L.s = s;
+    enq(L);
     CK(cudaGetLastError());
-    if (b->prof) {
-        CK(cudaStreamSynchronize(b->s));
-        for (int q = 0; q < L.k; ++q) {
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, b->prof_ev[2 * q], b->prof_ev[2 * q + 1]));
-            b->prof_ms[L.ids[q]] += ms;
-            b->prof_n[L.ids[q]] += 1;
-        }
+    CK(cudaStreamSynchronize(s));
+    for (int q = 0; q < L.k; ++q) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, ev[2 * q], ev[2 * q + 1]));
+        ms[L.ids[q]] += t;
+        n[L.ids[q]] += 1;
     }
 }
 
-void capture_graph(cfneb_band *b) {
-    if (b->gexec) {
-        CK(cudaGraphExecDestroy(b->gexec));
-        b->gexec = nullptr;
-    }
+// capture the launches of `enq` on stream s into an executable graph
+template <typename F>
+cudaGraphExec_t capture(cudaStream_t s, F enq) {
     cudaGraph_t g = nullptr;
-    CK(cudaStreamBeginCapture(b->s, cudaStreamCaptureModeThreadLocal));
-    Launcher L{b};
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    Launcher L;
     try {
-        if (b->precision == CFNEB_MIXED) enqueue_step<float>(b, L);
-        else enqueue_step<double>(b, L);
+        enq(L);
     } catch (...) {
-        cudaStreamEndCapture(b->s, &g);
+        cudaStreamEndCapture(s, &g);
         if (g) cudaGraphDestroy(g);
         throw;
     }
-    CK(cudaStreamEndCapture(b->s, &g));
-    cudaError_t e = cudaGraphInstantiate(&b->gexec, g, 0);
+    CK(cudaStreamEndCapture(s, &g));
+    cudaGraphExec_t ge = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
     cudaGraphDestroy(g);
     CK(e);
-    b->graph_dirty = false;
+    return ge;
 }
 
 void steps(cfneb_band *b, int n) {
     if (n <= 0 || b->N < 3) return;
+    const LaunchSet ls = band_step_set(b);
+    auto enq = [&](Launcher &L) {
+        if (b->precision == CFNEB_MIXED) enqueue_step_set<float>(ls, L);
+        else enqueue_step_set<double>(ls, L);
+    };
     if (b->prof) {
-        for (int i = 0; i < n; ++i) run_step_sequence(b);
+        for (int i = 0; i < n; ++i) profiled(b->s, b->prof_ev, b->prof_ms, b->prof_n, enq);
         return;
     }
-    if (b->graph_dirty || !b->gexec) capture_graph(b);
+    if (b->graph_dirty || !b->gexec) {
+        if (b->gexec) {
+            CK(cudaGraphExecDestroy(b->gexec));
+            b->gexec = nullptr;
+        }
+        b->gexec = capture(b->s, enq);
+        b->graph_dirty = false;
+    }
     for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(b->gexec, b->s));
 }
 
@@ -307,16 +407,13 @@ void eval_images(cfneb_band *b, const std::vector<int> &imgs) {
                        cudaMemcpyHostToDevice, b->s));
     CK(cudaMemcpyAsync(b->d_scratch_tiles, at.data(), at.size() * sizeof(Tile),
                        cudaMemcpyHostToDevice, b->s));
-    Launcher L{b};
-    bool prof = b->prof;
-    b->prof = false;
+    Launcher L;
     if (b->precision == CFNEB_MIXED)
         enqueue_eval<float>(b, L, b->d_scratch_imgs, (int)im.size(), b->d_scratch_tiles,
                             (int)at.size());
     else
         enqueue_eval<double>(b, L, b->d_scratch_imgs, (int)im.size(), b->d_scratch_tiles,
                              (int)at.size());
-    b->prof = prof;
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(b->s));
 }
@@ -334,16 +431,13 @@ void refine_energies(cfneb_band *b, int first, int count) {
                        cudaMemcpyHostToDevice, b->s));
     CK(cudaMemcpyAsync(b->d_scratch_tiles, at.data(), at.size() * sizeof(Tile),
                        cudaMemcpyHostToDevice, b->s));
-    Launcher L{b};
-    bool prof = b->prof;
-    b->prof = false;
+    Launcher L;
     if (b->precision == CFNEB_MIXED)
         enqueue_eval<float>(b, L, b->d_scratch_imgs, (int)im.size(), b->d_scratch_tiles,
                             (int)at.size(), false);
     else
         enqueue_eval<double>(b, L, b->d_scratch_imgs, (int)im.size(), b->d_scratch_tiles,
                              (int)at.size(), false);
-    b->prof = prof;
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(b->s));
 }
@@ -495,6 +589,7 @@ void refine(cfneb_band *b) {
 
 void set_control(cfneb_band *b, double ftol, long long move_limit) {
     read_params(b);
+    b->move_limit = move_limit;
     b->h_bp->ftol = ftol;
     b->h_bp->converged = 0;
     b->h_bp->move_limit = move_limit;
@@ -582,15 +677,23 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
         for (int k = 0; k < 11; ++k) P.pot[k] = zero ? kTersoff1988C[k] : pot->tersoff[k];
         rc = P.pot[9] + P.pot[10];
     }
-    double bscale = opt->bin_scale > 0 ? opt->bin_scale : 1.0;
+    // bin width: the caller's, the cached autotuned one for this class, or rc
+    const double dens = (double)b->n / std::fabs(det3(A->cell)) * rc * rc * rc;
+    b->tune_key = std::make_tuple(pot->kind, opt->precision,
+                                  (int)std::floor(std::log2((double)std::max(1, b->n))),
+                                  (int)std::floor(2.0 * std::log2(std::max(dens, 1e-3))));
+    double bscale = opt->bin_scale > 0 ? opt->bin_scale : tuned_scale(b->tune_key);
     double bin_w = rc * bscale;
+    b->rc = rc;
+    // reserve bins for the finest autotuning candidate when tuning may follow
+    const double cap_w = opt->bin_scale > 0 ? bin_w : rc * kTuneScales[0];
     // geometry
     const int n = b->n, rows = n + 3;
     BandDev &d = b->dv;
     d.n = n;
     d.rows = rows;
     d.ncap = b->ncap;
-    int nb0 = bins_for(A->cell, bin_w), nb1 = bins_for(B->cell, bin_w);
+    int nb0 = bins_for(A->cell, cap_w), nb1 = bins_for(B->cell, cap_w);
     d.nbins_cap = (int)std::min<long long>((long long)(1.5 * std::max(nb0, nb1)) + 64, 1LL << 26);
     d.atpi = (n + TILE - 1) / TILE;
     d.rtpi = (rows + TILE - 1) / TILE;
@@ -699,6 +802,430 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
     read_params(b);
     if (b->h_bp->status) *err = status_from_bits(b->h_bp->status);
     return b;
+}
+
+}  // namespace
+
+// ===========================================================================
+// Autotuning of the bin width
+// ===========================================================================
+
+namespace {
+
+void set_bin_w(cfneb_band *b, double w) {
+    read_params(b);
+    b->h_bp->bin_w = w;
+    CK(cudaMemcpyAsync(b->dv.bp, b->h_bp, sizeof(BandParams), cudaMemcpyHostToDevice, b->s));
+    CK(cudaStreamSynchronize(b->s));
+}
+
+// time `steps` non-moving steps of the band at bin width w (ms per step)
+double time_bin_w(cfneb_band *b, double w, int nsteps) {
+    set_bin_w(b, w);
+    steps(b, 2);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, b->s));
+    steps(b, nsteps);
+    CK(cudaEventRecord(e1, b->s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms / nsteps;
+}
+
+double autotune_band(cfneb_band *b, int steps) {
+    read_params(b);
+    const long long keep_limit = b->h_bp->move_limit;
+    const double keep_ftol = b->h_bp->ftol;
+    const long long now = b->h_bp->steps;
+    set_control(b, keep_ftol, now);  // evaluate, never move
+    double best = kTuneScales[2], best_ms = 1e300;
+    for (double sc : kTuneScales) {
+        const double ms = time_bin_w(b, sc * b->rc, steps);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = sc;
+        }
+    }
+    set_bin_w(b, best * b->rc);
+    set_control(b, keep_ftol, keep_limit);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[b->tune_key] = best;
+    return best;
+}
+
+}  // namespace
+
+// ===========================================================================
+// Batches
+// ===========================================================================
+
+struct cfneb_batch {
+    int precision = 0;
+    unsigned long long budget = 0, used = 0;
+    cudaStream_t user = nullptr, s = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    std::vector<cfneb_band *> bands;
+    // device tables (grown on demand)
+    BandDev *d_bands = nullptr;
+    Tile *d_tiles = nullptr;     // [atoms all | atoms LJ | atoms Tersoff | rows]
+    ImgRef *d_imgs = nullptr;
+    int *d_ids = nullptr;
+    double *d_status = nullptr;
+    double *h_status = nullptr;  // pinned
+    size_t cap_bands = 0, cap_tiles = 0, cap_imgs = 0;
+    LaunchSet ls;
+    bool dirty = true;
+    cudaGraphExec_t gexec = nullptr;
+    bool prof = false;
+    double prof_ms[K_COUNT]{};
+    long long prof_n[K_COUNT]{};
+    std::vector<cudaEvent_t> prof_ev;
+};
+
+namespace {
+
+void batch_mark_dirty(cfneb_batch *bt) { bt->dirty = true; }
+
+void bt_enter(cfneb_batch *bt) {
+    CK(cudaEventRecord(bt->ev_in, bt->user));
+    CK(cudaStreamWaitEvent(bt->s, bt->ev_in, 0));
+}
+void bt_leave(cfneb_batch *bt) {
+    CK(cudaEventRecord(bt->ev_out, bt->s));
+    CK(cudaStreamWaitEvent(bt->user, bt->ev_out, 0));
+}
+
+template <typename X>
+void grow(X **p, size_t *cap, size_t need) {
+    if (need <= *cap) return;
+    if (*p) CK(cudaFree(*p));
+    *p = nullptr;
+    size_t c = std::max<size_t>(need, 2 * *cap);
+    CK(cudaMalloc((void **)p, c * sizeof(X)));
+    *cap = c;
+}
+
+void batch_rebuild(cfneb_batch *bt) {
+    std::vector<BandDev> dv;
+    std::vector<ImgRef> im;
+    std::vector<Tile> all, lj, ters, rows;
+    std::vector<int> ids;
+    int max_bins = 0;
+    for (size_t k = 0; k < bt->bands.size(); ++k) {
+        cfneb_band *b = bt->bands[k];
+        dv.push_back(b->dv);
+        ids.push_back((int)k);
+        max_bins = std::max(max_bins, b->dv.nbins_cap);
+        for (int i = 1; i < b->N - 1; ++i) {
+            im.push_back({(int)k, i});
+            for (int t = 0; t < b->dv.atpi; ++t) {
+                all.push_back({(int)k, i, t, 0});
+                (b->kind == CFNEB_LJ ? lj : ters).push_back({(int)k, i, t, 0});
+            }
+            for (int t = 0; t < b->dv.rtpi; ++t) rows.push_back({(int)k, i, t, 0});
+        }
+    }
+    grow(&bt->d_bands, &bt->cap_bands, std::max<size_t>(dv.size(), 1));
+    std::vector<Tile> tiles;
+    tiles.insert(tiles.end(), all.begin(), all.end());
+    tiles.insert(tiles.end(), lj.begin(), lj.end());
+    tiles.insert(tiles.end(), ters.begin(), ters.end());
+    tiles.insert(tiles.end(), rows.begin(), rows.end());
+    grow(&bt->d_tiles, &bt->cap_tiles, std::max<size_t>(tiles.size(), 1));
+    grow(&bt->d_imgs, &bt->cap_imgs, std::max<size_t>(im.size(), 1));
+    if (bt->d_ids) CK(cudaFree(bt->d_ids));
+    if (bt->d_status) CK(cudaFree(bt->d_status));
+    if (bt->h_status) CK(cudaFreeHost(bt->h_status));
+    const size_t nb = std::max<size_t>(ids.size(), 1);
+    CK(cudaMalloc((void **)&bt->d_ids, nb * sizeof(int)));
+    CK(cudaMalloc((void **)&bt->d_status, nb * 6 * sizeof(double)));
+    CK(cudaMallocHost((void **)&bt->h_status, nb * 6 * sizeof(double)));
+    if (!dv.empty())
+        CK(cudaMemcpyAsync(bt->d_bands, dv.data(), dv.size() * sizeof(BandDev),
+                           cudaMemcpyHostToDevice, bt->s));
+    if (!tiles.empty())
+        CK(cudaMemcpyAsync(bt->d_tiles, tiles.data(), tiles.size() * sizeof(Tile),
+                           cudaMemcpyHostToDevice, bt->s));
+    if (!im.empty())
+        CK(cudaMemcpyAsync(bt->d_imgs, im.data(), im.size() * sizeof(ImgRef),
+                           cudaMemcpyHostToDevice, bt->s));
+    if (!ids.empty())
+        CK(cudaMemcpyAsync(bt->d_ids, ids.data(), ids.size() * sizeof(int),
+                           cudaMemcpyHostToDevice, bt->s));
+    CK(cudaStreamSynchronize(bt->s));
+    LaunchSet &ls = bt->ls;
+    ls = LaunchSet();
+    ls.d_bands = bt->d_bands;
+    ls.s = bt->s;
+    ls.imgs = bt->d_imgs;
+    ls.nimg = (int)im.size();
+    ls.atiles = bt->d_tiles;
+    ls.n_atiles = (int)all.size();
+    ls.atiles_lj = bt->d_tiles + all.size();
+    ls.n_lj = (int)lj.size();
+    ls.atiles_ters = bt->d_tiles + all.size() + lj.size();
+    ls.n_ters = (int)ters.size();
+    ls.rtiles = bt->d_tiles + all.size() + lj.size() + ters.size();
+    ls.n_rtiles = (int)rows.size();
+    ls.band_ids = bt->d_ids;
+    ls.nbands = (int)ids.size();
+    ls.max_bins = max_bins;
+    if (bt->gexec) {
+        CK(cudaGraphExecDestroy(bt->gexec));
+        bt->gexec = nullptr;
+    }
+    bt->dirty = false;
+}
+
+void batch_steps(cfneb_batch *bt, int n) {
+    if (n <= 0) return;
+    if (bt->dirty) batch_rebuild(bt);
+    if (bt->ls.nimg == 0) return;
+    const LaunchSet ls = bt->ls;
+    auto enq = [&](Launcher &L) {
+        if (bt->precision == CFNEB_MIXED) enqueue_step_set<float>(ls, L);
+        else enqueue_step_set<double>(ls, L);
+    };
+    if (bt->prof) {
+        for (int i = 0; i < n; ++i) profiled(bt->s, bt->prof_ev, bt->prof_ms, bt->prof_n, enq);
+        return;
+    }
+    if (!bt->gexec) bt->gexec = capture(bt->s, enq);
+    for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(bt->gexec, bt->s));
+}
+
+// per-member (moves, converged, status, fmax, ci, N)
+void batch_poll(cfneb_batch *bt) {
+    if (bt->dirty) batch_rebuild(bt);
+    const int nb = (int)bt->bands.size();
+    if (nb == 0) return;
+    launch_gather_status(bt->d_bands, nb, bt->d_status, bt->s);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(bt->h_status, bt->d_status, nb * 6 * sizeof(double),
+                       cudaMemcpyDeviceToHost, bt->s));
+    CK(cudaStreamSynchronize(bt->s));
+}
+
+// Relax (or, with stop = false and ftol < 0, just step) the members for up
+// to n_eval steps, with the members' refinement checks at their k_ref
+// boundaries.  Returns the first error status of a member, or OK.
+int batch_run(cfneb_batch *bt, long long n_eval, bool stop_on_converged) {
+    long long launched = 0;
+    int chunk = 8;
+    while (launched < n_eval) {
+        batch_poll(bt);
+        long long k = std::min<long long>(n_eval - launched, chunk);
+        for (size_t m = 0; m < bt->bands.size(); ++m) {
+            cfneb_band *b = bt->bands[m];
+            if (!b->opt.adaptive) continue;
+            long long cur = (long long)bt->h_status[6 * m];
+            k = std::min(k, (long long)(b->opt.k_ref - (cur % b->opt.k_ref)));
+        }
+        batch_steps(bt, (int)k);
+        launched += k;
+        batch_poll(bt);
+        bool all_done = true;
+        for (size_t m = 0; m < bt->bands.size(); ++m) {
+            const double *st = bt->h_status + 6 * m;
+            if ((int)st[2]) return status_from_bits((int)st[2]);
+            cfneb_band *b = bt->bands[m];
+            const long long cur = (long long)st[0];
+            const bool done = (int)st[1] != 0 || cur >= b->move_limit;
+            all_done = all_done && done;
+            if (b->opt.adaptive && cur > 0 && cur % b->opt.k_ref == 0 && cur != b->last_check &&
+                cur - b->last_change >= b->opt.cooldown) {
+                b->last_check = cur;
+                refine(b);
+            }
+        }
+        if (stop_on_converged && all_done) break;
+        chunk = std::min(chunk * 2, 64);
+    }
+    return CFNEB_OK;
+}
+
+void batch_free(cfneb_batch *bt) {
+    if (!bt) return;
+    if (bt->s) cudaStreamSynchronize(bt->s);
+    for (cfneb_band *b : bt->bands) {
+        b->batch = nullptr;
+        if (b->own_s) b->s = b->own_s;
+        b->own_s = nullptr;
+    }
+    if (bt->gexec) cudaGraphExecDestroy(bt->gexec);
+    if (bt->d_bands) cudaFree(bt->d_bands);
+    if (bt->d_tiles) cudaFree(bt->d_tiles);
+    if (bt->d_imgs) cudaFree(bt->d_imgs);
+    if (bt->d_ids) cudaFree(bt->d_ids);
+    if (bt->d_status) cudaFree(bt->d_status);
+    if (bt->h_status) cudaFreeHost(bt->h_status);
+    for (auto e : bt->prof_ev) cudaEventDestroy(e);
+    if (bt->ev_in) cudaEventDestroy(bt->ev_in);
+    if (bt->ev_out) cudaEventDestroy(bt->ev_out);
+    if (bt->s) cudaStreamDestroy(bt->s);
+    delete bt;
+}
+
+}  // namespace
+
+// ===========================================================================
+// Serving
+// ===========================================================================
+
+namespace {
+
+struct Request {
+    long long id = 0;
+    double arrival = 0.0;
+    std::vector<double> R0, R1;
+    double h0[9], h1[9];
+    int n = 0, n_images = 0;
+    cfneb_potential pot{};
+    cfneb_cell_filter filt{};
+    cfneb_options opt{};
+    double fmax = 0.0;
+    long long max_steps = 0;
+    int state = 0;  // 0 queued, 1 running, 2 retired
+    unsigned long long bytes = 0;  // device memory of its band, once known
+    cfneb_band *band = nullptr;
+    long long steps0 = 0;
+    double done_t = 0.0;
+    long long steps = 0;
+    int converged = 0;
+    int status = 0;
+    double barrier = 0.0;
+};
+
+}  // namespace
+
+struct cfneb_server {
+    int precision = 0;
+    cudaStream_t user = nullptr;
+    cfneb_batch *bt = nullptr;
+    std::vector<Request> req;
+    std::deque<long long> queue;   // ids waiting, in arrival order
+    std::vector<long long> running;
+    std::chrono::steady_clock::time_point t0;
+    double work = 0.0;             // atom-steps of retired requests
+    double now() const {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace {
+
+void server_retire(cfneb_server *sv, Request &r, int status) {
+    cfneb_band *b = r.band;
+    read_params(b);
+    r.steps = b->h_bp->steps - r.steps0;
+    r.converged = b->h_bp->converged;
+    r.status = status;
+    if (status == CFNEB_OK) {
+        std::vector<double> E(b->N);
+        int32_t N = 0;
+        cfneb_get_path(b, &N, nullptr, nullptr, E.data(), nullptr);
+        r.barrier = *std::max_element(E.begin(), E.end()) - E[0];
+    }
+    cfneb_batch_remove(sv->bt, b);
+    sv->work += (double)r.n * (b->N - 2) * (double)r.steps;
+    cfneb_destroy_band(b);
+    r.band = nullptr;
+    r.state = 2;
+    r.done_t = sv->now();
+}
+
+// admit arrived requests in order while they fit; false if the head waits
+void server_admit(cfneb_server *sv) {
+    const double t = sv->now();
+    while (!sv->queue.empty()) {
+        Request &r = sv->req[sv->queue.front()];
+        if (r.arrival > t) return;
+        // a request known not to fit waits without being rebuilt
+        if (r.bytes && sv->bt->budget && sv->bt->used + r.bytes > sv->bt->budget &&
+            !sv->running.empty())
+            return;
+        cfneb_structure A{r.n, nullptr, r.R0.data(), {}}, B{r.n, nullptr, r.R1.data(), {}};
+        std::memcpy(A.cell, r.h0, sizeof(r.h0));
+        std::memcpy(B.cell, r.h1, sizeof(r.h1));
+        cfneb_band *b = nullptr;
+        int st = cfneb_create_band(&A, &B, r.n_images, &r.pot, &r.filt, &r.opt, sv->user, &b);
+        if (st != CFNEB_OK) {  // cannot be built at all: retire with the error
+            r.status = st;
+            r.state = 2;
+            r.done_t = sv->now();
+            sv->queue.pop_front();
+            continue;
+        }
+        r.bytes = b->bytes;
+        st = cfneb_batch_add(sv->bt, b);
+        if (st == CFNEB_ERR_HBM_BUDGET && !sv->running.empty()) {
+            cfneb_destroy_band(b);  // wait for memory to free up
+            return;
+        }
+        if (st != CFNEB_OK && st != CFNEB_ERR_HBM_BUDGET) {
+            cfneb_destroy_band(b);
+            r.status = st;
+            r.state = 2;
+            r.done_t = sv->now();
+            sv->queue.pop_front();
+            continue;
+        }
+        if (st == CFNEB_ERR_HBM_BUDGET) {
+            // larger than the whole budget on an idle server: refuse
+            cfneb_destroy_band(b);
+            r.status = st;
+            r.state = 2;
+            r.done_t = sv->now();
+            sv->queue.pop_front();
+            continue;
+        }
+        r.band = b;
+        read_params(b);
+        r.steps0 = b->h_bp->steps;
+        set_control(b, r.fmax, r.steps0 + r.max_steps);
+        r.state = 1;
+        sv->running.push_back(r.id);
+        sv->queue.pop_front();
+    }
+}
+
+int server_run(cfneb_server *sv, double until) {
+    while (true) {
+        server_admit(sv);
+        if (sv->running.empty()) {
+            if (sv->queue.empty()) return CFNEB_OK;
+            const double wait = sv->req[sv->queue.front()].arrival - sv->now();
+            if (sv->now() > until) return CFNEB_NOT_CONVERGED;
+            if (wait > 0)
+                std::this_thread::sleep_for(std::chrono::duration<double>(std::min(wait, 0.01)));
+            continue;
+        }
+        if (sv->now() > until) return CFNEB_NOT_CONVERGED;
+        batch_run(sv->bt, 8, false);
+        batch_poll(sv->bt);
+        // decide from this poll's snapshot (indexed by the current member
+        // order) first, then retire: removals reorder the members
+        std::vector<long long> keep;
+        std::vector<std::pair<long long, int>> retire;
+        for (long long id : sv->running) {
+            Request &r = sv->req[id];
+            const size_t m = std::find(sv->bt->bands.begin(), sv->bt->bands.end(), r.band) -
+                             sv->bt->bands.begin();
+            const double *st = sv->bt->h_status + 6 * m;
+            const int bits = (int)st[2];
+            const bool conv = (int)st[1] != 0;
+            const bool spent = (long long)st[0] - r.steps0 >= r.max_steps;
+            if (bits || conv || spent) retire.push_back({id, status_from_bits(bits)});
+            else keep.push_back(id);
+        }
+        for (auto &rt : retire) server_retire(sv, sv->req[rt.first], rt.second);
+        sv->running.swap(keep);
+    }
 }
 
 }  // namespace
@@ -927,8 +1454,11 @@ int cfneb_get_state(const cfneb_band *cb, double *X, double *F, double *Fneb, do
     }
 }
 
+int cfneb_batch_remove(cfneb_batch *bt, cfneb_band *b);
+
 int cfneb_destroy_band(cfneb_band *b) {
     if (!b) return CFNEB_ERR_INVALID_ARG;
+    if (b->batch) cfneb_batch_remove(b->batch, b);
     try {
         enter(b);
     } catch (CudaFail &) {
@@ -979,6 +1509,306 @@ int cfneb_evaluate(const cfneb_structure *structures, int32_t count,
         off += (size_t)S.n_atoms * 3;
         cfneb_destroy_band(b);
     }
+    return CFNEB_OK;
+}
+
+int cfneb_band_bytes(const cfneb_band *b, uint64_t *bytes) {
+    if (!b || !bytes) return CFNEB_ERR_INVALID_ARG;
+    *bytes = b->bytes;
+    return CFNEB_OK;
+}
+
+int cfneb_batch_create(int32_t precision, uint64_t budget_bytes, void *cuda_stream,
+                       cfneb_batch **out) {
+    if (!out || (precision != CFNEB_FP64 && precision != CFNEB_MIXED))
+        return CFNEB_ERR_INVALID_ARG;
+    cfneb_batch *bt = new cfneb_batch();
+    bt->precision = precision;
+    bt->budget = budget_bytes;
+    bt->user = (cudaStream_t)cuda_stream;
+    try {
+        CK(cudaStreamCreateWithFlags(&bt->s, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&bt->ev_in, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&bt->ev_out, cudaEventDisableTiming));
+        bt->prof_ev.resize(2 * 64);
+        for (auto &e : bt->prof_ev) CK(cudaEventCreate(&e));
+    } catch (CudaFail &) {
+        batch_free(bt);
+        return CFNEB_ERR_CUDA;
+    }
+    *out = bt;
+    return CFNEB_OK;
+}
+
+int cfneb_batch_add(cfneb_batch *bt, cfneb_band *b) {
+    if (!bt || !b || b->batch || b->precision != bt->precision) return CFNEB_ERR_INVALID_ARG;
+    if (bt->budget && bt->used + b->bytes > bt->budget) return CFNEB_ERR_HBM_BUDGET;
+    try {
+        // the band's queued work finishes before the batch touches it
+        CK(cudaEventRecord(b->ev_out, b->s));
+        CK(cudaStreamWaitEvent(bt->s, b->ev_out, 0));
+    } catch (CudaFail &) {
+        return CFNEB_ERR_CUDA;
+    }
+    b->own_s = b->s;
+    b->s = bt->s;
+    b->batch = bt;
+    b->graph_dirty = true;
+    bt->bands.push_back(b);
+    bt->used += b->bytes;
+    bt->dirty = true;
+    return CFNEB_OK;
+}
+
+int cfneb_batch_remove(cfneb_batch *bt, cfneb_band *b) {
+    if (!bt || !b || b->batch != bt) return CFNEB_ERR_INVALID_ARG;
+    try {
+        CK(cudaEventRecord(bt->ev_out, bt->s));
+        CK(cudaStreamWaitEvent(b->own_s, bt->ev_out, 0));
+    } catch (CudaFail &) {
+        return CFNEB_ERR_CUDA;
+    }
+    b->s = b->own_s;
+    b->own_s = nullptr;
+    b->batch = nullptr;
+    b->graph_dirty = true;
+    bt->bands.erase(std::find(bt->bands.begin(), bt->bands.end(), b));
+    bt->used -= b->bytes;
+    bt->dirty = true;
+    return CFNEB_OK;
+}
+
+int cfneb_batch_step(cfneb_batch *bt, int32_t n_steps) {
+    if (!bt || n_steps < 0) return CFNEB_ERR_INVALID_ARG;
+    try {
+        bt_enter(bt);
+        bool adaptive = false;
+        for (cfneb_band *b : bt->bands) adaptive = adaptive || b->opt.adaptive;
+        int st = CFNEB_OK;
+        if (adaptive) st = batch_run(bt, n_steps, false);
+        else batch_steps(bt, n_steps);
+        bt_leave(bt);
+        return st;
+    } catch (CudaFail &) {
+        return CFNEB_ERR_CUDA;
+    }
+}
+
+int cfneb_batch_relax(cfneb_batch *bt, double fmax, int64_t max_steps, int32_t *n_converged) {
+    if (!bt || max_steps < 0 || !(fmax >= 0)) return CFNEB_ERR_INVALID_ARG;
+    try {
+        bt_enter(bt);
+        for (cfneb_band *b : bt->bands) {
+            read_params(b);
+            set_control(b, fmax, b->h_bp->steps + max_steps);
+        }
+        int st = batch_run(bt, max_steps + 1, true);
+        int conv = 0;
+        batch_poll(bt);
+        for (size_t m = 0; m < bt->bands.size(); ++m) conv += (int)bt->h_status[6 * m + 1];
+        for (cfneb_band *b : bt->bands) {
+            read_params(b);
+            b->h_bp->move_limit = 1LL << 62;
+            b->move_limit = 1LL << 62;
+            CK(cudaMemcpyAsync(b->dv.bp, b->h_bp, sizeof(BandParams), cudaMemcpyHostToDevice,
+                               b->s));
+        }
+        CK(cudaStreamSynchronize(bt->s));
+        bt_leave(bt);
+        if (n_converged) *n_converged = conv;
+        if (st != CFNEB_OK) return st;
+        return conv == (int)bt->bands.size() ? CFNEB_OK : CFNEB_NOT_CONVERGED;
+    } catch (CudaFail &) {
+        return CFNEB_ERR_CUDA;
+    }
+}
+
+int cfneb_batch_status(cfneb_batch *bt, int32_t *count, int64_t *steps, int32_t *converged,
+                       double *fmax, int32_t *status) {
+    if (!bt) return CFNEB_ERR_INVALID_ARG;
+    try {
+        bt_enter(bt);
+        batch_poll(bt);
+        const int nb = (int)bt->bands.size();
+        if (count) *count = nb;
+        for (int m = 0; m < nb; ++m) {
+            const double *st = bt->h_status + 6 * m;
+            if (steps) steps[m] = (int64_t)st[0];
+            if (converged) converged[m] = (int32_t)st[1];
+            if (fmax) fmax[m] = st[3];
+            if (status) status[m] = status_from_bits((int)st[2]);
+        }
+        bt_leave(bt);
+        return CFNEB_OK;
+    } catch (CudaFail &) {
+        return CFNEB_ERR_CUDA;
+    }
+}
+
+int cfneb_batch_bytes(const cfneb_batch *bt, uint64_t *used, uint64_t *budget) {
+    if (!bt) return CFNEB_ERR_INVALID_ARG;
+    if (used) *used = bt->used;
+    if (budget) *budget = bt->budget;
+    return CFNEB_OK;
+}
+
+int cfneb_batch_profile(cfneb_batch *bt, int32_t enable) {
+    if (!bt) return CFNEB_ERR_INVALID_ARG;
+    bt->prof = enable != 0;
+    for (int k = 0; k < K_COUNT; ++k) {
+        bt->prof_ms[k] = 0.0;
+        bt->prof_n[k] = 0;
+    }
+    return CFNEB_OK;
+}
+
+int cfneb_batch_profile_read(cfneb_batch *bt, int32_t kernel_id, double *total_ms,
+                             int64_t *launches) {
+    if (!bt || kernel_id < 0 || kernel_id >= K_COUNT) return CFNEB_ERR_INVALID_ARG;
+    if (total_ms) *total_ms = bt->prof_ms[kernel_id];
+    if (launches) *launches = bt->prof_n[kernel_id];
+    return CFNEB_OK;
+}
+
+int cfneb_autotune(cfneb_band *b, int32_t steps, double *best_scale) {
+    if (!b || steps <= 0) return CFNEB_ERR_INVALID_ARG;
+    try {
+        enter(b);
+        const double best = autotune_band(b, steps);
+        leave(b);
+        if (best_scale) *best_scale = best;
+        return CFNEB_OK;
+    } catch (CudaFail &) {
+        return CFNEB_ERR_CUDA;
+    }
+}
+
+int cfneb_batch_autotune(cfneb_batch *bt, int32_t steps) {
+    if (!bt || steps <= 0) return CFNEB_ERR_INVALID_ARG;
+    try {
+        bt_enter(bt);
+        std::map<std::tuple<int, int, int, int>, double> done;
+        for (cfneb_band *b : bt->bands) {
+            auto it = done.find(b->tune_key);
+            const double sc = it != done.end() ? it->second : autotune_band(b, steps);
+            done[b->tune_key] = sc;
+            set_bin_w(b, sc * b->rc);
+        }
+        bt_leave(bt);
+        return CFNEB_OK;
+    } catch (CudaFail &) {
+        return CFNEB_ERR_CUDA;
+    }
+}
+
+int cfneb_batch_destroy(cfneb_batch *bt) {
+    if (!bt) return CFNEB_ERR_INVALID_ARG;
+    batch_free(bt);
+    return CFNEB_OK;
+}
+
+int cfneb_server_create(int32_t precision, uint64_t budget_bytes, void *cuda_stream,
+                        cfneb_server **out) {
+    if (!out) return CFNEB_ERR_INVALID_ARG;
+    cfneb_server *sv = new cfneb_server();
+    sv->precision = precision;
+    sv->user = (cudaStream_t)cuda_stream;
+    int st = cfneb_batch_create(precision, budget_bytes, cuda_stream, &sv->bt);
+    if (st != CFNEB_OK) {
+        delete sv;
+        return st;
+    }
+    sv->t0 = std::chrono::steady_clock::now();
+    *out = sv;
+    return CFNEB_OK;
+}
+
+int cfneb_server_submit(cfneb_server *sv, const cfneb_structure *initial,
+                        const cfneb_structure *final_, int32_t n_images,
+                        const cfneb_potential *potential, const cfneb_cell_filter *cell_filter,
+                        const cfneb_options *options, double fmax, int64_t max_steps,
+                        double arrival_s, int64_t *id) {
+    if (!sv || !initial || !final_ || !potential || !options || n_images < 3 ||
+        initial->n_atoms <= 0 || initial->n_atoms != final_->n_atoms || !(fmax >= 0) ||
+        max_steps < 0)
+        return CFNEB_ERR_INVALID_ARG;
+    if (options->precision != sv->precision) return CFNEB_ERR_INVALID_ARG;
+    if (options->interior_noise) return CFNEB_ERR_INVALID_ARG;  // not copied by the server
+    Request r;
+    r.id = (long long)sv->req.size();
+    r.arrival = arrival_s;
+    r.n = initial->n_atoms;
+    r.R0.assign(initial->positions, initial->positions + 3 * (size_t)r.n);
+    r.R1.assign(final_->positions, final_->positions + 3 * (size_t)r.n);
+    std::memcpy(r.h0, initial->cell, sizeof(r.h0));
+    std::memcpy(r.h1, final_->cell, sizeof(r.h1));
+    r.n_images = n_images;
+    r.pot = *potential;
+    r.filt = cell_filter ? *cell_filter : cfneb_cell_filter{1, CFNEB_ROTFREE_B, 0.0, 0.0};
+    r.opt = *options;
+    r.fmax = fmax;
+    r.max_steps = max_steps;
+    sv->req.push_back(std::move(r));
+    // keep the queue in arrival order
+    auto pos = std::upper_bound(sv->queue.begin(), sv->queue.end(), arrival_s,
+                                [&](double t, long long q) { return t < sv->req[q].arrival; });
+    sv->queue.insert(pos, (long long)sv->req.size() - 1);
+    if (id) *id = (long long)sv->req.size() - 1;
+    return CFNEB_OK;
+}
+
+int cfneb_server_run(cfneb_server *sv, double until_s) {
+    if (!sv) return CFNEB_ERR_INVALID_ARG;
+    try {
+        return server_run(sv, until_s);
+    } catch (CudaFail &) {
+        return CFNEB_ERR_CUDA;
+    }
+}
+
+int cfneb_server_result(cfneb_server *sv, int64_t id, int32_t *state, double *latency_s,
+                        int64_t *steps, int32_t *converged, double *barrier, int32_t *status) {
+    if (!sv || id < 0 || id >= (int64_t)sv->req.size()) return CFNEB_ERR_INVALID_ARG;
+    const Request &r = sv->req[id];
+    if (state) *state = r.state;
+    if (latency_s) *latency_s = r.state == 2 ? r.done_t - r.arrival : -1.0;
+    if (steps) *steps = r.steps;
+    if (converged) *converged = r.converged;
+    if (barrier) *barrier = r.barrier;
+    if (status) *status = r.status;
+    return CFNEB_OK;
+}
+
+int cfneb_server_stats(cfneb_server *sv, double *p50_s, double *p99_s, int64_t *retired,
+                       double *atom_steps_per_s) {
+    if (!sv) return CFNEB_ERR_INVALID_ARG;
+    std::vector<double> lat;
+    for (const Request &r : sv->req)
+        if (r.state == 2 && r.status == CFNEB_OK) lat.push_back(r.done_t - r.arrival);
+    std::sort(lat.begin(), lat.end());
+    auto pct = [&](double p) {
+        if (lat.empty()) return 0.0;
+        const double x = p * (lat.size() - 1);
+        const size_t i = (size_t)x;
+        const double f = x - i;
+        return i + 1 < lat.size() ? lat[i] * (1 - f) + lat[i + 1] * f : lat[i];
+    };
+    if (p50_s) *p50_s = pct(0.5);
+    if (p99_s) *p99_s = pct(0.99);
+    if (retired) *retired = (int64_t)lat.size();
+    if (atom_steps_per_s) *atom_steps_per_s = sv->work / std::max(1e-9, sv->now());
+    return CFNEB_OK;
+}
+
+int cfneb_server_destroy(cfneb_server *sv) {
+    if (!sv) return CFNEB_ERR_INVALID_ARG;
+    for (Request &r : sv->req)
+        if (r.band) {
+            cfneb_batch_remove(sv->bt, r.band);
+            cfneb_destroy_band(r.band);
+        }
+    cfneb_batch_destroy(sv->bt);
+    delete sv;
     return CFNEB_OK;
 }
 

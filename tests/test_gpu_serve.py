@@ -1,0 +1,80 @@
+"""Serving: requests arrive while other bands are mid-relaxation, are admitted
+as the memory budget frees up, share the GPU in one batch and are retired on
+convergence.  Each result must equal the same band relaxed alone (per-band
+reductions in fixed slots make it bitwise equal)."""
+import numpy as np
+import pytest
+
+import cfneb_inputs as ci
+from _cases import gpu_band
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2510_16721_gb300 as g
+    g.build()
+    return g
+
+
+def _requests():
+    """LJ vacancy / divacancy hops that converge to fmax 0.05 within a few
+    thousand FIRE steps (checked with the oracle)."""
+    out = []
+    for reps, div, seed, amp, N in (((2, 2, 2), False, 1, 0.0, 7), ((3, 3, 3), True, 2, 0.0, 7),
+                                    ((3, 3, 2), False, 3, 0.003, 5),
+                                    ((3, 3, 3), False, 2, 0.003, 7)):
+        R0, h0, R1, h1 = ci.lj_vacancy_hop(ci.LJ_A, reps, divacancy=div)
+        h1s = ci.strained_cell(h1, seed, amp) if amp else h1
+        out.append((R0, h0, ci.affine(R1, h1, h1s), h1s, N))
+    return out
+
+
+def _opts(g, n_images):
+    o = g.default_options()
+    o.k_spring, o.dt, o.dt_max, o.precision, o.n_max = 1.0, 0.01, 0.1, g.FP64, n_images
+    return o
+
+
+def test_served_results_equal_alone(g):
+    reqs = _requests()
+    probe = [gpu_band(g, *r[:4], r[4], g.lj_potential(), k=1.0, dt=0.01) for r in reqs[:2]]
+    budget = sum(p.bytes() for p in probe) + 1024     # room for about two bands at once
+    for p in probe:
+        p.destroy()
+    sv = g.Server(g.FP64, budget_bytes=budget)
+    ids = []
+    for k, (R0, h0, R1, h1, N) in enumerate(reqs):
+        ids.append(sv.submit((R0, h0), (R1, h1), N, g.lj_potential(),
+                             g.CellFilter(1, g.ROTFREE_B, 0.0, 0.0), _opts(g, N), 5e-2, 4000,
+                             arrival_s=0.02 * k))
+    assert sv.run(until_s=120.0)
+    res = [sv.result(i) for i in ids]
+    assert all(r["state"] == 2 and r["status"] == 0 and r["converged"] for r in res), \
+        [(r["state"], r["status"], r["converged"], r["steps"]) for r in res]
+    for (R0, h0, R1, h1, N), r in zip(reqs, res):
+        b = gpu_band(g, R0, h0, R1, h1, N, g.lj_potential(), k=1.0, dt=0.01)
+        done, conv = b.relax(5e-2, 4000)
+        E = b.get_path()["energies"]
+        assert conv and done == r["steps"]
+        assert E.max() - E[0] == r["barrier"]
+        assert r["latency_s"] > 0
+    st = sv.stats()
+    assert st["retired"] == len(reqs) and st["p99_s"] >= st["p50_s"] > 0
+    assert st["atom_steps_per_s"] > 0
+    sv.destroy()
+
+
+def test_request_larger_than_budget_is_refused(g):
+    R0, h0, R1, h1, N = _requests()[1]
+    sv = g.Server(g.FP64, budget_bytes=1 << 16)
+    rid = sv.submit((R0, h0), (R1, h1), N, g.lj_potential(),
+                    g.CellFilter(1, g.ROTFREE_B, 0.0, 0.0), _opts(g, N), 5e-2, 100, 0.0)
+    assert sv.run(until_s=10.0)
+    r = sv.result(rid)
+    assert r["state"] == 2 and r["status"] == g.ERR_HBM_BUDGET
+    sv.destroy()
