@@ -82,15 +82,15 @@ __global__ void __launch_bounds__(TILE) k_band_dots(const Tile *tiles, BandDev *
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
     const int row = tl.t * TILE + threadIdx.x;
-    double acc[5] = {0, 0, 0, 0, 0};
+    T acc[5] = {0, 0, 0, 0, 0};
     if (row < b.rows) {
         const size_t stride = (size_t)b.rows * 3;
         const T *x0 = (const T *)b.X + tl.img * stride + (size_t)row * 3;
         const T *xm = x0 - stride, *xp = x0 + stride;
         const T *f = (const T *)b.F + tl.img * stride + (size_t)row * 3;
         for (int c = 0; c < 3; ++c) {
-            double a = (double)x0[c];
-            double dp = (double)xp[c] - a, dm = a - (double)xm[c], fc = (double)f[c];
+            const T a = x0[c];
+            const T dp = xp[c] - a, dm = a - xm[c], fc = f[c];
             acc[0] += dp * dp;
             acc[1] += dm * dm;
             acc[2] += dp * dm;
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(TILE) k_band_dots(const Tile *tiles, BandDev *
         }
     }
     double tot[5];
-    block_sum<5>(acc, tot);
+    block_sum_t<5, T>(acc, tot);
     if (threadIdx.x == 0) {
         double *part = b.row_part + ((size_t)tl.img * b.rtpi + tl.t) * NPART;
         for (int k = 0; k < 5; ++k) part[k] = tot[k];
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(TILE) k_neb_force(const Tile *tiles, BandDev *
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
     const int row = tl.t * TILE + threadIdx.x;
-    double acc[4] = {0, 0, 0, 0};
+    T acc[4] = {0, 0, 0, 0};
     if (row < b.rows) {
         const ImgScalars &sc = b.sc[tl.img];
         const T ca = (T)sc.coef[0], cb = (T)sc.coef[1];
@@ -201,17 +201,17 @@ __global__ void __launch_bounds__(TILE) k_neb_force(const Tile *tiles, BandDev *
             ff += g * g;
             vv += v[c] * v[c];
         }
-        acc[0] = (double)fv;
-        acc[1] = (double)ff;
-        acc[2] = (double)vv;
-        acc[3] = (double)ff;  // row norm^2 for fmax
+        acc[0] = fv;
+        acc[1] = ff;
+        acc[2] = vv;
+        acc[3] = ff;  // row norm^2 for fmax
     }
     double tot[3];
-    double three[3] = {acc[0], acc[1], acc[2]};
-    block_sum<3>(three, tot);
+    T three[3] = {acc[0], acc[1], acc[2]};
+    block_sum_t<3, T>(three, tot);
     // block max of the row norms
     __shared__ double smax[TILE / 32];
-    double m = warp_max(acc[3]);
+    double m = warp_max((double)acc[3]);
     if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -29,54 +29,122 @@
 
 namespace cfneb {
 
-// ---- 3x3 symmetric square root (cyclic Jacobi, FP64) --------------------
+// ---- 3x3 symmetric square root -----------------------------------------
+//
+// FP64 division and square root are long instruction sequences on this GPU
+// and a map-back is one thread's serial chain, so the eigen-decomposition of
+// B is found in two stages: cyclic Jacobi in FP32 gives an eigenbasis Q0 to
+// ~1e-7; A = Q0^T B Q0 (FP64) is then diagonal up to ~1e-7 and two FP64
+// Jacobi sweeps on it (quadratic convergence, any eigenvalue spacing) give
+// Q and w to FP64 accuracy; S = Q diag(sqrt w) Q^T, S^-1 = Q diag(1/sqrt w) Q^T.
+// Q0's columns are re-orthonormalised in FP64 (Gram-Schmidt) first, so that
+// Q0^T B Q0 is an exact similarity transform.
 
-// Returns false if B is not positive definite.
-__device__ bool sym_sqrt3(const double *Bin, double *S) {
-    double a[3][3], q[3][3];
+// FP64 inverse of a 3x3 matrix without an FP64 division: cofactors and an
+// FP32 reciprocal of the determinant refined by r <- r (2 - det r)
+__device__ inline double inv3n(const double *m, double *o) {
+    const double c00 = m[4] * m[8] - m[5] * m[7], c01 = m[5] * m[6] - m[3] * m[8],
+                 c02 = m[3] * m[7] - m[4] * m[6];
+    const double det = m[0] * c00 + m[1] * c01 + m[2] * c02;
+    double r = (double)(1.0f / (float)det);
+    r = r * (2.0 - det * r);
+    r = r * (2.0 - det * r);
+    o[0] = c00 * r;
+    o[1] = (m[2] * m[7] - m[1] * m[8]) * r;
+    o[2] = (m[1] * m[5] - m[2] * m[4]) * r;
+    o[3] = c01 * r;
+    o[4] = (m[0] * m[8] - m[2] * m[6]) * r;
+    o[5] = (m[2] * m[3] - m[0] * m[5]) * r;
+    o[6] = c02 * r;
+    o[7] = (m[1] * m[6] - m[0] * m[7]) * r;
+    o[8] = (m[0] * m[4] - m[1] * m[3]) * r;
+    return det;
+}
+
+// one cyclic Jacobi sweep on symmetric a, accumulating rotations into q
+template <typename R>
+__device__ inline void jacobi_sweep(R (&a)[3][3], R (&q)[3][3]) {
+    for (int p = 0; p < 2; ++p)
+        for (int r = p + 1; r < 3; ++r) {
+            const R apr = a[p][r];
+            if (apr == (R)0) continue;
+            // rotation angle that annihilates a[p][r]
+            const R theta = (a[r][r] - a[p][p]) / ((R)2 * apr);
+            const R t = (theta >= (R)0 ? (R)1 : (R)-1) / (fabs(theta) + sqrt(theta * theta + (R)1));
+            const R c = (R)1 / sqrt(t * t + (R)1), s = t * c;
+            for (int k = 0; k < 3; ++k) {  // A <- A J (columns p, r)
+                const R akp = a[k][p], akr = a[k][r];
+                a[k][p] = c * akp - s * akr;
+                a[k][r] = s * akp + c * akr;
+            }
+            for (int k = 0; k < 3; ++k) {  // A <- J^T A (rows p, r)
+                const R apk = a[p][k], ark = a[r][k];
+                a[p][k] = c * apk - s * ark;
+                a[r][k] = s * apk + c * ark;
+            }
+            for (int k = 0; k < 3; ++k) {  // Q <- Q J
+                const R qkp = q[k][p], qkr = q[k][r];
+                q[k][p] = c * qkp - s * qkr;
+                q[k][r] = s * qkp + c * qkr;
+            }
+        }
+}
+
+// Returns false if B is not positive definite.  S = B^(1/2), Si = S^-1.
+__device__ bool sym_sqrt3(const double *Bin, double *S, double *Si) {
+    double B[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) B[3 * i + j] = 0.5 * (Bin[3 * i + j] + Bin[3 * j + i]);
+    float af[3][3], qf[3][3];
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
-            a[i][j] = 0.5 * (Bin[3 * i + j] + Bin[3 * j + i]);
-            q[i][j] = (i == j) ? 1.0 : 0.0;
+            af[i][j] = (float)B[3 * i + j];
+            qf[i][j] = (i == j) ? 1.0f : 0.0f;
         }
-    for (int sweep = 0; sweep < 32; ++sweep) {
-        double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
-        double diag = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
-        if (off <= 1e-34 * diag) break;
-        for (int p = 0; p < 2; ++p)
-            for (int r = p + 1; r < 3; ++r) {
-                double apr = a[p][r];
-                if (apr == 0.0) continue;
-                // rotation angle that annihilates a[p][r]
-                double theta = (a[r][r] - a[p][p]) / (2.0 * apr);
-                double t = (theta >= 0.0 ? 1.0 : -1.0) /
-                           (fabs(theta) + sqrt(theta * theta + 1.0));
-                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-                for (int k = 0; k < 3; ++k) {  // A <- A J (columns p, r)
-                    double akp = a[k][p], akr = a[k][r];
-                    a[k][p] = c * akp - s * akr;
-                    a[k][r] = s * akp + c * akr;
-                }
-                for (int k = 0; k < 3; ++k) {  // A <- J^T A (rows p, r)
-                    double apk = a[p][k], ark = a[r][k];
-                    a[p][k] = c * apk - s * ark;
-                    a[r][k] = s * apk + c * ark;
-                }
-                for (int k = 0; k < 3; ++k) {  // Q <- Q J
-                    double qkp = q[k][p], qkr = q[k][r];
-                    q[k][p] = c * qkp - s * qkr;
-                    q[k][r] = s * qkp + c * qkr;
-                }
-            }
+    for (int sweep = 0; sweep < 16; ++sweep) {
+        const float off = af[0][1] * af[0][1] + af[0][2] * af[0][2] + af[1][2] * af[1][2];
+        const float diag = af[0][0] * af[0][0] + af[1][1] * af[1][1] + af[2][2] * af[2][2];
+        if (off <= 1e-14f * diag) break;
+        jacobi_sweep<float>(af, qf);
     }
-    double w[3] = {a[0][0], a[1][1], a[2][2]};
-    bool ok = (w[0] > 0.0) && (w[1] > 0.0) && (w[2] > 0.0);
-    for (int i = 0; i < 3; ++i) w[i] = ok ? sqrt(w[i]) : 1.0;
+    // orthonormal columns in FP64, A = Q0^T B Q0, then polish
+    double q[3][3], a[3][3], tmp[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) q[i][j] = (double)qf[i][j];
+    for (int c = 0; c < 3; ++c) {
+        for (int p = 0; p < c; ++p) {
+            const double d = q[0][p] * q[0][c] + q[1][p] * q[1][c] + q[2][p] * q[2][c];
+            for (int k = 0; k < 3; ++k) q[k][c] -= d * q[k][p];
+        }
+        const double nn = q[0][c] * q[0][c] + q[1][c] * q[1][c] + q[2][c] * q[2][c];
+        const double inv = 1.0 / sqrt(nn);
+        for (int k = 0; k < 3; ++k) q[k][c] *= inv;
+    }
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j)
-            S[3 * i + j] = q[i][0] * w[0] * q[j][0] + q[i][1] * w[1] * q[j][1] +
-                           q[i][2] * w[2] * q[j][2];
-    return ok;
+            tmp[i][j] = B[3 * i] * q[0][j] + B[3 * i + 1] * q[1][j] + B[3 * i + 2] * q[2][j];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            a[i][j] = q[0][i] * tmp[0][j] + q[1][i] * tmp[1][j] + q[2][i] * tmp[2][j];
+    for (int i = 0; i < 3; ++i)
+        for (int j = i + 1; j < 3; ++j) a[i][j] = a[j][i] = 0.5 * (a[i][j] + a[j][i]);
+    jacobi_sweep<double>(a, q);
+    jacobi_sweep<double>(a, q);
+    const double w[3] = {a[0][0], a[1][1], a[2][2]};
+    if (!(w[0] > 0.0 && w[1] > 0.0 && w[2] > 0.0)) return false;
+    double sw[3], isw[3];
+    for (int k = 0; k < 3; ++k) {
+        sw[k] = sqrt(w[k]);
+        isw[k] = 1.0 / sw[k];
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            S[3 * i + j] = q[i][0] * sw[0] * q[j][0] + q[i][1] * sw[1] * q[j][1] +
+                           q[i][2] * sw[2] * q[j][2];
+            Si[3 * i + j] = q[i][0] * isw[0] * q[j][0] + q[i][1] * isw[1] * q[j][1] +
+                            q[i][2] * isw[2] * q[j][2];
+        }
+    return true;
 }
 
 template <typename T>
@@ -88,46 +156,47 @@ __global__ void k_mapback(const ImgRef *imgs, int count, BandDev *bands) {
     BandParams *bp = b.bp;
     ImgScalars &sc = b.sc[r.img];
     const T *Xl = (const T *)b.X + ((size_t)r.img * b.rows + b.n) * 3;
-    double D[9];
+    double D[9], Di[9];
     bool ok = true;
     if (!bp->filter) {
-        for (int i = 0; i < 9; ++i) D[i] = (i % 4 == 0) ? 1.0 : 0.0;
+        for (int i = 0; i < 9; ++i) D[i] = Di[i] = (i % 4 == 0) ? 1.0 : 0.0;
     } else {
         double L[9];
         for (int i = 0; i < 9; ++i) L[i] = (double)Xl[i] / bp->c;
         if (bp->variant == 0) {
-            ok = sym_sqrt3(L, D);
+            ok = sym_sqrt3(L, D, Di);
         } else {
             for (int i = 0; i < 9; ++i) D[i] = L[i];
-            ok = det3(D) > 0.0;
+            ok = inv3n(D, Di) > 0.0;
         }
     }
     if (!ok) {
         atomicOr(&bp->status, ST_NOT_SPD);
-        for (int i = 0; i < 9; ++i) D[i] = (i % 4 == 0) ? 1.0 : 0.0;
+        for (int i = 0; i < 9; ++i) D[i] = Di[i] = (i % 4 == 0) ? 1.0 : 0.0;
     }
     double h[9];
     matmul3(bp->h0, D, h);
     for (int i = 0; i < 9; ++i) {
         sc.D[i] = D[i];
+        sc.Dinv[i] = Di[i];
         sc.h[i] = h[i];
     }
-    inv3(D, sc.Dinv);
-    inv3(h, sc.hinv);
-    double omega = fabs(det3(h));
+    matmul3(Di, bp->h0inv, sc.hinv);  // (h0 D)^-1 = D^-1 h0^-1
+    const double omega = fabs(det3(h));
     sc.omega = omega;
-    // perpendicular widths w_a = Omega / |h_b x h_c|
-    double w[3];
+    // perpendicular widths w_a = Omega / |h_b x h_c| (only choose the bin
+    // grid: FP32, shaded down by 1e-5 so the stencil is never too narrow)
+    float w[3];
     for (int a = 0; a < 3; ++a) {
         const double *u = h + 3 * ((a + 1) % 3), *v = h + 3 * ((a + 2) % 3);
-        double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2],
-               cz = u[0] * v[1] - u[1] * v[0];
-        w[a] = omega / sqrt(cx * cx + cy * cy + cz * cz);
+        const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2],
+                     cz = u[0] * v[1] - u[1] * v[0];
+        w[a] = (float)omega / sqrtf((float)(cx * cx + cy * cy + cz * cz)) * 0.99999f;
     }
     int nb[3];
     for (int a = 0; a < 3; ++a) {
-        double q = floor(w[a] / bp->bin_w);
-        nb[a] = q < 1.0 ? 1 : (q > 1024.0 ? 1024 : (int)q);
+        const float q = floorf(w[a] / (float)bp->bin_w);
+        nb[a] = q < 1.0f ? 1 : (q > 1024.0f ? 1024 : (int)q);
     }
     // keep within the bin capacity: coarser bins are always correct
     while ((long long)nb[0] * nb[1] * nb[2] > b.nbins_cap) {
@@ -143,8 +212,8 @@ __global__ void k_mapback(const ImgRef *imgs, int count, BandDev *bands) {
         for (int c = 0; c < 3; ++c) bmax = fmax(bmax, fabs(h[3 * a + c] / nb[a]));
     const double q = ldexp(1.0, ilogb(bmax) + 1 - 19);
     for (int a = 0; a < 3; ++a) {
-        double bw = w[a] / nb[a];
-        int m = (int)ceil(bp->rc / bw);
+        const float bw = w[a] / nb[a];
+        const int m = (int)ceilf((float)bp->rc / bw);
         sc.m[a] = m < 1 ? 1 : (m > MAX_STENCIL ? MAX_STENCIL : m);
         sc.nb[a] = nb[a];
         for (int c = 0; c < 3; ++c) {

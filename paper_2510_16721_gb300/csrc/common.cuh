@@ -102,6 +102,7 @@ struct BandDev {
     int *nbr_slot;       // [ncap][MAXN][n]
     int *nbr_code;       // [ncap][MAXN][n]
     void *nbr_P;         // [ncap][3*MAXN][n] of T
+    void *nbr_R;         // [ncap][4*MAXN][n] of T: pair vector (leading part), r - R
     // partial sums
     double *atom_part;   // [ncap][atpi][NPART]
     double *row_part;    // [ncap][rtpi][NPART]
@@ -198,6 +199,32 @@ __device__ inline void block_sum(double (&v)[K], double *out) {
     __syncthreads();  // red[] may be reused by a later call
 }
 
+// Sum K per-thread values of type T over a TILE-thread block: within each
+// warp in T (fixed butterfly), across warps in FP64; thread 0 receives the
+// totals.  With T = float the long accumulations (across warps, tiles and
+// images) stay FP64 while the per-element work avoids FP64 arithmetic.
+template <int K, typename T>
+__device__ inline void block_sum_t(T (&v)[K], double *out) {
+    __shared__ double red[TILE / 32][K > 0 ? K : 1];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        T s = v[k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[w][k] = (double)s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double s = 0.0;
+            for (int q = 0; q < TILE / 32; ++q) s += red[q][k];
+            out[k] = s;
+        }
+    }
+    __syncthreads();
+}
+
 // ---- launchers (defined in the kernel translation units) ---------------
 
 template <typename T>
@@ -213,6 +240,8 @@ void launch_bin_order(const ImgRef *imgs, int count, int max_bins, BandDev *band
                       cudaStream_t s);
 template <typename T>
 void launch_lj(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
+template <typename T>
+void launch_tersoff_list(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 template <typename T>
 void launch_tersoff_partials(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 template <typename T>

@@ -39,20 +39,17 @@ __device__ inline void for_neighbours64(const BandDev &b, int img, int t, const 
     const int b0 = bin / (nb1 * nb2), b1 = (bin / nb2) % nb1, b2 = bin % nb2;
     const T4 oi = off[t], oil = offl[t];
     for (int d0 = -sc.m[0]; d0 <= sc.m[0]; ++d0) {
-        const int u0 = b0 + d0;
-        int w0 = u0 % nb0;
-        w0 += (w0 < 0) ? nb0 : 0;
-        const int t0 = (u0 - w0) / nb0;
+        int w0 = b0 + d0, t0 = 0;
+        while (w0 < 0) { w0 += nb0; --t0; }
+        while (w0 >= nb0) { w0 -= nb0; ++t0; }
         for (int d1 = -sc.m[1]; d1 <= sc.m[1]; ++d1) {
-            const int u1 = b1 + d1;
-            int w1 = u1 % nb1;
-            w1 += (w1 < 0) ? nb1 : 0;
-            const int t1 = (u1 - w1) / nb1;
+            int w1 = b1 + d1, t1 = 0;
+            while (w1 < 0) { w1 += nb1; --t1; }
+            while (w1 >= nb1) { w1 -= nb1; ++t1; }
             for (int d2 = -sc.m[2]; d2 <= sc.m[2]; ++d2) {
-                const int u2 = b2 + d2;
-                int w2 = u2 % nb2;
-                w2 += (w2 < 0) ? nb2 : 0;
-                const int t2 = (u2 - w2) / nb2;
+                int w2 = b2 + d2, t2 = 0;
+                while (w2 < 0) { w2 += nb2; --t2; }
+                while (w2 >= nb2) { w2 -= nb2; ++t2; }
                 const int w = (w0 * nb1 + w1) * nb2 + w2;
                 double c[3];
                 for (int k = 0; k < 3; ++k)

@@ -48,13 +48,14 @@ struct CudaFail {
 
 enum KernelId {
     K_MAPBACK, K_BIN_ASSIGN, K_BIN_TILESUM, K_BIN_TILESCAN, K_BIN_SCANFILL, K_BIN_SCATTER,
-    K_BIN_ORDER, K_LJ, K_TERS_PARTIALS, K_TERS_GATHER, K_IMAGE_FINALIZE, K_BAND_DOTS,
-    K_DOTS_REDUCE, K_NEB_COEF, K_NEB_FORCE, K_FIRE_SCALARS, K_FIRE_UPDATE, K_COUNT
+    K_BIN_ORDER, K_LJ, K_TERS_LIST, K_TERS_PARTIALS, K_TERS_GATHER, K_IMAGE_FINALIZE,
+    K_BAND_DOTS, K_DOTS_REDUCE, K_NEB_COEF, K_NEB_FORCE, K_FIRE_SCALARS, K_FIRE_UPDATE, K_COUNT
 };
 const char *kKernelNames[K_COUNT] = {
     "mapback", "bin_assign", "bin_tilesum", "bin_tilescan", "bin_scanfill", "bin_scatter",
-    "bin_order", "lj_force", "tersoff_partials", "tersoff_gather", "image_finalize",
-    "band_dots", "dots_reduce", "neb_coef", "neb_force", "fire_scalars", "fire_update"};
+    "bin_order", "lj_force", "tersoff_list", "tersoff_partials", "tersoff_gather",
+    "image_finalize", "band_dots", "dots_reduce", "neb_coef", "neb_force", "fire_scalars",
+    "fire_update"};
 
 const double kTersoff1988C[11] = {1393.6, 346.74, 3.4879, 2.2119, 1.5724e-7, 0.72751,
                                   38049.0, 4.3484, -0.57058, 1.95, 0.15};
@@ -270,6 +271,8 @@ void enqueue_eval_set(const LaunchSet &ls, Launcher &L, bool forces = true) {
         L.pre(K_LJ); launch_lj<T>(ls.atiles_lj, ls.n_lj, d, s); L.post(K_LJ);
     }
     if (ls.n_ters) {
+        L.pre(K_TERS_LIST); launch_tersoff_list<T>(ls.atiles_ters, ls.n_ters, d, s);
+        L.post(K_TERS_LIST);
         L.pre(K_TERS_PARTIALS); launch_tersoff_partials<T>(ls.atiles_ters, ls.n_ters, d, s);
         L.post(K_TERS_PARTIALS);
         L.pre(K_TERS_GATHER); launch_tersoff_gather<T>(ls.atiles_ters, ls.n_ters, d, s);
@@ -293,7 +296,7 @@ void enqueue_step_set(const LaunchSet &ls, Launcher &L) {
 }
 
 int launches_in_set(const LaunchSet &ls) {
-    return 7 + (ls.n_lj ? 1 : 0) + (ls.n_ters ? 2 : 0) + 1 + 6;
+    return 7 + (ls.n_lj ? 1 : 0) + (ls.n_ters ? 3 : 0) + 1 + 6;
 }
 
 LaunchSet band_set(cfneb_band *b, const ImgRef *imgs, int nimg, const Tile *atiles, int nat) {
@@ -725,6 +728,7 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
         d.nbr_slot = (int *)dalloc(b, na * MAXN_TERSOFF * sizeof(int));
         d.nbr_code = (int *)dalloc(b, na * MAXN_TERSOFF * sizeof(int));
         d.nbr_P = dalloc(b, na * 3 * MAXN_TERSOFF * b->ts);
+        d.nbr_R = dalloc(b, na * 4 * MAXN_TERSOFF * b->ts);
     }
     d.atom_part = (double *)dalloc(b, nc * d.atpi * NPART * sizeof(double));
     d.row_part = (double *)dalloc(b, nc * d.rtpi * NPART * sizeof(double));

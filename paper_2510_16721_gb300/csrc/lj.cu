@@ -59,20 +59,17 @@ __global__ void __launch_bounds__(TILE) k_lj(const Tile *tiles, BandDev *bands) 
         const int b0 = bin / (nb1 * nb2), b1 = (bin / nb2) % nb1, b2 = bin % nb2;
         const T4 oi = off[t];
         for (int d0 = -s_m[0]; d0 <= s_m[0]; ++d0) {
-            const int u0 = b0 + d0;
-            int w0 = u0 % s_nb[0];
-            w0 += (w0 < 0) ? s_nb[0] : 0;
-            const int t0 = (u0 - w0) / s_nb[0];
+            int w0 = b0 + d0, t0 = 0;
+            while (w0 < 0) { w0 += s_nb[0]; --t0; }
+            while (w0 >= s_nb[0]) { w0 -= s_nb[0]; ++t0; }
             for (int d1 = -s_m[1]; d1 <= s_m[1]; ++d1) {
-                const int u1 = b1 + d1;
-                int w1 = u1 % nb1;
-                w1 += (w1 < 0) ? nb1 : 0;
-                const int t1 = (u1 - w1) / nb1;
+                int w1 = b1 + d1, t1 = 0;
+                while (w1 < 0) { w1 += nb1; --t1; }
+                while (w1 >= nb1) { w1 -= nb1; ++t1; }
                 for (int d2 = -s_m[2]; d2 <= s_m[2]; ++d2) {
-                    const int u2 = b2 + d2;
-                    int w2 = u2 % nb2;
-                    w2 += (w2 < 0) ? nb2 : 0;
-                    const int t2 = (u2 - w2) / nb2;
+                    int w2 = b2 + d2, t2 = 0;
+                    while (w2 < 0) { w2 += nb2; --t2; }
+                    while (w2 >= nb2) { w2 -= nb2; ++t2; }
                     const int w = (w0 * nb1 + w1) * nb2 + w2;
                     // displacement between the two bin centres (exact in T
                     // for |delta| <= 1 in orthorhombic cells)
@@ -127,20 +124,20 @@ __global__ void __launch_bounds__(TILE) k_lj(const Tile *tiles, BandDev *bands) 
         F[2] = g2;
     }
     // U_i = 1/2 sum_j [4 eps (sr12 - sr6) - phi(rc)];  V = -1/2 sum r (x) f
-    double acc[11];
-    acc[0] = 0.5 * ((double)eps4 * (double)e - p.ephi_c * cnt);
-    acc[10] = (double)cnt;
-    acc[1] = -0.5 * (double)v00;
-    acc[2] = -0.5 * (double)v01;
-    acc[3] = -0.5 * (double)v02;
-    acc[4] = -0.5 * (double)v01;
-    acc[5] = -0.5 * (double)v11;
-    acc[6] = -0.5 * (double)v12;
-    acc[7] = -0.5 * (double)v02;
-    acc[8] = -0.5 * (double)v12;
-    acc[9] = -0.5 * (double)v22;
-    double tot[11];
-    block_sum<11>(acc, tot);
+    T acc[8];
+    acc[0] = (T)0.5 * (eps4 * e - (T)p.ephi_c * (T)cnt);
+    acc[1] = (T)(-0.5) * v00;
+    acc[2] = (T)(-0.5) * v01;
+    acc[3] = (T)(-0.5) * v02;
+    acc[4] = (T)(-0.5) * v11;
+    acc[5] = (T)(-0.5) * v12;
+    acc[6] = (T)(-0.5) * v22;
+    acc[7] = (T)cnt;
+    double r8[8];
+    block_sum_t<8, T>(acc, r8);
+    // symmetric virial, row-major
+    const double tot[11] = {r8[0], r8[1], r8[2], r8[3], r8[2], r8[4], r8[5],
+                            r8[3], r8[5], r8[6], r8[7]};
     if (threadIdx.x == 0) {
         double *part = b.atom_part + ((size_t)tl.img * b.atpi + tl.t) * NPART;
         for (int k = 0; k < 11; ++k) part[k] = tot[k];

@@ -139,9 +139,174 @@ __device__ inline void gfun(const TP<T> &q, T cs, T &g, T &dg) {
     dg = -(T)2 * q.c2 * u / (den * den);
 }
 
+// atoms with at most this many neighbours take the register-resident path
+// (their neighbour loops are unrolled); the rest take a looped path
+constexpr int NFAST = 4;
+
+// Neighbour entries of slot t inside R + D into the global list (slot, stencil
+// code, leading pair vector, s = r - R); returns the total count.
 template <typename T>
-__global__ void __launch_bounds__(TILE) k_ters_partials(const Tile *tiles, BandDev *bands) {
+__device__ inline int ters_collect_list(const TP<T> &q, const BandDev &b, int img, int t,
+                                        const T *s_bv, const T *s_dh, const int *s_nb,
+                                        const int *s_m, T *nR) {
     using T4 = typename Vec4<T>::type;
+    const int n = b.n;
+    const size_t base = (size_t)img * n;
+    const T4 *off = (const T4 *)b.slot_off + base;
+    const T4 *offl = (const T4 *)b.slot_off_lo + base;
+    const int *start = b.bin_start + (size_t)img * (b.nbins_cap + 1);
+    int *nslot = b.nbr_slot + (size_t)img * MAXN_TERSOFF * n;
+    int *ncode = b.nbr_code + (size_t)img * MAXN_TERSOFF * n;
+    const T rc2_screen = q.Rhi * q.Rhi * (T)1.00001;
+    const int bin = b.slot_bin[base + t];
+    const int nb1 = s_nb[1], nb2 = s_nb[2];
+    const int b0 = bin / (nb1 * nb2), b1 = (bin / nb2) % nb1, b2 = bin % nb2;
+    const T4 oi = off[t];
+    const T4 oil = offl[t];
+    int total = 0;
+    for (int d0 = -s_m[0]; d0 <= s_m[0]; ++d0) {
+        int w0 = b0 + d0, t0 = 0;
+        while (w0 < 0) { w0 += s_nb[0]; --t0; }
+        while (w0 >= s_nb[0]) { w0 -= s_nb[0]; ++t0; }
+        for (int d1 = -s_m[1]; d1 <= s_m[1]; ++d1) {
+            int w1 = b1 + d1, t1 = 0;
+            while (w1 < 0) { w1 += nb1; --t1; }
+            while (w1 >= nb1) { w1 -= nb1; ++t1; }
+            for (int d2 = -s_m[2]; d2 <= s_m[2]; ++d2) {
+                int w2 = b2 + d2, t2 = 0;
+                while (w2 < 0) { w2 += nb2; --t2; }
+                while (w2 >= nb2) { w2 -= nb2; ++t2; }
+                const int w = (w0 * nb1 + w1) * nb2 + w2;
+                // bin-centre displacement: exact (quantised bin vectors)
+                const T cx = d0 * s_bv[0] + d1 * s_bv[3] + d2 * s_bv[6];
+                const T cy = d0 * s_bv[1] + d1 * s_bv[4] + d2 * s_bv[7];
+                const T cz = d0 * s_bv[2] + d1 * s_bv[5] + d2 * s_bv[8];
+                // periodic-wrap remainder (tiny)
+                const T wx = t0 * s_dh[0] + t1 * s_dh[3] + t2 * s_dh[6];
+                const T wy = t0 * s_dh[1] + t1 * s_dh[4] + t2 * s_dh[7];
+                const T wz = t0 * s_dh[2] + t1 * s_dh[5] + t2 * s_dh[8];
+                const T ux0 = (cx + wx) - oi.x, uy0 = (cy + wy) - oi.y, uz0 = (cz + wz) - oi.z;
+                const int q1 = start[w + 1];
+                for (int qs = start[w]; qs < q1; ++qs) {
+                    const T4 oj = off[qs];
+                    const T ux = oj.x + ux0, uy = oj.y + uy0, uz = oj.z + uz0;
+                    if (ux * ux + uy * uy + uz * uz >= rc2_screen) continue;
+                    const T4 ojl = offl[qs];
+                    T x, y, z, ex1, ey1, ez1, ex2, ey2, ez2;
+                    two_sum(oj.x, -oi.x, x, ex1);
+                    two_sum(oj.y, -oi.y, y, ey1);
+                    two_sum(oj.z, -oi.z, z, ez1);
+                    two_sum(x, cx, x, ex2);
+                    two_sum(y, cy, y, ey2);
+                    two_sum(z, cz, z, ez2);
+                    T xl = ((ojl.x - oil.x) + wx) + (ex1 + ex2);
+                    T yl = ((ojl.y - oil.y) + wy) + (ey1 + ey2);
+                    T zl = ((ojl.z - oil.z) + wz) + (ez1 + ez2);
+                    // renormalise: the leading part (used for directions)
+                    // takes the wrap remainder, the low part keeps the rest
+                    fast_two_sum(x, xl, x, xl);
+                    fast_two_sum(y, yl, y, yl);
+                    fast_two_sum(z, zl, z, zl);
+                    T r, s;
+                    dist_s(q, x, y, z, xl, yl, zl, r, s);
+                    if (!(sub_rn(s, q.D) < q.Dlo && r > (T)0)) continue;
+                    if (total < MAXN_TERSOFF) {
+                        nslot[(size_t)total * n + t] = qs;
+                        ncode[(size_t)total * n + t] = pack_code(d0, d1, d2);
+                        nR[(size_t)(4 * total + 0) * n + t] = x;
+                        nR[(size_t)(4 * total + 1) * n + t] = y;
+                        nR[(size_t)(4 * total + 2) * n + t] = z;
+                        nR[(size_t)(4 * total + 3) * n + t] = s;
+                    }
+                    ++total;
+                }
+            }
+        }
+    }
+    return total;
+}
+
+// Site energy U_i, partials P_ij (written to the list) and the site virial
+// for the cnt <= NM neighbours in the arrays.
+template <typename T, int NM>
+__device__ inline void ters_site(const TP<T> &q, int cnt, const T (&rx)[NM], const T (&ry)[NM],
+                                 const T (&rz)[NM], const T (&rd)[NM], const T (&sr)[NM],
+                                 T *nP, int n, int t, T &U, T (&vir)[9]) {
+    T fc[NM], dfc[NM], Px[NM], Py[NM], Pz[NM];
+#pragma unroll (NM <= NFAST ? NM : 1)
+    for (int j = 0; j < NM; ++j) {
+        fc[j] = dfc[j] = (T)0;
+        if (j < cnt) cutoff(q, sr[j], fc[j], dfc[j]);
+        Px[j] = Py[j] = Pz[j] = (T)0;
+    }
+#pragma unroll (NM <= NFAST ? NM : 1)
+    for (int j = 0; j < NM; ++j) {
+        if (j >= cnt) continue;
+        // zeta_ij and the bond order
+        T zeta = 0;
+#pragma unroll (NM <= NFAST ? NM : 1)
+        for (int k = 0; k < NM; ++k) {
+            if (k == j || k >= cnt) continue;
+            const T cs = (rx[j] * rx[k] + ry[j] * ry[k] + rz[j] * rz[k]) / (rd[j] * rd[k]);
+            T g, dg;
+            gfun(q, cs, g, dg);
+            zeta += fc[k] * g;
+        }
+        T bij = (T)1, dbij = (T)0;
+        if (zeta > (T)0) {
+            const T x = M<T>::ex(q.n * M<T>::lg(q.beta * zeta));
+            bij = M<T>::ex(-q.inv2n * M<T>::l1p(x));
+            dbij = (T)(-0.5) * bij * x / (((T)1 + x) * zeta);
+        }
+        const T fr = q.AeR * M<T>::ex(-q.l1 * sr[j]);
+        const T fa = -q.BeR * M<T>::ex(-q.l2 * sr[j]);
+        const T dfr = -q.l1 * fr, dfa = -q.l2 * fa;
+        U += (T)0.5 * fc[j] * (fr + bij * fa);
+        const T radial = (T)0.5 * (dfc[j] * (fr + bij * fa) + fc[j] * (dfr + bij * dfa)) / rd[j];
+        Px[j] += radial * rx[j];
+        Py[j] += radial * ry[j];
+        Pz[j] += radial * rz[j];
+        const T pref = (T)0.5 * fc[j] * fa * dbij;
+        if (pref == (T)0) continue;
+#pragma unroll (NM <= NFAST ? NM : 1)
+        for (int k = 0; k < NM; ++k) {
+            if (k == j || k >= cnt) continue;
+            const T ijk = (T)1 / (rd[j] * rd[k]);
+            const T cs = (rx[j] * rx[k] + ry[j] * ry[k] + rz[j] * rz[k]) * ijk;
+            T g, dg;
+            gfun(q, cs, g, dg);
+            // d cos / d r^ij and d cos / d r^ik
+            const T aj = cs / (rd[j] * rd[j]), ak = cs / (rd[k] * rd[k]);
+            const T sj = pref * fc[k] * dg;
+            Px[j] += sj * (rx[k] * ijk - aj * rx[j]);
+            Py[j] += sj * (ry[k] * ijk - aj * ry[j]);
+            Pz[j] += sj * (rz[k] * ijk - aj * rz[j]);
+            const T rk = pref * dfc[k] * g / rd[k];
+            Px[k] += rk * rx[k] + sj * (rx[j] * ijk - ak * rx[k]);
+            Py[k] += rk * ry[k] + sj * (ry[j] * ijk - ak * ry[k]);
+            Pz[k] += rk * rz[k] + sj * (rz[j] * ijk - ak * rz[k]);
+        }
+    }
+#pragma unroll (NM <= NFAST ? NM : 1)
+    for (int j = 0; j < NM; ++j) {
+        if (j >= cnt) continue;
+        nP[(size_t)(3 * j + 0) * n + t] = Px[j];
+        nP[(size_t)(3 * j + 1) * n + t] = Py[j];
+        nP[(size_t)(3 * j + 2) * n + t] = Pz[j];
+        // V_mn -= r_m P_n
+        vir[0] -= rx[j] * Px[j]; vir[1] -= rx[j] * Py[j]; vir[2] -= rx[j] * Pz[j];
+        vir[3] -= ry[j] * Px[j]; vir[4] -= ry[j] * Py[j]; vir[5] -= ry[j] * Pz[j];
+        vir[6] -= rz[j] * Px[j]; vir[7] -= rz[j] * Py[j]; vir[8] -= rz[j] * Pz[j];
+    }
+}
+
+
+// Neighbour list of one step: one light thread per atom walks the cell-list
+// stencil (high occupancy hides the chained bin loads) and writes, for each
+// entry inside R + D, the neighbour slot, the stencil code, the leading part
+// of the pair vector and s = r - R, coalesced as [entry][atom].
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_ters_list(const Tile *tiles, BandDev *bands) {
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
     const ImgScalars &sc = b.sc[tl.img];
@@ -156,165 +321,72 @@ __global__ void __launch_bounds__(TILE) k_ters_partials(const Tile *tiles, BandD
         s_m[threadIdx.x] = sc.m[threadIdx.x];
     }
     __syncthreads();
+    const int n = b.n;
+    const int t = tl.t * TILE + threadIdx.x;
+    if (t >= n) return;
+    TP<T> q;
+    q.load(*(const TersoffParams *)b.bp->pot);
+    T *nR = (T *)b.nbr_R + (size_t)tl.img * 4 * MAXN_TERSOFF * n;
+    const int total = ters_collect_list<T>(q, b, tl.img, t, s_bv, s_dh, s_nb, s_m, nR);
+    b.nbr_cnt[(size_t)tl.img * n + t] = total < MAXN_TERSOFF ? total : MAXN_TERSOFF;
+    if (total > MAXN_TERSOFF) atomicOr(&b.bp->status, ST_NBR_OVERFLOW);
+}
+
+// load the neighbour records of slot t into arrays (compile-time indices
+// for small NM: registers)
+template <typename T, int NM>
+__device__ inline void ters_load(const TP<T> &q, const T *nR, int n, int t, int cnt,
+                                 T (&rx)[NM], T (&ry)[NM], T (&rz)[NM], T (&rd)[NM],
+                                 T (&sr)[NM]) {
+#pragma unroll (NM <= NFAST ? NM : 1)
+    for (int k = 0; k < NM; ++k) {
+        if (k >= cnt) {
+            rx[k] = ry[k] = rz[k] = sr[k] = (T)0;
+            rd[k] = (T)1;
+            continue;
+        }
+        rx[k] = nR[(size_t)(4 * k + 0) * n + t];
+        ry[k] = nR[(size_t)(4 * k + 1) * n + t];
+        rz[k] = nR[(size_t)(4 * k + 2) * n + t];
+        sr[k] = nR[(size_t)(4 * k + 3) * n + t];
+        rd[k] = q.R + sr[k];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_ters_partials(const Tile *tiles, BandDev *bands) {
+    Tile tl = tiles[blockIdx.x];
+    BandDev &b = bands[tl.band];
     TP<T> q;
     q.load(*(const TersoffParams *)b.bp->pot);
     const int n = b.n;
     const int t = tl.t * TILE + threadIdx.x;
     const size_t base = (size_t)tl.img * n;
-    const T4 *off = (const T4 *)b.slot_off + base;
-    const T4 *offl = (const T4 *)b.slot_off_lo + base;
-    const int *start = b.bin_start + (size_t)tl.img * (b.nbins_cap + 1);
-    int *nslot = b.nbr_slot + (size_t)tl.img * MAXN_TERSOFF * n;
-    int *ncode = b.nbr_code + (size_t)tl.img * MAXN_TERSOFF * n;
     T *nP = (T *)b.nbr_P + (size_t)tl.img * 3 * MAXN_TERSOFF * n;
-    const T rc2_screen = q.Rhi * q.Rhi * (T)1.00001;
-
-    T rx[MAXN_TERSOFF], ry[MAXN_TERSOFF], rz[MAXN_TERSOFF], rd[MAXN_TERSOFF];
-    T sr[MAXN_TERSOFF];  // r - R
-    T fc[MAXN_TERSOFF], dfc[MAXN_TERSOFF];
-    T Px[MAXN_TERSOFF], Py[MAXN_TERSOFF], Pz[MAXN_TERSOFF];
-    int cnt = 0, total = 0;
+    const T *nR = (const T *)b.nbr_R + (size_t)tl.img * 4 * MAXN_TERSOFF * n;
+    int cnt = 0;
     T U = 0;
     T vir[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (t < n) {
-        const int bin = b.slot_bin[base + t];
-        const int nb1 = s_nb[1], nb2 = s_nb[2];
-        const int b0 = bin / (nb1 * nb2), b1 = (bin / nb2) % nb1, b2 = bin % nb2;
-        const T4 oi = off[t];
-        const T4 oil = offl[t];
-        for (int d0 = -s_m[0]; d0 <= s_m[0]; ++d0) {
-            const int u0 = b0 + d0;
-            int w0 = u0 % s_nb[0];
-            w0 += (w0 < 0) ? s_nb[0] : 0;
-            const int t0 = (u0 - w0) / s_nb[0];
-            for (int d1 = -s_m[1]; d1 <= s_m[1]; ++d1) {
-                const int u1 = b1 + d1;
-                int w1 = u1 % nb1;
-                w1 += (w1 < 0) ? nb1 : 0;
-                const int t1 = (u1 - w1) / nb1;
-                for (int d2 = -s_m[2]; d2 <= s_m[2]; ++d2) {
-                    const int u2 = b2 + d2;
-                    int w2 = u2 % nb2;
-                    w2 += (w2 < 0) ? nb2 : 0;
-                    const int t2 = (u2 - w2) / nb2;
-                    const int w = (w0 * nb1 + w1) * nb2 + w2;
-                    // bin-centre displacement: exact (quantised bin vectors)
-                    const T cx = d0 * s_bv[0] + d1 * s_bv[3] + d2 * s_bv[6];
-                    const T cy = d0 * s_bv[1] + d1 * s_bv[4] + d2 * s_bv[7];
-                    const T cz = d0 * s_bv[2] + d1 * s_bv[5] + d2 * s_bv[8];
-                    // periodic-wrap remainder (tiny)
-                    const T wx = t0 * s_dh[0] + t1 * s_dh[3] + t2 * s_dh[6];
-                    const T wy = t0 * s_dh[1] + t1 * s_dh[4] + t2 * s_dh[7];
-                    const T wz = t0 * s_dh[2] + t1 * s_dh[5] + t2 * s_dh[8];
-                    const T ux0 = (cx + wx) - oi.x, uy0 = (cy + wy) - oi.y,
-                            uz0 = (cz + wz) - oi.z;
-                    const int q1 = start[w + 1];
-                    for (int qs = start[w]; qs < q1; ++qs) {
-                        const T4 oj = off[qs];
-                        const T ux = oj.x + ux0, uy = oj.y + uy0, uz = oj.z + uz0;
-                        if (ux * ux + uy * uy + uz * uz >= rc2_screen) continue;
-                        const T4 ojl = offl[qs];
-                        T x, y, z, ex1, ey1, ez1, ex2, ey2, ez2;
-                        two_sum(oj.x, -oi.x, x, ex1);
-                        two_sum(oj.y, -oi.y, y, ey1);
-                        two_sum(oj.z, -oi.z, z, ez1);
-                        two_sum(x, cx, x, ex2);
-                        two_sum(y, cy, y, ey2);
-                        two_sum(z, cz, z, ez2);
-                        T xl = ((ojl.x - oil.x) + wx) + (ex1 + ex2);
-                        T yl = ((ojl.y - oil.y) + wy) + (ey1 + ey2);
-                        T zl = ((ojl.z - oil.z) + wz) + (ez1 + ez2);
-                        // renormalise: the leading part (used for directions)
-                        // takes the wrap remainder, the low part keeps the rest
-                        fast_two_sum(x, xl, x, xl);
-                        fast_two_sum(y, yl, y, yl);
-                        fast_two_sum(z, zl, z, zl);
-                        T r, s;
-                        dist_s(q, x, y, z, xl, yl, zl, r, s);
-                        if (sub_rn(s, q.D) < q.Dlo && r > (T)0) {
-                            if (cnt < MAXN_TERSOFF) {
-                                rx[cnt] = x; ry[cnt] = y; rz[cnt] = z;
-                                rd[cnt] = r;
-                                sr[cnt] = s;
-                                nslot[(size_t)cnt * n + t] = qs;
-                                ncode[(size_t)cnt * n + t] = pack_code(d0, d1, d2);
-                                ++cnt;
-                            }
-                            ++total;
-                        }
-                    }
-                }
-            }
-        }
-        b.nbr_cnt[base + t] = cnt;
-        if (total > MAXN_TERSOFF) atomicOr(&b.bp->status, ST_NBR_OVERFLOW);
-        for (int j = 0; j < cnt; ++j) {
-            cutoff(q, sr[j], fc[j], dfc[j]);
-            Px[j] = Py[j] = Pz[j] = (T)0;
-        }
-        for (int j = 0; j < cnt; ++j) {
-            // zeta_ij and the bond order
-            T zeta = 0;
-            for (int k = 0; k < cnt; ++k) {
-                if (k == j) continue;
-                T cs = (rx[j] * rx[k] + ry[j] * ry[k] + rz[j] * rz[k]) / (rd[j] * rd[k]);
-                T g, dg;
-                gfun(q, cs, g, dg);
-                zeta += fc[k] * g;
-            }
-            T bij = (T)1, dbij = (T)0;
-            if (zeta > (T)0) {
-                T x = M<T>::ex(q.n * M<T>::lg(q.beta * zeta));
-                bij = M<T>::ex(-q.inv2n * M<T>::l1p(x));
-                dbij = (T)(-0.5) * bij * x / (((T)1 + x) * zeta);
-            }
-            const T fr = q.AeR * M<T>::ex(-q.l1 * sr[j]);
-            const T fa = -q.BeR * M<T>::ex(-q.l2 * sr[j]);
-            const T dfr = -q.l1 * fr, dfa = -q.l2 * fa;
-            U += (T)0.5 * fc[j] * (fr + bij * fa);
-            const T radial =
-                (T)0.5 * (dfc[j] * (fr + bij * fa) + fc[j] * (dfr + bij * dfa)) / rd[j];
-            Px[j] += radial * rx[j];
-            Py[j] += radial * ry[j];
-            Pz[j] += radial * rz[j];
-            const T pref = (T)0.5 * fc[j] * fa * dbij;
-            if (pref == (T)0) continue;
-            for (int k = 0; k < cnt; ++k) {
-                if (k == j) continue;
-                const T ijk = (T)1 / (rd[j] * rd[k]);
-                const T cs = (rx[j] * rx[k] + ry[j] * ry[k] + rz[j] * rz[k]) * ijk;
-                T g, dg;
-                gfun(q, cs, g, dg);
-                // d cos / d r^ij and d cos / d r^ik
-                const T aj = cs / (rd[j] * rd[j]), ak = cs / (rd[k] * rd[k]);
-                const T sj = pref * fc[k] * dg;
-                Px[j] += sj * (rx[k] * ijk - aj * rx[j]);
-                Py[j] += sj * (ry[k] * ijk - aj * ry[j]);
-                Pz[j] += sj * (rz[k] * ijk - aj * rz[j]);
-                const T rk = pref * dfc[k] * g / rd[k];
-                const T sk = pref * fc[k] * dg;
-                Px[k] += rk * rx[k] + sk * (rx[j] * ijk - ak * rx[k]);
-                Py[k] += rk * ry[k] + sk * (ry[j] * ijk - ak * ry[k]);
-                Pz[k] += rk * rz[k] + sk * (rz[j] * ijk - ak * rz[k]);
-            }
-        }
-        for (int j = 0; j < cnt; ++j) {
-            nP[(size_t)(3 * j + 0) * n + t] = Px[j];
-            nP[(size_t)(3 * j + 1) * n + t] = Py[j];
-            nP[(size_t)(3 * j + 2) * n + t] = Pz[j];
-            // V_mn -= r_m P_n
-            vir[0] -= rx[j] * Px[j]; vir[1] -= rx[j] * Py[j]; vir[2] -= rx[j] * Pz[j];
-            vir[3] -= ry[j] * Px[j]; vir[4] -= ry[j] * Py[j]; vir[5] -= ry[j] * Pz[j];
-            vir[6] -= rz[j] * Px[j]; vir[7] -= rz[j] * Py[j]; vir[8] -= rz[j] * Pz[j];
+        cnt = b.nbr_cnt[base + t];
+        if (cnt <= NFAST) {
+            T rx[NFAST], ry[NFAST], rz[NFAST], rd[NFAST], sr[NFAST];
+            ters_load<T, NFAST>(q, nR, n, t, cnt, rx, ry, rz, rd, sr);
+            ters_site<T, NFAST>(q, cnt, rx, ry, rz, rd, sr, nP, n, t, U, vir);
+        } else {
+            T Rx[MAXN_TERSOFF], Ry[MAXN_TERSOFF], Rz[MAXN_TERSOFF], Rd[MAXN_TERSOFF],
+                Sr[MAXN_TERSOFF];
+            ters_load<T, MAXN_TERSOFF>(q, nR, n, t, cnt, Rx, Ry, Rz, Rd, Sr);
+            ters_site<T, MAXN_TERSOFF>(q, cnt, Rx, Ry, Rz, Rd, Sr, nP, n, t, U, vir);
         }
     }
-    double acc[12];
-    acc[0] = (double)U;
-    for (int k = 0; k < 9; ++k) acc[1 + k] = (double)vir[k];
-    acc[10] = (double)cnt;
-    acc[11] = (double)(cnt * (cnt - 1));
+    T acc[12];
+    acc[0] = U;
+    for (int k = 0; k < 9; ++k) acc[1 + k] = vir[k];
+    acc[10] = (T)cnt;
+    acc[11] = (T)(cnt * (cnt - 1));
     double tot[12];
-    block_sum<12>(acc, tot);
+    block_sum_t<12, T>(acc, tot);
     if (threadIdx.x == 0) {
         double *part = b.atom_part + ((size_t)tl.img * b.atpi + tl.t) * NPART;
         for (int k = 0; k < 12; ++k) part[k] = tot[k];
@@ -363,6 +435,11 @@ __global__ void __launch_bounds__(TILE) k_ters_gather(const Tile *tiles, BandDev
 }
 
 template <typename T>
+void launch_tersoff_list(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    k_ters_list<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
+}
+template <typename T>
 void launch_tersoff_partials(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
     if (ntiles <= 0) return;
     k_ters_partials<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
@@ -372,6 +449,8 @@ void launch_tersoff_gather(const Tile *tiles, int ntiles, BandDev *bands, cudaSt
     if (ntiles <= 0) return;
     k_ters_gather<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
 }
+template void launch_tersoff_list<float>(const Tile *, int, BandDev *, cudaStream_t);
+template void launch_tersoff_list<double>(const Tile *, int, BandDev *, cudaStream_t);
 template void launch_tersoff_partials<float>(const Tile *, int, BandDev *, cudaStream_t);
 template void launch_tersoff_partials<double>(const Tile *, int, BandDev *, cudaStream_t);
 template void launch_tersoff_gather<float>(const Tile *, int, BandDev *, cudaStream_t);
