@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(TILE) k_bin_assign(const Tile *tiles, BandDev 
     o.x = (T)off[0];
     o.y = (T)off[1];
     o.z = (T)off[2];
-    o.w = (T)0;
+    o.w = (T)bi[2];  // bin index along the innermost axis (row traversal)
     lo.x = (T)(off[0] - (double)o.x);
     lo.y = (T)(off[1] - (double)o.y);
     lo.z = (T)(off[2] - (double)o.z);

@@ -23,8 +23,41 @@ __device__ inline float rcp<float>(float x) { return __frcp_rn(x); }
 template <>
 __device__ inline double rcp<double>(double x) { return 1.0 / x; }
 
+// Per-thread LJ accumulators: force on atom i, energy sum, virial, pair count
 template <typename T>
-__global__ void __launch_bounds__(TILE) k_lj(const Tile *tiles, BandDev *bands) {
+struct LJAcc {
+    T fx = 0, fy = 0, fz = 0, e = 0;
+    T v00 = 0, v01 = 0, v02 = 0, v11 = 0, v12 = 0, v22 = 0;
+    int cnt = 0;
+    __device__ inline void pair(T rx, T ry, T rz, T sig2, T eps24) {
+        const T r2 = rx * rx + ry * ry + rz * rz;
+        const T ir2 = rcp<T>(r2);
+        const T sr2 = sig2 * ir2;
+        const T sr6 = sr2 * sr2 * sr2;
+        // phi'(r)/r = 24 eps (sr6 - 2 sr6^2) / r^2
+        const T fr = eps24 * sr6 * ((T)1 - (T)2 * sr6) * ir2;
+        fx += fr * rx;
+        fy += fr * ry;
+        fz += fr * rz;
+        e += sr6 * (sr6 - (T)1);
+        v00 += fr * rx * rx;
+        v01 += fr * rx * ry;
+        v02 += fr * rx * rz;
+        v11 += fr * ry * ry;
+        v12 += fr * ry * rz;
+        v22 += fr * rz * rz;
+        ++cnt;
+    }
+};
+
+// One thread per atom in slot order.  The stencil is walked as rows along
+// the innermost bin axis: where the row does not wrap around the cell its
+// bins are consecutive in the cell list, so the row is one contiguous range
+// of atoms (one pair of bin-start loads instead of one per bin) and each
+// atom's displacement comes from its own innermost bin index, stored in the
+// offset's fourth lane.  Rows that wrap are walked bin by bin.
+template <typename T>
+__global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 8 : 4) k_lj(const Tile *tiles, BandDev *bands) {
     using T4 = typename Vec4<T>::type;
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
@@ -48,75 +81,66 @@ __global__ void __launch_bounds__(TILE) k_lj(const Tile *tiles, BandDev *bands) 
     const T4 *off = (const T4 *)b.slot_off + base;
     const int *start = b.bin_start + (size_t)tl.img * (b.nbins_cap + 1);
     const T rc2 = (T)(p.rc * p.rc), sig2 = (T)(p.sigma * p.sigma);
-    const T rc2_screen = rc2 * (T)1.00001;  // cheap test first, exact test after
     const T eps4 = (T)(4.0 * p.eps), eps24 = (T)(24.0 * p.eps);
-    T fx = 0, fy = 0, fz = 0, e = 0;
-    T v00 = 0, v01 = 0, v02 = 0, v11 = 0, v12 = 0, v22 = 0;
-    int cnt = 0;
+    LJAcc<T> A;
     if (t < n) {
-        const int bin = b.slot_bin[base + t];
-        const int nb1 = s_nb[1], nb2 = s_nb[2];
-        const int b0 = bin / (nb1 * nb2), b1 = (bin / nb2) % nb1, b2 = bin % nb2;
+        const int nb0 = s_nb[0], nb1 = s_nb[1], nb2 = s_nb[2];
+        const int m2 = s_m[2];
         const T4 oi = off[t];
+        const int b2 = (int)oi.w;
+        const int bin = b.slot_bin[base + t];
+        const int b0 = bin / (nb1 * nb2), b1 = (bin / nb2) % nb1;
+        const bool row_ok = (b2 - m2 >= 0) && (b2 + m2 < nb2);
         for (int d0 = -s_m[0]; d0 <= s_m[0]; ++d0) {
             int w0 = b0 + d0, t0 = 0;
-            while (w0 < 0) { w0 += s_nb[0]; --t0; }
-            while (w0 >= s_nb[0]) { w0 -= s_nb[0]; ++t0; }
+            while (w0 < 0) { w0 += nb0; --t0; }
+            while (w0 >= nb0) { w0 -= nb0; ++t0; }
             for (int d1 = -s_m[1]; d1 <= s_m[1]; ++d1) {
                 int w1 = b1 + d1, t1 = 0;
                 while (w1 < 0) { w1 += nb1; --t1; }
                 while (w1 >= nb1) { w1 -= nb1; ++t1; }
-                for (int d2 = -s_m[2]; d2 <= s_m[2]; ++d2) {
-                    int w2 = b2 + d2, t2 = 0;
-                    while (w2 < 0) { w2 += nb2; --t2; }
-                    while (w2 >= nb2) { w2 -= nb2; ++t2; }
-                    const int w = (w0 * nb1 + w1) * nb2 + w2;
-                    // displacement between the two bin centres (exact in T
-                    // for |delta| <= 1 in orthorhombic cells)
-                    const T cx = (d0 * s_bv[0] + d1 * s_bv[3] + d2 * s_bv[6]) +
-                                 (t0 * s_dh[0] + t1 * s_dh[3] + t2 * s_dh[6]);
-                    const T cy = (d0 * s_bv[1] + d1 * s_bv[4] + d2 * s_bv[7]) +
-                                 (t0 * s_dh[1] + t1 * s_dh[4] + t2 * s_dh[7]);
-                    const T cz = (d0 * s_bv[2] + d1 * s_bv[5] + d2 * s_bv[8]) +
-                                 (t0 * s_dh[2] + t1 * s_dh[5] + t2 * s_dh[8]);
-                    const T sx = cx - oi.x, sy = cy - oi.y, sz = cz - oi.z;
-                    const int q1 = start[w + 1];
-                    for (int q = start[w]; q < q1; ++q) {
+                const int rowbase = (w0 * nb1 + w1) * nb2;
+                // displacement for d2 = 0 (row base) and the wrap remainder
+                const T cx = (d0 * s_bv[0] + d1 * s_bv[3]) + (t0 * s_dh[0] + t1 * s_dh[3]);
+                const T cy = (d0 * s_bv[1] + d1 * s_bv[4]) + (t0 * s_dh[1] + t1 * s_dh[4]);
+                const T cz = (d0 * s_bv[2] + d1 * s_bv[5]) + (t0 * s_dh[2] + t1 * s_dh[5]);
+                if (row_ok) {
+                    const int q0 = start[rowbase + b2 - m2], q1 = start[rowbase + b2 + m2 + 1];
+                    for (int q = q0; q < q1; ++q) {
                         const T4 oj = off[q];
-                        const T ux = oj.x + sx, uy = oj.y + sy, uz = oj.z + sz;
-                        if (ux * ux + uy * uy + uz * uz >= rc2_screen) continue;
-                        // accepted: pair vector with the small offsets
-                        // subtracted first
-                        const T rx = (oj.x - oi.x) + cx, ry = (oj.y - oi.y) + cy,
-                                rz = (oj.z - oi.z) + cz;
-                        const T r2 = rx * rx + ry * ry + rz * rz;
+                        const T d2 = oj.w - (T)b2;
+                        const T ex = cx + d2 * s_bv[6], ey = cy + d2 * s_bv[7],
+                                ez = cz + d2 * s_bv[8];
+                        const T ux = (oj.x - oi.x) + ex, uy = (oj.y - oi.y) + ey,
+                                uz = (oj.z - oi.z) + ez;
+                        const T r2 = ux * ux + uy * uy + uz * uz;
                         // r2 == 0 only for the atom itself at zero shift
-                        if (r2 < rc2 && r2 > (T)0) {
-                            const T ir2 = rcp<T>(r2);
-                            const T sr2 = sig2 * ir2;
-                            const T sr6 = sr2 * sr2 * sr2;
-                            // phi'(r)/r = 24 eps (sr6 - 2 sr6^2) / r^2
-                            const T fr = eps24 * sr6 * ((T)1 - (T)2 * sr6) * ir2;
-                            fx += fr * rx;
-                            fy += fr * ry;
-                            fz += fr * rz;
-                            e += sr6 * (sr6 - (T)1);
-                            v00 += fr * rx * rx;
-                            v01 += fr * rx * ry;
-                            v02 += fr * rx * rz;
-                            v11 += fr * ry * ry;
-                            v12 += fr * ry * rz;
-                            v22 += fr * rz * rz;
-                            ++cnt;
+                        if (r2 < rc2 && r2 > (T)0) A.pair(ux, uy, uz, sig2, eps24);
+                    }
+                } else {
+                    for (int d2 = -m2; d2 <= m2; ++d2) {
+                        int w2 = b2 + d2, t2 = 0;
+                        while (w2 < 0) { w2 += nb2; --t2; }
+                        while (w2 >= nb2) { w2 -= nb2; ++t2; }
+                        const T ex = cx + (d2 * s_bv[6] + t2 * s_dh[6]);
+                        const T ey = cy + (d2 * s_bv[7] + t2 * s_dh[7]);
+                        const T ez = cz + (d2 * s_bv[8] + t2 * s_dh[8]);
+                        const int q1 = start[rowbase + w2 + 1];
+                        for (int q = start[rowbase + w2]; q < q1; ++q) {
+                            const T4 oj = off[q];
+                            const T ux = (oj.x - oi.x) + ex, uy = (oj.y - oi.y) + ey,
+                                    uz = (oj.z - oi.z) + ez;
+                            const T r2 = ux * ux + uy * uy + uz * uz;
+                            if (r2 < rc2 && r2 > (T)0) A.pair(ux, uy, uz, sig2, eps24);
                         }
                     }
                 }
             }
         }
         // generalised atom force F D^T (row vector times D^T)
-        T g0 = fx * s_D[0] + fy * s_D[1] + fz * s_D[2];
-        T g1 = fx * s_D[3] + fy * s_D[4] + fz * s_D[5];
-        T g2 = fx * s_D[6] + fy * s_D[7] + fz * s_D[8];
+        const T g0 = A.fx * s_D[0] + A.fy * s_D[1] + A.fz * s_D[2];
+        const T g1 = A.fx * s_D[3] + A.fy * s_D[4] + A.fz * s_D[5];
+        const T g2 = A.fx * s_D[6] + A.fy * s_D[7] + A.fz * s_D[8];
         const int atom = b.slot_atom[base + t];
         T *F = (T *)b.F + ((size_t)tl.img * b.rows + atom) * 3;
         F[0] = g0;
@@ -125,14 +149,14 @@ __global__ void __launch_bounds__(TILE) k_lj(const Tile *tiles, BandDev *bands) 
     }
     // U_i = 1/2 sum_j [4 eps (sr12 - sr6) - phi(rc)];  V = -1/2 sum r (x) f
     T acc[8];
-    acc[0] = (T)0.5 * (eps4 * e - (T)p.ephi_c * (T)cnt);
-    acc[1] = (T)(-0.5) * v00;
-    acc[2] = (T)(-0.5) * v01;
-    acc[3] = (T)(-0.5) * v02;
-    acc[4] = (T)(-0.5) * v11;
-    acc[5] = (T)(-0.5) * v12;
-    acc[6] = (T)(-0.5) * v22;
-    acc[7] = (T)cnt;
+    acc[0] = (T)0.5 * (eps4 * A.e - (T)p.ephi_c * (T)A.cnt);
+    acc[1] = (T)(-0.5) * A.v00;
+    acc[2] = (T)(-0.5) * A.v01;
+    acc[3] = (T)(-0.5) * A.v02;
+    acc[4] = (T)(-0.5) * A.v11;
+    acc[5] = (T)(-0.5) * A.v12;
+    acc[6] = (T)(-0.5) * A.v22;
+    acc[7] = (T)A.cnt;
     double r8[8];
     block_sum_t<8, T>(acc, r8);
     // symmetric virial, row-major
