@@ -41,6 +41,7 @@ WORKLOADS = {
     # 64 LJ vacancy / divacancy bands, 256..32768 atoms log-uniform, 5..15
     # images, +-2% end strain, cell filter on, one batch (one launch per kernel)
     "lj_batch64": dict(kind="lj_batch", n_bands=64, precision="mixed"),
+    "serve_poisson20": dict(kind="serve", rate=20.0, precision="mixed", budget_gb=150.0),
 }
 CPU_SAMPLE_REPS = (6, 4, 3)   # the 576-atom tile the large band is built from
 
@@ -548,6 +549,133 @@ def run_batch(args):
     return 0
 
 
+def _serve_options(g, spec, precision):
+    opt = g.default_options()
+    opt.k_spring = spec["k"]
+    opt.climb = 1
+    opt.precision = precision
+    opt.dt = spec["dt"]
+    opt.dt_max = 10 * spec["dt"]
+    opt.maxstep = 0.2
+    opt.n_max = spec["n_images"]
+    opt.bin_scale = 0.0
+    return opt
+
+
+def serve_once(g, stream, specs, built, budget, max_steps, lead, drain, window):
+    """Submit a request stream to one server, serve it to the end, and
+    summarise latencies (retirement - arrival) and served throughput."""
+    import numpy as np
+    pots = {"lj": g.lj_potential(), "tersoff": g.tersoff_potential()}
+    cf = g.CellFilter(1, g.ROTFREE_B, 0.0, 0.0)
+    sv = g.Server(g.MIXED, budget_bytes=budget, stream=stream)
+    t0 = time.perf_counter()
+    ids = []
+    for sp, ((R0, h0, R1, h1), pot) in zip(specs, built):
+        ids.append(sv.submit((R0, h0), (R1, h1), sp["n_images"], pots[pot], cf,
+                             _serve_options(g, sp, g.MIXED), sp["fmax"], max_steps,
+                             lead + sp["arrival"]))
+    t_sub = time.perf_counter() - t0
+    if t_sub >= lead:
+        raise RuntimeError("submission took %.2f s, longer than the %.1f s lead" % (t_sub, lead))
+    finished = sv.run(lead + window + drain)
+    res = [sv.result(i) for i in ids]
+    stats = sv.stats()
+    sv.destroy()
+    done = [r for r in res if r["state"] == 2]
+    lat = np.array([r["latency_s"] for r in done])
+    work = [len(b[0][0]) * (sp["n_images"] - 2) * r["steps"]
+            for sp, b, r in zip(specs, built, res) if r["state"] == 2]
+    t_end = max(sp["arrival"] + r["latency_s"] for sp, r in zip(specs, res) if r["state"] == 2)
+    atom_images = sum(len(b[0][0]) * (sp["n_images"] - 2) for sp, b in zip(specs, built))
+    by_kind = {}
+    for sp, r in zip(specs, res):
+        k = by_kind.setdefault(sp["kind"], {"requests": 0, "converged": 0, "lat": []})
+        k["requests"] += 1
+        k["converged"] += int(r["converged"])
+        if r["state"] == 2:
+            k["lat"].append(r["latency_s"])
+    for k in by_kind.values():
+        L = k.pop("lat")
+        k["p50_s"] = float(np.percentile(L, 50)) if L else None
+    return {"requests": len(specs), "window_s": window, "retired": len(done),
+            "all_retired": bool(finished),
+            "converged": sum(int(r["converged"]) for r in res),
+            "errors": sum(int(r["status"] != 0) for r in res),
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()),
+            "offered_rate_per_s": len(specs) / window,
+            "offered_atom_images_per_s": atom_images / window,
+            "offered_atom_steps_per_s": sum(work) / window,
+            "sustained_atom_steps_per_s": sum(work) / t_end,
+            "mean_work_per_request": sum(work) / max(1, len(done)),
+            "server_stats": stats, "by_kind": by_kind, "submit_s": t_sub}
+
+
+def run_serve(args):
+    """Served bands: Poisson request stream at the offered rate, then at a
+    stable rate (70% of the sustained capacity measured in the first run)."""
+    import torch
+    import cfneb_inputs as ci
+    ws, rank, local = dist_info()
+    if ws > 1 and rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    import paper_2510_16721_gb300 as g
+    g.build()
+    wl = WORKLOADS[args.workload]
+    stream = torch.cuda.current_stream()
+    budget = int(wl["budget_gb"] * 1e9)
+    specs = ci.serve_requests(seed=5, rate=wl["rate"], window=args.serve_window)
+    t = time.perf_counter()
+    built = [ci.build_request(sp) for sp in specs]
+    t_build = time.perf_counter() - t
+    # warm the library (kernels loaded, allocator primed) on one small request
+    warm = min(range(len(specs)), key=lambda q: len(built[q][0][0]))
+    serve_once(g, stream, [dict(specs[warm], arrival=0.0)], [built[warm]], budget, 20, 0.5, 60.0,
+               1.0)
+    clocks = ClockSampler(local)
+    clocks.start()
+    offered = serve_once(g, stream, specs, built, budget, args.serve_max_steps, 3.0,
+                         args.serve_drain, args.serve_window)
+    clk = clocks.stop()
+    rate_s = 0.7 * offered["sustained_atom_steps_per_s"] / offered["mean_work_per_request"]
+    specs2 = ci.serve_requests(seed=6, rate=rate_s, window=args.serve_window / 2)
+    built2 = [ci.build_request(sp) for sp in specs2]
+    stable = serve_once(g, stream, specs2, built2, budget, args.serve_max_steps, 3.0,
+                        args.serve_drain, args.serve_window / 2)
+    lj = [dict(endpoints=b[0], n_images=sp["n_images"], k=sp["k"], dt=sp["dt"])
+          for sp, b in zip(specs, built) if b[1] == "lj"]
+    cpu = None if args.no_cpu_baseline else cpu_oracle_lj_rate(lj, args.cpu_seconds)
+    h2d = sum(2 * len(b[0][0]) * 3 * 8 + 18 * 8 for b in built)
+    d2h = sum(sp["n_images"] * 8 for sp in specs)
+    line = {"metric": METRIC, "value": offered["sustained_atom_steps_per_s"], "unit": UNIT,
+            "n_gpus": 1, "steps": None, "warmup": None, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 pair/three-body arithmetic, f64 reductions and 3x3 cell work",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "rate_per_s": wl["rate"],
+                       "window_s": args.serve_window, "budget_gb": wl["budget_gb"],
+                       "atoms": "log-uniform 500-50,000", "images": "uniform 7-16",
+                       "mix": "LJ FCC vacancy 50%, Tersoff C graphite->hex-diamond 25%, "
+                              "Tersoff C diamond vacancy 25%",
+                       "fmax": 0.05, "max_steps": args.serve_max_steps, "precision": "mixed",
+                       "cell_filter": "rotation-free (B)",
+                       "steps": "not applicable: a request stream, value = served "
+                                "atom-steps/s at the offered rate",
+                       "l2": "working set > 129 MB L2, no flush", "parallelism": "x1"},
+            "serving": {"offered": offered, "stable": dict(stable, rate_per_s=rate_s)},
+            "cpu_baseline": cpu,
+            "e2e": {"value": offered["sustained_atom_steps_per_s"], "unit": UNIT,
+                    "h2d_bytes_per_request": h2d / len(specs),
+                    "d2h_bytes_per_request": d2h / len(specs),
+                    "includes": "host endpoints in, band creation, relaxation, FP64 "
+                                "energies out: the serving loop is end to end"},
+            "gpu_launches": None, "clocks": clk, "build_inputs_s": t_build}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -559,15 +687,20 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--serve-window", type=float, default=30.0)
+    ap.add_argument("--serve-max-steps", type=int, default=3000)
+    ap.add_argument("--serve-drain", type=float, default=300.0)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
-        if WORKLOADS[args.workload]["kind"] == "lj_batch":
+        if WORKLOADS[args.workload]["kind"] in ("lj_batch", "serve"):
             args.workload = "tersoff_graphite_hexdiamond_98304"
         return run_reference(args, args.workload)
     if WORKLOADS[args.workload]["kind"] == "lj_batch":
         return run_batch(args)
+    if WORKLOADS[args.workload]["kind"] == "serve":
+        return run_serve(args)
     return run_ours(args, args.workload)
 
 

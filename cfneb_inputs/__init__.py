@@ -27,14 +27,17 @@ FCC_BASIS = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.0], [0.5, 0.0, 0.5], [0.0, 0
 LJ_A = 1.5496  # FCC lattice constant (sigma units) used by the LJ workloads
 
 
+def _lattice(basis, a, n1, n2, n3):
+    """Cubic supercell: cells in (i, j, k) order, basis sites within each."""
+    ijk = np.array(list(itertools.product(range(n1), range(n2), range(n3))), dtype=np.float64)
+    R = ((ijk[:, None, :] + basis[None, :, :]) * a).reshape(-1, 3)
+    h = np.diag([n1 * a, n2 * a, n3 * a]).astype(np.float64)
+    return R, h
+
+
 def fcc(a, n1, n2, n3):
     """Conventional FCC supercell n1 x n2 x n3 (4 atoms per cell)."""
-    R = []
-    for i, j, k in itertools.product(range(n1), range(n2), range(n3)):
-        for b in FCC_BASIS:
-            R.append((np.array([i, j, k], dtype=np.float64) + b) * a)
-    h = np.diag([n1 * a, n2 * a, n3 * a]).astype(np.float64)
-    return np.array(R), h
+    return _lattice(FCC_BASIS, a, n1, n2, n3)
 
 
 def _nearest_neighbour(R, h, i, exclude=()):
@@ -65,6 +68,30 @@ def lj_vacancy_hop(a=LJ_A, reps=(2, 2, 2), divacancy=False):
         removed.append(_nearest_neighbour(R, h, 0))
     hop = _nearest_neighbour(R, h, 0, exclude=removed)
     keep = [i for i in range(len(R)) if i not in removed]
+    R0 = R[keep].copy()
+    R1 = R0.copy()
+    R1[keep.index(hop)] = site
+    return R0, h.copy(), R1, h.copy()
+
+
+# cubic diamond: FCC sites plus the same sites shifted by (1/4, 1/4, 1/4)
+DIAMOND_BASIS = np.vstack([FCC_BASIS, FCC_BASIS + 0.25])
+DIAMOND_A = 3.5656  # cubic diamond lattice constant (Angstrom), Tersoff C workloads
+
+
+def diamond(a, n1, n2, n3):
+    """Conventional cubic-diamond supercell n1 x n2 x n3 (8 atoms per cell)."""
+    return _lattice(DIAMOND_BASIS, a, n1, n2, n3)
+
+
+def diamond_vacancy_hop(a=DIAMOND_A, reps=(2, 2, 2)):
+    """Vacancy hop in cubic diamond: atom 0 is removed and, in the final
+    state, its nearest neighbour (lowest index) sits on the vacant site.
+    Unrelaxed lattice sites.  Returns (R0, h, R1, h) with matched order."""
+    R, h = diamond(a, *reps)
+    site = R[0].copy()
+    hop = _nearest_neighbour(R, h, 0)
+    keep = list(range(1, len(R)))
     R0 = R[keep].copy()
     R1 = R0.copy()
     R1[keep.index(hop)] = site
@@ -127,11 +154,10 @@ def graphite_hexdiamond_cells(a_g=2.46, c_g=6.70, a_d=2.52, c_d=4.12, delta=1.0 
 def tile(R, h, reps):
     """Replicate a periodic structure reps = (n1, n2, n3) times."""
     n1, n2, n3 = reps
-    out = []
-    for i, j, k in itertools.product(range(n1), range(n2), range(n3)):
-        shift = i * h[0] + j * h[1] + k * h[2]
-        out.append(R + shift)
-    return np.vstack(out), np.array([h[0] * n1, h[1] * n2, h[2] * n3])
+    ijk = np.array(list(itertools.product(range(n1), range(n2), range(n3))), dtype=np.float64)
+    shift = ijk[:, 0:1] * h[0] + ijk[:, 1:2] * h[1] + ijk[:, 2:3] * h[2]
+    out = (R[None, :, :] + shift[:, None, :]).reshape(-1, 3)
+    return out, np.array([h[0] * n1, h[1] * n2, h[2] * n3])
 
 
 def tersoff_endpoint_cells():
@@ -239,3 +265,62 @@ def poisson_arrivals(seed, rate, window):
         if t >= window:
             return np.array(out)
         out.append(t)
+
+
+def _orthohex_reps(n_target):
+    """Tiling of the 8-atom orthohexagonal carbon cell with about n_target
+    atoms and a near-cubic box (at least 2 cells per side)."""
+    lens = (2.46, 4.26, 6.70)
+    L = (n_target / 8.0 * lens[0] * lens[1] * lens[2]) ** (1.0 / 3.0)
+    return tuple(max(2, int(round(L / x))) for x in lens)
+
+
+def serve_requests(seed=5, rate=20.0, window=60.0, n_lo=500, n_hi=50000, img_lo=7, img_hi=16,
+                   fmax=0.05, lj_strain=0.003):
+    """Request stream for the serving loop: Poisson arrivals at `rate` per
+    second over `window` seconds; each request is an LJ or a Tersoff carbon
+    band (even odds).  LJ: FCC vacancy hop, end cell strained by up to
+    lj_strain.  Tersoff: graphite -> hexagonal diamond tiled, or a cubic
+    diamond vacancy hop (even odds).  Atom counts log-uniform in
+    [n_lo, n_hi], image counts (endpoints included) uniform in
+    [img_lo, img_hi].  Returns specs; build_request() makes the structures.
+    """
+    rng = np.random.default_rng(seed)
+    arrivals = poisson_arrivals(seed, rate, window)
+    specs = []
+    for q, t in enumerate(arrivals):
+        target = math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))
+        n_images = int(rng.integers(img_lo, img_hi + 1))
+        if rng.integers(0, 2) == 0:
+            m = max(8, int(round(target / 4.0)))
+            reps = near_cubic_factors(m)
+            while min(reps) < 2:
+                m += 1
+                reps = near_cubic_factors(m)
+            specs.append(dict(id=q, arrival=float(t), kind="lj_vacancy", reps=reps,
+                              n_images=n_images, k=1.0, dt=0.01, fmax=fmax,
+                              strain_seed=seed * 100000 + q, strain=lj_strain))
+        elif rng.integers(0, 2) == 0:
+            specs.append(dict(id=q, arrival=float(t), kind="tersoff_graphite_hexdiamond",
+                              reps=_orthohex_reps(target), n_images=n_images, k=0.1, dt=0.1,
+                              fmax=fmax))
+        else:
+            m = max(8, int(round(target / 8.0)))
+            reps = near_cubic_factors(m)
+            while min(reps) < 2:
+                m += 1
+                reps = near_cubic_factors(m)
+            specs.append(dict(id=q, arrival=float(t), kind="tersoff_diamond_vacancy", reps=reps,
+                              n_images=n_images, k=0.1, dt=0.1, fmax=fmax))
+    return specs
+
+
+def build_request(spec):
+    """Endpoints (R0, h0, R1, h1) and potential name of a serve_requests spec."""
+    if spec["kind"] == "lj_vacancy":
+        R0, h0, R1, h1 = lj_vacancy_hop(LJ_A, spec["reps"])
+        h1s = strained_cell(h1, spec["strain_seed"], spec["strain"])
+        return (R0, h0, affine(R1, h1, h1s), h1s), "lj"
+    if spec["kind"] == "tersoff_graphite_hexdiamond":
+        return graphite_hexdiamond_path(spec["reps"]), "tersoff"
+    return diamond_vacancy_hop(DIAMOND_A, spec["reps"]), "tersoff"
