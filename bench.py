@@ -275,10 +275,16 @@ def run_ours(args, wl_name):
     # warm-up (also captures the CUDA graph)
     band.step(args.warmup)
     torch.cuda.synchronize()
+    lb0 = band.list_stats()
     clocks = ClockSampler(local)
     clocks.start()
     ms = time_steps(torch, band, stream, args.steps, dist)
     clk = clocks.stop()
+    lb1 = band.list_stats()
+    lists = {"skin": lb1[2], "builds_per_image_step":
+             (lb1[0] - lb0[0]) / max(1, lb1[1] - lb0[1]),
+             "note": "cell and neighbour lists cover rc + skin and are kept while no pair "
+                     "can have crossed into rc; the timed steps include every rebuild"}
     if dist is not None:
         t = torch.tensor([ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -373,7 +379,7 @@ def run_ours(args, wl_name):
                        "l2": "working set > 129 MB L2, no flush", "graph": "CUDA graph per step",
                        "parallelism": "replicas x%d" % ws},
             "roofline": roof, "kernel_share": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clk, "fp64_plain": fp64}
+            "gpu_launches": launches, "clocks": clk, "fp64_plain": fp64, "lists": lists}
     print(json.dumps(line))
     if dist is not None:
         dist.barrier()

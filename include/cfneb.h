@@ -114,14 +114,22 @@ typedef struct {
                                  cooldown steps after the previous change    */
     double alpha_ins, alpha_del; /* insert if l_s > alpha_ins mean(l); delete
                                  if l_(j-1) + l_j < alpha_del mean(l)        */
-    double bin_scale;         /* cell-list bin width / cutoff (>= 1, or 0.5);
+    double bin_scale;         /* cell-list bin width / list cutoff (>= 0.25);
                                  0 selects the tuned default                 */
+    double skin;              /* neighbour-list skin (length units): cell
+                                 lists and lists cover rc + skin and are kept
+                                 while no pair can have crossed into rc (a
+                                 bound from the largest displacement and the
+                                 cell change since the build); 0 rebuilds at
+                                 every evaluation; < 0 selects the default
+                                 (Tersoff 0.15, LJ 0).  At most rc.          */
 } cfneb_options;
 
 /* Fill *opt with the defaults: k 0.1, climb on, FP64, FIRE dt 0.1,
  * dt_max 1.0, maxstep 0.2, no noise, adaptive off, n_min 3, n_max = the
  * image count given at creation, k_ref 10, cooldown 20, alpha_ins 1.5,
- * alpha_del 0.5, bin_scale 0 (tuned).  Returns CFNEB_OK. */
+ * alpha_del 0.5, bin_scale 0 (tuned), skin -1 (per-potential default).
+ * Returns CFNEB_OK. */
 int cfneb_default_options(cfneb_options *opt);
 
 /* Create a band between two endpoint structures (Sec. III: the cell filter
@@ -324,6 +332,15 @@ const char *cfneb_kernel_name(int32_t kernel_id);
  * three-body terms of Tersoff; 0 for LJ).  Used to turn kernel times into
  * arithmetic rates.  Synchronises. */
 int cfneb_get_work(const cfneb_band *band, double *pairs, double *triples);
+
+/* Cell-list reuse counters summed over the interior image slots since the
+ * band was created: *builds = cell-list (and neighbour-list) builds,
+ * *evaluations = force evaluations; *skin = the skin in use.  The paper
+ * prints no list policy: a skin is this library's way to skip rebuilds and
+ * leaves every force unchanged up to rounding.  Synchronises.  Any output
+ * pointer may be NULL. */
+int cfneb_get_list_stats(const cfneb_band *band, int64_t *builds, int64_t *evaluations,
+                         double *skin);
 
 /* Number of kernel launches one cfneb_step makes for this band (for
  * launch accounting). */

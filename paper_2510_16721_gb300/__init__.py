@@ -43,7 +43,7 @@ EXPORTS = [
     "cfneb_insert_image", "cfneb_delete_image", "cfneb_get_path", "cfneb_get_state",
     "cfneb_destroy_band", "cfneb_evaluate", "cfneb_profile", "cfneb_profile_read",
     "cfneb_kernel_count", "cfneb_kernel_name", "cfneb_launches_per_step",
-    "cfneb_status_string", "cfneb_get_work", "cfneb_lj_evaluate_noalloc",
+    "cfneb_status_string", "cfneb_get_work", "cfneb_get_list_stats", "cfneb_lj_evaluate_noalloc",
     "cfneb_band_bytes", "cfneb_batch_create", "cfneb_batch_add", "cfneb_batch_remove",
     "cfneb_batch_step", "cfneb_batch_relax", "cfneb_batch_status", "cfneb_batch_bytes",
     "cfneb_batch_profile", "cfneb_batch_profile_read", "cfneb_batch_destroy",
@@ -82,7 +82,8 @@ class Options(ctypes.Structure):
                 ("adaptive", ctypes.c_int32), ("n_min", ctypes.c_int32),
                 ("n_max", ctypes.c_int32), ("k_ref", ctypes.c_int32),
                 ("cooldown", ctypes.c_int32), ("alpha_ins", ctypes.c_double),
-                ("alpha_del", ctypes.c_double), ("bin_scale", ctypes.c_double)]
+                ("alpha_del", ctypes.c_double), ("bin_scale", ctypes.c_double),
+                ("skin", ctypes.c_double)]
 
 
 _lib = None
@@ -118,6 +119,7 @@ def lib():
             "cfneb_launches_per_step": ([vp, P(i32)], ctypes.c_int),
             "cfneb_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "cfneb_get_work": ([vp, dp, dp], ctypes.c_int),
+            "cfneb_get_list_stats": ([vp, P(i64), P(i64), dp], ctypes.c_int),
             "cfneb_lj_evaluate_noalloc": ([vp, i32, dp, dbl, dbl, dbl, i32, vp, vp, vp, vp],
                                           ctypes.c_int),
             "cfneb_band_bytes": ([vp, P(ctypes.c_uint64)], ctypes.c_int),
@@ -295,8 +297,15 @@ class Band:
         _check(lib().cfneb_get_work(self._h, ctypes.byref(p), ctypes.byref(t)), "cfneb_get_work")
         return float(p.value), float(t.value)
 
+    def list_stats(self):
+        """cfneb_get_list_stats: (cell-list builds, evaluations, skin)."""
+        nb, ne, sk = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_double(0.0)
+        _check(lib().cfneb_get_list_stats(self._h, ctypes.byref(nb), ctypes.byref(ne),
+                                          ctypes.byref(sk)), "cfneb_get_list_stats")
+        return int(nb.value), int(ne.value), float(sk.value)
+
     def autotune(self, steps=5):
-        """cfneb_autotune: returns the chosen bin width / cutoff."""
+        """cfneb_autotune: returns the chosen bin width / list cutoff."""
         best = ctypes.c_double(0.0)
         _check(lib().cfneb_autotune(self._h, int(steps), ctypes.byref(best)), "cfneb_autotune")
         return float(best.value)

@@ -265,6 +265,7 @@ __global__ void k_fire_scalars(const int *band_ids, BandDev *bands) {
         __syncthreads();
     }
     if (threadIdx.x != 0) return;
+    bp->stale = 0;  // every image of the band has rebuilt its cell list
     const double P = tot[0], FF = tot[1], VV = tot[2];
     const double fmax_ = sqrt(tot[3]);
     bp->P = P;

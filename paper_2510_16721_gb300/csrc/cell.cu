@@ -25,6 +25,17 @@
 // Determinism: atoms are counted into bins with integer atomics, then each
 // bin's atoms are ordered by atom index, so the slot order (and every
 // summation order downstream) is the same on every run.
+//
+// Reuse with a skin: with skin > 0 the stencil and any neighbour list cover
+// rl = rc + skin, and an image keeps its bins (and lists) while they still
+// hold every pair inside rc.  With R = R~ D, a pair vector is rho D where
+// rho is its R~-frame vector; from the build (D_b) to now (D), a pair that
+// was at |r_b| >= rl is now at least rl (1 - |D_b^-1 D - I|) - 2 d |D| away,
+// d being the largest displacement |R~ - R~_b| of any atom.  While that
+// bound stays above rc the bins of the build are kept: each atom's offset is
+// recomputed from its current position against the centre of its old bin
+// (the pair-vector identity above holds for any position, inside the bin or
+// not), which costs one pass over the atoms instead of a rebuild.
 #include "common.cuh"
 
 namespace cfneb {
@@ -147,6 +158,60 @@ __device__ bool sym_sqrt3(const double *Bin, double *S, double *Si) {
     return true;
 }
 
+// Bin grid of an image with cell h: with keep_grid false the bin counts
+// nb and stencil half widths m are chosen from the perpendicular widths and
+// the list cutoff; with keep_grid true they stay as built and only the bin
+// vectors follow the cell.
+__device__ void bin_geometry(const BandParams *bp, int nbins_cap, const double *h, double omega,
+                             bool keep_grid, ImgScalars &sc) {
+    const double rl = bp->rl > 0.0 ? bp->rl : bp->rc;
+    int nb[3];
+    float w[3];
+    if (keep_grid) {
+        for (int a = 0; a < 3; ++a) nb[a] = sc.nb[a];
+    } else {
+        // perpendicular widths w_a = Omega / |h_b x h_c| (only choose the bin
+        // grid: FP32, shaded down by 1e-5 so the stencil is never too narrow)
+        for (int a = 0; a < 3; ++a) {
+            const double *u = h + 3 * ((a + 1) % 3), *v = h + 3 * ((a + 2) % 3);
+            const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2],
+                         cz = u[0] * v[1] - u[1] * v[0];
+            w[a] = (float)omega / sqrtf((float)(cx * cx + cy * cy + cz * cz)) * 0.99999f;
+        }
+        for (int a = 0; a < 3; ++a) {
+            const float q = floorf(w[a] / (float)bp->bin_w);
+            nb[a] = q < 1.0f ? 1 : (q > 1024.0f ? 1024 : (int)q);
+        }
+        // keep within the bin capacity: coarser bins are always correct
+        while ((long long)nb[0] * nb[1] * nb[2] > nbins_cap) {
+            int a = (nb[0] >= nb[1] && nb[0] >= nb[2]) ? 0 : (nb[1] >= nb[2] ? 1 : 2);
+            nb[a] -= 1;
+        }
+    }
+    // bin vectors on a grid of q = 2^(e - 19), 2^e >= max |h_a / nb_a|: every
+    // sum of three products delta_a bv_a (|delta| <= 7) is then exact in
+    // FP32; dh = h - nb bv carries the (sub-1e-4 A) quantisation to the
+    // periodic wrap
+    double bmax = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) bmax = fmax(bmax, fabs(h[3 * a + c] / nb[a]));
+    const double q = ldexp(1.0, ilogb(bmax) + 1 - 19);
+    for (int a = 0; a < 3; ++a) {
+        if (!keep_grid) {
+            const float bw = w[a] / nb[a];
+            const int m = (int)ceilf((float)rl / bw);
+            sc.m[a] = m < 1 ? 1 : (m > MAX_STENCIL ? MAX_STENCIL : m);
+            sc.nb[a] = nb[a];
+        }
+        for (int c = 0; c < 3; ++c) {
+            const double v = q * rint(h[3 * a + c] / nb[a] / q);
+            sc.bv[3 * a + c] = v;
+            sc.dh[3 * a + c] = h[3 * a + c] - nb[a] * v;
+        }
+    }
+    sc.nbins = nb[0] * nb[1] * nb[2];
+}
+
 template <typename T>
 __global__ void k_mapback(const ImgRef *imgs, int count, BandDev *bands) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -184,45 +249,13 @@ __global__ void k_mapback(const ImgRef *imgs, int count, BandDev *bands) {
     matmul3(Di, bp->h0inv, sc.hinv);  // (h0 D)^-1 = D^-1 h0^-1
     const double omega = fabs(det3(h));
     sc.omega = omega;
-    // perpendicular widths w_a = Omega / |h_b x h_c| (only choose the bin
-    // grid: FP32, shaded down by 1e-5 so the stencil is never too narrow)
-    float w[3];
-    for (int a = 0; a < 3; ++a) {
-        const double *u = h + 3 * ((a + 1) % 3), *v = h + 3 * ((a + 2) % 3);
-        const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2],
-                     cz = u[0] * v[1] - u[1] * v[0];
-        w[a] = (float)omega / sqrtf((float)(cx * cx + cy * cy + cz * cz)) * 0.99999f;
+    if (bp->skin <= 0.0) {
+        // no skin: the cell list is rebuilt at every evaluation
+        bin_geometry(bp, b.nbins_cap, h, omega, false, sc);
+        sc.rebuild = 1;
+        sc.builds += 1;
+        sc.evals += 1;
     }
-    int nb[3];
-    for (int a = 0; a < 3; ++a) {
-        const float q = floorf(w[a] / (float)bp->bin_w);
-        nb[a] = q < 1.0f ? 1 : (q > 1024.0f ? 1024 : (int)q);
-    }
-    // keep within the bin capacity: coarser bins are always correct
-    while ((long long)nb[0] * nb[1] * nb[2] > b.nbins_cap) {
-        int a = (nb[0] >= nb[1] && nb[0] >= nb[2]) ? 0 : (nb[1] >= nb[2] ? 1 : 2);
-        nb[a] -= 1;
-    }
-    // bin vectors on a grid of q = 2^(e - 19), 2^e >= max |h_a / nb_a|: every
-    // sum of three products delta_a bv_a (|delta| <= 7) is then exact in
-    // FP32; dh = h - nb bv carries the (sub-1e-4 A) quantisation to the
-    // periodic wrap
-    double bmax = 0.0;
-    for (int a = 0; a < 3; ++a)
-        for (int c = 0; c < 3; ++c) bmax = fmax(bmax, fabs(h[3 * a + c] / nb[a]));
-    const double q = ldexp(1.0, ilogb(bmax) + 1 - 19);
-    for (int a = 0; a < 3; ++a) {
-        const float bw = w[a] / nb[a];
-        const int m = (int)ceilf((float)bp->rc / bw);
-        sc.m[a] = m < 1 ? 1 : (m > MAX_STENCIL ? MAX_STENCIL : m);
-        sc.nb[a] = nb[a];
-        for (int c = 0; c < 3; ++c) {
-            const double v = q * rint(h[3 * a + c] / nb[a] / q);
-            sc.bv[3 * a + c] = v;
-            sc.dh[3 * a + c] = h[3 * a + c] - nb[a] * v;
-        }
-    }
-    sc.nbins = nb[0] * nb[1] * nb[2];
 }
 
 template <typename T>
@@ -230,18 +263,58 @@ __global__ void __launch_bounds__(TILE) k_bin_assign(const Tile *tiles, BandDev 
     using T4 = typename Vec4<T>::type;
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
-    int i = tl.t * TILE + threadIdx.x;
-    if (i >= b.n) return;
     const ImgScalars &sc = b.sc[tl.img];
     const BandParams *bp = b.bp;
+    if (!sc.rebuild) {
+        // keep the bins of the build: thread = slot, offset from the centre
+        // of the slot's bin at the current position (unwrapped as at the build)
+        const int t = tl.t * TILE + threadIdx.x;
+        if (t >= b.n) return;
+        const size_t st = (size_t)tl.img * b.n + t;
+        const int i = b.slot_atom[st];
+        const int bin = b.slot_bin[st];
+        const int *wr = b.atom_wrap + ((size_t)tl.img * b.n + i) * 3;
+        const T *Xi = (const T *)b.X + ((size_t)tl.img * b.rows + i) * 3;
+        const double rt[3] = {(double)Xi[0], (double)Xi[1], (double)Xi[2]};
+        const int bi[3] = {bin / (sc.nb[1] * sc.nb[2]), (bin / sc.nb[2]) % sc.nb[1], bin % sc.nb[2]};
+        double s[3], off[3];
+        for (int a = 0; a < 3; ++a)
+            s[a] = (rt[0] * bp->h0inv[a] + rt[1] * bp->h0inv[3 + a] + rt[2] * bp->h0inv[6 + a]) -
+                   (double)wr[a];
+        for (int c = 0; c < 3; ++c) {
+            const double R = s[0] * sc.h[c] + s[1] * sc.h[3 + c] + s[2] * sc.h[6 + c];
+            const double ctr = (bi[0] + 0.5) * sc.bv[c] + (bi[1] + 0.5) * sc.bv[3 + c] +
+                               (bi[2] + 0.5) * sc.bv[6 + c];
+            off[c] = R - ctr;
+        }
+        T4 o, lo;
+        o.x = (T)off[0];
+        o.y = (T)off[1];
+        o.z = (T)off[2];
+        o.w = (T)bi[2];
+        lo.x = (T)(off[0] - (double)o.x);
+        lo.y = (T)(off[1] - (double)o.y);
+        lo.z = (T)(off[2] - (double)o.z);
+        lo.w = (T)0;
+        ((T4 *)b.slot_off)[st] = o;
+        ((T4 *)b.slot_off_lo)[st] = lo;
+        return;
+    }
+    int i = tl.t * TILE + threadIdx.x;
+    if (i >= b.n) return;
     const T *Xi = (const T *)b.X + ((size_t)tl.img * b.rows + i) * 3;
     double rt[3] = {(double)Xi[0], (double)Xi[1], (double)Xi[2]};
     double s[3];
-    int bi[3];
+    int bi[3], wrap[3];
     for (int a = 0; a < 3; ++a) {
         s[a] = rt[0] * bp->h0inv[a] + rt[1] * bp->h0inv[3 + a] + rt[2] * bp->h0inv[6 + a];
-        s[a] -= floor(s[a]);
-        if (s[a] >= 1.0) s[a] = 0.0;
+        const double fl = floor(s[a]);
+        s[a] -= fl;
+        wrap[a] = (int)fl;
+        if (s[a] >= 1.0) {
+            s[a] = 0.0;
+            wrap[a] += 1;
+        }
         int q = (int)(s[a] * sc.nb[a]);
         bi[a] = q >= sc.nb[a] ? sc.nb[a] - 1 : q;
     }
@@ -269,6 +342,95 @@ __global__ void __launch_bounds__(TILE) k_bin_assign(const Tile *tiles, BandDev 
     lo.w = (T)0;
     ((T4 *)b.atom_off)[ai] = o;
     ((T4 *)b.atom_off_lo)[ai] = lo;
+    if (bp->skin > 0.0) {  // reference state of the build
+        T4 x;
+        x.x = Xi[0];
+        x.y = Xi[1];
+        x.z = Xi[2];
+        x.w = (T)0;
+        ((T4 *)b.ref_X)[ai] = x;
+        for (int a = 0; a < 3; ++a) b.atom_wrap[ai * 3 + a] = wrap[a];
+    }
+}
+
+// Largest displacement |R~ - R~_b| since the build, one value per atom tile.
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_skin_check(const Tile *tiles, BandDev *bands) {
+    using T4 = typename Vec4<T>::type;
+    Tile tl = tiles[blockIdx.x];
+    BandDev &b = bands[tl.band];
+    if (b.bp->skin <= 0.0) return;  // uniform over the block
+    const int i = tl.t * TILE + threadIdx.x;
+    T d2 = (T)0;
+    if (i < b.n) {
+        const T *Xi = (const T *)b.X + ((size_t)tl.img * b.rows + i) * 3;
+        const T4 r = ((const T4 *)b.ref_X)[(size_t)tl.img * b.n + i];
+        const T dx = Xi[0] - r.x, dy = Xi[1] - r.y, dz = Xi[2] - r.z;
+        d2 = dx * dx + dy * dy + dz * dz;
+    }
+    for (int o = 16; o > 0; o >>= 1) d2 = fmax(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+    __shared__ T wmax[TILE / 32];
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = d2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T m = wmax[0];
+        for (int q = 1; q < TILE / 32; ++q) m = fmax(m, wmax[q]);
+        b.skin_part[(size_t)tl.img * b.atpi + tl.t] = sqrt((double)m);
+    }
+}
+
+// upper bound of the spectral norm of a 3x3 matrix: the smaller of the
+// Frobenius norm and sqrt(|A|_1 |A|_inf)
+__device__ inline double norm2_bound(const double *A) {
+    double f = 0.0, c1 = 0.0, ci = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        double rs = 0.0, cs = 0.0;
+        for (int j = 0; j < 3; ++j) {
+            f += A[3 * i + j] * A[3 * i + j];
+            rs += fabs(A[3 * i + j]);
+            cs += fabs(A[3 * j + i]);
+        }
+        ci = fmax(ci, rs);
+        c1 = fmax(c1, cs);
+    }
+    return fmin(sqrt(f), sqrt(c1 * ci));
+}
+
+// One warp per image: keep the bins of the build while the bound in the
+// header comment holds, else rebuild (and always when forced, when the
+// band's images were rearranged, or while autotuning).
+__global__ void k_skin_decide(const ImgRef *imgs, BandDev *bands, int force) {
+    ImgRef r = imgs[blockIdx.x];
+    BandDev &b = bands[r.band];
+    const BandParams *bp = b.bp;
+    if (bp->skin <= 0.0) return;
+    ImgScalars &sc = b.sc[r.img];
+    const double *part = b.skin_part + (size_t)r.img * b.atpi;
+    double d = 0.0;
+    for (int t = threadIdx.x; t < b.atpi; t += 32) d = fmax(d, part[t]);
+    d = warp_max(d);
+    if (threadIdx.x != 0) return;
+    bool rebuild = force || bp->stale || bp->tune_rebuild || sc.builds == 0;
+    if (!rebuild) {
+        double Dbi[9], M[9];
+        inv3(sc.Db, Dbi);
+        matmul3(Dbi, sc.D, M);
+        for (int k = 0; k < 9; k += 4) M[k] -= 1.0;
+        // small relative margins cover the FP32 list test and displacement
+        const double bound = bp->rl * (1.0 - 1e-5) * (1.0 - norm2_bound(M)) -
+                             2.0 * d * norm2_bound(sc.D) * (1.0 + 1e-5);
+        rebuild = !(bound > bp->rc);
+    }
+    if (rebuild) {
+        bin_geometry(bp, b.nbins_cap, sc.h, sc.omega, false, sc);
+        for (int k = 0; k < 9; ++k) sc.Db[k] = sc.D[k];
+        sc.builds += 1;
+    } else {
+        bin_geometry(bp, b.nbins_cap, sc.h, sc.omega, true, sc);
+    }
+    sc.rebuild = rebuild ? 1 : 0;
+    sc.dmax = d;
+    sc.evals += 1;
 }
 
 // Exclusive scan of the bin counts, in three passes over SCAN_TILE-bin
@@ -305,6 +467,7 @@ __device__ inline int block_excl_scan_1024(int v, int *total) {
 __global__ void __launch_bounds__(256) k_bin_tilesum(const ImgRef *imgs, BandDev *bands) {
     ImgRef r = imgs[blockIdx.y];
     BandDev &b = bands[r.band];
+    if (!b.sc[r.img].rebuild) return;
     const int nb = b.sc[r.img].nbins;
     const int t0 = blockIdx.x * SCAN_TILE;
     if (t0 >= nb) return;
@@ -325,6 +488,7 @@ __global__ void __launch_bounds__(256) k_bin_tilesum(const ImgRef *imgs, BandDev
 __global__ void __launch_bounds__(1024) k_bin_tilescan(const ImgRef *imgs, BandDev *bands) {
     ImgRef r = imgs[blockIdx.x];
     BandDev &b = bands[r.band];
+    if (!b.sc[r.img].rebuild) return;
     const int nt = (b.sc[r.img].nbins + SCAN_TILE - 1) / SCAN_TILE;
     int *ts = b.bin_tsum + (size_t)r.img * b.tsum_cap;
     int carry = 0;
@@ -341,6 +505,7 @@ __global__ void __launch_bounds__(1024) k_bin_tilescan(const ImgRef *imgs, BandD
 __global__ void __launch_bounds__(1024) k_bin_scanfill(const ImgRef *imgs, BandDev *bands) {
     ImgRef r = imgs[blockIdx.y];
     BandDev &b = bands[r.band];
+    if (!b.sc[r.img].rebuild) return;
     const int nb = b.sc[r.img].nbins;
     const int t0 = blockIdx.x * SCAN_TILE;
     if (t0 >= nb) return;
@@ -361,6 +526,7 @@ __global__ void __launch_bounds__(1024) k_bin_scanfill(const ImgRef *imgs, BandD
 __global__ void __launch_bounds__(TILE) k_bin_scatter(const Tile *tiles, BandDev *bands) {
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
+    if (!b.sc[tl.img].rebuild) return;
     int i = tl.t * TILE + threadIdx.x;
     if (i >= b.n) return;
     size_t ai = (size_t)tl.img * b.n + i;
@@ -375,6 +541,7 @@ __global__ void k_bin_order(const ImgRef *imgs, BandDev *bands) {
     using T4 = typename Vec4<T>::type;
     ImgRef r = imgs[blockIdx.y];
     BandDev &b = bands[r.band];
+    if (!b.sc[r.img].rebuild) return;
     int bin = blockIdx.x * blockDim.x + threadIdx.x;
     if (bin >= b.sc[r.img].nbins) return;
     const int *start = b.bin_start + (size_t)r.img * (b.nbins_cap + 1);
@@ -420,6 +587,15 @@ void launch_bin_assign(const Tile *tiles, int ntiles, BandDev *bands, cudaStream
     if (ntiles <= 0) return;
     k_bin_assign<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
 }
+template <typename T>
+void launch_skin_check(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    k_skin_check<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
+}
+void launch_skin_decide(const ImgRef *imgs, int count, BandDev *bands, int force, cudaStream_t s) {
+    if (count <= 0) return;
+    k_skin_decide<<<count, 32, 0, s>>>(imgs, bands, force);
+}
 void launch_bin_scan(const ImgRef *imgs, int count, int max_bins, BandDev *bands,
                      cudaStream_t s, int part) {
     if (count <= 0 || max_bins <= 0) return;
@@ -449,6 +625,7 @@ void launch_cartesian(const ImgRef *imgs, int count, int max_n, BandDev *bands, 
 #define CFNEB_INST(T)                                                                     \
     template void launch_mapback<T>(const ImgRef *, int, BandDev *, cudaStream_t);       \
     template void launch_bin_assign<T>(const Tile *, int, BandDev *, cudaStream_t);      \
+    template void launch_skin_check<T>(const Tile *, int, BandDev *, cudaStream_t);      \
     template void launch_bin_order<T>(const ImgRef *, int, int, BandDev *, cudaStream_t); \
     template void launch_cartesian<T>(const ImgRef *, int, int, BandDev *, cudaStream_t);
 CFNEB_INST(float)

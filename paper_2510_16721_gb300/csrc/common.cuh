@@ -21,7 +21,7 @@
 namespace cfneb {
 
 constexpr int TILE = 128;           // rows per tile = threads per block
-constexpr int MAXN_TERSOFF = 12;    // Tersoff neighbour capacity per atom
+constexpr int MAXN_TERSOFF = 16;    // Tersoff list capacity per atom (entries within rl)
 constexpr int NPART = 12;           // doubles per tile partial record
 constexpr int MAX_STENCIL = 7;      // |delta| <= 7 bins per axis
 
@@ -48,10 +48,14 @@ struct ImgScalars {
     double coef[2];      // f_NEB = F + coef[0] dX+ + coef[1] dX-
     double pairs;        // neighbour entries inside the cutoff (last evaluation)
     double triples;      // ordered neighbour pairs (j, k != j) of the atoms (Tersoff)
+    double Db[9];        // D when the cell list was last built (skin test)
+    double dmax;         // largest |R~ - R~ at the build| of this evaluation
+    long long builds;    // cell-list builds of this image slot
+    long long evals;     // evaluations of this image slot
     int nb[3];           // bins per axis
     int m[3];            // stencil half width per axis
     int nbins;
-    int pad;
+    int rebuild;         // this evaluation rebuilds the cell list
 };
 
 struct BandParams {
@@ -62,6 +66,8 @@ struct BandParams {
     double k;            // spring constant
     double dt0, dt_max, maxstep;
     double rc;           // potential cutoff
+    double skin;         // neighbour-list skin (0: rebuild every evaluation)
+    double rl;           // list cutoff rc + skin (0 in records made before skins: rc)
     double bin_w;        // target bin width
     double ftol;         // convergence tolerance (< 0: never converged)
     double pot[12];      // LJ: eps, sigma, rc, phi(rc) or 0; Tersoff: A, B,
@@ -81,6 +87,8 @@ struct BandParams {
     int converged;       // fmax < ftol at the last evaluation
     int move;            // the last step moved the images
     int status;
+    int stale;           // every image rebuilds at the next evaluation
+    int tune_rebuild;    // rebuild at every evaluation (autotuning)
 };
 
 struct BandDev {
@@ -97,12 +105,15 @@ struct BandDev {
     int *atom_bin, *atom_rank, *slot_unsorted, *slot_atom, *slot_bin, *atom_slot;  // [ncap][n]
     void *atom_off, *slot_off;   // [ncap][n] x 4 T (x, y, z, pad): offsets, leading part
     void *atom_off_lo, *slot_off_lo;  // [ncap][n] x 4 T: offset - leading part
+    // neighbour-list reuse: positions and periodic wraps at the last build
+    void *ref_X;         // [ncap][n] x 4 T: R~ at the build (atom order)
+    int *atom_wrap;      // [ncap][n][3]: floor(s) at the build
+    double *skin_part;   // [ncap][atpi]: per-tile max displacement
     // Tersoff per-slot neighbour data
     int *nbr_cnt;        // [ncap][n]
     int *nbr_slot;       // [ncap][MAXN][n]
     int *nbr_code;       // [ncap][MAXN][n]
     void *nbr_P;         // [ncap][3*MAXN][n] of T
-    void *nbr_R;         // [ncap][4*MAXN][n] of T: pair vector (leading part), r - R
     // partial sums
     double *atom_part;   // [ncap][atpi][NPART]
     double *row_part;    // [ncap][rtpi][NPART]
@@ -229,6 +240,10 @@ __device__ inline void block_sum_t(T (&v)[K], double *out) {
 
 template <typename T>
 void launch_mapback(const ImgRef *imgs, int count, BandDev *bands, cudaStream_t s);
+// displacement since the last build (per tile) and the per-image decision
+template <typename T>
+void launch_skin_check(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
+void launch_skin_decide(const ImgRef *imgs, int count, BandDev *bands, int force, cudaStream_t s);
 template <typename T>
 void launch_bin_assign(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 // part 0: tile sums, 1: scan of the tile sums, 2: final per-bin scan

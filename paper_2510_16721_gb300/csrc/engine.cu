@@ -47,12 +47,12 @@ struct CudaFail {
     } while (0)
 
 enum KernelId {
-    K_MAPBACK, K_BIN_ASSIGN, K_BIN_TILESUM, K_BIN_TILESCAN, K_BIN_SCANFILL, K_BIN_SCATTER,
+    K_MAPBACK, K_SKIN_CHECK, K_SKIN_DECIDE, K_BIN_ASSIGN, K_BIN_TILESUM, K_BIN_TILESCAN, K_BIN_SCANFILL, K_BIN_SCATTER,
     K_BIN_ORDER, K_LJ, K_TERS_LIST, K_TERS_PARTIALS, K_TERS_GATHER, K_IMAGE_FINALIZE,
     K_BAND_DOTS, K_DOTS_REDUCE, K_NEB_COEF, K_NEB_FORCE, K_FIRE_SCALARS, K_FIRE_UPDATE, K_COUNT
 };
 const char *kKernelNames[K_COUNT] = {
-    "mapback", "bin_assign", "bin_tilesum", "bin_tilescan", "bin_scanfill", "bin_scatter",
+    "mapback", "skin_check", "skin_decide", "bin_assign", "bin_tilesum", "bin_tilescan", "bin_scanfill", "bin_scatter",
     "bin_order", "lj_force", "tersoff_list", "tersoff_partials", "tersoff_gather",
     "image_finalize", "band_dots", "dots_reduce", "neb_coef", "neb_force", "fire_scalars",
     "fire_update"};
@@ -97,6 +97,7 @@ struct cfneb_band {
     long long last_check = -1;
     long long move_limit = 1LL << 62;  // host copy of BandParams::move_limit
     double rc = 0.0;             // potential cutoff
+    double rl = 0.0;             // list cutoff rc + skin
     std::tuple<int, int, int, int> tune_key{};
     double ftol = -1.0;
     // stream ordering
@@ -231,6 +232,7 @@ struct LaunchSet {
     const int *band_ids = nullptr;
     int nbands = 0;
     int max_bins = 0;                    // largest nbins_cap among the bands
+    int force_rebuild = 0;               // rebuild every listed image's cell list
 };
 
 // optional CUDA-event bracketing of every launch (profiling)
@@ -257,12 +259,21 @@ void enqueue_eval_set(const LaunchSet &ls, Launcher &L, bool forces = true) {
     BandDev *d = ls.d_bands;
     cudaStream_t s = ls.s;
     L.pre(K_MAPBACK); launch_mapback<T>(ls.imgs, ls.nimg, d, s); L.post(K_MAPBACK);
+    L.pre(K_SKIN_CHECK); launch_skin_check<T>(ls.atiles, ls.n_atiles, d, s); L.post(K_SKIN_CHECK);
+    L.pre(K_SKIN_DECIDE); launch_skin_decide(ls.imgs, ls.nimg, d, ls.force_rebuild, s);
+    L.post(K_SKIN_DECIDE);
     L.pre(K_BIN_ASSIGN); launch_bin_assign<T>(ls.atiles, ls.n_atiles, d, s); L.post(K_BIN_ASSIGN);
     L.pre(K_BIN_TILESUM); launch_bin_scan(ls.imgs, ls.nimg, ls.max_bins, d, s, 0); L.post(K_BIN_TILESUM);
     L.pre(K_BIN_TILESCAN); launch_bin_scan(ls.imgs, ls.nimg, ls.max_bins, d, s, 1); L.post(K_BIN_TILESCAN);
     L.pre(K_BIN_SCANFILL); launch_bin_scan(ls.imgs, ls.nimg, ls.max_bins, d, s, 2); L.post(K_BIN_SCANFILL);
     L.pre(K_BIN_SCATTER); launch_bin_scatter(ls.atiles, ls.n_atiles, d, s); L.post(K_BIN_SCATTER);
     L.pre(K_BIN_ORDER); launch_bin_order<T>(ls.imgs, ls.nimg, ls.max_bins, d, s); L.post(K_BIN_ORDER);
+    // the Tersoff list indexes cell-list slots: it is rebuilt with every
+    // cell list, also by an energy-only evaluation
+    if (ls.n_ters) {
+        L.pre(K_TERS_LIST); launch_tersoff_list<T>(ls.atiles_ters, ls.n_ters, d, s);
+        L.post(K_TERS_LIST);
+    }
     if (!forces) {
         launch_energy64<T>(ls.atiles, ls.n_atiles, ls.imgs, ls.nimg, d, s);
         return;
@@ -271,8 +282,6 @@ void enqueue_eval_set(const LaunchSet &ls, Launcher &L, bool forces = true) {
         L.pre(K_LJ); launch_lj<T>(ls.atiles_lj, ls.n_lj, d, s); L.post(K_LJ);
     }
     if (ls.n_ters) {
-        L.pre(K_TERS_LIST); launch_tersoff_list<T>(ls.atiles_ters, ls.n_ters, d, s);
-        L.post(K_TERS_LIST);
         L.pre(K_TERS_PARTIALS); launch_tersoff_partials<T>(ls.atiles_ters, ls.n_ters, d, s);
         L.post(K_TERS_PARTIALS);
         L.pre(K_TERS_GATHER); launch_tersoff_gather<T>(ls.atiles_ters, ls.n_ters, d, s);
@@ -296,7 +305,7 @@ void enqueue_step_set(const LaunchSet &ls, Launcher &L) {
 }
 
 int launches_in_set(const LaunchSet &ls) {
-    return 7 + (ls.n_lj ? 1 : 0) + (ls.n_ters ? 3 : 0) + 1 + 6;
+    return 9 + (ls.n_lj ? 1 : 0) + (ls.n_ters ? 3 : 0) + 1 + 6;
 }
 
 LaunchSet band_set(cfneb_band *b, const ImgRef *imgs, int nimg, const Tile *atiles, int nat) {
@@ -329,7 +338,11 @@ LaunchSet band_step_set(cfneb_band *b) {
 template <typename T>
 void enqueue_eval(cfneb_band *b, Launcher &L, const ImgRef *imgs, int nimg, const Tile *atiles,
                   int natiles, bool forces = true) {
-    enqueue_eval_set<T>(band_set(b, imgs, nimg, atiles, natiles), L, forces);
+    // ad-hoc image sets (endpoints, new images, reported energies) are
+    // evaluated from freshly built cell lists
+    LaunchSet ls = band_set(b, imgs, nimg, atiles, natiles);
+    ls.force_rebuild = 1;
+    enqueue_eval_set<T>(ls, L, forces);
 }
 
 int launches_per_step(const cfneb_band *b) {
@@ -465,6 +478,7 @@ void fire_reset(cfneb_band *b) {
     p->alpha = 0.1;
     p->npos = 0;
     p->fresh = 1;
+    p->stale = 1;  // images were inserted, removed or moved: rebuild every list
     CK(cudaMemcpyAsync(b->dv.bp, p, sizeof(BandParams), cudaMemcpyHostToDevice, b->s));
     CK(cudaMemsetAsync(b->dv.v, 0, (size_t)b->ncap * b->dv.rows * 3 * b->ts, b->s));
     CK(cudaStreamSynchronize(b->s));
@@ -680,16 +694,23 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
         for (int k = 0; k < 11; ++k) P.pot[k] = zero ? kTersoff1988C[k] : pot->tersoff[k];
         rc = P.pot[9] + P.pot[10];
     }
+    // neighbour-list skin: the caller's, or 0.15 A for Tersoff (carbon's
+    // second neighbours, 2.46-2.52 A, stay outside R + D + skin, so the lists
+    // keep their 3-4 entries) and none for LJ (its force kernel walks the
+    // cell list directly)
+    const double skin = opt->skin >= 0.0 ? opt->skin : (pot->kind == CFNEB_TERSOFF ? 0.15 : 0.0);
+    const double rl = rc + skin;
+    b->rl = rl;
     // bin width: the caller's, the cached autotuned one for this class, or rc
     const double dens = (double)b->n / std::fabs(det3(A->cell)) * rc * rc * rc;
     b->tune_key = std::make_tuple(pot->kind, opt->precision,
                                   (int)std::floor(std::log2((double)std::max(1, b->n))),
                                   (int)std::floor(2.0 * std::log2(std::max(dens, 1e-3))));
     double bscale = opt->bin_scale > 0 ? opt->bin_scale : tuned_scale(b->tune_key);
-    double bin_w = rc * bscale;
+    double bin_w = rl * bscale;
     b->rc = rc;
     // reserve bins for the finest autotuning candidate when tuning may follow
-    const double cap_w = opt->bin_scale > 0 ? bin_w : rc * kTuneScales[0];
+    const double cap_w = opt->bin_scale > 0 ? bin_w : rl * kTuneScales[0];
     // geometry
     const int n = b->n, rows = n + 3;
     BandDev &d = b->dv;
@@ -723,12 +744,16 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
     d.slot_off = dalloc(b, na * 4 * b->ts);
     d.atom_off_lo = dalloc(b, na * 4 * b->ts);
     d.slot_off_lo = dalloc(b, na * 4 * b->ts);
+    if (skin > 0.0) {
+        d.ref_X = dalloc(b, na * 4 * b->ts);
+        d.atom_wrap = (int *)dalloc(b, na * 3 * sizeof(int));
+        d.skin_part = (double *)dalloc(b, nc * d.atpi * sizeof(double));
+    }
     if (pot->kind == CFNEB_TERSOFF) {
         d.nbr_cnt = (int *)dalloc(b, na * sizeof(int));
         d.nbr_slot = (int *)dalloc(b, na * MAXN_TERSOFF * sizeof(int));
         d.nbr_code = (int *)dalloc(b, na * MAXN_TERSOFF * sizeof(int));
         d.nbr_P = dalloc(b, na * 3 * MAXN_TERSOFF * b->ts);
-        d.nbr_R = dalloc(b, na * 4 * MAXN_TERSOFF * b->ts);
     }
     d.atom_part = (double *)dalloc(b, nc * d.atpi * NPART * sizeof(double));
     d.row_part = (double *)dalloc(b, nc * d.rtpi * NPART * sizeof(double));
@@ -760,6 +785,9 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
     P.dt_max = opt->dt_max > 0 ? opt->dt_max : 10.0 * opt->dt;
     P.maxstep = opt->maxstep;
     P.rc = rc;
+    P.skin = skin;
+    P.rl = rl;
+    P.stale = 1;
     P.bin_w = bin_w;
     P.ftol = -1.0;
     P.move_limit = 1LL << 62;
@@ -819,6 +847,14 @@ namespace {
 void set_bin_w(cfneb_band *b, double w) {
     read_params(b);
     b->h_bp->bin_w = w;
+    b->h_bp->stale = 1;  // the next evaluation bins at the new width
+    CK(cudaMemcpyAsync(b->dv.bp, b->h_bp, sizeof(BandParams), cudaMemcpyHostToDevice, b->s));
+    CK(cudaStreamSynchronize(b->s));
+}
+
+void set_tune_rebuild(cfneb_band *b, int on) {
+    read_params(b);
+    b->h_bp->tune_rebuild = on;
     CK(cudaMemcpyAsync(b->dv.bp, b->h_bp, sizeof(BandParams), cudaMemcpyHostToDevice, b->s));
     CK(cudaStreamSynchronize(b->s));
 }
@@ -847,15 +883,18 @@ double autotune_band(cfneb_band *b, int steps) {
     const double keep_ftol = b->h_bp->ftol;
     const long long now = b->h_bp->steps;
     set_control(b, keep_ftol, now);  // evaluate, never move
+    // time full rebuilds: with a skin the bin width only matters there
+    set_tune_rebuild(b, 1);
     double best = kTuneScales[2], best_ms = 1e300;
     for (double sc : kTuneScales) {
-        const double ms = time_bin_w(b, sc * b->rc, steps);
+        const double ms = time_bin_w(b, sc * b->rl, steps);
         if (ms < best_ms) {
             best_ms = ms;
             best = sc;
         }
     }
-    set_bin_w(b, best * b->rc);
+    set_tune_rebuild(b, 0);
+    set_bin_w(b, best * b->rl);
     set_control(b, keep_ftol, keep_limit);
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[b->tune_key] = best;
@@ -1258,6 +1297,7 @@ int cfneb_default_options(cfneb_options *o) {
     o->alpha_ins = 1.5;
     o->alpha_del = 0.5;
     o->bin_scale = 0.0;
+    o->skin = -1.0;
     return CFNEB_OK;
 }
 
@@ -1291,6 +1331,17 @@ int cfneb_create_band(const cfneb_structure *initial, const cfneb_structure *fin
     if (opt.dt <= 0 || opt.maxstep <= 0) return CFNEB_ERR_INVALID_ARG;
     if (opt.k_ref <= 0) opt.k_ref = 10;
     if (opt.bin_scale != 0 && opt.bin_scale < 0.25) return CFNEB_ERR_INVALID_ARG;
+    {
+        // a skin (< 0: the default) of at most the potential's cutoff
+        double rcut = potential->rc;
+        if (potential->kind == CFNEB_TERSOFF) {
+            const bool dflt = std::all_of(potential->tersoff, potential->tersoff + 11,
+                                          [](double v) { return v == 0.0; });
+            rcut = dflt ? kTersoff1988C[9] + kTersoff1988C[10]
+                        : potential->tersoff[9] + potential->tersoff[10];
+        }
+        if (!(opt.skin < 0.0 || opt.skin <= rcut)) return CFNEB_ERR_INVALID_ARG;
+    }
     if (cell_filter && cell_filter->variant != CFNEB_ROTFREE_B &&
         cell_filter->variant != CFNEB_DEFGRAD_D)
         return CFNEB_ERR_INVALID_ARG;
@@ -1483,6 +1534,7 @@ int cfneb_evaluate(const cfneb_structure *structures, int32_t count,
         cfneb_options opt;
         cfneb_default_options(&opt);
         opt.precision = precision;
+        opt.skin = 0.0;  // one evaluation: nothing to reuse
         cfneb_cell_filter cf{1, CFNEB_ROTFREE_B, 0.0, 0.0};
         cfneb_band *b = nullptr;
         int st = cfneb_create_band(&S, &S, 3, potential, &cf, &opt, cuda_stream, &b);
@@ -1696,7 +1748,7 @@ int cfneb_batch_autotune(cfneb_batch *bt, int32_t steps) {
             auto it = done.find(b->tune_key);
             const double sc = it != done.end() ? it->second : autotune_band(b, steps);
             done[b->tune_key] = sc;
-            set_bin_w(b, sc * b->rc);
+            set_bin_w(b, sc * b->rl);
         }
         bt_leave(bt);
         return CFNEB_OK;
@@ -1855,6 +1907,31 @@ int cfneb_get_work(const cfneb_band *cb, double *pairs, double *triples) {
         }
         if (pairs) *pairs = p;
         if (triples) *triples = t;
+        leave(b);
+        return CFNEB_OK;
+    } catch (CudaFail &) {
+        return CFNEB_ERR_CUDA;
+    }
+}
+
+int cfneb_get_list_stats(const cfneb_band *cb, int64_t *builds, int64_t *evaluations,
+                         double *skin) {
+    cfneb_band *b = const_cast<cfneb_band *>(cb);
+    if (!b) return CFNEB_ERR_INVALID_ARG;
+    try {
+        enter(b);
+        std::vector<ImgScalars> sc(b->N);
+        CK(cudaMemcpyAsync(sc.data(), b->dv.sc, b->N * sizeof(ImgScalars),
+                           cudaMemcpyDeviceToHost, b->s));
+        CK(cudaStreamSynchronize(b->s));
+        long long nb = 0, ne = 0;
+        for (int i = 1; i < b->N - 1; ++i) {
+            nb += sc[i].builds;
+            ne += sc[i].evals;
+        }
+        if (builds) *builds = nb;
+        if (evaluations) *evaluations = ne;
+        if (skin) *skin = b->rl - b->rc;
         leave(b);
         return CFNEB_OK;
     } catch (CudaFail &) {

@@ -143,26 +143,70 @@ __device__ inline void gfun(const TP<T> &q, T cs, T &g, T &dg) {
 // (their neighbour loops are unrolled); the rest take a looped path
 constexpr int NFAST = 4;
 
-// Neighbour entries of slot t inside R + D into the global list (slot, stencil
-// code, leading pair vector, s = r - R); returns the total count.
+// Pair vector of entry (slot qs, stencil code) of slot t: leading parts
+// x, y, z (directions) and s = r - R to twice the working precision.
+// (b0, b1, b2) is t's bin; the entry's bin offset and periodic wrap follow
+// from the code.
 template <typename T>
-__device__ inline int ters_collect_list(const TP<T> &q, const BandDev &b, int img, int t,
-                                        const T *s_bv, const T *s_dh, const int *s_nb,
-                                        const int *s_m, T *nR) {
+__device__ inline void ters_pair(const TP<T> &q, const typename Vec4<T>::type &oi,
+                                 const typename Vec4<T>::type &oil,
+                                 const typename Vec4<T>::type &oj,
+                                 const typename Vec4<T>::type &ojl, int code, int b0, int b1,
+                                 int b2, const T *s_bv, const T *s_dh, const int *s_nb, T &x,
+                                 T &y, T &z, T &s) {
+    const int d0 = (code & 31) - 16, d1 = ((code >> 5) & 31) - 16, d2 = ((code >> 10) & 31) - 16;
+    int w0 = b0 + d0, t0 = 0, w1 = b1 + d1, t1 = 0, w2 = b2 + d2, t2 = 0;
+    while (w0 < 0) { w0 += s_nb[0]; --t0; }
+    while (w0 >= s_nb[0]) { w0 -= s_nb[0]; ++t0; }
+    while (w1 < 0) { w1 += s_nb[1]; --t1; }
+    while (w1 >= s_nb[1]) { w1 -= s_nb[1]; ++t1; }
+    while (w2 < 0) { w2 += s_nb[2]; --t2; }
+    while (w2 >= s_nb[2]) { w2 -= s_nb[2]; ++t2; }
+    // bin-centre displacement: exact (quantised bin vectors)
+    const T cx = d0 * s_bv[0] + d1 * s_bv[3] + d2 * s_bv[6];
+    const T cy = d0 * s_bv[1] + d1 * s_bv[4] + d2 * s_bv[7];
+    const T cz = d0 * s_bv[2] + d1 * s_bv[5] + d2 * s_bv[8];
+    // periodic-wrap remainder (tiny)
+    const T wx = t0 * s_dh[0] + t1 * s_dh[3] + t2 * s_dh[6];
+    const T wy = t0 * s_dh[1] + t1 * s_dh[4] + t2 * s_dh[7];
+    const T wz = t0 * s_dh[2] + t1 * s_dh[5] + t2 * s_dh[8];
+    T ex1, ey1, ez1, ex2, ey2, ez2;
+    two_sum(oj.x, -oi.x, x, ex1);
+    two_sum(oj.y, -oi.y, y, ey1);
+    two_sum(oj.z, -oi.z, z, ez1);
+    two_sum(x, cx, x, ex2);
+    two_sum(y, cy, y, ey2);
+    two_sum(z, cz, z, ez2);
+    T xl = ((ojl.x - oil.x) + wx) + (ex1 + ex2);
+    T yl = ((ojl.y - oil.y) + wy) + (ey1 + ey2);
+    T zl = ((ojl.z - oil.z) + wz) + (ez1 + ez2);
+    // renormalise: the leading part (used for directions) takes the wrap
+    // remainder, the low part keeps the rest
+    fast_two_sum(x, xl, x, xl);
+    fast_two_sum(y, yl, y, yl);
+    fast_two_sum(z, zl, z, zl);
+    T r;
+    dist_s(q, x, y, z, xl, yl, zl, r, s);
+}
+
+// Neighbour entries of slot t within rl into the global list (slot, stencil
+// code); returns the total count.  A plain FP32 screen with a 1e-5 relative
+// margin: an entry just outside R + D costs nothing but a zero term.
+template <typename T>
+__device__ inline int ters_collect_list(T rl2, const BandDev &b, int img, int t, const T *s_bv,
+                                        const T *s_dh, const int *s_nb, const int *s_m) {
     using T4 = typename Vec4<T>::type;
     const int n = b.n;
     const size_t base = (size_t)img * n;
     const T4 *off = (const T4 *)b.slot_off + base;
-    const T4 *offl = (const T4 *)b.slot_off_lo + base;
     const int *start = b.bin_start + (size_t)img * (b.nbins_cap + 1);
     int *nslot = b.nbr_slot + (size_t)img * MAXN_TERSOFF * n;
     int *ncode = b.nbr_code + (size_t)img * MAXN_TERSOFF * n;
-    const T rc2_screen = q.Rhi * q.Rhi * (T)1.00001;
+    const T rc2_screen = rl2 * (T)1.00001;
     const int bin = b.slot_bin[base + t];
     const int nb1 = s_nb[1], nb2 = s_nb[2];
     const int b0 = bin / (nb1 * nb2), b1 = (bin / nb2) % nb1, b2 = bin % nb2;
     const T4 oi = off[t];
-    const T4 oil = offl[t];
     int total = 0;
     for (int d0 = -s_m[0]; d0 <= s_m[0]; ++d0) {
         int w0 = b0 + d0, t0 = 0;
@@ -177,46 +221,24 @@ __device__ inline int ters_collect_list(const TP<T> &q, const BandDev &b, int im
                 while (w2 < 0) { w2 += nb2; --t2; }
                 while (w2 >= nb2) { w2 -= nb2; ++t2; }
                 const int w = (w0 * nb1 + w1) * nb2 + w2;
-                // bin-centre displacement: exact (quantised bin vectors)
-                const T cx = d0 * s_bv[0] + d1 * s_bv[3] + d2 * s_bv[6];
-                const T cy = d0 * s_bv[1] + d1 * s_bv[4] + d2 * s_bv[7];
-                const T cz = d0 * s_bv[2] + d1 * s_bv[5] + d2 * s_bv[8];
-                // periodic-wrap remainder (tiny)
-                const T wx = t0 * s_dh[0] + t1 * s_dh[3] + t2 * s_dh[6];
-                const T wy = t0 * s_dh[1] + t1 * s_dh[4] + t2 * s_dh[7];
-                const T wz = t0 * s_dh[2] + t1 * s_dh[5] + t2 * s_dh[8];
-                const T ux0 = (cx + wx) - oi.x, uy0 = (cy + wy) - oi.y, uz0 = (cz + wz) - oi.z;
+                const T ux0 = (d0 * s_bv[0] + d1 * s_bv[3] + d2 * s_bv[6]) +
+                              (t0 * s_dh[0] + t1 * s_dh[3] + t2 * s_dh[6]) - oi.x;
+                const T uy0 = (d0 * s_bv[1] + d1 * s_bv[4] + d2 * s_bv[7]) +
+                              (t0 * s_dh[1] + t1 * s_dh[4] + t2 * s_dh[7]) - oi.y;
+                const T uz0 = (d0 * s_bv[2] + d1 * s_bv[5] + d2 * s_bv[8]) +
+                              (t0 * s_dh[2] + t1 * s_dh[5] + t2 * s_dh[8]) - oi.z;
                 const int q1 = start[w + 1];
                 for (int qs = start[w]; qs < q1; ++qs) {
                     const T4 oj = off[qs];
                     const T ux = oj.x + ux0, uy = oj.y + uy0, uz = oj.z + uz0;
-                    if (ux * ux + uy * uy + uz * uz >= rc2_screen) continue;
-                    const T4 ojl = offl[qs];
-                    T x, y, z, ex1, ey1, ez1, ex2, ey2, ez2;
-                    two_sum(oj.x, -oi.x, x, ex1);
-                    two_sum(oj.y, -oi.y, y, ey1);
-                    two_sum(oj.z, -oi.z, z, ez1);
-                    two_sum(x, cx, x, ex2);
-                    two_sum(y, cy, y, ey2);
-                    two_sum(z, cz, z, ez2);
-                    T xl = ((ojl.x - oil.x) + wx) + (ex1 + ex2);
-                    T yl = ((ojl.y - oil.y) + wy) + (ey1 + ey2);
-                    T zl = ((ojl.z - oil.z) + wz) + (ez1 + ez2);
-                    // renormalise: the leading part (used for directions)
-                    // takes the wrap remainder, the low part keeps the rest
-                    fast_two_sum(x, xl, x, xl);
-                    fast_two_sum(y, yl, y, yl);
-                    fast_two_sum(z, zl, z, zl);
-                    T r, s;
-                    dist_s(q, x, y, z, xl, yl, zl, r, s);
-                    if (!(sub_rn(s, q.D) < q.Dlo && r > (T)0)) continue;
+                    const T r2 = ux * ux + uy * uy + uz * uz;
+                    // r2 == 0: the atom itself at zero shift
+                    if (!(r2 < rc2_screen) || (qs == t && d0 == 0 && d1 == 0 && d2 == 0 &&
+                                               t0 == 0 && t1 == 0 && t2 == 0))
+                        continue;
                     if (total < MAXN_TERSOFF) {
                         nslot[(size_t)total * n + t] = qs;
                         ncode[(size_t)total * n + t] = pack_code(d0, d1, d2);
-                        nR[(size_t)(4 * total + 0) * n + t] = x;
-                        nR[(size_t)(4 * total + 1) * n + t] = y;
-                        nR[(size_t)(4 * total + 2) * n + t] = z;
-                        nR[(size_t)(4 * total + 3) * n + t] = s;
                     }
                     ++total;
                 }
@@ -242,6 +264,7 @@ __device__ inline void ters_site(const TP<T> &q, int cnt, const T (&rx)[NM], con
 #pragma unroll (NM <= NFAST ? NM : 1)
     for (int j = 0; j < NM; ++j) {
         if (j >= cnt) continue;
+        if (fc[j] == (T)0 && dfc[j] == (T)0) continue;  // beyond R + D: no terms
         // zeta_ij and the bond order
         T zeta = 0;
 #pragma unroll (NM <= NFAST ? NM : 1)
@@ -301,15 +324,17 @@ __device__ inline void ters_site(const TP<T> &q, int cnt, const T (&rx)[NM], con
 }
 
 
-// Neighbour list of one step: one light thread per atom walks the cell-list
-// stencil (high occupancy hides the chained bin loads) and writes, for each
-// entry inside R + D, the neighbour slot, the stencil code, the leading part
-// of the pair vector and s = r - R, coalesced as [entry][atom].
+// Neighbour list of a rebuilt image: one light thread per atom walks the
+// cell-list stencil (high occupancy hides the chained bin loads) and writes,
+// for each entry within rl, the neighbour slot and the stencil code,
+// coalesced as [entry][atom].  Images that keep their cell list keep their
+// list too.
 template <typename T>
 __global__ void __launch_bounds__(TILE) k_ters_list(const Tile *tiles, BandDev *bands) {
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
     const ImgScalars &sc = b.sc[tl.img];
+    if (!sc.rebuild) return;  // uniform over the block
     __shared__ T s_bv[9], s_dh[9];
     __shared__ int s_nb[3], s_m[3];
     if (threadIdx.x < 9) {
@@ -324,20 +349,28 @@ __global__ void __launch_bounds__(TILE) k_ters_list(const Tile *tiles, BandDev *
     const int n = b.n;
     const int t = tl.t * TILE + threadIdx.x;
     if (t >= n) return;
-    TP<T> q;
-    q.load(*(const TersoffParams *)b.bp->pot);
-    T *nR = (T *)b.nbr_R + (size_t)tl.img * 4 * MAXN_TERSOFF * n;
-    const int total = ters_collect_list<T>(q, b, tl.img, t, s_bv, s_dh, s_nb, s_m, nR);
+    const double rl = b.bp->rl > 0.0 ? b.bp->rl : b.bp->rc;
+    const int total = ters_collect_list<T>((T)(rl * rl), b, tl.img, t, s_bv, s_dh, s_nb, s_m);
     b.nbr_cnt[(size_t)tl.img * n + t] = total < MAXN_TERSOFF ? total : MAXN_TERSOFF;
     if (total > MAXN_TERSOFF) atomicOr(&b.bp->status, ST_NBR_OVERFLOW);
 }
 
-// load the neighbour records of slot t into arrays (compile-time indices
-// for small NM: registers)
+// pair vectors of the list entries of slot t from the current offsets, into
+// arrays (compile-time indices for small NM: registers)
 template <typename T, int NM>
-__device__ inline void ters_load(const TP<T> &q, const T *nR, int n, int t, int cnt,
-                                 T (&rx)[NM], T (&ry)[NM], T (&rz)[NM], T (&rd)[NM],
-                                 T (&sr)[NM]) {
+__device__ inline void ters_load(const TP<T> &q, const BandDev &b, int img, int t, int cnt,
+                                 const T *s_bv, const T *s_dh, const int *s_nb, T (&rx)[NM],
+                                 T (&ry)[NM], T (&rz)[NM], T (&rd)[NM], T (&sr)[NM]) {
+    using T4 = typename Vec4<T>::type;
+    const int n = b.n;
+    const size_t base = (size_t)img * n;
+    const T4 *off = (const T4 *)b.slot_off + base;
+    const T4 *offl = (const T4 *)b.slot_off_lo + base;
+    const int *nslot = b.nbr_slot + (size_t)img * MAXN_TERSOFF * n;
+    const int *ncode = b.nbr_code + (size_t)img * MAXN_TERSOFF * n;
+    const int bin = b.slot_bin[base + t];
+    const int b0 = bin / (s_nb[1] * s_nb[2]), b1 = (bin / s_nb[2]) % s_nb[1], b2 = bin % s_nb[2];
+    const T4 oi = off[t], oil = offl[t];
 #pragma unroll (NM <= NFAST ? NM : 1)
     for (int k = 0; k < NM; ++k) {
         if (k >= cnt) {
@@ -345,10 +378,10 @@ __device__ inline void ters_load(const TP<T> &q, const T *nR, int n, int t, int 
             rd[k] = (T)1;
             continue;
         }
-        rx[k] = nR[(size_t)(4 * k + 0) * n + t];
-        ry[k] = nR[(size_t)(4 * k + 1) * n + t];
-        rz[k] = nR[(size_t)(4 * k + 2) * n + t];
-        sr[k] = nR[(size_t)(4 * k + 3) * n + t];
+        const int qs = nslot[(size_t)k * n + t];
+        const int code = ncode[(size_t)k * n + t];
+        ters_pair<T>(q, oi, oil, off[qs], offl[qs], code, b0, b1, b2, s_bv, s_dh, s_nb, rx[k],
+                     ry[k], rz[k], sr[k]);
         rd[k] = q.R + sr[k];
     }
 }
@@ -357,34 +390,45 @@ template <typename T>
 __global__ void __launch_bounds__(TILE) k_ters_partials(const Tile *tiles, BandDev *bands) {
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
+    const ImgScalars &sc = b.sc[tl.img];
+    __shared__ T s_bv[9], s_dh[9];
+    __shared__ int s_nb[3];
+    if (threadIdx.x < 9) {
+        s_bv[threadIdx.x] = (T)sc.bv[threadIdx.x];
+        s_dh[threadIdx.x] = (T)sc.dh[threadIdx.x];
+    }
+    if (threadIdx.x < 3) s_nb[threadIdx.x] = sc.nb[threadIdx.x];
+    __syncthreads();
     TP<T> q;
     q.load(*(const TersoffParams *)b.bp->pot);
     const int n = b.n;
     const int t = tl.t * TILE + threadIdx.x;
     const size_t base = (size_t)tl.img * n;
     T *nP = (T *)b.nbr_P + (size_t)tl.img * 3 * MAXN_TERSOFF * n;
-    const T *nR = (const T *)b.nbr_R + (size_t)tl.img * 4 * MAXN_TERSOFF * n;
-    int cnt = 0;
+    int nin = 0;
     T U = 0;
     T vir[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (t < n) {
-        cnt = b.nbr_cnt[base + t];
+        const int cnt = b.nbr_cnt[base + t];
         if (cnt <= NFAST) {
             T rx[NFAST], ry[NFAST], rz[NFAST], rd[NFAST], sr[NFAST];
-            ters_load<T, NFAST>(q, nR, n, t, cnt, rx, ry, rz, rd, sr);
+            ters_load<T, NFAST>(q, b, tl.img, t, cnt, s_bv, s_dh, s_nb, rx, ry, rz, rd, sr);
+            for (int k = 0; k < cnt && k < NFAST; ++k) nin += sub_rn(sr[k], q.D) < q.Dlo;
             ters_site<T, NFAST>(q, cnt, rx, ry, rz, rd, sr, nP, n, t, U, vir);
         } else {
             T Rx[MAXN_TERSOFF], Ry[MAXN_TERSOFF], Rz[MAXN_TERSOFF], Rd[MAXN_TERSOFF],
                 Sr[MAXN_TERSOFF];
-            ters_load<T, MAXN_TERSOFF>(q, nR, n, t, cnt, Rx, Ry, Rz, Rd, Sr);
+            ters_load<T, MAXN_TERSOFF>(q, b, tl.img, t, cnt, s_bv, s_dh, s_nb, Rx, Ry, Rz, Rd,
+                                       Sr);
+            for (int k = 0; k < cnt; ++k) nin += sub_rn(Sr[k], q.D) < q.Dlo;
             ters_site<T, MAXN_TERSOFF>(q, cnt, Rx, Ry, Rz, Rd, Sr, nP, n, t, U, vir);
         }
     }
     T acc[12];
     acc[0] = U;
     for (int k = 0; k < 9; ++k) acc[1 + k] = vir[k];
-    acc[10] = (T)cnt;
-    acc[11] = (T)(cnt * (cnt - 1));
+    acc[10] = (T)nin;
+    acc[11] = (T)(nin * (nin - 1));
     double tot[12];
     block_sum_t<12, T>(acc, tot);
     if (threadIdx.x == 0) {

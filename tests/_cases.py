@@ -63,8 +63,11 @@ def lj_band_case(n_images=7, strain_seed=None):
 
 def gpu_band(g, R0, h0, R1, h1, n_images, potential, k, dt, maxstep=0.2, climb=True,
              cell_filter=True, precision=0, noise=None, dt_max=None, adaptive=False, n_min=3,
-             n_max=None, variant=0, pressure=0.0, bin_scale=0.0, alpha_ins=1.5, alpha_del=0.5):
+             n_max=None, variant=0, pressure=0.0, bin_scale=0.0, alpha_ins=1.5, alpha_del=0.5,
+             skin=None):
     opt = g.default_options()
+    if skin is not None:
+        opt.skin = skin
     opt.k_spring = k
     opt.climb = int(climb)
     opt.precision = precision
