@@ -258,6 +258,76 @@ __global__ void k_mapback(const ImgRef *imgs, int count, BandDev *bands) {
     }
 }
 
+// Offset of an atom from the centre of its (kept) bin, R - K with R = R~ D
+// and K = sum_a (wrap_a h_a + (b_a + 1/2) bv_a), as a leading part and a
+// remainder.  FP64 path: in FP64.  FP32 path: in pairs of FP32 (products
+// split exactly with FMA, sums with Knuth's two-sum), from the FP32 pairs
+// of D and h that k_skin_decide stores; bv is exact in FP32 by construction.
+// Both keep the offset to ~1e-14 relative of the cell size, far below the
+// FP32 leading part's rounding.
+__device__ inline void refresh_offset(const ImgScalars &sc, const BandParams *bp, const double *X,
+                                      const int *wr, const int *bi, double4_32a &o,
+                                      double4_32a &lo) {
+    double off[3];
+    double s[3];
+    for (int a = 0; a < 3; ++a)
+        s[a] = (X[0] * bp->h0inv[a] + X[1] * bp->h0inv[3 + a] + X[2] * bp->h0inv[6 + a]) -
+               (double)wr[a];
+    for (int c = 0; c < 3; ++c) {
+        const double R = s[0] * sc.h[c] + s[1] * sc.h[3 + c] + s[2] * sc.h[6 + c];
+        const double ctr = (bi[0] + 0.5) * sc.bv[c] + (bi[1] + 0.5) * sc.bv[3 + c] +
+                           (bi[2] + 0.5) * sc.bv[6 + c];
+        off[c] = R - ctr;
+    }
+    o.x = off[0];
+    o.y = off[1];
+    o.z = off[2];
+    o.w = (double)bi[2];
+    lo.x = lo.y = lo.z = lo.w = 0.0;
+}
+
+struct F2 {  // unevaluated sum hi + lo of two floats
+    float hi, lo;
+};
+// a (hi + lo) exactly up to the rounding of the low product
+__device__ inline F2 f2_mul(float a, float bh, float bl) {
+    const float p = __fmul_rn(a, bh);
+    float e = fmaf(a, bh, -p);
+    e = fmaf(a, bl, e);
+    return {p, e};
+}
+__device__ inline F2 f2_add(F2 a, F2 b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float hi = __fadd_rn(s, e);
+    return {hi, __fsub_rn(e, __fsub_rn(hi, s))};
+}
+
+__device__ inline void refresh_offset(const ImgScalars &sc, const BandParams *, const float *X,
+                                      const int *wr, const int *bi, float4 &o, float4 &lo) {
+    const float *Dh = sc.dfl, *Dl = sc.dfl + 9, *hh = sc.dfl + 18, *hl = sc.dfl + 27;
+    float off[2][3];
+    for (int c = 0; c < 3; ++c) {
+        // R_c = sum_k X_k D_kc (X exact in FP32)
+        F2 R = f2_mul(X[0], Dh[c], Dl[c]);
+        R = f2_add(R, f2_mul(X[1], Dh[3 + c], Dl[3 + c]));
+        R = f2_add(R, f2_mul(X[2], Dh[6 + c], Dl[6 + c]));
+        // K_c = sum_a wrap_a h_ac + (b_a + 1/2) bv_ac
+        F2 K = {0.0f, 0.0f};
+        for (int a = 0; a < 3; ++a) {
+            K = f2_add(K, f2_mul((float)wr[a], hh[3 * a + c], hl[3 * a + c]));
+            K = f2_add(K, f2_mul((float)bi[a] + 0.5f, (float)sc.bv[3 * a + c], 0.0f));
+        }
+        const F2 d = f2_add(R, {-K.hi, -K.lo});
+        off[0][c] = d.hi;
+        off[1][c] = d.lo;
+    }
+    o = make_float4(off[0][0], off[0][1], off[0][2], (float)bi[2]);
+    lo = make_float4(off[1][0], off[1][1], off[1][2], 0.0f);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(TILE) k_bin_assign(const Tile *tiles, BandDev *bands) {
     using T4 = typename Vec4<T>::type;
@@ -275,27 +345,9 @@ __global__ void __launch_bounds__(TILE) k_bin_assign(const Tile *tiles, BandDev 
         const int bin = b.slot_bin[st];
         const int *wr = b.atom_wrap + ((size_t)tl.img * b.n + i) * 3;
         const T *Xi = (const T *)b.X + ((size_t)tl.img * b.rows + i) * 3;
-        const double rt[3] = {(double)Xi[0], (double)Xi[1], (double)Xi[2]};
         const int bi[3] = {bin / (sc.nb[1] * sc.nb[2]), (bin / sc.nb[2]) % sc.nb[1], bin % sc.nb[2]};
-        double s[3], off[3];
-        for (int a = 0; a < 3; ++a)
-            s[a] = (rt[0] * bp->h0inv[a] + rt[1] * bp->h0inv[3 + a] + rt[2] * bp->h0inv[6 + a]) -
-                   (double)wr[a];
-        for (int c = 0; c < 3; ++c) {
-            const double R = s[0] * sc.h[c] + s[1] * sc.h[3 + c] + s[2] * sc.h[6 + c];
-            const double ctr = (bi[0] + 0.5) * sc.bv[c] + (bi[1] + 0.5) * sc.bv[3 + c] +
-                               (bi[2] + 0.5) * sc.bv[6 + c];
-            off[c] = R - ctr;
-        }
         T4 o, lo;
-        o.x = (T)off[0];
-        o.y = (T)off[1];
-        o.z = (T)off[2];
-        o.w = (T)bi[2];
-        lo.x = (T)(off[0] - (double)o.x);
-        lo.y = (T)(off[1] - (double)o.y);
-        lo.z = (T)(off[2] - (double)o.z);
-        lo.w = (T)0;
+        refresh_offset(sc, bp, Xi, wr, bi, o, lo);
         ((T4 *)b.slot_off)[st] = o;
         ((T4 *)b.slot_off_lo)[st] = lo;
         return;
@@ -427,6 +479,13 @@ __global__ void k_skin_decide(const ImgRef *imgs, BandDev *bands, int force) {
         sc.builds += 1;
     } else {
         bin_geometry(bp, b.nbins_cap, sc.h, sc.omega, true, sc);
+    }
+    for (int k = 0; k < 9; ++k) {
+        const float dh_ = (float)sc.D[k], hh_ = (float)sc.h[k];
+        sc.dfl[k] = dh_;
+        sc.dfl[9 + k] = (float)(sc.D[k] - (double)dh_);
+        sc.dfl[18 + k] = hh_;
+        sc.dfl[27 + k] = (float)(sc.h[k] - (double)hh_);
     }
     sc.rebuild = rebuild ? 1 : 0;
     sc.dmax = d;

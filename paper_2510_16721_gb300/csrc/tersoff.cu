@@ -139,9 +139,21 @@ __device__ inline void gfun(const TP<T> &q, T cs, T &g, T &dg) {
     dg = -(T)2 * q.c2 * u / (den * den);
 }
 
-// atoms with at most this many neighbours take the register-resident path
-// (their neighbour loops are unrolled); the rest take a looped path
-constexpr int NFAST = 4;
+// list entries of an atom held in shared memory by the force kernel (atoms
+// with more entries keep theirs in local memory)
+template <typename T> struct NShared;
+template <> struct NShared<float> { static constexpr int value = 6; };
+template <> struct NShared<double> { static constexpr int value = 4; };
+
+// Per-thread neighbour records: field f of entry k at p[(f * cap + k) * stride]
+// (stride TILE in shared memory, 1 in a local array).
+enum { NB_RX, NB_RY, NB_RZ, NB_SR, NB_FC, NB_DFC, NB_PX, NB_PY, NB_PZ, NB_FIELDS };
+template <typename T>
+struct Nbr {
+    T *p;
+    int stride, cap;
+    __device__ T &operator()(int f, int k) const { return p[(f * cap + k) * stride]; }
+};
 
 // Pair vector of entry (slot qs, stencil code) of slot t: leading parts
 // x, y, z (directions) and s = r - R to twice the working precision.
@@ -249,31 +261,31 @@ __device__ inline int ters_collect_list(T rl2, const BandDev &b, int img, int t,
 }
 
 // Site energy U_i, partials P_ij (written to the list) and the site virial
-// for the cnt <= NM neighbours in the arrays.
-template <typename T, int NM>
-__device__ inline void ters_site(const TP<T> &q, int cnt, const T (&rx)[NM], const T (&ry)[NM],
-                                 const T (&rz)[NM], const T (&rd)[NM], const T (&sr)[NM],
-                                 T *nP, int n, int t, T &U, T (&vir)[9]) {
-    T fc[NM], dfc[NM], Px[NM], Py[NM], Pz[NM];
-#pragma unroll (NM <= NFAST ? NM : 1)
-    for (int j = 0; j < NM; ++j) {
-        fc[j] = dfc[j] = (T)0;
-        if (j < cnt) cutoff(q, sr[j], fc[j], dfc[j]);
-        Px[j] = Py[j] = Pz[j] = (T)0;
+// of slot t from its cnt neighbour records (r^ij and s = r - R filled in).
+template <typename T>
+__device__ inline void ters_site(const TP<T> &q, int cnt, const Nbr<T> &nb, T *nP, int n, int t,
+                                 T &U, T (&vir)[9]) {
+    for (int j = 0; j < cnt; ++j) {
+        T fc, dfc;
+        cutoff(q, nb(NB_SR, j), fc, dfc);
+        nb(NB_FC, j) = fc;
+        nb(NB_DFC, j) = dfc;
+        nb(NB_PX, j) = nb(NB_PY, j) = nb(NB_PZ, j) = (T)0;
     }
-#pragma unroll (NM <= NFAST ? NM : 1)
-    for (int j = 0; j < NM; ++j) {
-        if (j >= cnt) continue;
-        if (fc[j] == (T)0 && dfc[j] == (T)0) continue;  // beyond R + D: no terms
+    for (int j = 0; j < cnt; ++j) {
+        const T fcj = nb(NB_FC, j), dfcj = nb(NB_DFC, j);
+        if (fcj == (T)0 && dfcj == (T)0) continue;  // beyond R + D: no terms
+        const T xj = nb(NB_RX, j), yj = nb(NB_RY, j), zj = nb(NB_RZ, j), sj_ = nb(NB_SR, j);
+        const T rj = q.R + sj_;
         // zeta_ij and the bond order
         T zeta = 0;
-#pragma unroll (NM <= NFAST ? NM : 1)
-        for (int k = 0; k < NM; ++k) {
-            if (k == j || k >= cnt) continue;
-            const T cs = (rx[j] * rx[k] + ry[j] * ry[k] + rz[j] * rz[k]) / (rd[j] * rd[k]);
+        for (int k = 0; k < cnt; ++k) {
+            if (k == j) continue;
+            const T rk = q.R + nb(NB_SR, k);
+            const T cs = (xj * nb(NB_RX, k) + yj * nb(NB_RY, k) + zj * nb(NB_RZ, k)) / (rj * rk);
             T g, dg;
             gfun(q, cs, g, dg);
-            zeta += fc[k] * g;
+            zeta += nb(NB_FC, k) * g;
         }
         T bij = (T)1, dbij = (T)0;
         if (zeta > (T)0) {
@@ -281,45 +293,48 @@ __device__ inline void ters_site(const TP<T> &q, int cnt, const T (&rx)[NM], con
             bij = M<T>::ex(-q.inv2n * M<T>::l1p(x));
             dbij = (T)(-0.5) * bij * x / (((T)1 + x) * zeta);
         }
-        const T fr = q.AeR * M<T>::ex(-q.l1 * sr[j]);
-        const T fa = -q.BeR * M<T>::ex(-q.l2 * sr[j]);
+        const T fr = q.AeR * M<T>::ex(-q.l1 * sj_);
+        const T fa = -q.BeR * M<T>::ex(-q.l2 * sj_);
         const T dfr = -q.l1 * fr, dfa = -q.l2 * fa;
-        U += (T)0.5 * fc[j] * (fr + bij * fa);
-        const T radial = (T)0.5 * (dfc[j] * (fr + bij * fa) + fc[j] * (dfr + bij * dfa)) / rd[j];
-        Px[j] += radial * rx[j];
-        Py[j] += radial * ry[j];
-        Pz[j] += radial * rz[j];
-        const T pref = (T)0.5 * fc[j] * fa * dbij;
-        if (pref == (T)0) continue;
-#pragma unroll (NM <= NFAST ? NM : 1)
-        for (int k = 0; k < NM; ++k) {
-            if (k == j || k >= cnt) continue;
-            const T ijk = (T)1 / (rd[j] * rd[k]);
-            const T cs = (rx[j] * rx[k] + ry[j] * ry[k] + rz[j] * rz[k]) * ijk;
-            T g, dg;
-            gfun(q, cs, g, dg);
-            // d cos / d r^ij and d cos / d r^ik
-            const T aj = cs / (rd[j] * rd[j]), ak = cs / (rd[k] * rd[k]);
-            const T sj = pref * fc[k] * dg;
-            Px[j] += sj * (rx[k] * ijk - aj * rx[j]);
-            Py[j] += sj * (ry[k] * ijk - aj * ry[j]);
-            Pz[j] += sj * (rz[k] * ijk - aj * rz[j]);
-            const T rk = pref * dfc[k] * g / rd[k];
-            Px[k] += rk * rx[k] + sj * (rx[j] * ijk - ak * rx[k]);
-            Py[k] += rk * ry[k] + sj * (ry[j] * ijk - ak * ry[k]);
-            Pz[k] += rk * rz[k] + sj * (rz[j] * ijk - ak * rz[k]);
+        U += (T)0.5 * fcj * (fr + bij * fa);
+        const T radial = (T)0.5 * (dfcj * (fr + bij * fa) + fcj * (dfr + bij * dfa)) / rj;
+        T Pxj = radial * xj, Pyj = radial * yj, Pzj = radial * zj;
+        const T pref = (T)0.5 * fcj * fa * dbij;
+        if (pref != (T)0) {
+            for (int k = 0; k < cnt; ++k) {
+                if (k == j) continue;
+                const T xk = nb(NB_RX, k), yk = nb(NB_RY, k), zk = nb(NB_RZ, k);
+                const T rk = q.R + nb(NB_SR, k);
+                const T ijk = (T)1 / (rj * rk);
+                const T cs = (xj * xk + yj * yk + zj * zk) * ijk;
+                T g, dg;
+                gfun(q, cs, g, dg);
+                // d cos / d r^ij and d cos / d r^ik
+                const T aj = cs / (rj * rj), ak = cs / (rk * rk);
+                const T sj = pref * nb(NB_FC, k) * dg;
+                Pxj += sj * (xk * ijk - aj * xj);
+                Pyj += sj * (yk * ijk - aj * yj);
+                Pzj += sj * (zk * ijk - aj * zj);
+                const T rkk = pref * nb(NB_DFC, k) * g / rk;
+                nb(NB_PX, k) += rkk * xk + sj * (xj * ijk - ak * xk);
+                nb(NB_PY, k) += rkk * yk + sj * (yj * ijk - ak * yk);
+                nb(NB_PZ, k) += rkk * zk + sj * (zj * ijk - ak * zk);
+            }
         }
+        nb(NB_PX, j) += Pxj;
+        nb(NB_PY, j) += Pyj;
+        nb(NB_PZ, j) += Pzj;
     }
-#pragma unroll (NM <= NFAST ? NM : 1)
-    for (int j = 0; j < NM; ++j) {
-        if (j >= cnt) continue;
-        nP[(size_t)(3 * j + 0) * n + t] = Px[j];
-        nP[(size_t)(3 * j + 1) * n + t] = Py[j];
-        nP[(size_t)(3 * j + 2) * n + t] = Pz[j];
+    for (int j = 0; j < cnt; ++j) {
+        const T Px = nb(NB_PX, j), Py = nb(NB_PY, j), Pz = nb(NB_PZ, j);
+        const T rx = nb(NB_RX, j), ry = nb(NB_RY, j), rz = nb(NB_RZ, j);
+        nP[(size_t)(3 * j + 0) * n + t] = Px;
+        nP[(size_t)(3 * j + 1) * n + t] = Py;
+        nP[(size_t)(3 * j + 2) * n + t] = Pz;
         // V_mn -= r_m P_n
-        vir[0] -= rx[j] * Px[j]; vir[1] -= rx[j] * Py[j]; vir[2] -= rx[j] * Pz[j];
-        vir[3] -= ry[j] * Px[j]; vir[4] -= ry[j] * Py[j]; vir[5] -= ry[j] * Pz[j];
-        vir[6] -= rz[j] * Px[j]; vir[7] -= rz[j] * Py[j]; vir[8] -= rz[j] * Pz[j];
+        vir[0] -= rx * Px; vir[1] -= rx * Py; vir[2] -= rx * Pz;
+        vir[3] -= ry * Px; vir[4] -= ry * Py; vir[5] -= ry * Pz;
+        vir[6] -= rz * Px; vir[7] -= rz * Py; vir[8] -= rz * Pz;
     }
 }
 
@@ -356,11 +371,11 @@ __global__ void __launch_bounds__(TILE) k_ters_list(const Tile *tiles, BandDev *
 }
 
 // pair vectors of the list entries of slot t from the current offsets, into
-// arrays (compile-time indices for small NM: registers)
-template <typename T, int NM>
+// its neighbour records
+template <typename T>
 __device__ inline void ters_load(const TP<T> &q, const BandDev &b, int img, int t, int cnt,
-                                 const T *s_bv, const T *s_dh, const int *s_nb, T (&rx)[NM],
-                                 T (&ry)[NM], T (&rz)[NM], T (&rd)[NM], T (&sr)[NM]) {
+                                 const T *s_bv, const T *s_dh, const int *s_nb,
+                                 const Nbr<T> &nb) {
     using T4 = typename Vec4<T>::type;
     const int n = b.n;
     const size_t base = (size_t)img * n;
@@ -371,36 +386,41 @@ __device__ inline void ters_load(const TP<T> &q, const BandDev &b, int img, int 
     const int bin = b.slot_bin[base + t];
     const int b0 = bin / (s_nb[1] * s_nb[2]), b1 = (bin / s_nb[2]) % s_nb[1], b2 = bin % s_nb[2];
     const T4 oi = off[t], oil = offl[t];
-#pragma unroll (NM <= NFAST ? NM : 1)
-    for (int k = 0; k < NM; ++k) {
-        if (k >= cnt) {
-            rx[k] = ry[k] = rz[k] = sr[k] = (T)0;
-            rd[k] = (T)1;
-            continue;
-        }
+    for (int k = 0; k < cnt; ++k) {
         const int qs = nslot[(size_t)k * n + t];
         const int code = ncode[(size_t)k * n + t];
-        ters_pair<T>(q, oi, oil, off[qs], offl[qs], code, b0, b1, b2, s_bv, s_dh, s_nb, rx[k],
-                     ry[k], rz[k], sr[k]);
-        rd[k] = q.R + sr[k];
+        T x, y, z, sr;
+        ters_pair<T>(q, oi, oil, off[qs], offl[qs], code, b0, b1, b2, s_bv, s_dh, s_nb, x, y, z,
+                     sr);
+        nb(NB_RX, k) = x;
+        nb(NB_RY, k) = y;
+        nb(NB_RZ, k) = z;
+        nb(NB_SR, k) = sr;
     }
 }
 
+// One thread per atom.  Each thread's neighbour records (pair vector, s,
+// cutoff values, partials) sit in shared memory, strided by the block size
+// so that the threads of a warp hit distinct banks; an atom with more list
+// entries than the shared slots keeps them in local memory.
 template <typename T>
-__global__ void __launch_bounds__(TILE) k_ters_partials(const Tile *tiles, BandDev *bands) {
+__global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 8 : 1) k_ters_partials(const Tile *tiles, BandDev *bands) {
+    constexpr int NS = NShared<T>::value;
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
     const ImgScalars &sc = b.sc[tl.img];
     __shared__ T s_bv[9], s_dh[9];
     __shared__ int s_nb[3];
+    __shared__ TP<T> s_q;
+    __shared__ T s_rec[NB_FIELDS * NS * TILE];
     if (threadIdx.x < 9) {
         s_bv[threadIdx.x] = (T)sc.bv[threadIdx.x];
         s_dh[threadIdx.x] = (T)sc.dh[threadIdx.x];
     }
     if (threadIdx.x < 3) s_nb[threadIdx.x] = sc.nb[threadIdx.x];
+    if (threadIdx.x == 0) s_q.load(*(const TersoffParams *)b.bp->pot);
     __syncthreads();
-    TP<T> q;
-    q.load(*(const TersoffParams *)b.bp->pot);
+    const TP<T> &q = s_q;
     const int n = b.n;
     const int t = tl.t * TILE + threadIdx.x;
     const size_t base = (size_t)tl.img * n;
@@ -410,18 +430,17 @@ __global__ void __launch_bounds__(TILE) k_ters_partials(const Tile *tiles, BandD
     T vir[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (t < n) {
         const int cnt = b.nbr_cnt[base + t];
-        if (cnt <= NFAST) {
-            T rx[NFAST], ry[NFAST], rz[NFAST], rd[NFAST], sr[NFAST];
-            ters_load<T, NFAST>(q, b, tl.img, t, cnt, s_bv, s_dh, s_nb, rx, ry, rz, rd, sr);
-            for (int k = 0; k < cnt && k < NFAST; ++k) nin += sub_rn(sr[k], q.D) < q.Dlo;
-            ters_site<T, NFAST>(q, cnt, rx, ry, rz, rd, sr, nP, n, t, U, vir);
+        if (cnt <= NS) {
+            const Nbr<T> nb{s_rec + threadIdx.x, TILE, NS};
+            ters_load<T>(q, b, tl.img, t, cnt, s_bv, s_dh, s_nb, nb);
+            for (int k = 0; k < cnt; ++k) nin += sub_rn(nb(NB_SR, k), q.D) < q.Dlo;
+            ters_site<T>(q, cnt, nb, nP, n, t, U, vir);
         } else {
-            T Rx[MAXN_TERSOFF], Ry[MAXN_TERSOFF], Rz[MAXN_TERSOFF], Rd[MAXN_TERSOFF],
-                Sr[MAXN_TERSOFF];
-            ters_load<T, MAXN_TERSOFF>(q, b, tl.img, t, cnt, s_bv, s_dh, s_nb, Rx, Ry, Rz, Rd,
-                                       Sr);
-            for (int k = 0; k < cnt; ++k) nin += sub_rn(Sr[k], q.D) < q.Dlo;
-            ters_site<T, MAXN_TERSOFF>(q, cnt, Rx, Ry, Rz, Rd, Sr, nP, n, t, U, vir);
+            T rec[NB_FIELDS * MAXN_TERSOFF];
+            const Nbr<T> nb{rec, 1, MAXN_TERSOFF};
+            ters_load<T>(q, b, tl.img, t, cnt, s_bv, s_dh, s_nb, nb);
+            for (int k = 0; k < cnt; ++k) nin += sub_rn(nb(NB_SR, k), q.D) < q.Dlo;
+            ters_site<T>(q, cnt, nb, nP, n, t, U, vir);
         }
     }
     T acc[12];
