@@ -8,7 +8,7 @@
 //                   gradient (Sec. II.C).
 // k_band_dots       per row tile: |dX+|^2, |dX-|^2, dX+.dX-, F.dX+, F.dX- in
 //                   FP64 (dX+ = X_{i+1} - X_i, dX- = X_i - X_{i-1}).
-// k_dots_reduce     sums those tile partials per image (one warp per image).
+// k_dots_reduce     sums those tile partials per image (one block per image).
 // k_neb_coef        per band: climbing image, upwind tangent weights and the
 //                   two coefficients with f_NEB = F + a dX+ + b dX-.  Since
 //                   tau = w+ dX+ + w- dX-, |tau| and F.tau follow from the five
@@ -32,12 +32,11 @@ __global__ void k_image_finalize(const ImgRef *imgs, BandDev *bands) {
     const BandParams *bp = b.bp;
     ImgScalars &sc = b.sc[r.img];
     const double *part = b.atom_part + (size_t)r.img * b.atpi * NPART;
-    double s[12];
-    for (int k = 0; k < 12; ++k) {
-        double v = 0.0;
-        for (int t = threadIdx.x; t < b.atpi; t += 32) v += part[(size_t)t * NPART + k];
-        s[k] = warp_sum(v);
-    }
+    double v[12], s[12];
+    for (int k = 0; k < 12; ++k) v[k] = 0.0;
+    for (int t = threadIdx.x; t < b.atpi; t += blockDim.x)
+        for (int k = 0; k < 12; ++k) v[k] += part[(size_t)t * NPART + k];
+    block_sum_any<12>(v, s);
     if (threadIdx.x != 0) return;
     sc.pairs = s[10];
     sc.triples = s[11];
@@ -106,17 +105,15 @@ __global__ void __launch_bounds__(TILE) k_band_dots(const Tile *tiles, BandDev *
     }
 }
 
-// one warp per image: sum the row-tile partials k = 0..K-1 into dst
+// one block per image: sum the row-tile partials of the five dots
 __global__ void k_dots_reduce(const ImgRef *imgs, BandDev *bands) {
     ImgRef r = imgs[blockIdx.x];
     BandDev &b = bands[r.band];
     const double *part = b.row_part + (size_t)r.img * b.rtpi * NPART;
-    double s[5];
-    for (int k = 0; k < 5; ++k) {
-        double v = 0.0;
-        for (int t = threadIdx.x; t < b.rtpi; t += 32) v += part[(size_t)t * NPART + k];
-        s[k] = warp_sum(v);
-    }
+    double v[5] = {0, 0, 0, 0, 0}, s[5];
+    for (int t = threadIdx.x; t < b.rtpi; t += blockDim.x)
+        for (int k = 0; k < 5; ++k) v[k] += part[(size_t)t * NPART + k];
+    block_sum_any<5>(v, s);
     if (threadIdx.x == 0)
         for (int k = 0; k < 5; ++k) b.sc[r.img].dots[k] = s[k];
 }
@@ -225,45 +222,27 @@ __global__ void __launch_bounds__(TILE) k_neb_force(const Tile *tiles, BandDev *
     }
 }
 
-// one block per band; warps sum the per-image tile partials, thread 0 runs
-// the FIRE logic
+// one block per band; the threads sum the tile partials of every interior
+// image, thread 0 runs the FIRE logic
 __global__ void k_fire_scalars(const int *band_ids, BandDev *bands) {
     BandDev &b = bands[band_ids[blockIdx.x]];
     BandParams *bp = b.bp;
     const int N = bp->N;
-    __shared__ double s_img[64][4];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    double tot[4] = {0, 0, 0, 0};
-    // images 1..N-2 in fixed groups of nw
-    for (int g0 = 1; g0 < N - 1; g0 += nw) {
-        const int i = g0 + w;
-        if (i < N - 1) {
-            const double *part = b.row_part + (size_t)i * b.rtpi * NPART;
-            double v[4] = {0, 0, 0, 0};
-            for (int t = lane; t < b.rtpi; t += 32) {
-                v[0] += part[(size_t)t * NPART + 5];
-                v[1] += part[(size_t)t * NPART + 6];
-                v[2] += part[(size_t)t * NPART + 7];
-                v[3] = fmax(v[3], part[(size_t)t * NPART + 8]);
-            }
-            v[0] = warp_sum(v[0]);
-            v[1] = warp_sum(v[1]);
-            v[2] = warp_sum(v[2]);
-            v[3] = warp_max(v[3]);
-            if (lane == 0)
-                for (int k = 0; k < 4; ++k) s_img[w][k] = v[k];
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int q = 0; q < nw && g0 + q < N - 1; ++q) {
-                tot[0] += s_img[q][0];
-                tot[1] += s_img[q][1];
-                tot[2] += s_img[q][2];
-                tot[3] = fmax(tot[3], s_img[q][3]);
-            }
-        }
-        __syncthreads();
+    // the row-tile partials of images 1..N-2, one fixed strided subset per
+    // thread, then a fixed-order block sum
+    const int nt = (N - 2) * b.rtpi;
+    const double *part0 = b.row_part + (size_t)b.rtpi * NPART;
+    double v[3] = {0, 0, 0}, tot[4];
+    double m = 0.0;
+    for (int q = threadIdx.x; q < nt; q += blockDim.x) {
+        const double *p = part0 + (size_t)q * NPART;
+        v[0] += p[5];
+        v[1] += p[6];
+        v[2] += p[7];
+        m = fmax(m, p[8]);
     }
+    block_sum_any<3>(v, tot);
+    tot[3] = block_max_any(m);
     if (threadIdx.x != 0) return;
     bp->stale = 0;  // every image of the band has rebuilt its cell list
     const double P = tot[0], FF = tot[1], VV = tot[2];
@@ -453,7 +432,7 @@ void launch_setup(const double *R0, const double *R1, const double *noise, int n
 template <typename T>
 void launch_image_finalize(const ImgRef *imgs, int count, BandDev *bands, cudaStream_t s) {
     if (count <= 0) return;
-    k_image_finalize<T><<<count, 32, 0, s>>>(imgs, bands);
+    k_image_finalize<T><<<count, RED_THREADS, 0, s>>>(imgs, bands);
 }
 template <typename T>
 void launch_band_dots(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
@@ -462,7 +441,7 @@ void launch_band_dots(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_
 }
 void launch_dots_reduce(const ImgRef *imgs, int count, BandDev *bands, cudaStream_t s) {
     if (count <= 0) return;
-    k_dots_reduce<<<count, 32, 0, s>>>(imgs, bands);
+    k_dots_reduce<<<count, RED_THREADS, 0, s>>>(imgs, bands);
 }
 void launch_neb_coef(const int *band_ids, int nbands, BandDev *bands, cudaStream_t s) {
     if (nbands <= 0) return;
@@ -475,7 +454,7 @@ void launch_neb_force(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_
 }
 void launch_fire_scalars(const int *band_ids, int nbands, BandDev *bands, cudaStream_t s) {
     if (nbands <= 0) return;
-    k_fire_scalars<<<nbands, 256, 0, s>>>(band_ids, bands);
+    k_fire_scalars<<<nbands, 1024, 0, s>>>(band_ids, bands);
 }
 template <typename T>
 void launch_fire_update(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {

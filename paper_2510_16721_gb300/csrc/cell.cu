@@ -36,6 +36,8 @@
 // recomputed from its current position against the centre of its old bin
 // (the pair-vector identity above holds for any position, inside the bin or
 // not), which costs one pass over the atoms instead of a rebuild.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace cfneb {
@@ -72,17 +74,33 @@ __device__ inline double inv3n(const double *m, double *o) {
     return det;
 }
 
+// rotation of one Jacobi step: t = tan, c = cos for the pivot (p, r)
+__device__ inline void jacobi_angle(float app, float arr, float apr, float &t, float &c) {
+    const float theta = (arr - app) / (2.0f * apr);
+    t = (theta >= 0.0f ? 1.0f : -1.0f) / (fabsf(theta) + sqrtf(theta * theta + 1.0f));
+    c = 1.0f / sqrtf(t * t + 1.0f);
+}
+__device__ inline void jacobi_angle(double app, double arr, double apr, double &t, double &c) {
+    const double theta = (arr - app) * rcp64(2.0 * apr);
+    const double at = fabs(theta);
+    // tan of the smaller root of t^2 + 2 theta t - 1 = 0 (1 / 2theta when
+    // theta^2 would leave FP32's range in the seed)
+    const double mag = at > 1e15 ? 0.5 * rcp64(at) : rcp64(at + sqrt64(theta * theta + 1.0));
+    t = theta >= 0.0 ? mag : -mag;
+    c = rsqrt64(t * t + 1.0);
+}
+
 // one cyclic Jacobi sweep on symmetric a, accumulating rotations into q
 template <typename R>
 __device__ inline void jacobi_sweep(R (&a)[3][3], R (&q)[3][3]) {
     for (int p = 0; p < 2; ++p)
         for (int r = p + 1; r < 3; ++r) {
             const R apr = a[p][r];
-            if (apr == (R)0) continue;
-            // rotation angle that annihilates a[p][r]
-            const R theta = (a[r][r] - a[p][p]) / ((R)2 * apr);
-            const R t = (theta >= (R)0 ? (R)1 : (R)-1) / (fabs(theta) + sqrt(theta * theta + (R)1));
-            const R c = (R)1 / sqrt(t * t + (R)1), s = t * c;
+            // already diagonal to far below rounding: nothing to rotate
+            if (fabs(apr) <= (R)1e-30 * (fabs(a[p][p]) + fabs(a[r][r]))) continue;
+            R t, c;
+            jacobi_angle(a[p][p], a[r][r], apr, t, c);
+            const R s = t * c;
             for (int k = 0; k < 3; ++k) {  // A <- A J (columns p, r)
                 const R akp = a[k][p], akr = a[k][r];
                 a[k][p] = c * akp - s * akr;
@@ -128,7 +146,7 @@ __device__ bool sym_sqrt3(const double *Bin, double *S, double *Si) {
             for (int k = 0; k < 3; ++k) q[k][c] -= d * q[k][p];
         }
         const double nn = q[0][c] * q[0][c] + q[1][c] * q[1][c] + q[2][c] * q[2][c];
-        const double inv = 1.0 / sqrt(nn);
+        const double inv = rsqrt64(nn);
         for (int k = 0; k < 3; ++k) q[k][c] *= inv;
     }
     for (int i = 0; i < 3; ++i)
@@ -145,8 +163,8 @@ __device__ bool sym_sqrt3(const double *Bin, double *S, double *Si) {
     if (!(w[0] > 0.0 && w[1] > 0.0 && w[2] > 0.0)) return false;
     double sw[3], isw[3];
     for (int k = 0; k < 3; ++k) {
-        sw[k] = sqrt(w[k]);
-        isw[k] = 1.0 / sw[k];
+        isw[k] = rsqrt64(w[k]);
+        sw[k] = w[k] * isw[k];
     }
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
@@ -192,10 +210,12 @@ __device__ void bin_geometry(const BandParams *bp, int nbins_cap, const double *
     // sum of three products delta_a bv_a (|delta| <= 7) is then exact in
     // FP32; dh = h - nb bv carries the (sub-1e-4 A) quantisation to the
     // periodic wrap
-    double bmax = 0.0;
+    double bmax = 0.0, inb[3];
+    for (int a = 0; a < 3; ++a) inb[a] = rcp64((double)nb[a]);
     for (int a = 0; a < 3; ++a)
-        for (int c = 0; c < 3; ++c) bmax = fmax(bmax, fabs(h[3 * a + c] / nb[a]));
-    const double q = ldexp(1.0, ilogb(bmax) + 1 - 19);
+        for (int c = 0; c < 3; ++c) bmax = fmax(bmax, fabs(h[3 * a + c] * inb[a]));
+    const int e = ilogb(bmax) + 1 - 19;
+    const double q = ldexp(1.0, e), iq = ldexp(1.0, -e);  // exact powers of two
     for (int a = 0; a < 3; ++a) {
         if (!keep_grid) {
             const float bw = w[a] / nb[a];
@@ -204,7 +224,7 @@ __device__ void bin_geometry(const BandParams *bp, int nbins_cap, const double *
             sc.nb[a] = nb[a];
         }
         for (int c = 0; c < 3; ++c) {
-            const double v = q * rint(h[3 * a + c] / nb[a] / q);
+            const double v = q * rint(h[3 * a + c] * inb[a] * iq);
             sc.bv[3 * a + c] = v;
             sc.dh[3 * a + c] = h[3 * a + c] - nb[a] * v;
         }
@@ -227,7 +247,8 @@ __global__ void k_mapback(const ImgRef *imgs, int count, BandDev *bands) {
         for (int i = 0; i < 9; ++i) D[i] = Di[i] = (i % 4 == 0) ? 1.0 : 0.0;
     } else {
         double L[9];
-        for (int i = 0; i < 9; ++i) L[i] = (double)Xl[i] / bp->c;
+        const double ic = rcp64(bp->c);
+        for (int i = 0; i < 9; ++i) L[i] = (double)Xl[i] * ic;
         if (bp->variant == 0) {
             ok = sym_sqrt3(L, D, Di);
         } else {
@@ -427,7 +448,7 @@ __global__ void __launch_bounds__(TILE) k_skin_check(const Tile *tiles, BandDev 
     if (threadIdx.x == 0) {
         T m = wmax[0];
         for (int q = 1; q < TILE / 32; ++q) m = fmax(m, wmax[q]);
-        b.skin_part[(size_t)tl.img * b.atpi + tl.t] = sqrt((double)m);
+        b.skin_part[(size_t)tl.img * b.atpi + tl.t] = sqrt64((double)m);
     }
 }
 
@@ -445,10 +466,10 @@ __device__ inline double norm2_bound(const double *A) {
         ci = fmax(ci, rs);
         c1 = fmax(c1, cs);
     }
-    return fmin(sqrt(f), sqrt(c1 * ci));
+    return fmin(sqrt64(f), sqrt64(c1 * ci));
 }
 
-// One warp per image: keep the bins of the build while the bound in the
+// One block per image: keep the bins of the build while the bound in the
 // header comment holds, else rebuild (and always when forced, when the
 // band's images were rearranged, or while autotuning).
 __global__ void k_skin_decide(const ImgRef *imgs, BandDev *bands, int force) {
@@ -459,13 +480,13 @@ __global__ void k_skin_decide(const ImgRef *imgs, BandDev *bands, int force) {
     ImgScalars &sc = b.sc[r.img];
     const double *part = b.skin_part + (size_t)r.img * b.atpi;
     double d = 0.0;
-    for (int t = threadIdx.x; t < b.atpi; t += 32) d = fmax(d, part[t]);
-    d = warp_max(d);
+    for (int t = threadIdx.x; t < b.atpi; t += blockDim.x) d = fmax(d, part[t]);
+    d = block_max_any(d);
     if (threadIdx.x != 0) return;
     bool rebuild = force || bp->stale || bp->tune_rebuild || sc.builds == 0;
     if (!rebuild) {
         double Dbi[9], M[9];
-        inv3(sc.Db, Dbi);
+        inv3n(sc.Db, Dbi);
         matmul3(Dbi, sc.D, M);
         for (int k = 0; k < 9; k += 4) M[k] -= 1.0;
         // small relative margins cover the FP32 list test and displacement
@@ -528,19 +549,23 @@ __global__ void __launch_bounds__(256) k_bin_tilesum(const ImgRef *imgs, BandDev
     BandDev &b = bands[r.band];
     if (!b.sc[r.img].rebuild) return;
     const int nb = b.sc[r.img].nbins;
-    const int t0 = blockIdx.x * SCAN_TILE;
-    if (t0 >= nb) return;
     const int *cnt = b.bin_count + (size_t)r.img * b.nbins_cap;
-    int s = 0;
-    for (int k = threadIdx.x; k < SCAN_TILE && t0 + k < nb; k += blockDim.x) s += cnt[t0 + k];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     __shared__ int ws[8];
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int tot = 0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += ws[q];
-        b.bin_tsum[(size_t)r.img * b.tsum_cap + blockIdx.x] = tot;
+    // a fixed grid strides over the tiles: images that keep their cell list
+    // cost one read per block
+    for (int c = blockIdx.x; c * SCAN_TILE < nb; c += gridDim.x) {
+        const int t0 = c * SCAN_TILE;
+        int s = 0;
+        for (int k = threadIdx.x; k < SCAN_TILE && t0 + k < nb; k += blockDim.x) s += cnt[t0 + k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += ws[q];
+            b.bin_tsum[(size_t)r.img * b.tsum_cap + c] = tot;
+        }
+        __syncthreads();
     }
 }
 
@@ -566,19 +591,19 @@ __global__ void __launch_bounds__(1024) k_bin_scanfill(const ImgRef *imgs, BandD
     BandDev &b = bands[r.band];
     if (!b.sc[r.img].rebuild) return;
     const int nb = b.sc[r.img].nbins;
-    const int t0 = blockIdx.x * SCAN_TILE;
-    if (t0 >= nb) return;
     int *cnt = b.bin_count + (size_t)r.img * b.nbins_cap;
     int *start = b.bin_start + (size_t)r.img * (b.nbins_cap + 1);
-    const int bin = t0 + threadIdx.x;
-    const int v = bin < nb ? cnt[bin] : 0;
-    int tot;
-    const int ex = block_excl_scan_1024(v, &tot);
-    const int off = b.bin_tsum[(size_t)r.img * b.tsum_cap + blockIdx.x];
-    if (bin < nb) {
-        start[bin] = off + ex;
-        cnt[bin] = 0;
-        if (bin == nb - 1) start[nb] = off + ex + v;
+    for (int c = blockIdx.x; c * SCAN_TILE < nb; c += gridDim.x) {
+        const int bin = c * SCAN_TILE + threadIdx.x;
+        const int v = bin < nb ? cnt[bin] : 0;
+        int tot;
+        const int ex = block_excl_scan_1024(v, &tot);
+        const int off = b.bin_tsum[(size_t)r.img * b.tsum_cap + c];
+        if (bin < nb) {
+            start[bin] = off + ex;
+            cnt[bin] = 0;
+            if (bin == nb - 1) start[nb] = off + ex + v;
+        }
     }
 }
 
@@ -593,30 +618,32 @@ __global__ void __launch_bounds__(TILE) k_bin_scatter(const Tile *tiles, BandDev
     b.slot_unsorted[(size_t)tl.img * b.n + start[b.atom_bin[ai]] + b.atom_rank[ai]] = i;
 }
 
-// One thread per bin: order the bin's atoms by atom index and write the
-// sorted slot arrays.
+// Threads stride over the bins: order each bin's atoms by atom index and
+// write the sorted slot arrays.
 template <typename T>
 __global__ void k_bin_order(const ImgRef *imgs, BandDev *bands) {
     using T4 = typename Vec4<T>::type;
     ImgRef r = imgs[blockIdx.y];
     BandDev &b = bands[r.band];
     if (!b.sc[r.img].rebuild) return;
-    int bin = blockIdx.x * blockDim.x + threadIdx.x;
-    if (bin >= b.sc[r.img].nbins) return;
+    const int nbins = b.sc[r.img].nbins;
     const int *start = b.bin_start + (size_t)r.img * (b.nbins_cap + 1);
-    size_t base = (size_t)r.img * b.n;
-    int s0 = start[bin], s1 = start[bin + 1];
+    const size_t base = (size_t)r.img * b.n;
     const int *un = b.slot_unsorted + base;
-    for (int p = s0; p < s1; ++p) {
-        int idx = un[p];
-        int rk = 0;
-        for (int q = s0; q < s1; ++q) rk += (un[q] < idx);
-        int dst = s0 + rk;
-        b.slot_atom[base + dst] = idx;
-        b.slot_bin[base + dst] = bin;
-        b.atom_slot[base + idx] = dst;
-        ((T4 *)b.slot_off)[base + dst] = ((const T4 *)b.atom_off)[base + idx];
-        ((T4 *)b.slot_off_lo)[base + dst] = ((const T4 *)b.atom_off_lo)[base + idx];
+    for (int bin = blockIdx.x * blockDim.x + threadIdx.x; bin < nbins;
+         bin += gridDim.x * blockDim.x) {
+        const int s0 = start[bin], s1 = start[bin + 1];
+        for (int p = s0; p < s1; ++p) {
+            const int idx = un[p];
+            int rk = 0;
+            for (int q = s0; q < s1; ++q) rk += (un[q] < idx);
+            const int dst = s0 + rk;
+            b.slot_atom[base + dst] = idx;
+            b.slot_bin[base + dst] = bin;
+            b.atom_slot[base + idx] = dst;
+            ((T4 *)b.slot_off)[base + dst] = ((const T4 *)b.atom_off)[base + idx];
+            ((T4 *)b.slot_off_lo)[base + dst] = ((const T4 *)b.atom_off_lo)[base + idx];
+        }
     }
 }
 
@@ -653,12 +680,12 @@ void launch_skin_check(const Tile *tiles, int ntiles, BandDev *bands, cudaStream
 }
 void launch_skin_decide(const ImgRef *imgs, int count, BandDev *bands, int force, cudaStream_t s) {
     if (count <= 0) return;
-    k_skin_decide<<<count, 32, 0, s>>>(imgs, bands, force);
+    k_skin_decide<<<count, RED_THREADS, 0, s>>>(imgs, bands, force);
 }
 void launch_bin_scan(const ImgRef *imgs, int count, int max_bins, BandDev *bands,
                      cudaStream_t s, int part) {
     if (count <= 0 || max_bins <= 0) return;
-    dim3 grid((max_bins + SCAN_TILE - 1) / SCAN_TILE, count);
+    dim3 grid(std::min((max_bins + SCAN_TILE - 1) / SCAN_TILE, 32), count);
     if (part == 0) k_bin_tilesum<<<grid, 256, 0, s>>>(imgs, bands);
     else if (part == 1) k_bin_tilescan<<<count, 1024, 0, s>>>(imgs, bands);
     else k_bin_scanfill<<<grid, 1024, 0, s>>>(imgs, bands);
@@ -671,7 +698,7 @@ template <typename T>
 void launch_bin_order(const ImgRef *imgs, int count, int max_bins, BandDev *bands,
                       cudaStream_t s) {
     if (count <= 0 || max_bins <= 0) return;
-    dim3 grid((max_bins + 127) / 128, count);
+    dim3 grid(std::min((max_bins + 127) / 128, 128), count);
     k_bin_order<T><<<grid, 128, 0, s>>>(imgs, bands);
 }
 template <typename T>

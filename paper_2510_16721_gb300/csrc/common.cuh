@@ -159,6 +159,25 @@ __host__ __device__ inline void inv3(const double *m, double *o) {
     o[8] = (m[0] * m[4] - m[1] * m[3]) * id;
 }
 
+// FP64 reciprocal and reciprocal square root from an FP32 seed and two
+// Newton-Raphson steps (relative error ~1e-7 -> ~1e-14 -> ~1 ulp).  FP64
+// divide and square root are long instruction sequences on this GPU; these
+// serve the per-image 3x3 chains (map-back, list decisions), which run on
+// one thread per image.  Arguments must lie within FP32's normal range.
+__device__ inline double rcp64(double x) {
+    double r = (double)(1.0f / (float)x);
+    r = r * (2.0 - x * r);
+    r = r * (2.0 - x * r);
+    return r;
+}
+__device__ inline double rsqrt64(double x) {
+    double y = (double)rsqrtf((float)x);
+    y = y * (1.5 - 0.5 * x * y * y);
+    y = y * (1.5 - 0.5 * x * y * y);
+    return y;
+}
+__device__ inline double sqrt64(double x) { return x > 0.0 ? x * rsqrt64(x) : 0.0; }
+
 __host__ __device__ inline void matmul3(const double *a, const double *b, double *o) {
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j)
@@ -236,6 +255,46 @@ __device__ inline void block_sum_t(T (&v)[K], double *out) {
     }
     __syncthreads();
 }
+
+// Sum K per-thread values over a block of any multiple of 32 threads (up to
+// 1024) in FP64, fixed order (warp butterflies, then warps in order); thread
+// 0 receives the totals.
+template <int K>
+__device__ inline void block_sum_any(double (&v)[K], double *out) {
+    __shared__ double red[32][K];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const double s = warp_sum(v[k]);
+        if (lane == 0) red[w][k] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < K; ++k) {
+            double s = 0.0;
+            for (int q = 0; q < nw; ++q) s += red[q][k];
+            out[k] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// block-wide maximum; thread 0 receives it
+__device__ inline double block_max_any(double v) {
+    __shared__ double red[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_max(v);
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double m = red[0];
+    if (threadIdx.x == 0)
+        for (int q = 1; q < nw; ++q) m = fmax(m, red[q]);
+    __syncthreads();
+    return m;
+}
+
+// threads of the per-image / per-band reduction kernels
+constexpr int RED_THREADS = 256;
 
 // ---- launchers (defined in the kernel translation units) ---------------
 

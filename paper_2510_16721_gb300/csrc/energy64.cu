@@ -11,6 +11,13 @@
 // Lennard-Jones or Tersoff energy of Sec. II.B's per-atom split summed over
 // atoms in FP64.  Used by cfneb_get_path and cfneb_evaluate, never inside a
 // relaxation step.
+//
+// FP64 arithmetic is scarce on this GPU, so it is spent on the terms only:
+// LJ candidates from the cell-list stencil are screened with the leading
+// (working-precision) parts first, with a relative margin far above their
+// rounding, and only the survivors are formed and tested in FP64; Tersoff
+// walks the atom's neighbour list (rebuilt with the cell list) instead of
+// the stencil.
 #include "common.cuh"
 
 namespace cfneb {
@@ -38,6 +45,9 @@ __device__ inline void for_neighbours64(const BandDev &b, int img, int t, const 
     const int nb0 = sc.nb[0], nb1 = sc.nb[1], nb2 = sc.nb[2];
     const int b0 = bin / (nb1 * nb2), b1 = (bin / nb2) % nb1, b2 = bin % nb2;
     const T4 oi = off[t], oil = offl[t];
+    // leading-part screen: its error (~1e-6 relative in FP32) is far inside
+    // the 1e-3 margin; the FP64 test below decides
+    const T screen2 = (T)(rc2 * 1.001) + (T)1e-6;
     for (int d0 = -sc.m[0]; d0 <= sc.m[0]; ++d0) {
         int w0 = b0 + d0, t0 = 0;
         while (w0 < 0) { w0 += nb0; --t0; }
@@ -55,10 +65,14 @@ __device__ inline void for_neighbours64(const BandDev &b, int img, int t, const 
                 for (int k = 0; k < 3; ++k)
                     c[k] = d0 * sc.bv[k] + d1 * sc.bv[3 + k] + d2 * sc.bv[6 + k] +
                            t0 * sc.dh[k] + t1 * sc.dh[3 + k] + t2 * sc.dh[6 + k];
+                const T cx = (T)c[0] - oi.x, cy = (T)c[1] - oi.y, cz = (T)c[2] - oi.z;
                 const int q1 = start[w + 1];
                 for (int q = start[w]; q < q1; ++q) {
+                    const T4 oj = off[q];
+                    const T ux = oj.x + cx, uy = oj.y + cy, uz = oj.z + cz;
+                    if (!(ux * ux + uy * uy + uz * uz < screen2)) continue;
                     double r[3];
-                    pair_vec64<T>(oi, oil, off[q], offl[q], c, r);
+                    pair_vec64<T>(oi, oil, oj, offl[q], c, r);
                     const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
                     if (r2 < rc2 && r2 > 0.0) f(r, r2);
                 }
@@ -88,17 +102,53 @@ __global__ void __launch_bounds__(TILE) k_energy64(const Tile *tiles, BandDev *b
             const double rc = p.R + p.D;
             double rx[MAXN_TERSOFF], ry[MAXN_TERSOFF], rz[MAXN_TERSOFF], rd[MAXN_TERSOFF];
             int cnt = 0;
-            for_neighbours64<T>(b, tl.img, t, sc, rc * rc, [&](const double *r, double r2) {
-                if (cnt < MAXN_TERSOFF) {
+            // the neighbour list (within rc + skin) of slot t
+            using T4 = typename Vec4<T>::type;
+            const size_t base = (size_t)tl.img * b.n;
+            const T4 *off = (const T4 *)b.slot_off + base;
+            const T4 *offl = (const T4 *)b.slot_off_lo + base;
+            const int *nslot = b.nbr_slot + (size_t)tl.img * MAXN_TERSOFF * b.n;
+            const int *ncode = b.nbr_code + (size_t)tl.img * MAXN_TERSOFF * b.n;
+            const int ne = b.nbr_cnt[base + t];
+            const int bin = b.slot_bin[base + t];
+            const int nb1 = sc.nb[1], nb2 = sc.nb[2];
+            const int bb[3] = {bin / (nb1 * nb2), (bin / nb2) % nb1, bin % nb2};
+            const T4 oi = off[t], oil = offl[t];
+            for (int e = 0; e < ne; ++e) {
+                const int q = nslot[(size_t)e * b.n + t];
+                const int code = ncode[(size_t)e * b.n + t];
+                const int dd[3] = {(code & 31) - 16, ((code >> 5) & 31) - 16,
+                                   ((code >> 10) & 31) - 16};
+                int tt[3];
+                for (int a = 0; a < 3; ++a) {
+                    int w = bb[a] + dd[a];
+                    tt[a] = 0;
+                    while (w < 0) { w += sc.nb[a]; --tt[a]; }
+                    while (w >= sc.nb[a]) { w -= sc.nb[a]; ++tt[a]; }
+                }
+                double c[3];
+                for (int k = 0; k < 3; ++k)
+                    c[k] = dd[0] * sc.bv[k] + dd[1] * sc.bv[3 + k] + dd[2] * sc.bv[6 + k] +
+                           tt[0] * sc.dh[k] + tt[1] * sc.dh[3 + k] + tt[2] * sc.dh[6 + k];
+                double r[3];
+                pair_vec64<T>(oi, oil, off[q], offl[q], c, r);
+                const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+                if (r2 < rc * rc && r2 > 0.0) {
                     rx[cnt] = r[0];
                     ry[cnt] = r[1];
                     rz[cnt] = r[2];
                     rd[cnt] = sqrt(r2);
                     ++cnt;
                 }
-            });
+            }
             const double pi = 3.14159265358979323846;
             const double c2 = p.c * p.c, d2 = p.d * p.d;
+            double fc[MAXN_TERSOFF];
+            for (int k = 0; k < cnt; ++k) {
+                const double sk = rd[k] - p.R;
+                const double sn = sin(0.25 * pi * (p.D - sk) / p.D);
+                fc[k] = sk <= -p.D ? 1.0 : (sk >= p.D ? 0.0 : sn * sn);
+            }
             for (int j = 0; j < cnt; ++j) {
                 double zeta = 0.0;
                 for (int k = 0; k < cnt; ++k) {
@@ -107,14 +157,10 @@ __global__ void __launch_bounds__(TILE) k_energy64(const Tile *tiles, BandDev *b
                                       (rd[j] * rd[k]);
                     const double u = p.h - cs;
                     const double g = 1.0 + c2 * u * u / (d2 * (d2 + u * u));
-                    const double sk = rd[k] - p.R;
-                    const double fck = sk <= -p.D ? 1.0 : (sk >= p.D ? 0.0 : pow(sin(0.25 * pi * (p.D - sk) / p.D), 2.0));
-                    zeta += fck * g;
+                    zeta += fc[k] * g;
                 }
                 const double b_ = zeta > 0.0 ? pow(1.0 + pow(p.beta * zeta, p.n), -0.5 / p.n) : 1.0;
-                const double sj = rd[j] - p.R;
-                const double fcj = sj <= -p.D ? 1.0 : (sj >= p.D ? 0.0 : pow(sin(0.25 * pi * (p.D - sj) / p.D), 2.0));
-                U += 0.5 * fcj * (p.A * exp(-p.lambda1 * rd[j]) - b_ * p.B * exp(-p.lambda2 * rd[j]));
+                U += 0.5 * fc[j] * (p.A * exp(-p.lambda1 * rd[j]) - b_ * p.B * exp(-p.lambda2 * rd[j]));
             }
         }
     }
@@ -124,15 +170,15 @@ __global__ void __launch_bounds__(TILE) k_energy64(const Tile *tiles, BandDev *b
     if (threadIdx.x == 0) b.atom_part[((size_t)tl.img * b.atpi + tl.t) * NPART] = tot[0];
 }
 
-// one warp per image: E64 = sum of the tile energies (+ P Omega)
+// one block per image: E64 = sum of the tile energies (+ P Omega)
 __global__ void k_energy_finalize(const ImgRef *imgs, BandDev *bands) {
     ImgRef r = imgs[blockIdx.x];
     BandDev &b = bands[r.band];
     const double *part = b.atom_part + (size_t)r.img * b.atpi * NPART;
-    double v = 0.0;
-    for (int t = threadIdx.x; t < b.atpi; t += 32) v += part[(size_t)t * NPART];
-    v = warp_sum(v);
-    if (threadIdx.x == 0) b.sc[r.img].E64 = v + b.bp->pressure * b.sc[r.img].omega;
+    double v[1] = {0.0}, s[1];
+    for (int t = threadIdx.x; t < b.atpi; t += blockDim.x) v[0] += part[(size_t)t * NPART];
+    block_sum_any<1>(v, s);
+    if (threadIdx.x == 0) b.sc[r.img].E64 = s[0] + b.bp->pressure * b.sc[r.img].omega;
 }
 
 template <typename T>
@@ -140,7 +186,7 @@ void launch_energy64(const Tile *tiles, int ntiles, const ImgRef *imgs, int nimg
                      cudaStream_t s) {
     if (ntiles <= 0 || nimg <= 0) return;
     k_energy64<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
-    k_energy_finalize<<<nimg, 32, 0, s>>>(imgs, bands);
+    k_energy_finalize<<<nimg, RED_THREADS, 0, s>>>(imgs, bands);
 }
 template void launch_energy64<float>(const Tile *, int, const ImgRef *, int, BandDev *,
                                      cudaStream_t);

@@ -22,10 +22,13 @@ def g():
 
 
 def _requests():
-    """LJ vacancy / divacancy hops that converge to fmax 0.05 within a few
-    thousand FIRE steps (checked with the oracle)."""
+    """LJ vacancy / divacancy hops that converge to fmax 0.05 within 2,000
+    FIRE steps (checked with the oracle: 1411, 1263, 1468 and 1859 steps).
+    Strained end cells where the hop is symmetric: a mirror-symmetric band
+    can break its symmetry either way, and a rounding-level difference then
+    changes how long it takes."""
     out = []
-    for reps, div, seed, amp, N in (((2, 2, 2), False, 1, 0.0, 7), ((3, 3, 3), True, 2, 0.0, 7),
+    for reps, div, seed, amp, N in (((2, 2, 2), False, 1, 0.0, 7), ((3, 3, 3), True, 5, 0.003, 7),
                                     ((3, 3, 2), False, 3, 0.003, 5),
                                     ((3, 3, 3), False, 2, 0.003, 7)):
         R0, h0, R1, h1 = ci.lj_vacancy_hop(ci.LJ_A, reps, divacancy=div)
