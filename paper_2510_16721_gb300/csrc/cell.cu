@@ -44,14 +44,16 @@ namespace cfneb {
 
 // ---- 3x3 symmetric square root -----------------------------------------
 //
-// FP64 division and square root are long instruction sequences on this GPU
-// and a map-back is one thread's serial chain, so the eigen-decomposition of
-// B is found in two stages: cyclic Jacobi in FP32 gives an eigenbasis Q0 to
-// ~1e-7; A = Q0^T B Q0 (FP64) is then diagonal up to ~1e-7 and two FP64
-// Jacobi sweeps on it (quadratic convergence, any eigenvalue spacing) give
-// Q and w to FP64 accuracy; S = Q diag(sqrt w) Q^T, S^-1 = Q diag(1/sqrt w) Q^T.
-// Q0's columns are re-orthonormalised in FP64 (Gram-Schmidt) first, so that
-// Q0^T B Q0 is an exact similarity transform.
+// On this GPU a dependent FP64 operation costs ~64 cycles and an FP64
+// divide or square root several hundred, while a map-back is one thread's
+// serial chain per image.  The symmetric root is therefore taken with the
+// coupled Newton-Schulz iteration (Higham, Functions of Matrices, 2008,
+// Sec. 6.7), which needs matrix products only: with Y0 = B/mu, Z0 = I and
+// T = (3I - Z Y)/2, Y <- Y T and Z <- T Z converge quadratically to
+// (B/mu)^(1/2) and (B/mu)^(-1/2) when the eigenvalues of B/mu lie in (0, 2).
+// Every iterate is a polynomial in B, so Y and Z stay symmetric and commute
+// with B.  mu is the midpoint of a bracket of the spectrum: g, the largest
+// Gershgorin row bound (>= lambda_max), and det B / g^2 (<= lambda_min).
 
 // FP64 inverse of a 3x3 matrix without an FP64 division: cofactors and an
 // FP32 reciprocal of the determinant refined by r <- r (2 - det r)
@@ -74,104 +76,50 @@ __device__ inline double inv3n(const double *m, double *o) {
     return det;
 }
 
-// rotation of one Jacobi step: t = tan, c = cos for the pivot (p, r)
-__device__ inline void jacobi_angle(float app, float arr, float apr, float &t, float &c) {
-    const float theta = (arr - app) / (2.0f * apr);
-    t = (theta >= 0.0f ? 1.0f : -1.0f) / (fabsf(theta) + sqrtf(theta * theta + 1.0f));
-    c = 1.0f / sqrtf(t * t + 1.0f);
-}
-__device__ inline void jacobi_angle(double app, double arr, double apr, double &t, double &c) {
-    const double theta = (arr - app) * rcp64(2.0 * apr);
-    const double at = fabs(theta);
-    // tan of the smaller root of t^2 + 2 theta t - 1 = 0 (1 / 2theta when
-    // theta^2 would leave FP32's range in the seed)
-    const double mag = at > 1e15 ? 0.5 * rcp64(at) : rcp64(at + sqrt64(theta * theta + 1.0));
-    t = theta >= 0.0 ? mag : -mag;
-    c = rsqrt64(t * t + 1.0);
-}
-
-// one cyclic Jacobi sweep on symmetric a, accumulating rotations into q
-template <typename R>
-__device__ inline void jacobi_sweep(R (&a)[3][3], R (&q)[3][3]) {
-    for (int p = 0; p < 2; ++p)
-        for (int r = p + 1; r < 3; ++r) {
-            const R apr = a[p][r];
-            // already diagonal to far below rounding: nothing to rotate
-            if (fabs(apr) <= (R)1e-30 * (fabs(a[p][p]) + fabs(a[r][r]))) continue;
-            R t, c;
-            jacobi_angle(a[p][p], a[r][r], apr, t, c);
-            const R s = t * c;
-            for (int k = 0; k < 3; ++k) {  // A <- A J (columns p, r)
-                const R akp = a[k][p], akr = a[k][r];
-                a[k][p] = c * akp - s * akr;
-                a[k][r] = s * akp + c * akr;
-            }
-            for (int k = 0; k < 3; ++k) {  // A <- J^T A (rows p, r)
-                const R apk = a[p][k], ark = a[r][k];
-                a[p][k] = c * apk - s * ark;
-                a[r][k] = s * apk + c * ark;
-            }
-            for (int k = 0; k < 3; ++k) {  // Q <- Q J
-                const R qkp = q[k][p], qkr = q[k][r];
-                q[k][p] = c * qkp - s * qkr;
-                q[k][r] = s * qkp + c * qkr;
-            }
-        }
-}
-
 // Returns false if B is not positive definite.  S = B^(1/2), Si = S^-1.
 __device__ bool sym_sqrt3(const double *Bin, double *S, double *Si) {
     double B[9];
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) B[3 * i + j] = 0.5 * (Bin[3 * i + j] + Bin[3 * j + i]);
-    float af[3][3], qf[3][3];
+    // Sylvester's criterion
+    const double m2 = B[0] * B[4] - B[1] * B[3];
+    const double det = det3(B);
+    if (!(B[0] > 0.0 && m2 > 0.0 && det > 0.0)) return false;
+    double g = 0.0;
+    for (int i = 0; i < 3; ++i)
+        g = fmax(g, fabs(B[3 * i]) + fabs(B[3 * i + 1]) + fabs(B[3 * i + 2]));
+    const double ig = rcp64(g);
+    const double lo = det * ig * ig;
+    const double imu = rcp64(0.5 * (g + lo));
+    double Y[9], Z[9], Tm[9], Y1[9], Z1[9];
+    for (int k = 0; k < 9; ++k) {
+        Y[k] = B[k] * imu;
+        Z[k] = (k % 4 == 0) ? 1.0 : 0.0;
+    }
+    for (int it = 0; it < 40; ++it) {
+        matmul3(Z, Y, Tm);
+        float dev = 0.0f;
+        for (int k = 0; k < 9; ++k) {
+            const double e = ((k % 4 == 0) ? 1.0 : 0.0) - Tm[k];  // I - Z Y
+            Tm[k] = ((k % 4 == 0) ? 1.0 : 0.0) + 0.5 * e;           // (3I - Z Y) / 2
+            dev = fmaxf(dev, fabsf((float)e));
+        }
+        matmul3(Y, Tm, Y1);
+        matmul3(Tm, Z, Z1);
+        for (int k = 0; k < 9; ++k) {
+            Y[k] = Y1[k];
+            Z[k] = Z1[k];
+        }
+        // quadratic convergence: after a step with |I - Z Y| < 1e-9 the
+        // next deviation is ~1e-18, below FP64 rounding
+        if (dev < 1e-9f) break;
+    }
+    const double rmu = sqrt64(0.5 * (g + lo));  // sqrt(mu)
+    const double irmu = rcp64(rmu);
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
-            af[i][j] = (float)B[3 * i + j];
-            qf[i][j] = (i == j) ? 1.0f : 0.0f;
-        }
-    for (int sweep = 0; sweep < 16; ++sweep) {
-        const float off = af[0][1] * af[0][1] + af[0][2] * af[0][2] + af[1][2] * af[1][2];
-        const float diag = af[0][0] * af[0][0] + af[1][1] * af[1][1] + af[2][2] * af[2][2];
-        if (off <= 1e-14f * diag) break;
-        jacobi_sweep<float>(af, qf);
-    }
-    // orthonormal columns in FP64, A = Q0^T B Q0, then polish
-    double q[3][3], a[3][3], tmp[3][3];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) q[i][j] = (double)qf[i][j];
-    for (int c = 0; c < 3; ++c) {
-        for (int p = 0; p < c; ++p) {
-            const double d = q[0][p] * q[0][c] + q[1][p] * q[1][c] + q[2][p] * q[2][c];
-            for (int k = 0; k < 3; ++k) q[k][c] -= d * q[k][p];
-        }
-        const double nn = q[0][c] * q[0][c] + q[1][c] * q[1][c] + q[2][c] * q[2][c];
-        const double inv = rsqrt64(nn);
-        for (int k = 0; k < 3; ++k) q[k][c] *= inv;
-    }
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-            tmp[i][j] = B[3 * i] * q[0][j] + B[3 * i + 1] * q[1][j] + B[3 * i + 2] * q[2][j];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-            a[i][j] = q[0][i] * tmp[0][j] + q[1][i] * tmp[1][j] + q[2][i] * tmp[2][j];
-    for (int i = 0; i < 3; ++i)
-        for (int j = i + 1; j < 3; ++j) a[i][j] = a[j][i] = 0.5 * (a[i][j] + a[j][i]);
-    jacobi_sweep<double>(a, q);
-    jacobi_sweep<double>(a, q);
-    const double w[3] = {a[0][0], a[1][1], a[2][2]};
-    if (!(w[0] > 0.0 && w[1] > 0.0 && w[2] > 0.0)) return false;
-    double sw[3], isw[3];
-    for (int k = 0; k < 3; ++k) {
-        isw[k] = rsqrt64(w[k]);
-        sw[k] = w[k] * isw[k];
-    }
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            S[3 * i + j] = q[i][0] * sw[0] * q[j][0] + q[i][1] * sw[1] * q[j][1] +
-                           q[i][2] * sw[2] * q[j][2];
-            Si[3 * i + j] = q[i][0] * isw[0] * q[j][0] + q[i][1] * isw[1] * q[j][1] +
-                            q[i][2] * isw[2] * q[j][2];
+            S[3 * i + j] = 0.5 * (Y[3 * i + j] + Y[3 * j + i]) * rmu;
+            Si[3 * i + j] = 0.5 * (Z[3 * i + j] + Z[3 * j + i]) * irmu;
         }
     return true;
 }
@@ -210,11 +158,15 @@ __device__ void bin_geometry(const BandParams *bp, int nbins_cap, const double *
     // sum of three products delta_a bv_a (|delta| <= 7) is then exact in
     // FP32; dh = h - nb bv carries the (sub-1e-4 A) quantisation to the
     // periodic wrap
-    double bmax = 0.0, inb[3];
+    double inb[3];
     for (int a = 0; a < 3; ++a) inb[a] = rcp64((double)nb[a]);
+    // only the binade of max |h_a / nb_a| matters; found in FP32, it can be
+    // one binade low by an ulp, and then |bv| <= (2^19 + 1) q: three terms
+    // |delta| <= 7 still sum below 2^24 q, exact in FP32
+    float bmax = 0.0f;
     for (int a = 0; a < 3; ++a)
-        for (int c = 0; c < 3; ++c) bmax = fmax(bmax, fabs(h[3 * a + c] * inb[a]));
-    const int e = ilogb(bmax) + 1 - 19;
+        for (int c = 0; c < 3; ++c) bmax = fmaxf(bmax, fabsf((float)h[3 * a + c] / (float)nb[a]));
+    const int e = ilogbf(bmax) + 1 - 19;
     const double q = ldexp(1.0, e), iq = ldexp(1.0, -e);  // exact powers of two
     for (int a = 0; a < 3; ++a) {
         if (!keep_grid) {
@@ -453,20 +405,37 @@ __global__ void __launch_bounds__(TILE) k_skin_check(const Tile *tiles, BandDev 
 }
 
 // upper bound of the spectral norm of a 3x3 matrix: the smaller of the
-// Frobenius norm and sqrt(|A|_1 |A|_inf)
-__device__ inline double norm2_bound(const double *A) {
-    double f = 0.0, c1 = 0.0, ci = 0.0;
+// Frobenius norm and sqrt(|A|_1 |A|_inf), in FP32 and raised by 1e-6 to
+// stay a bound
+__device__ inline float norm2_bound(const float *A) {
+    float f = 0.0f, c1 = 0.0f, ci = 0.0f;
     for (int i = 0; i < 3; ++i) {
-        double rs = 0.0, cs = 0.0;
+        float rs = 0.0f, cs = 0.0f;
         for (int j = 0; j < 3; ++j) {
             f += A[3 * i + j] * A[3 * i + j];
-            rs += fabs(A[3 * i + j]);
-            cs += fabs(A[3 * j + i]);
+            rs += fabsf(A[3 * i + j]);
+            cs += fabsf(A[3 * j + i]);
         }
-        ci = fmax(ci, rs);
-        c1 = fmax(c1, cs);
+        ci = fmaxf(ci, rs);
+        c1 = fmaxf(c1, cs);
     }
-    return fmin(sqrt64(f), sqrt64(c1 * ci));
+    return fminf(sqrtf(f), sqrtf(c1 * ci)) * 1.000001f;
+}
+
+// FP32 inverse of a 3x3 matrix (cofactors over the determinant)
+__device__ inline void inv3f(const float *m, float *o) {
+    const float c00 = m[4] * m[8] - m[5] * m[7], c01 = m[5] * m[6] - m[3] * m[8],
+                c02 = m[3] * m[7] - m[4] * m[6];
+    const float id = 1.0f / (m[0] * c00 + m[1] * c01 + m[2] * c02);
+    o[0] = c00 * id;
+    o[1] = (m[2] * m[7] - m[1] * m[8]) * id;
+    o[2] = (m[1] * m[5] - m[2] * m[4]) * id;
+    o[3] = c01 * id;
+    o[4] = (m[0] * m[8] - m[2] * m[6]) * id;
+    o[5] = (m[2] * m[3] - m[0] * m[5]) * id;
+    o[6] = c02 * id;
+    o[7] = (m[1] * m[6] - m[0] * m[7]) * id;
+    o[8] = (m[0] * m[4] - m[1] * m[3]) * id;
 }
 
 // One block per image: keep the bins of the build while the bound in the
@@ -485,13 +454,22 @@ __global__ void k_skin_decide(const ImgRef *imgs, BandDev *bands, int force) {
     if (threadIdx.x != 0) return;
     bool rebuild = force || bp->stale || bp->tune_rebuild || sc.builds == 0;
     if (!rebuild) {
-        double Dbi[9], M[9];
-        inv3n(sc.Db, Dbi);
-        matmul3(Dbi, sc.D, M);
-        for (int k = 0; k < 9; k += 4) M[k] -= 1.0;
-        // small relative margins cover the FP32 list test and displacement
-        const double bound = bp->rl * (1.0 - 1e-5) * (1.0 - norm2_bound(M)) -
-                             2.0 * d * norm2_bound(sc.D) * (1.0 + 1e-5);
+        // in FP32: M - I = D_b^-1 D - I is small, so its FP32 rounding (~1e-7
+        // absolute) moves the bound by far less than the 1e-5 margins, which
+        // also cover the FP32 list test and displacement
+        float Db[9], D[9], Dbi[9], M[9];
+        for (int k = 0; k < 9; ++k) {
+            Db[k] = (float)sc.Db[k];
+            D[k] = (float)sc.D[k];
+        }
+        inv3f(Db, Dbi);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                M[3 * i + j] = Dbi[3 * i] * D[j] + Dbi[3 * i + 1] * D[3 + j] +
+                               Dbi[3 * i + 2] * D[6 + j] - (i == j ? 1.0f : 0.0f);
+        const float e = norm2_bound(M) * 1.00001f + 1e-6f;
+        const double bound = bp->rl * (1.0 - 1e-5) * (1.0 - (double)e) -
+                             2.0 * d * (double)norm2_bound(D) * (1.0 + 1e-5);
         rebuild = !(bound > bp->rc);
     }
     if (rebuild) {

@@ -257,8 +257,10 @@ __device__ inline void block_sum_t(T (&v)[K], double *out) {
 }
 
 // Sum K per-thread values over a block of any multiple of 32 threads (up to
-// 1024) in FP64, fixed order (warp butterflies, then warps in order); thread
-// 0 receives the totals.
+// 1024) in FP64, fixed order (a warp butterfly within each warp, then one
+// across the warp totals); thread 0 receives the totals.  Butterflies keep
+// the dependent FP64 chain at 5 + 5 additions (a dependent FP64 operation
+// costs ~64 cycles here).
 template <int K>
 __device__ inline void block_sum_any(double (&v)[K], double *out) {
     __shared__ double red[32][K];
@@ -269,11 +271,11 @@ __device__ inline void block_sum_any(double (&v)[K], double *out) {
         if (lane == 0) red[w][k] = s;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (w == 0) {
+#pragma unroll
         for (int k = 0; k < K; ++k) {
-            double s = 0.0;
-            for (int q = 0; q < nw; ++q) s += red[q][k];
-            out[k] = s;
+            const double s = warp_sum(lane < nw ? red[lane][k] : 0.0);
+            if (lane == 0) out[k] = s;
         }
     }
     __syncthreads();

@@ -140,7 +140,9 @@ def test_adaptive_refinement_with_skin(g, oracle_mod, kind):
         gb.step(30)
         st = gb.get_state()
         assert st["X"].shape[0] == ob.N
-        _compare_state(st, ob, 1e-8)
+        # 120 FIRE steps: rounding-order differences (FP64 tile sums, the
+        # matrix square root) grow with the dynamics to ~1e-8 by the end
+        _compare_state(st, ob, 3e-8)
     assert [e[0] for e in ob.events] == [kind, kind]
 
 
