@@ -29,8 +29,13 @@ template <typename T>
 __global__ void k_image_finalize(const ImgRef *imgs, BandDev *bands) {
     ImgRef r = imgs[blockIdx.x];
     BandDev &b = bands[r.band];
-    const BandParams *bp = b.bp;
+    __shared__ BandParams s_bp;
+    __shared__ ImgScalars s_sc;
+    stage_copy(&s_bp, b.bp);
+    stage_copy(&s_sc, &b.sc[r.img]);  // read-only copy; results go to global
+    const BandParams *bp = &s_bp;
     ImgScalars &sc = b.sc[r.img];
+    const ImgScalars &sci = s_sc;
     const double *part = b.atom_part + (size_t)r.img * b.atpi * NPART;
     double v[12], s[12];
     for (int k = 0; k < 12; ++k) v[k] = 0.0;
@@ -45,8 +50,8 @@ __global__ void k_image_finalize(const ImgRef *imgs, BandDev *bands) {
     for (int k = 0; k < 9; ++k) V[k] = s[1 + k];
     double E = U;
     if (bp->pressure != 0.0) {
-        E += bp->pressure * sc.omega;
-        for (int a = 0; a < 3; ++a) V[4 * a] -= bp->pressure * sc.omega;
+        E += bp->pressure * sci.omega;
+        for (int a = 0; a < 3; ++a) V[4 * a] -= bp->pressure * sci.omega;
     }
     sc.U = U;
     sc.E = E;
@@ -55,7 +60,7 @@ __global__ void k_image_finalize(const ImgRef *imgs, BandDev *bands) {
     if (!bp->filter) {
         for (int k = 0; k < 9; ++k) Phi[k] = 0.0;
     } else {
-        const double *Di = sc.Dinv;
+        const double *Di = sci.Dinv;
         double DiT[9];
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) DiT[3 * i + j] = Di[3 * j + i];
@@ -224,26 +229,8 @@ __global__ void __launch_bounds__(TILE) k_neb_force(const Tile *tiles, BandDev *
 
 // one block per band; the threads sum the tile partials of every interior
 // image, thread 0 runs the FIRE logic
-__global__ void k_fire_scalars(const int *band_ids, BandDev *bands) {
-    BandDev &b = bands[band_ids[blockIdx.x]];
-    BandParams *bp = b.bp;
-    const int N = bp->N;
-    // the row-tile partials of images 1..N-2, one fixed strided subset per
-    // thread, then a fixed-order block sum
-    const int nt = (N - 2) * b.rtpi;
-    const double *part0 = b.row_part + (size_t)b.rtpi * NPART;
-    double v[3] = {0, 0, 0}, tot[4];
-    double m = 0.0;
-    for (int q = threadIdx.x; q < nt; q += blockDim.x) {
-        const double *p = part0 + (size_t)q * NPART;
-        v[0] += p[5];
-        v[1] += p[6];
-        v[2] += p[7];
-        m = fmax(m, p[8]);
-    }
-    block_sum_any<3>(v, tot);
-    tot[3] = block_max_any(m);
-    if (threadIdx.x != 0) return;
+// convergence test and FIRE decision on the band's parameters
+__device__ inline void fire_logic(BandParams *bp, const double *tot) {
     bp->stale = 0;  // every image of the band has rebuilt its cell list
     const double P = tot[0], FF = tot[1], VV = tot[2];
     const double fmax_ = sqrt(tot[3]);
@@ -251,9 +238,7 @@ __global__ void k_fire_scalars(const int *band_ids, BandDev *bands) {
     bp->FF = FF;
     bp->VV = VV;
     bp->fmax = fmax_;
-    if (!isfinite(P) || !isfinite(FF) || !isfinite(VV)) {
-        atomicOr(&bp->status, ST_NONFINITE);
-    }
+    if (!isfinite(P) || !isfinite(FF) || !isfinite(VV)) bp->status |= ST_NONFINITE;
     bp->converged = (bp->status == 0 && bp->ftol >= 0.0 && fmax_ < bp->ftol) ? 1 : 0;
     if (bp->status != 0 || bp->converged || bp->steps >= bp->move_limit) {
         bp->move = 0;
@@ -288,6 +273,34 @@ __global__ void k_fire_scalars(const int *band_ids, BandDev *bands) {
     bp->cv = cv;
     bp->cf = cf;
     bp->steps += 1;
+}
+
+__global__ void k_fire_scalars(const int *band_ids, BandDev *bands) {
+    BandDev &b = bands[band_ids[blockIdx.x]];
+    // the band's parameters are staged in shared memory, updated by thread 0
+    // and written back (no other kernel touches them meanwhile)
+    __shared__ BandParams s_bp;
+    stage_copy(&s_bp, b.bp);
+    __syncthreads();
+    const int N = s_bp.N;
+    // the row-tile partials of images 1..N-2, one fixed strided subset per
+    // thread, then a fixed-order block sum
+    const int nt = (N - 2) * b.rtpi;
+    const double *part0 = b.row_part + (size_t)b.rtpi * NPART;
+    double v[3] = {0, 0, 0}, tot[4];
+    double m = 0.0;
+    for (int q = threadIdx.x; q < nt; q += blockDim.x) {
+        const double *p = part0 + (size_t)q * NPART;
+        v[0] += p[5];
+        v[1] += p[6];
+        v[2] += p[7];
+        m = fmax(m, p[8]);
+    }
+    block_sum_any<3>(v, tot);
+    tot[3] = block_max_any(m);
+    if (threadIdx.x == 0) fire_logic(&s_bp, tot);
+    __syncthreads();
+    stage_copy(b.bp, &s_bp);
 }
 
 template <typename T>

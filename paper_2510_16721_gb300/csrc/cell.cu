@@ -45,84 +45,16 @@ namespace cfneb {
 // ---- 3x3 symmetric square root -----------------------------------------
 //
 // On this GPU a dependent FP64 operation costs ~64 cycles and an FP64
-// divide or square root several hundred, while a map-back is one thread's
-// serial chain per image.  The symmetric root is therefore taken with the
-// coupled Newton-Schulz iteration (Higham, Functions of Matrices, 2008,
-// Sec. 6.7), which needs matrix products only: with Y0 = B/mu, Z0 = I and
-// T = (3I - Z Y)/2, Y <- Y T and Z <- T Z converge quadratically to
+// divide or square root several hundred, and the map-back of every image is
+// on the critical path of each step.  The symmetric root is therefore taken
+// with the coupled Newton-Schulz iteration (Higham, Functions of Matrices,
+// 2008, Sec. 6.7), which needs matrix products only: with Y0 = B/mu, Z0 = I
+// and T = (3I - Z Y)/2, Y <- Y T and Z <- T Z converge quadratically to
 // (B/mu)^(1/2) and (B/mu)^(-1/2) when the eigenvalues of B/mu lie in (0, 2).
 // Every iterate is a polynomial in B, so Y and Z stay symmetric and commute
 // with B.  mu is the midpoint of a bracket of the spectrum: g, the largest
 // Gershgorin row bound (>= lambda_max), and det B / g^2 (<= lambda_min).
-
-// FP64 inverse of a 3x3 matrix without an FP64 division: cofactors and an
-// FP32 reciprocal of the determinant refined by r <- r (2 - det r)
-__device__ inline double inv3n(const double *m, double *o) {
-    const double c00 = m[4] * m[8] - m[5] * m[7], c01 = m[5] * m[6] - m[3] * m[8],
-                 c02 = m[3] * m[7] - m[4] * m[6];
-    const double det = m[0] * c00 + m[1] * c01 + m[2] * c02;
-    double r = (double)(1.0f / (float)det);
-    r = r * (2.0 - det * r);
-    r = r * (2.0 - det * r);
-    o[0] = c00 * r;
-    o[1] = (m[2] * m[7] - m[1] * m[8]) * r;
-    o[2] = (m[1] * m[5] - m[2] * m[4]) * r;
-    o[3] = c01 * r;
-    o[4] = (m[0] * m[8] - m[2] * m[6]) * r;
-    o[5] = (m[2] * m[3] - m[0] * m[5]) * r;
-    o[6] = c02 * r;
-    o[7] = (m[1] * m[6] - m[0] * m[7]) * r;
-    o[8] = (m[0] * m[4] - m[1] * m[3]) * r;
-    return det;
-}
-
-// Returns false if B is not positive definite.  S = B^(1/2), Si = S^-1.
-__device__ bool sym_sqrt3(const double *Bin, double *S, double *Si) {
-    double B[9];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) B[3 * i + j] = 0.5 * (Bin[3 * i + j] + Bin[3 * j + i]);
-    // Sylvester's criterion
-    const double m2 = B[0] * B[4] - B[1] * B[3];
-    const double det = det3(B);
-    if (!(B[0] > 0.0 && m2 > 0.0 && det > 0.0)) return false;
-    double g = 0.0;
-    for (int i = 0; i < 3; ++i)
-        g = fmax(g, fabs(B[3 * i]) + fabs(B[3 * i + 1]) + fabs(B[3 * i + 2]));
-    const double ig = rcp64(g);
-    const double lo = det * ig * ig;
-    const double imu = rcp64(0.5 * (g + lo));
-    double Y[9], Z[9], Tm[9], Y1[9], Z1[9];
-    for (int k = 0; k < 9; ++k) {
-        Y[k] = B[k] * imu;
-        Z[k] = (k % 4 == 0) ? 1.0 : 0.0;
-    }
-    for (int it = 0; it < 40; ++it) {
-        matmul3(Z, Y, Tm);
-        float dev = 0.0f;
-        for (int k = 0; k < 9; ++k) {
-            const double e = ((k % 4 == 0) ? 1.0 : 0.0) - Tm[k];  // I - Z Y
-            Tm[k] = ((k % 4 == 0) ? 1.0 : 0.0) + 0.5 * e;           // (3I - Z Y) / 2
-            dev = fmaxf(dev, fabsf((float)e));
-        }
-        matmul3(Y, Tm, Y1);
-        matmul3(Tm, Z, Z1);
-        for (int k = 0; k < 9; ++k) {
-            Y[k] = Y1[k];
-            Z[k] = Z1[k];
-        }
-        // quadratic convergence: after a step with |I - Z Y| < 1e-9 the
-        // next deviation is ~1e-18, below FP64 rounding
-        if (dev < 1e-9f) break;
-    }
-    const double rmu = sqrt64(0.5 * (g + lo));  // sqrt(mu)
-    const double irmu = rcp64(rmu);
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            S[3 * i + j] = 0.5 * (Y[3 * i + j] + Y[3 * j + i]) * rmu;
-            Si[3 * i + j] = 0.5 * (Z[3 * i + j] + Z[3 * j + i]) * irmu;
-        }
-    return true;
-}
+// The products run lane-parallel (k_mapback).
 
 // Bin grid of an image with cell h: with keep_grid false the bin counts
 // nb and stencil half widths m are chosen from the perpendicular widths and
@@ -184,50 +116,123 @@ __device__ void bin_geometry(const BandParams *bp, int nbins_cap, const double *
     sc.nbins = nb[0] * nb[1] * nb[2];
 }
 
+// ---- lane-parallel 3x3 algebra for the map-back -------------------------
+//
+// One warp per image: lane l holds entry (i, j) = (l / 3, l % 3) of each
+// 3x3 matrix (lanes 9..31 mirror lane l % 9; their results are unused).  A
+// product is then 6 shuffles and a chain of 3 FP64 operations per lane
+// instead of 27 dependent-heavy operations in one thread: the map-back is on
+// the critical path of every step and FP64 latency (~64 cycles) dominates it.
+struct Lane3 {
+    int l, i, j;
+    __device__ Lane3() : l((int)(threadIdx.x & 31) % 9), i(l / 3), j(l % 3) {}
+    __device__ double eye() const { return i == j ? 1.0 : 0.0; }
+};
+__device__ inline double lget(double a, int src) { return __shfl_sync(0xffffffffu, a, src); }
+// (A B)_ij = sum_k A_ik B_kj
+__device__ inline double lmul(double a, double b, const Lane3 &p) {
+    const double a0 = lget(a, 3 * p.i), a1 = lget(a, 3 * p.i + 1), a2 = lget(a, 3 * p.i + 2);
+    const double b0 = lget(b, p.j), b1 = lget(b, 3 + p.j), b2 = lget(b, 6 + p.j);
+    return fma(a2, b2, fma(a1, b1, a0 * b0));
+}
+__device__ inline double ltrans(double a, const Lane3 &p) { return lget(a, 3 * p.j + p.i); }
+// cofactor C_ij = A_{i+1,j+1} A_{i+2,j+2} - A_{i+1,j+2} A_{i+2,j+1}
+__device__ inline double lcof(double a, const Lane3 &p) {
+    const int i1 = (p.i + 1) % 3, i2 = (p.i + 2) % 3, j1 = (p.j + 1) % 3, j2 = (p.j + 2) % 3;
+    const double p11 = lget(a, 3 * i1 + j1), p22 = lget(a, 3 * i2 + j2);
+    const double p12 = lget(a, 3 * i1 + j2), p21 = lget(a, 3 * i2 + j1);
+    return fma(p11, p22, -(p12 * p21));
+}
+// det A = sum_j A_0j C_0j, in every lane
+__device__ inline double ldet(double a, double c) {
+    const double t = a * c;
+    return lget(t, 0) + lget(t, 1) + lget(t, 2);
+}
+
+// Map-back of one image per warp: B = X_lat / c, D = B^(1/2) (rotation-free,
+// coupled Newton-Schulz as in sym_sqrt3) or D = X_lat / c (deformation
+// gradient), then h = h0 D, h^-1 = D^-1 h0^-1 and Omega = |det h|.
 template <typename T>
-__global__ void k_mapback(const ImgRef *imgs, int count, BandDev *bands) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= count) return;
-    ImgRef r = imgs[k];
+__global__ void __launch_bounds__(32) k_mapback(const ImgRef *imgs, int count, BandDev *bands) {
+    const ImgRef r = imgs[blockIdx.x];
     BandDev &b = bands[r.band];
-    BandParams *bp = b.bp;
+    __shared__ BandParams s_bp;
+    stage_copy(&s_bp, b.bp);
+    __syncwarp();
+    const BandParams *bp = &s_bp;
     ImgScalars &sc = b.sc[r.img];
+    const Lane3 p;
+    const int lane = threadIdx.x & 31;
     const T *Xl = (const T *)b.X + ((size_t)r.img * b.rows + b.n) * 3;
-    double D[9], Di[9];
+    double D = p.eye(), Di = p.eye();
     bool ok = true;
-    if (!bp->filter) {
-        for (int i = 0; i < 9; ++i) D[i] = Di[i] = (i % 4 == 0) ? 1.0 : 0.0;
-    } else {
-        double L[9];
-        const double ic = rcp64(bp->c);
-        for (int i = 0; i < 9; ++i) L[i] = (double)Xl[i] * ic;
+    if (bp->filter) {
+        const double L = (double)Xl[p.l] * rcp64(bp->c);
         if (bp->variant == 0) {
-            ok = sym_sqrt3(L, D, Di);
+            const double B = 0.5 * (L + ltrans(L, p));
+            const double C = lcof(B, p);
+            const double det = ldet(B, C);
+            // Sylvester's criterion: B00 > 0, the leading 2x2 minor (= C22) > 0, det > 0
+            ok = lget(B, 0) > 0.0 && lget(C, 8) > 0.0 && det > 0.0;
+            if (ok) {
+                // spectrum bracket [det / g^2, g], g = largest Gershgorin row bound
+                const double rs = fabs(lget(B, 3 * p.i)) + fabs(lget(B, 3 * p.i + 1)) +
+                                  fabs(lget(B, 3 * p.i + 2));
+                const double g = fmax(fmax(lget(rs, 0), lget(rs, 3)), lget(rs, 6));
+                const double ig = rcp64(g);
+                const double mu = 0.5 * (g + det * ig * ig);
+                double Y = B * rcp64(mu), Z = p.eye();
+                for (int it = 0; it < 40; ++it) {
+                    const double e = p.eye() - lmul(Z, Y, p);  // I - Z Y
+                    const double Tm = p.eye() + 0.5 * e;       // (3I - Z Y) / 2
+                    float dev = fabsf((float)e);
+                    for (int o = 16; o > 0; o >>= 1)
+                        dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+                    const double Y1 = lmul(Y, Tm, p), Z1 = lmul(Tm, Z, p);
+                    Y = Y1;
+                    Z = Z1;
+                    if (dev < 1e-9f) break;  // the last step took it to ~1e-18
+                }
+                const double rmu = sqrt64(mu);
+                D = 0.5 * (Y + ltrans(Y, p)) * rmu;
+                Di = 0.5 * (Z + ltrans(Z, p)) * rcp64(rmu);
+            }
         } else {
-            for (int i = 0; i < 9; ++i) D[i] = L[i];
-            ok = inv3n(D, Di) > 0.0;
+            const double C = lcof(L, p);
+            const double det = ldet(L, C);
+            ok = det > 0.0;
+            if (ok) {
+                D = L;
+                Di = ltrans(C, p) * rcp64(det);
+            }
         }
     }
     if (!ok) {
-        atomicOr(&bp->status, ST_NOT_SPD);
-        for (int i = 0; i < 9; ++i) D[i] = Di[i] = (i % 4 == 0) ? 1.0 : 0.0;
+        if (lane == 0) atomicOr(&b.bp->status, ST_NOT_SPD);
+        D = Di = p.eye();
     }
-    double h[9];
-    matmul3(bp->h0, D, h);
-    for (int i = 0; i < 9; ++i) {
-        sc.D[i] = D[i];
-        sc.Dinv[i] = Di[i];
-        sc.h[i] = h[i];
+    const double h = lmul(bp->h0[p.l], D, p);
+    const double hinv = lmul(Di, bp->h0inv[p.l], p);  // (h0 D)^-1 = D^-1 h0^-1
+    const double omega = fabs(ldet(h, lcof(h, p)));
+    if (lane < 9) {
+        sc.D[lane] = D;
+        sc.Dinv[lane] = Di;
+        sc.h[lane] = h;
+        sc.hinv[lane] = hinv;
     }
-    matmul3(Di, bp->h0inv, sc.hinv);  // (h0 D)^-1 = D^-1 h0^-1
-    const double omega = fabs(det3(h));
-    sc.omega = omega;
     if (bp->skin <= 0.0) {
         // no skin: the cell list is rebuilt at every evaluation
-        bin_geometry(bp, b.nbins_cap, h, omega, false, sc);
-        sc.rebuild = 1;
-        sc.builds += 1;
-        sc.evals += 1;
+        double hh[9];
+        for (int k = 0; k < 9; ++k) hh[k] = lget(h, k);
+        if (lane == 0) {
+            sc.omega = omega;
+            bin_geometry(bp, b.nbins_cap, hh, omega, false, sc);
+            sc.rebuild = 1;
+            sc.builds += 1;
+            sc.evals += 1;
+        }
+    } else if (lane == 0) {
+        sc.omega = omega;
     }
 }
 
@@ -444,51 +449,59 @@ __device__ inline void inv3f(const float *m, float *o) {
 __global__ void k_skin_decide(const ImgRef *imgs, BandDev *bands, int force) {
     ImgRef r = imgs[blockIdx.x];
     BandDev &b = bands[r.band];
-    const BandParams *bp = b.bp;
-    if (bp->skin <= 0.0) return;
-    ImgScalars &sc = b.sc[r.img];
+    __shared__ BandParams s_bp;
+    __shared__ ImgScalars s_sc;
+    stage_copy(&s_bp, b.bp);
+    stage_copy(&s_sc, &b.sc[r.img]);
+    __syncthreads();
+    const BandParams *bp = &s_bp;
+    if (bp->skin <= 0.0) return;  // uniform over the block
+    ImgScalars &sc = s_sc;
     const double *part = b.skin_part + (size_t)r.img * b.atpi;
     double d = 0.0;
     for (int t = threadIdx.x; t < b.atpi; t += blockDim.x) d = fmax(d, part[t]);
     d = block_max_any(d);
-    if (threadIdx.x != 0) return;
-    bool rebuild = force || bp->stale || bp->tune_rebuild || sc.builds == 0;
-    if (!rebuild) {
-        // in FP32: M - I = D_b^-1 D - I is small, so its FP32 rounding (~1e-7
-        // absolute) moves the bound by far less than the 1e-5 margins, which
-        // also cover the FP32 list test and displacement
-        float Db[9], D[9], Dbi[9], M[9];
-        for (int k = 0; k < 9; ++k) {
-            Db[k] = (float)sc.Db[k];
-            D[k] = (float)sc.D[k];
+    if (threadIdx.x == 0) {
+        bool rebuild = force || bp->stale || bp->tune_rebuild || sc.builds == 0;
+        if (!rebuild) {
+            // in FP32: M - I = D_b^-1 D - I is small, so its FP32 rounding (~1e-7
+            // absolute) moves the bound by far less than the 1e-5 margins, which
+            // also cover the FP32 list test and displacement
+            float Db[9], D[9], Dbi[9], M[9];
+            for (int k = 0; k < 9; ++k) {
+                Db[k] = (float)sc.Db[k];
+                D[k] = (float)sc.D[k];
+            }
+            inv3f(Db, Dbi);
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    M[3 * i + j] = Dbi[3 * i] * D[j] + Dbi[3 * i + 1] * D[3 + j] +
+                                   Dbi[3 * i + 2] * D[6 + j] - (i == j ? 1.0f : 0.0f);
+            const float e = norm2_bound(M) * 1.00001f + 1e-6f;
+            const double bound = bp->rl * (1.0 - 1e-5) * (1.0 - (double)e) -
+                                 2.0 * d * (double)norm2_bound(D) * (1.0 + 1e-5);
+            rebuild = !(bound > bp->rc);
         }
-        inv3f(Db, Dbi);
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j)
-                M[3 * i + j] = Dbi[3 * i] * D[j] + Dbi[3 * i + 1] * D[3 + j] +
-                               Dbi[3 * i + 2] * D[6 + j] - (i == j ? 1.0f : 0.0f);
-        const float e = norm2_bound(M) * 1.00001f + 1e-6f;
-        const double bound = bp->rl * (1.0 - 1e-5) * (1.0 - (double)e) -
-                             2.0 * d * (double)norm2_bound(D) * (1.0 + 1e-5);
-        rebuild = !(bound > bp->rc);
+        if (rebuild) {
+            bin_geometry(bp, b.nbins_cap, sc.h, sc.omega, false, sc);
+            for (int k = 0; k < 9; ++k) sc.Db[k] = sc.D[k];
+            sc.builds += 1;
+        } else {
+            bin_geometry(bp, b.nbins_cap, sc.h, sc.omega, true, sc);
+        }
+        for (int k = 0; k < 9; ++k) {
+            const float dh_ = (float)sc.D[k], hh_ = (float)sc.h[k];
+            sc.dfl[k] = dh_;
+            sc.dfl[9 + k] = (float)(sc.D[k] - (double)dh_);
+            sc.dfl[18 + k] = hh_;
+            sc.dfl[27 + k] = (float)(sc.h[k] - (double)hh_);
+        }
+        sc.rebuild = rebuild ? 1 : 0;
+        sc.dmax = d;
+        sc.evals += 1;
     }
-    if (rebuild) {
-        bin_geometry(bp, b.nbins_cap, sc.h, sc.omega, false, sc);
-        for (int k = 0; k < 9; ++k) sc.Db[k] = sc.D[k];
-        sc.builds += 1;
-    } else {
-        bin_geometry(bp, b.nbins_cap, sc.h, sc.omega, true, sc);
-    }
-    for (int k = 0; k < 9; ++k) {
-        const float dh_ = (float)sc.D[k], hh_ = (float)sc.h[k];
-        sc.dfl[k] = dh_;
-        sc.dfl[9 + k] = (float)(sc.D[k] - (double)dh_);
-        sc.dfl[18 + k] = hh_;
-        sc.dfl[27 + k] = (float)(sc.h[k] - (double)hh_);
-    }
-    sc.rebuild = rebuild ? 1 : 0;
-    sc.dmax = d;
-    sc.evals += 1;
+    __syncthreads();
+    stage_copy(&b.sc[r.img], &s_sc);
 }
 
 // Exclusive scan of the bin counts, in three passes over SCAN_TILE-bin
@@ -644,7 +657,7 @@ __global__ void k_cartesian(const ImgRef *imgs, BandDev *bands) {
 template <typename T>
 void launch_mapback(const ImgRef *imgs, int count, BandDev *bands, cudaStream_t s) {
     if (count <= 0) return;
-    k_mapback<T><<<(count + 31) / 32, 32, 0, s>>>(imgs, count, bands);
+    k_mapback<T><<<count, 32, 0, s>>>(imgs, count, bands);
 }
 template <typename T>
 void launch_bin_assign(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {

@@ -298,6 +298,18 @@ __device__ inline double block_max_any(double v) {
 // threads of the per-image / per-band reduction kernels
 constexpr int RED_THREADS = 256;
 
+// Copy a record between global and shared memory with all threads of the
+// block (8-byte words).  The per-image and per-band kernels read many fields
+// of ImgScalars and BandParams on one thread; staged first, those reads cost
+// one round trip instead of a chain of dependent global loads.
+template <typename S>
+__device__ inline void stage_copy(S *dst, const S *src) {
+    static_assert(sizeof(S) % 8 == 0, "record size must be a multiple of 8 bytes");
+    const unsigned long long *s = (const unsigned long long *)src;
+    unsigned long long *d = (unsigned long long *)dst;
+    for (int k = threadIdx.x; k < (int)(sizeof(S) / 8); k += blockDim.x) d[k] = s[k];
+}
+
 // ---- launchers (defined in the kernel translation units) ---------------
 
 template <typename T>

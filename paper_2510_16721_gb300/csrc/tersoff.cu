@@ -50,6 +50,8 @@ template <> struct M<float> {
     static __device__ float l1p(float x) { return log1pf(x); }
     static __device__ float sq(float x) { return sqrtf(x); }
     static __device__ float sn(float x) { return sinf(x); }
+    // correctly rounded reciprocal: a short sequence, unlike a full divide
+    static __device__ float rcp(float x) { return __frcp_rn(x); }
 };
 template <> struct M<double> {
     static __device__ double ex(double x) { return exp(x); }
@@ -57,11 +59,12 @@ template <> struct M<double> {
     static __device__ double l1p(double x) { return log1p(x); }
     static __device__ double sq(double x) { return sqrt(x); }
     static __device__ double sn(double x) { return sin(x); }
+    static __device__ double rcp(double x) { return 1.0 / x; }
 };
 
 template <typename T>
 struct TP {  // Tersoff constants in T
-    T A, B, l1, l2, beta, n, c2, d2, h, R, D, Rhi, pi_2D, pi_4D, inv2n;
+    T A, B, l1, l2, beta, n, c2, d2, h, R, D, Rhi, pi_2D, pi_4D, inv2n, c2d2;
     T AeR, BeR;        // A exp(-l1 R), B exp(-l2 R)
     T R2hi, R2lo;      // R^2 as a two-term sum
     T Dlo;             // D - (T)D
@@ -72,6 +75,7 @@ struct TP {  // Tersoff constants in T
         pi_2D = (T)(0.5 * 3.14159265358979323846 / p.D);
         pi_4D = (T)(0.25 * 3.14159265358979323846 / p.D);
         inv2n = (T)(0.5 / p.n);
+        c2d2 = (T)(p.c * p.c / (p.d * p.d));
         AeR = (T)(p.A * exp(-p.lambda1 * p.R));
         BeR = (T)(p.B * exp(-p.lambda2 * p.R));
         R2hi = (T)(p.R * p.R);
@@ -116,7 +120,7 @@ __device__ inline void dist_s(const TP<T> &q, T x, T y, T z, T xl, T yl, T zl, T
     // s2 - R^2 is exact when r^2 lies within a factor 2 of R^2
     const T d = add_rn(sub_rn(s2, q.R2hi), sub_rn(lo, q.R2lo));
     r = M<T>::sq(add_rn(s2, lo));
-    s = d / (r + q.R);
+    s = d * M<T>::rcp(r + q.R);
 }
 
 // cutoff function and derivative from s = r - R (see the header comment)
@@ -131,12 +135,14 @@ __device__ inline void cutoff(const TP<T> &q, T s, T &fc, T &dfc) {
     dfc = -q.pi_2D * sa * sb;
 }
 
+// g = 1 + (c^2/d^2) u^2 / (d^2 + u^2) and dg/dcos = -2 c^2 u / (d^2 + u^2)^2
+// with u = h - cos, from one reciprocal
 template <typename T>
 __device__ inline void gfun(const TP<T> &q, T cs, T &g, T &dg) {
-    T u = q.h - cs;
-    T den = q.d2 + u * u;
-    g = (T)1 + q.c2 * u * u / (q.d2 * den);
-    dg = -(T)2 * q.c2 * u / (den * den);
+    const T u = q.h - cs;
+    const T inv = M<T>::rcp(q.d2 + u * u);
+    g = (T)1 + q.c2d2 * u * u * inv;
+    dg = -(T)2 * q.c2 * u * inv * inv;
 }
 
 // list entries of an atom held in shared memory by the force kernel (atoms
@@ -147,7 +153,7 @@ template <> struct NShared<double> { static constexpr int value = 4; };
 
 // Per-thread neighbour records: field f of entry k at p[(f * cap + k) * stride]
 // (stride TILE in shared memory, 1 in a local array).
-enum { NB_RX, NB_RY, NB_RZ, NB_SR, NB_FC, NB_DFC, NB_PX, NB_PY, NB_PZ, NB_FIELDS };
+enum { NB_RX, NB_RY, NB_RZ, NB_SR, NB_IR, NB_FC, NB_DFC, NB_PX, NB_PY, NB_PZ, NB_FIELDS };
 template <typename T>
 struct Nbr {
     T *p;
@@ -270,19 +276,20 @@ __device__ inline void ters_site(const TP<T> &q, int cnt, const Nbr<T> &nb, T *n
         cutoff(q, nb(NB_SR, j), fc, dfc);
         nb(NB_FC, j) = fc;
         nb(NB_DFC, j) = dfc;
+        nb(NB_IR, j) = M<T>::rcp(q.R + nb(NB_SR, j));  // 1 / r
         nb(NB_PX, j) = nb(NB_PY, j) = nb(NB_PZ, j) = (T)0;
     }
     for (int j = 0; j < cnt; ++j) {
         const T fcj = nb(NB_FC, j), dfcj = nb(NB_DFC, j);
         if (fcj == (T)0 && dfcj == (T)0) continue;  // beyond R + D: no terms
         const T xj = nb(NB_RX, j), yj = nb(NB_RY, j), zj = nb(NB_RZ, j), sj_ = nb(NB_SR, j);
-        const T rj = q.R + sj_;
+        const T irj = nb(NB_IR, j);
         // zeta_ij and the bond order
         T zeta = 0;
         for (int k = 0; k < cnt; ++k) {
             if (k == j) continue;
-            const T rk = q.R + nb(NB_SR, k);
-            const T cs = (xj * nb(NB_RX, k) + yj * nb(NB_RY, k) + zj * nb(NB_RZ, k)) / (rj * rk);
+            const T cs = (xj * nb(NB_RX, k) + yj * nb(NB_RY, k) + zj * nb(NB_RZ, k)) * irj *
+                         nb(NB_IR, k);
             T g, dg;
             gfun(q, cs, g, dg);
             zeta += nb(NB_FC, k) * g;
@@ -297,25 +304,25 @@ __device__ inline void ters_site(const TP<T> &q, int cnt, const Nbr<T> &nb, T *n
         const T fa = -q.BeR * M<T>::ex(-q.l2 * sj_);
         const T dfr = -q.l1 * fr, dfa = -q.l2 * fa;
         U += (T)0.5 * fcj * (fr + bij * fa);
-        const T radial = (T)0.5 * (dfcj * (fr + bij * fa) + fcj * (dfr + bij * dfa)) / rj;
+        const T radial = (T)0.5 * (dfcj * (fr + bij * fa) + fcj * (dfr + bij * dfa)) * irj;
         T Pxj = radial * xj, Pyj = radial * yj, Pzj = radial * zj;
         const T pref = (T)0.5 * fcj * fa * dbij;
         if (pref != (T)0) {
             for (int k = 0; k < cnt; ++k) {
                 if (k == j) continue;
                 const T xk = nb(NB_RX, k), yk = nb(NB_RY, k), zk = nb(NB_RZ, k);
-                const T rk = q.R + nb(NB_SR, k);
-                const T ijk = (T)1 / (rj * rk);
+                const T irk = nb(NB_IR, k);
+                const T ijk = irj * irk;
                 const T cs = (xj * xk + yj * yk + zj * zk) * ijk;
                 T g, dg;
                 gfun(q, cs, g, dg);
                 // d cos / d r^ij and d cos / d r^ik
-                const T aj = cs / (rj * rj), ak = cs / (rk * rk);
+                const T aj = cs * irj * irj, ak = cs * irk * irk;
                 const T sj = pref * nb(NB_FC, k) * dg;
                 Pxj += sj * (xk * ijk - aj * xj);
                 Pyj += sj * (yk * ijk - aj * yj);
                 Pzj += sj * (zk * ijk - aj * zj);
-                const T rkk = pref * nb(NB_DFC, k) * g / rk;
+                const T rkk = pref * nb(NB_DFC, k) * g * irk;
                 nb(NB_PX, k) += rkk * xk + sj * (xj * ijk - ak * xk);
                 nb(NB_PY, k) += rkk * yk + sj * (yj * ijk - ak * yk);
                 nb(NB_PZ, k) += rkk * zk + sj * (zj * ijk - ak * zk);
