@@ -85,21 +85,25 @@ template <typename T>
 __global__ void __launch_bounds__(TILE) k_band_dots(const Tile *tiles, BandDev *bands) {
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
-    const int row = tl.t * TILE + threadIdx.x;
     T acc[5] = {0, 0, 0, 0, 0};
-    if (row < b.rows) {
-        const size_t stride = (size_t)b.rows * 3;
-        const T *x0 = (const T *)b.X + tl.img * stride + (size_t)row * 3;
-        const T *xm = x0 - stride, *xp = x0 + stride;
-        const T *f = (const T *)b.F + tl.img * stride + (size_t)row * 3;
-        for (int c = 0; c < 3; ++c) {
-            const T a = x0[c];
-            const T dp = xp[c] - a, dm = a - xm[c], fc = f[c];
-            acc[0] += dp * dp;
-            acc[1] += dm * dm;
-            acc[2] += dp * dm;
-            acc[3] += fc * dp;
-            acc[4] += fc * dm;
+    const size_t stride = (size_t)b.rows * 3;
+    const size_t o0 = tl.img * stride + ((size_t)tl.t * RTILE + threadIdx.x) * 3;
+    const T *__restrict__ X0 = (const T *)b.X + o0;
+    const T *__restrict__ F0 = (const T *)b.F + o0;
+    const int nrow = b.rows - tl.t * RTILE - (int)threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        if (k * TILE < nrow) {
+            const T *x0 = X0 + k * TILE * 3, *f = F0 + k * TILE * 3;
+            for (int c = 0; c < 3; ++c) {
+                const T a = x0[c];
+                const T dp = x0[stride + c] - a, dm = a - x0[c - (long long)stride], fc = f[c];
+                acc[0] += dp * dp;
+                acc[1] += dm * dm;
+                acc[2] += dp * dm;
+                acc[3] += fc * dp;
+                acc[4] += fc * dm;
+            }
         }
     }
     double tot[5];
@@ -182,31 +186,34 @@ template <typename T>
 __global__ void __launch_bounds__(TILE) k_neb_force(const Tile *tiles, BandDev *bands) {
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
-    const int row = tl.t * TILE + threadIdx.x;
-    T acc[4] = {0, 0, 0, 0};
-    if (row < b.rows) {
-        const ImgScalars &sc = b.sc[tl.img];
-        const T ca = (T)sc.coef[0], cb = (T)sc.coef[1];
-        const size_t stride = (size_t)b.rows * 3;
-        const size_t o = tl.img * stride + (size_t)row * 3;
-        const T *x0 = (const T *)b.X + o;
-        const T *xm = x0 - stride, *xp = x0 + stride;
-        const T *f = (const T *)b.F + o;
-        const T *v = (const T *)b.v + o;
-        T *fn = (T *)b.Fneb + o;
-        T fv = 0, ff = 0, vv = 0;
-        for (int c = 0; c < 3; ++c) {
-            const T a = x0[c];
-            const T g = f[c] + ca * (xp[c] - a) + cb * (a - xm[c]);
-            fn[c] = g;
-            fv += g * v[c];
-            ff += g * g;
-            vv += v[c] * v[c];
+    T acc[4] = {0, 0, 0, 0};  // F.v, F.F, v.v, largest row |F|^2 (fmax)
+    const ImgScalars &sc = b.sc[tl.img];
+    const T ca = (T)sc.coef[0], cb = (T)sc.coef[1];
+    const size_t stride = (size_t)b.rows * 3;
+    const size_t o0 = tl.img * stride + ((size_t)tl.t * RTILE + threadIdx.x) * 3;
+    const T *__restrict__ X0 = (const T *)b.X + o0;
+    const T *__restrict__ F0 = (const T *)b.F + o0;
+    const T *__restrict__ V0 = (const T *)b.v + o0;
+    T *__restrict__ G0 = (T *)b.Fneb + o0;
+    const int nrow = b.rows - tl.t * RTILE - (int)threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        if (k * TILE < nrow) {
+            const size_t q = (size_t)k * TILE * 3;
+            T ff = 0;
+            for (int c = 0; c < 3; ++c) {
+                const T a = X0[q + c];
+                const T g = F0[q + c] + ca * (X0[q + stride + c] - a) +
+                            cb * (a - X0[q + c - stride]);
+                const T vc = V0[q + c];
+                G0[q + c] = g;
+                acc[0] += g * vc;
+                ff += g * g;
+                acc[2] += vc * vc;
+            }
+            acc[1] += ff;
+            acc[3] = fmax(acc[3], ff);
         }
-        acc[0] = fv;
-        acc[1] = ff;
-        acc[2] = vv;
-        acc[3] = ff;  // row norm^2 for fmax
     }
     double tot[3];
     T three[3] = {acc[0], acc[1], acc[2]};
@@ -309,28 +316,40 @@ __global__ void __launch_bounds__(TILE) k_fire_update(const Tile *tiles, BandDev
     BandDev &b = bands[tl.band];
     const BandParams *bp = b.bp;
     if (!bp->move) return;
-    const int row = tl.t * TILE + threadIdx.x;
-    if (row >= b.rows) return;
-    const size_t o = (tl.img * (size_t)b.rows + row) * 3;
-    T *x = (T *)b.X + o;
-    T *v = (T *)b.v + o;
-    const T *f = (const T *)b.Fneb + o;
-    const T cv = (T)bp->cv, cf = (T)bp->cf, dt = (T)bp->dt;
-    T dx[3];
-    T n2 = 0;
-    for (int c = 0; c < 3; ++c) {
-        T vc = cv * v[c] + cf * f[c];
-        vc += dt * f[c];
-        v[c] = vc;
-        dx[c] = dt * vc;
-        n2 += dx[c] * dx[c];
+    const T cv = (T)bp->cv, cf = (T)bp->cf, dt = (T)bp->dt, ms = (T)bp->maxstep;
+    const size_t o0 = (tl.img * (size_t)b.rows + (size_t)tl.t * RTILE + threadIdx.x) * 3;
+    T *__restrict__ X = (T *)b.X + o0;
+    T *__restrict__ V = (T *)b.v + o0;
+    const T *__restrict__ Fn = (const T *)b.Fneb + o0;
+    const int nrow = b.rows - tl.t * RTILE - (int)threadIdx.x;  // rows k * TILE < nrow exist
+    // all loads first (rows of one thread are TILE apart: independent)
+    T xr[RPT][3], vr[RPT][3], fr[RPT][3];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k)
+        if (k * TILE < nrow)
+            for (int c = 0; c < 3; ++c) {
+                xr[k][c] = X[k * TILE * 3 + c];
+                vr[k][c] = V[k * TILE * 3 + c];
+                fr[k][c] = Fn[k * TILE * 3 + c];
+            }
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        if (k * TILE >= nrow) break;
+        T dx[3];
+        T n2 = 0;
+        for (int c = 0; c < 3; ++c) {
+            T vc = cv * vr[k][c] + cf * fr[k][c];
+            vc += dt * fr[k][c];
+            V[k * TILE * 3 + c] = vc;
+            dx[c] = dt * vc;
+            n2 += dx[c] * dx[c];
+        }
+        if (n2 > ms * ms) {
+            const T s = ms / sqrt(n2);
+            for (int c = 0; c < 3; ++c) dx[c] *= s;
+        }
+        for (int c = 0; c < 3; ++c) X[k * TILE * 3 + c] = xr[k][c] + dx[c];
     }
-    const T ms = (T)bp->maxstep;
-    if (n2 > ms * ms) {
-        const T s = ms / sqrt(n2);
-        for (int c = 0; c < 3; ++c) dx[c] *= s;
-    }
-    for (int c = 0; c < 3; ++c) x[c] += dx[c];
 }
 
 // X_img <- 1/2 (X_{img-1} + X_{img+1}) (image insertion; all rows)

@@ -9,8 +9,10 @@
 // ImgScalars[ncap]; per-band constants and FIRE state in BandParams.
 //
 // Kernels are launched over tile tables: each tile is (band, image, t) and
-// covers rows [t*TILE, (t+1)*TILE) of that image, so any mix of bands of
-// different sizes runs in one launch.  Partial sums of a tile land in a
+// covers atoms [t*TILE, (t+1)*TILE) (atom tiles, one thread per atom) or
+// rows [t*RTILE, (t+1)*RTILE) (row tiles of the band-vector kernels, RPT
+// rows per thread) of that image, so any mix of bands of different sizes
+// runs in one launch.  Partial sums of a tile land in a
 // fixed slot (image, t) of its band, and every reduction sums the slots of a
 // band in slot order: results do not depend on which other bands share the
 // launch.
@@ -21,6 +23,8 @@
 namespace cfneb {
 
 constexpr int TILE = 128;           // rows per tile = threads per block
+constexpr int RPT = 8;              // rows per thread of the row-tile kernels
+constexpr int RTILE = TILE * RPT;   // rows per row tile (band vector kernels)
 constexpr int MAXN_TERSOFF = 16;    // Tersoff list capacity per atom (entries within rl)
 constexpr int NPART = 12;           // doubles per tile partial record
 constexpr int MAX_STENCIL = 7;      // |delta| <= 7 bins per axis

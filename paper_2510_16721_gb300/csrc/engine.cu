@@ -720,7 +720,7 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
     int nb0 = bins_for(A->cell, cap_w), nb1 = bins_for(B->cell, cap_w);
     d.nbins_cap = (int)std::min<long long>((long long)(1.5 * std::max(nb0, nb1)) + 64, 1LL << 26);
     d.atpi = (n + TILE - 1) / TILE;
-    d.rtpi = (rows + TILE - 1) / TILE;
+    d.rtpi = (rows + RTILE - 1) / RTILE;
     const size_t nc = (size_t)b->ncap;
     const size_t vec = nc * rows * 3 * b->ts;
     d.X = dalloc(b, vec);

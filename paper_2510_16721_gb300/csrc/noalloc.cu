@@ -124,7 +124,7 @@ extern "C" int cfneb_lj_evaluate_noalloc(const double *d_positions, int32_t n_at
     dv.ncap = NA_IMAGES;
     dv.nbins_cap = NA_MAX_BINS;
     dv.atpi = (n + TILE - 1) / TILE;
-    dv.rtpi = (n + 3 + TILE - 1) / TILE;
+    dv.rtpi = (n + 3 + RTILE - 1) / RTILE;
     dv.X = base + O_X;
     dv.F = base + O_F;
     dv.Fneb = dv.F;  // not used by an evaluation
