@@ -69,12 +69,13 @@ __device__ void bin_geometry(const BandParams *bp, int nbins_cap, const double *
         for (int a = 0; a < 3; ++a) nb[a] = sc.nb[a];
     } else {
         // perpendicular widths w_a = Omega / |h_b x h_c| (only choose the bin
-        // grid: FP32, shaded down by 1e-5 so the stencil is never too narrow)
+        // grid: FP32, shaded down by 1e-4 so the stencil is never too narrow,
+        // also for atoms binned in FP32)
         for (int a = 0; a < 3; ++a) {
             const double *u = h + 3 * ((a + 1) % 3), *v = h + 3 * ((a + 2) % 3);
             const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2],
                          cz = u[0] * v[1] - u[1] * v[0];
-            w[a] = (float)omega / sqrtf((float)(cx * cx + cy * cy + cz * cz)) * 0.99999f;
+            w[a] = (float)omega / sqrtf((float)(cx * cx + cy * cy + cz * cz)) * 0.9999f;
         }
         for (int a = 0; a < 3; ++a) {
             const float q = floorf(w[a] / (float)bp->bin_w);
@@ -219,6 +220,13 @@ __global__ void __launch_bounds__(32) k_mapback(const ImgRef *imgs, int count, B
         sc.Dinv[lane] = Di;
         sc.h[lane] = h;
         sc.hinv[lane] = hinv;
+        // FP32 pairs of D and h and FP32 h0^-1 for the FP32 cell-list path
+        const float Dh = (float)D, hh = (float)h;
+        sc.dfl[lane] = Dh;
+        sc.dfl[9 + lane] = (float)(D - (double)Dh);
+        sc.dfl[18 + lane] = hh;
+        sc.dfl[27 + lane] = (float)(h - (double)hh);
+        sc.dfl[36 + lane] = (float)bp->h0inv[lane];
     }
     if (bp->skin <= 0.0) {
         // no skin: the cell list is rebuilt at every evaluation
@@ -306,6 +314,42 @@ __device__ inline void refresh_offset(const ImgScalars &sc, const BandParams *, 
     lo = make_float4(off[1][0], off[1][1], off[1][2], 0.0f);
 }
 
+// Bin and periodic wrap of an atom: s = R~ h0^-1 wrapped into [0, 1).  FP64
+// path in FP64; FP32 path in FP32 (a bin choice off by FP32 rounding near a
+// bin face puts the atom ~1e-7 of the cell outside its bin, inside the
+// 1e-4 margin the stencil widths are shaded by; the offset itself is exact).
+__device__ inline void bin_of(const ImgScalars &sc, const BandParams *bp, const double *X, int *bi,
+                              int *wrap) {
+    for (int a = 0; a < 3; ++a) {
+        double s = X[0] * bp->h0inv[a] + X[1] * bp->h0inv[3 + a] + X[2] * bp->h0inv[6 + a];
+        const double fl = floor(s);
+        s -= fl;
+        wrap[a] = (int)fl;
+        if (s >= 1.0) {
+            s = 0.0;
+            wrap[a] += 1;
+        }
+        const int q = (int)(s * sc.nb[a]);
+        bi[a] = q >= sc.nb[a] ? sc.nb[a] - 1 : q;
+    }
+}
+__device__ inline void bin_of(const ImgScalars &sc, const BandParams *, const float *X, int *bi,
+                              int *wrap) {
+    const float *hi = sc.dfl + 36;  // h0^-1 in FP32
+    for (int a = 0; a < 3; ++a) {
+        float s = X[0] * hi[a] + X[1] * hi[3 + a] + X[2] * hi[6 + a];
+        const float fl = floorf(s);
+        s -= fl;
+        wrap[a] = (int)fl;
+        if (s >= 1.0f) {
+            s = 0.0f;
+            wrap[a] += 1;
+        }
+        const int q = (int)(s * (float)sc.nb[a]);
+        bi[a] = q >= sc.nb[a] ? sc.nb[a] - 1 : (q < 0 ? 0 : q);
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(TILE) k_bin_assign(const Tile *tiles, BandDev *bands) {
     using T4 = typename Vec4<T>::type;
@@ -333,43 +377,17 @@ __global__ void __launch_bounds__(TILE) k_bin_assign(const Tile *tiles, BandDev 
     int i = tl.t * TILE + threadIdx.x;
     if (i >= b.n) return;
     const T *Xi = (const T *)b.X + ((size_t)tl.img * b.rows + i) * 3;
-    double rt[3] = {(double)Xi[0], (double)Xi[1], (double)Xi[2]};
-    double s[3];
     int bi[3], wrap[3];
-    for (int a = 0; a < 3; ++a) {
-        s[a] = rt[0] * bp->h0inv[a] + rt[1] * bp->h0inv[3 + a] + rt[2] * bp->h0inv[6 + a];
-        const double fl = floor(s[a]);
-        s[a] -= fl;
-        wrap[a] = (int)fl;
-        if (s[a] >= 1.0) {
-            s[a] = 0.0;
-            wrap[a] += 1;
-        }
-        int q = (int)(s[a] * sc.nb[a]);
-        bi[a] = q >= sc.nb[a] ? sc.nb[a] - 1 : q;
-    }
+    bin_of(sc, bp, Xi, bi, wrap);
     int lin = (bi[0] * sc.nb[1] + bi[1]) * sc.nb[2] + bi[2];
-    // offset from the bin centre: R (wrapped) - sum_a (b_a + 1/2) bv_a
-    double off[3];
-    for (int c = 0; c < 3; ++c) {
-        const double R = s[0] * sc.h[c] + s[1] * sc.h[3 + c] + s[2] * sc.h[6 + c];
-        const double ctr = (bi[0] + 0.5) * sc.bv[c] + (bi[1] + 0.5) * sc.bv[3 + c] +
-                           (bi[2] + 0.5) * sc.bv[6 + c];
-        off[c] = R - ctr;
-    }
     size_t ai = (size_t)tl.img * b.n + i;
     int rank = atomicAdd(&b.bin_count[(size_t)tl.img * b.nbins_cap + lin], 1);
     b.atom_bin[ai] = lin;
     b.atom_rank[ai] = rank;
+    // offset from the bin centre (the w lane holds the innermost bin index,
+    // for the row traversal of the LJ kernel)
     T4 o, lo;
-    o.x = (T)off[0];
-    o.y = (T)off[1];
-    o.z = (T)off[2];
-    o.w = (T)bi[2];  // bin index along the innermost axis (row traversal)
-    lo.x = (T)(off[0] - (double)o.x);
-    lo.y = (T)(off[1] - (double)o.y);
-    lo.z = (T)(off[2] - (double)o.z);
-    lo.w = (T)0;
+    refresh_offset(sc, bp, Xi, wrap, bi, o, lo);
     ((T4 *)b.atom_off)[ai] = o;
     ((T4 *)b.atom_off_lo)[ai] = lo;
     if (bp->skin > 0.0) {  // reference state of the build
@@ -488,13 +506,6 @@ __global__ void k_skin_decide(const ImgRef *imgs, BandDev *bands, int force) {
             sc.builds += 1;
         } else {
             bin_geometry(bp, b.nbins_cap, sc.h, sc.omega, true, sc);
-        }
-        for (int k = 0; k < 9; ++k) {
-            const float dh_ = (float)sc.D[k], hh_ = (float)sc.h[k];
-            sc.dfl[k] = dh_;
-            sc.dfl[9 + k] = (float)(sc.D[k] - (double)dh_);
-            sc.dfl[18 + k] = hh_;
-            sc.dfl[27 + k] = (float)(sc.h[k] - (double)hh_);
         }
         sc.rebuild = rebuild ? 1 : 0;
         sc.dmax = d;

@@ -56,7 +56,7 @@ struct ImgScalars {
     double dmax;         // largest |R~ - R~ at the build| of this evaluation
     long long builds;    // cell-list builds of this image slot
     long long evals;     // evaluations of this image slot
-    float dfl[36];       // D and h as FP32 pairs: D hi, D lo, h hi, h lo (refresh)
+    float dfl[45];       // FP32: D hi, D lo, h hi, h lo (pairs), h0^-1 (cell list)
     int nb[3];           // bins per axis
     int m[3];            // stencil half width per axis
     int nbins;
