@@ -18,6 +18,8 @@
 // launch.
 #pragma once
 #include <cuda_runtime.h>
+
+#include <cmath>
 #include <stdint.h>
 
 namespace cfneb {
@@ -63,6 +65,35 @@ struct ImgScalars {
     int rebuild;         // this evaluation rebuilds the cell list
 };
 
+struct TersoffParams {
+    double A, B, lambda1, lambda2, beta, n, c, d, h, R, D;
+};
+
+template <typename T>
+struct __align__(8) TP {  // Tersoff constants in T (derived once per band, on the host)
+    T A, B, l1, l2, beta, n, c2, d2, h, R, D, Rhi, pi_2D, pi_4D, inv2n, c2d2;
+    T AeR, BeR;        // A exp(-l1 R), B exp(-l2 R)
+    T R2hi, R2lo;      // R^2 as a two-term sum
+    T Dlo;             // D - (T)D
+    T pad_;            // (a whole number of 8-byte words: staged by word copies)
+    // host only (std::exp of the host library): the device reads the result
+    __host__ void load(const TersoffParams &p) {
+        A = (T)p.A; B = (T)p.B; l1 = (T)p.lambda1; l2 = (T)p.lambda2; beta = (T)p.beta;
+        n = (T)p.n; c2 = (T)(p.c * p.c); d2 = (T)(p.d * p.d); h = (T)p.h; R = (T)p.R;
+        D = (T)p.D; Rhi = (T)(p.R + p.D);
+        pi_2D = (T)(0.5 * 3.14159265358979323846 / p.D);
+        pi_4D = (T)(0.25 * 3.14159265358979323846 / p.D);
+        inv2n = (T)(0.5 / p.n);
+        c2d2 = (T)(p.c * p.c / (p.d * p.d));
+        AeR = (T)(p.A * std::exp(-p.lambda1 * p.R));
+        BeR = (T)(p.B * std::exp(-p.lambda2 * p.R));
+        R2hi = (T)(p.R * p.R);
+        R2lo = (T)(p.R * p.R - (double)R2hi);
+        Dlo = (T)(p.D - (double)D);
+    }
+};
+
+
 struct BandParams {
     // constants of the band
     double h0[9], h0inv[9];
@@ -94,7 +125,17 @@ struct BandParams {
     int status;
     int stale;           // every image rebuilds at the next evaluation
     int tune_rebuild;    // rebuild at every evaluation (autotuning)
+    TP<float> tpf;       // Tersoff constants in FP32 / FP64 (Tersoff bands)
+    TP<double> tpd;
 };
+
+template <typename T> __host__ __device__ inline const TP<T> &tp_of(const BandParams &p);
+template <> __host__ __device__ inline const TP<float> &tp_of<float>(const BandParams &p) {
+    return p.tpf;
+}
+template <> __host__ __device__ inline const TP<double> &tp_of<double>(const BandParams &p) {
+    return p.tpd;
+}
 
 struct BandDev {
     int n, rows, ncap, nbins_cap;
@@ -118,6 +159,7 @@ struct BandDev {
     int *nbr_cnt;        // [ncap][n]
     int *nbr_slot;       // [ncap][MAXN][n]
     int *nbr_code;       // [ncap][MAXN][n]
+    unsigned char *nbr_rev;  // [ncap][MAXN][n]: entry of j's list pointing back (255: none)
     void *nbr_P;         // [ncap][3*MAXN][n] of T
     // partial sums
     double *atom_part;   // [ncap][atpi][NPART]
@@ -138,9 +180,6 @@ struct LJParams {
     double eps, sigma, rc, ephi_c;   // ephi_c = phi(rc) if shifted, else 0
 };
 
-struct TersoffParams {
-    double A, B, lambda1, lambda2, beta, n, c, d, h, R, D;
-};
 
 // ---- small helpers ------------------------------------------------------
 
@@ -309,6 +348,7 @@ constexpr int RED_THREADS = 256;
 template <typename S>
 __device__ inline void stage_copy(S *dst, const S *src) {
     static_assert(sizeof(S) % 8 == 0, "record size must be a multiple of 8 bytes");
+    static_assert(alignof(S) >= 8, "record must be 8-byte aligned for word copies");
     const unsigned long long *s = (const unsigned long long *)src;
     unsigned long long *d = (unsigned long long *)dst;
     for (int k = threadIdx.x; k < (int)(sizeof(S) / 8); k += blockDim.x) d[k] = s[k];
@@ -335,6 +375,8 @@ template <typename T>
 void launch_lj(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 template <typename T>
 void launch_tersoff_list(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
+template <typename T>
+void launch_tersoff_reverse(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 template <typename T>
 void launch_tersoff_partials(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 template <typename T>

@@ -48,12 +48,12 @@ struct CudaFail {
 
 enum KernelId {
     K_MAPBACK, K_SKIN_CHECK, K_SKIN_DECIDE, K_BIN_ASSIGN, K_BIN_TILESUM, K_BIN_TILESCAN, K_BIN_SCANFILL, K_BIN_SCATTER,
-    K_BIN_ORDER, K_LJ, K_TERS_LIST, K_TERS_PARTIALS, K_TERS_GATHER, K_IMAGE_FINALIZE,
+    K_BIN_ORDER, K_LJ, K_TERS_LIST, K_TERS_REVERSE, K_TERS_PARTIALS, K_TERS_GATHER, K_IMAGE_FINALIZE,
     K_BAND_DOTS, K_DOTS_REDUCE, K_NEB_COEF, K_NEB_FORCE, K_FIRE_SCALARS, K_FIRE_UPDATE, K_COUNT
 };
 const char *kKernelNames[K_COUNT] = {
     "mapback", "skin_check", "skin_decide", "bin_assign", "bin_tilesum", "bin_tilescan", "bin_scanfill", "bin_scatter",
-    "bin_order", "lj_force", "tersoff_list", "tersoff_partials", "tersoff_gather",
+    "bin_order", "lj_force", "tersoff_list", "tersoff_reverse", "tersoff_partials", "tersoff_gather",
     "image_finalize", "band_dots", "dots_reduce", "neb_coef", "neb_force", "fire_scalars",
     "fire_update"};
 
@@ -273,6 +273,8 @@ void enqueue_eval_set(const LaunchSet &ls, Launcher &L, bool forces = true) {
     if (ls.n_ters) {
         L.pre(K_TERS_LIST); launch_tersoff_list<T>(ls.atiles_ters, ls.n_ters, d, s);
         L.post(K_TERS_LIST);
+        L.pre(K_TERS_REVERSE); launch_tersoff_reverse<T>(ls.atiles_ters, ls.n_ters, d, s);
+        L.post(K_TERS_REVERSE);
     }
     if (!forces) {
         launch_energy64<T>(ls.atiles, ls.n_atiles, ls.imgs, ls.nimg, d, s);
@@ -305,7 +307,7 @@ void enqueue_step_set(const LaunchSet &ls, Launcher &L) {
 }
 
 int launches_in_set(const LaunchSet &ls) {
-    return 9 + (ls.n_lj ? 1 : 0) + (ls.n_ters ? 3 : 0) + 1 + 6;
+    return 9 + (ls.n_lj ? 1 : 0) + (ls.n_ters ? 4 : 0) + 1 + 6;
 }
 
 LaunchSet band_set(cfneb_band *b, const ImgRef *imgs, int nimg, const Tile *atiles, int nat) {
@@ -693,6 +695,12 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
         for (int k = 0; k < 11; ++k) zero = zero && pot->tersoff[k] == 0.0;
         for (int k = 0; k < 11; ++k) P.pot[k] = zero ? kTersoff1988C[k] : pot->tersoff[k];
         rc = P.pot[9] + P.pot[10];
+        // a copy, not a cast of pot[] (type-based aliasing lets the host
+        // compiler read the cast view before the stores above)
+        TersoffParams tp;
+        std::memcpy(&tp, P.pot, sizeof(tp));
+        P.tpf.load(tp);
+        P.tpd.load(tp);
     }
     // neighbour-list skin: the caller's, or 0.15 A for Tersoff (carbon's
     // second neighbours, 2.46-2.52 A, stay outside R + D + skin, so the lists
@@ -753,6 +761,7 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
         d.nbr_cnt = (int *)dalloc(b, na * sizeof(int));
         d.nbr_slot = (int *)dalloc(b, na * MAXN_TERSOFF * sizeof(int));
         d.nbr_code = (int *)dalloc(b, na * MAXN_TERSOFF * sizeof(int));
+        d.nbr_rev = (unsigned char *)dalloc(b, na * MAXN_TERSOFF);
         d.nbr_P = dalloc(b, na * 3 * MAXN_TERSOFF * b->ts);
     }
     d.atom_part = (double *)dalloc(b, nc * d.atpi * NPART * sizeof(double));

@@ -62,28 +62,6 @@ template <> struct M<double> {
     static __device__ double rcp(double x) { return 1.0 / x; }
 };
 
-template <typename T>
-struct TP {  // Tersoff constants in T
-    T A, B, l1, l2, beta, n, c2, d2, h, R, D, Rhi, pi_2D, pi_4D, inv2n, c2d2;
-    T AeR, BeR;        // A exp(-l1 R), B exp(-l2 R)
-    T R2hi, R2lo;      // R^2 as a two-term sum
-    T Dlo;             // D - (T)D
-    __device__ void load(const TersoffParams &p) {
-        A = (T)p.A; B = (T)p.B; l1 = (T)p.lambda1; l2 = (T)p.lambda2; beta = (T)p.beta;
-        n = (T)p.n; c2 = (T)(p.c * p.c); d2 = (T)(p.d * p.d); h = (T)p.h; R = (T)p.R;
-        D = (T)p.D; Rhi = (T)(p.R + p.D);
-        pi_2D = (T)(0.5 * 3.14159265358979323846 / p.D);
-        pi_4D = (T)(0.25 * 3.14159265358979323846 / p.D);
-        inv2n = (T)(0.5 / p.n);
-        c2d2 = (T)(p.c * p.c / (p.d * p.d));
-        AeR = (T)(p.A * exp(-p.lambda1 * p.R));
-        BeR = (T)(p.B * exp(-p.lambda2 * p.R));
-        R2hi = (T)(p.R * p.R);
-        R2lo = (T)(p.R * p.R - (double)R2hi);
-        Dlo = (T)(p.D - (double)D);
-    }
-};
-
 __device__ inline float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ inline double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ inline float add_rn(float a, float b) { return __fadd_rn(a, b); }
@@ -418,14 +396,14 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 8 : 1) k_ters_partials(
     const ImgScalars &sc = b.sc[tl.img];
     __shared__ T s_bv[9], s_dh[9];
     __shared__ int s_nb[3];
-    __shared__ TP<T> s_q;
+    __shared__ TP<T> s_q;  // per-band constants, staged by the whole block
     __shared__ T s_rec[NB_FIELDS * NS * TILE];
     if (threadIdx.x < 9) {
         s_bv[threadIdx.x] = (T)sc.bv[threadIdx.x];
         s_dh[threadIdx.x] = (T)sc.dh[threadIdx.x];
     }
     if (threadIdx.x < 3) s_nb[threadIdx.x] = sc.nb[threadIdx.x];
-    if (threadIdx.x == 0) s_q.load(*(const TersoffParams *)b.bp->pot);
+    stage_copy(&s_q, &tp_of<T>(*b.bp));
     __syncthreads();
     const TP<T> &q = s_q;
     const int n = b.n;
@@ -463,6 +441,36 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 8 : 1) k_ters_partials(
     }
 }
 
+// Reverse entries of a rebuilt list: for entry k of slot t (neighbour slot
+// qs, stencil code c), the entry of qs's list that points back to t under
+// -c, so that the force gather needs no search.
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_ters_reverse(const Tile *tiles, BandDev *bands) {
+    Tile tl = tiles[blockIdx.x];
+    BandDev &b = bands[tl.band];
+    if (!b.sc[tl.img].rebuild) return;
+    const int n = b.n;
+    const int t = tl.t * TILE + threadIdx.x;
+    if (t >= n) return;
+    const size_t base = (size_t)tl.img * n;
+    const int *nslot = b.nbr_slot + (size_t)tl.img * MAXN_TERSOFF * n;
+    const int *ncode = b.nbr_code + (size_t)tl.img * MAXN_TERSOFF * n;
+    unsigned char *nrev = b.nbr_rev + (size_t)tl.img * MAXN_TERSOFF * n;
+    const int cnt = b.nbr_cnt[base + t];
+    for (int k = 0; k < cnt; ++k) {
+        const int qs = nslot[(size_t)k * n + t];
+        const int back = neg_code(ncode[(size_t)k * n + t]);
+        const int cq = b.nbr_cnt[base + qs];
+        int r = 255;
+        for (int k2 = 0; k2 < cq; ++k2)
+            if (nslot[(size_t)k2 * n + qs] == t && ncode[(size_t)k2 * n + qs] == back) {
+                r = k2;
+                break;
+            }
+        nrev[(size_t)k * n + t] = (unsigned char)r;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(TILE) k_ters_gather(const Tile *tiles, BandDev *bands) {
     Tile tl = tiles[blockIdx.x];
@@ -473,25 +481,20 @@ __global__ void __launch_bounds__(TILE) k_ters_gather(const Tile *tiles, BandDev
     const ImgScalars &sc = b.sc[tl.img];
     const size_t base = (size_t)tl.img * n;
     const int *nslot = b.nbr_slot + (size_t)tl.img * MAXN_TERSOFF * n;
-    const int *ncode = b.nbr_code + (size_t)tl.img * MAXN_TERSOFF * n;
-    const int *ncnt = b.nbr_cnt + base;
+    const unsigned char *nrev = b.nbr_rev + (size_t)tl.img * MAXN_TERSOFF * n;
     const T *nP = (const T *)b.nbr_P + (size_t)tl.img * 3 * MAXN_TERSOFF * n;
     T fx = 0, fy = 0, fz = 0;
-    const int cnt = ncnt[t];
+    const int cnt = b.nbr_cnt[base + t];
     for (int k = 0; k < cnt; ++k) {
         fx += nP[(size_t)(3 * k + 0) * n + t];
         fy += nP[(size_t)(3 * k + 1) * n + t];
         fz += nP[(size_t)(3 * k + 2) * n + t];
         const int qs = nslot[(size_t)k * n + t];
-        const int back = neg_code(ncode[(size_t)k * n + t]);
-        const int cq = ncnt[qs];
-        for (int k2 = 0; k2 < cq; ++k2) {
-            if (nslot[(size_t)k2 * n + qs] == t && ncode[(size_t)k2 * n + qs] == back) {
-                fx -= nP[(size_t)(3 * k2 + 0) * n + qs];
-                fy -= nP[(size_t)(3 * k2 + 1) * n + qs];
-                fz -= nP[(size_t)(3 * k2 + 2) * n + qs];
-                break;
-            }
+        const int k2 = nrev[(size_t)k * n + t];
+        if (k2 != 255) {  // f^ij = P_ij - P_ji
+            fx -= nP[(size_t)(3 * k2 + 0) * n + qs];
+            fy -= nP[(size_t)(3 * k2 + 1) * n + qs];
+            fz -= nP[(size_t)(3 * k2 + 2) * n + qs];
         }
     }
     const T g0 = fx * (T)sc.D[0] + fy * (T)sc.D[1] + fz * (T)sc.D[2];
@@ -510,6 +513,11 @@ void launch_tersoff_list(const Tile *tiles, int ntiles, BandDev *bands, cudaStre
     k_ters_list<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
 }
 template <typename T>
+void launch_tersoff_reverse(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    k_ters_reverse<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
+}
+template <typename T>
 void launch_tersoff_partials(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
     if (ntiles <= 0) return;
     k_ters_partials<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
@@ -521,6 +529,8 @@ void launch_tersoff_gather(const Tile *tiles, int ntiles, BandDev *bands, cudaSt
 }
 template void launch_tersoff_list<float>(const Tile *, int, BandDev *, cudaStream_t);
 template void launch_tersoff_list<double>(const Tile *, int, BandDev *, cudaStream_t);
+template void launch_tersoff_reverse<float>(const Tile *, int, BandDev *, cudaStream_t);
+template void launch_tersoff_reverse<double>(const Tile *, int, BandDev *, cudaStream_t);
 template void launch_tersoff_partials<float>(const Tile *, int, BandDev *, cudaStream_t);
 template void launch_tersoff_partials<double>(const Tile *, int, BandDev *, cudaStream_t);
 template void launch_tersoff_gather<float>(const Tile *, int, BandDev *, cudaStream_t);
