@@ -166,9 +166,13 @@ def time_steps(torch, band, stream, k, dist=None):
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
+    # NVTX range "cfneb_timed": lets a profiler select the timed launches
+    # (ncu --nvtx --nvtx-include cfneb_timed/); no effect otherwise
+    torch.cuda.nvtx.range_push("cfneb_timed")
     start.record(stream)
     band.step(k)
     end.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
