@@ -340,3 +340,46 @@ def test_large_tersoff_band_runs(g):
     assert np.all(np.isfinite(p["energies"]))
     assert np.isfinite(p["fmax"]) and p["fmax"] > 0
     assert abs(p["energies"][0] / len(R0) - (-7.3955)) < 1e-3
+
+
+# ---------------------------------------------------------------------------
+# deformation-gradient filter variant and external pressure (Sec. II.C; the
+# enthalpy H = U + P Omega of the 40 GPa example)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("variant,pressure", [(1, 0.0), (0, 0.05), (1, 0.05)])
+def test_lj_filter_variant_and_pressure_fp64(g, oracle_mod, variant, pressure):
+    """Strained vacancy hop with the cell filter on: the deformation-gradient
+    coordinate D and/or an external pressure (eps/sigma^3), 8 FP64 steps
+    against the oracle, energies (H) and virials included."""
+    R0, h0, R1, h1 = lj_band_case(strain_seed=3)
+    kw = dict(k=1.0, dt=0.01, cell_filter=True, variant=variant, pressure=pressure)
+    gb = gpu_band(g, R0, h0, R1, h1, 7, g.lj_potential(), **kw)
+    ob = oracle_band(oracle_mod, oracle_mod.LJ(), R0, h0, R1, h1, 7, **kw)
+    gb.step(8)
+    ob.step(8)
+    st = gb.get_state()
+    _compare_state(st, ob, 1e-9)
+    for i in range(1, 6):
+        assert _rel(st["virials"][i], ob.info[i]["V"]) <= 1e-10
+    E = gb.get_path()["energies"]
+    ob.compute()
+    for i in range(1, 6):
+        assert abs(E[i] - ob.E[i]) <= 1e-10 * max(1.0, abs(ob.E[i])), i
+
+
+def test_tersoff_filter_variant_and_pressure_fp64(g, oracle_mod):
+    """Graphite -> hexagonal diamond with D as the lattice coordinate and a
+    pressure of 0.25 eV/A^3 (40 GPa), 5 FP64 steps against the oracle."""
+    cfg = ci.tersoff_graphite_hexdiamond()
+    R0, h0, R1, h1 = cfg["endpoints"]
+    kw = dict(k=0.1, dt=0.1, cell_filter=True, variant=1, pressure=0.25)
+    gb = gpu_band(g, R0, h0, R1, h1, 9, g.tersoff_potential(), noise=cfg["noise"], **kw)
+    ob = oracle_band(oracle_mod, oracle_mod.Tersoff(), R0, h0, R1, h1, 9, noise=cfg["noise"],
+                     **kw)
+    gb.step(5)
+    ob.step(5)
+    st = gb.get_state()
+    _compare_state(st, ob, 1e-9)
+    for i in range(1, 8):
+        assert _rel(st["virials"][i], ob.info[i]["V"]) <= 1e-10
