@@ -101,6 +101,23 @@ __device__ inline void dist_s(const TP<T> &q, T x, T y, T z, T xl, T yl, T zl, T
     s = d * M<T>::rcp(r + q.R);
 }
 
+// sin a for a in [0, pi/2], the cutoff's only arguments.  FP32: the Taylor
+// series to the a^13 term in nested form, sin a = a (1 - a^2/(2.3) (1 -
+// a^2/(4.5) (1 - ...))) (truncation below 7e-10 relative at pi/2, rounding a
+// few ulp, full relative accuracy as a -> 0); a handful of FMAs instead of
+// a general-range sine.  FP64: the library sine.
+__device__ inline float sin_quarter(float a) {
+    const float a2 = a * a;
+    float p = 1.0f - a2 * (1.0f / 156.0f);
+    p = 1.0f - a2 * (1.0f / 110.0f) * p;
+    p = 1.0f - a2 * (1.0f / 72.0f) * p;
+    p = 1.0f - a2 * (1.0f / 42.0f) * p;
+    p = 1.0f - a2 * (1.0f / 20.0f) * p;
+    p = 1.0f - a2 * (1.0f / 6.0f) * p;
+    return a * p;
+}
+__device__ inline double sin_quarter(double a) { return sin(a); }
+
 // cutoff function and derivative from s = r - R (see the header comment)
 template <typename T>
 __device__ inline void cutoff(const TP<T> &q, T s, T &fc, T &dfc) {
@@ -108,7 +125,7 @@ __device__ inline void cutoff(const TP<T> &q, T s, T &fc, T &dfc) {
     const T v = add_rn(q.D, s) + q.Dlo;  // D + s
     if (v <= (T)0) { fc = (T)1; dfc = (T)0; return; }
     if (u <= (T)0) { fc = (T)0; dfc = (T)0; return; }
-    const T sa = M<T>::sn(q.pi_4D * u), sb = M<T>::sn(q.pi_4D * v);
+    const T sa = sin_quarter(q.pi_4D * u), sb = sin_quarter(q.pi_4D * v);
     fc = sa * sa;
     dfc = -q.pi_2D * sa * sb;
 }
@@ -389,7 +406,7 @@ __device__ inline void ters_load(const TP<T> &q, const BandDev &b, int img, int 
 // so that the threads of a warp hit distinct banks; an atom with more list
 // entries than the shared slots keeps them in local memory.
 template <typename T>
-__global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 8 : 1) k_ters_partials(const Tile *tiles, BandDev *bands) {
+__global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 7 : 1) k_ters_partials(const Tile *tiles, BandDev *bands) {
     constexpr int NS = NShared<T>::value;
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
@@ -485,16 +502,37 @@ __global__ void __launch_bounds__(TILE) k_ters_gather(const Tile *tiles, BandDev
     const T *nP = (const T *)b.nbr_P + (size_t)tl.img * 3 * MAXN_TERSOFF * n;
     T fx = 0, fy = 0, fz = 0;
     const int cnt = b.nbr_cnt[base + t];
-    for (int k = 0; k < cnt; ++k) {
+    // f^ij = P_ij - P_ji, in list order; the first GK entries with every
+    // index loaded before the partials they point to
+    constexpr int GK = 6;
+    int qs[GK], k2[GK];
+#pragma unroll
+    for (int k = 0; k < GK; ++k) {
+        qs[k] = k < cnt ? nslot[(size_t)k * n + t] : 0;
+        k2[k] = k < cnt ? nrev[(size_t)k * n + t] : 255;
+    }
+#pragma unroll
+    for (int k = 0; k < GK; ++k) {
+        if (k >= cnt) break;
         fx += nP[(size_t)(3 * k + 0) * n + t];
         fy += nP[(size_t)(3 * k + 1) * n + t];
         fz += nP[(size_t)(3 * k + 2) * n + t];
-        const int qs = nslot[(size_t)k * n + t];
-        const int k2 = nrev[(size_t)k * n + t];
-        if (k2 != 255) {  // f^ij = P_ij - P_ji
-            fx -= nP[(size_t)(3 * k2 + 0) * n + qs];
-            fy -= nP[(size_t)(3 * k2 + 1) * n + qs];
-            fz -= nP[(size_t)(3 * k2 + 2) * n + qs];
+        if (k2[k] != 255) {
+            fx -= nP[(size_t)(3 * k2[k] + 0) * n + qs[k]];
+            fy -= nP[(size_t)(3 * k2[k] + 1) * n + qs[k]];
+            fz -= nP[(size_t)(3 * k2[k] + 2) * n + qs[k]];
+        }
+    }
+    for (int k = GK; k < cnt; ++k) {
+        fx += nP[(size_t)(3 * k + 0) * n + t];
+        fy += nP[(size_t)(3 * k + 1) * n + t];
+        fz += nP[(size_t)(3 * k + 2) * n + t];
+        const int q = nslot[(size_t)k * n + t];
+        const int r = nrev[(size_t)k * n + t];
+        if (r != 255) {
+            fx -= nP[(size_t)(3 * r + 0) * n + q];
+            fy -= nP[(size_t)(3 * r + 1) * n + q];
+            fz -= nP[(size_t)(3 * r + 2) * n + q];
         }
     }
     const T g0 = fx * (T)sc.D[0] + fy * (T)sc.D[1] + fz * (T)sc.D[2];
