@@ -117,6 +117,78 @@ __device__ void bin_geometry(const BandParams *bp, int nbins_cap, const double *
     sc.nbins = nb[0] * nb[1] * nb[2];
 }
 
+// upper bound of the spectral norm of a 3x3 matrix: the smaller of the
+// Frobenius norm and sqrt(|A|_1 |A|_inf), in FP32 and raised by 1e-6 to
+// stay a bound
+__device__ inline float norm2_bound(const float *A) {
+    float f = 0.0f, c1 = 0.0f, ci = 0.0f;
+    for (int i = 0; i < 3; ++i) {
+        float rs = 0.0f, cs = 0.0f;
+        for (int j = 0; j < 3; ++j) {
+            f += A[3 * i + j] * A[3 * i + j];
+            rs += fabsf(A[3 * i + j]);
+            cs += fabsf(A[3 * j + i]);
+        }
+        ci = fmaxf(ci, rs);
+        c1 = fmaxf(c1, cs);
+    }
+    return fminf(sqrtf(f), sqrtf(c1 * ci)) * 1.000001f;
+}
+
+// FP32 inverse of a 3x3 matrix (cofactors over the determinant)
+__device__ inline void inv3f(const float *m, float *o) {
+    const float c00 = m[4] * m[8] - m[5] * m[7], c01 = m[5] * m[6] - m[3] * m[8],
+                c02 = m[3] * m[7] - m[4] * m[6];
+    const float id = 1.0f / (m[0] * c00 + m[1] * c01 + m[2] * c02);
+    o[0] = c00 * id;
+    o[1] = (m[2] * m[7] - m[1] * m[8]) * id;
+    o[2] = (m[1] * m[5] - m[2] * m[4]) * id;
+    o[3] = c01 * id;
+    o[4] = (m[0] * m[8] - m[2] * m[6]) * id;
+    o[5] = (m[2] * m[3] - m[0] * m[5]) * id;
+    o[6] = c02 * id;
+    o[7] = (m[1] * m[6] - m[0] * m[7]) * id;
+    o[8] = (m[0] * m[4] - m[1] * m[3]) * id;
+}
+
+// The rebuild decision of one image on its staged record sc (one thread):
+// keep the bins of the build while the bound in the header comment holds,
+// else rebuild (always when forced, when the band's images were rearranged,
+// or while autotuning).  d = the largest displacement since the build.
+__device__ void skin_decide_one(const BandParams *bp, int nbins_cap, ImgScalars &sc, double d,
+                                int force) {
+    bool rebuild = force || bp->stale || bp->tune_rebuild || sc.builds == 0;
+    if (!rebuild) {
+        // in FP32: M - I = D_b^-1 D - I is small, so its FP32 rounding (~1e-7
+        // absolute) moves the bound by far less than the 1e-5 margins, which
+        // also cover the FP32 list test and displacement
+        float Db[9], D[9], Dbi[9], M[9];
+        for (int k = 0; k < 9; ++k) {
+            Db[k] = (float)sc.Db[k];
+            D[k] = (float)sc.D[k];
+        }
+        inv3f(Db, Dbi);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                M[3 * i + j] = Dbi[3 * i] * D[j] + Dbi[3 * i + 1] * D[3 + j] +
+                               Dbi[3 * i + 2] * D[6 + j] - (i == j ? 1.0f : 0.0f);
+        const float e = norm2_bound(M) * 1.00001f + 1e-6f;
+        const double bound = bp->rl * (1.0 - 1e-5) * (1.0 - (double)e) -
+                             2.0 * d * (double)norm2_bound(D) * (1.0 + 1e-5);
+        rebuild = !(bound > bp->rc);
+    }
+    if (rebuild) {
+        bin_geometry(bp, nbins_cap, sc.h, sc.omega, false, sc);
+        for (int k = 0; k < 9; ++k) sc.Db[k] = sc.D[k];
+        sc.builds += 1;
+    } else {
+        bin_geometry(bp, nbins_cap, sc.h, sc.omega, true, sc);
+    }
+    sc.rebuild = rebuild ? 1 : 0;
+    sc.dmax = d;
+    sc.evals += 1;
+}
+
 // ---- lane-parallel 3x3 algebra for the map-back -------------------------
 //
 // One warp per image: lane l holds entry (i, j) = (l / 3, l % 3) of each
@@ -151,17 +223,24 @@ __device__ inline double ldet(double a, double c) {
 }
 
 // Map-back of one image per warp: B = X_lat / c, D = B^(1/2) (rotation-free,
-// coupled Newton-Schulz as in sym_sqrt3) or D = X_lat / c (deformation
-// gradient), then h = h0 D, h^-1 = D^-1 h0^-1 and Omega = |det h|.
+// coupled Newton-Schulz as in the header comment) or D = X_lat / c
+// (deformation gradient), then h = h0 D, h^-1 = D^-1 h0^-1 and
+// Omega = |det h|; then the image's cell-list decision: with no skin a
+// rebuild on the new cell, with a skin the reuse test on the displacements
+// k_skin_check left per tile.  The image record is staged in shared memory,
+// updated and written back whole.
 template <typename T>
-__global__ void __launch_bounds__(32) k_mapback(const ImgRef *imgs, int count, BandDev *bands) {
+__global__ void __launch_bounds__(32) k_mapback(const ImgRef *imgs, int count, BandDev *bands,
+                                                int force) {
     const ImgRef r = imgs[blockIdx.x];
     BandDev &b = bands[r.band];
     __shared__ BandParams s_bp;
+    __shared__ ImgScalars s_sc;
     stage_copy(&s_bp, b.bp);
+    stage_copy(&s_sc, &b.sc[r.img]);
     __syncwarp();
     const BandParams *bp = &s_bp;
-    ImgScalars &sc = b.sc[r.img];
+    ImgScalars &sc = s_sc;
     const Lane3 p;
     const int lane = threadIdx.x & 31;
     const T *Xl = (const T *)b.X + ((size_t)r.img * b.rows + b.n) * 3;
@@ -215,6 +294,13 @@ __global__ void __launch_bounds__(32) k_mapback(const ImgRef *imgs, int count, B
     const double h = lmul(bp->h0[p.l], D, p);
     const double hinv = lmul(Di, bp->h0inv[p.l], p);  // (h0 D)^-1 = D^-1 h0^-1
     const double omega = fabs(ldet(h, lcof(h, p)));
+    // largest displacement since the last build (skin > 0)
+    double dmax = 0.0;
+    if (bp->skin > 0.0) {
+        const double *part = b.skin_part + (size_t)r.img * b.atpi;
+        for (int t = lane; t < b.atpi; t += 32) dmax = fmax(dmax, part[t]);
+        dmax = warp_max(dmax);
+    }
     if (lane < 9) {
         sc.D[lane] = D;
         sc.Dinv[lane] = Di;
@@ -228,27 +314,28 @@ __global__ void __launch_bounds__(32) k_mapback(const ImgRef *imgs, int count, B
         sc.dfl[27 + lane] = (float)(h - (double)hh);
         sc.dfl[36 + lane] = (float)bp->h0inv[lane];
     }
-    if (bp->skin <= 0.0) {
-        // no skin: the cell list is rebuilt at every evaluation
-        double hh[9];
-        for (int k = 0; k < 9; ++k) hh[k] = lget(h, k);
-        if (lane == 0) {
-            sc.omega = omega;
-            bin_geometry(bp, b.nbins_cap, hh, omega, false, sc);
+    __syncwarp();
+    if (lane == 0) {
+        sc.omega = omega;
+        if (bp->skin <= 0.0) {
+            // no skin: the cell list is rebuilt at every evaluation
+            bin_geometry(bp, b.nbins_cap, sc.h, omega, false, sc);
             sc.rebuild = 1;
             sc.builds += 1;
             sc.evals += 1;
+        } else {
+            skin_decide_one(bp, b.nbins_cap, sc, dmax, force);
         }
-    } else if (lane == 0) {
-        sc.omega = omega;
     }
+    __syncwarp();
+    stage_copy(&b.sc[r.img], &s_sc);
 }
 
 // Offset of an atom from the centre of its (kept) bin, R - K with R = R~ D
 // and K = sum_a (wrap_a h_a + (b_a + 1/2) bv_a), as a leading part and a
 // remainder.  FP64 path: in FP64.  FP32 path: in pairs of FP32 (products
 // split exactly with FMA, sums with Knuth's two-sum), from the FP32 pairs
-// of D and h that k_skin_decide stores; bv is exact in FP32 by construction.
+// of D and h that k_mapback stores; bv is exact in FP32 by construction.
 // Both keep the offset to ~1e-14 relative of the cell size, far below the
 // FP32 leading part's rounding.
 __device__ inline void refresh_offset(const ImgScalars &sc, const BandParams *bp, const double *X,
@@ -427,93 +514,6 @@ __global__ void __launch_bounds__(TILE) k_skin_check(const Tile *tiles, BandDev 
     }
 }
 
-// upper bound of the spectral norm of a 3x3 matrix: the smaller of the
-// Frobenius norm and sqrt(|A|_1 |A|_inf), in FP32 and raised by 1e-6 to
-// stay a bound
-__device__ inline float norm2_bound(const float *A) {
-    float f = 0.0f, c1 = 0.0f, ci = 0.0f;
-    for (int i = 0; i < 3; ++i) {
-        float rs = 0.0f, cs = 0.0f;
-        for (int j = 0; j < 3; ++j) {
-            f += A[3 * i + j] * A[3 * i + j];
-            rs += fabsf(A[3 * i + j]);
-            cs += fabsf(A[3 * j + i]);
-        }
-        ci = fmaxf(ci, rs);
-        c1 = fmaxf(c1, cs);
-    }
-    return fminf(sqrtf(f), sqrtf(c1 * ci)) * 1.000001f;
-}
-
-// FP32 inverse of a 3x3 matrix (cofactors over the determinant)
-__device__ inline void inv3f(const float *m, float *o) {
-    const float c00 = m[4] * m[8] - m[5] * m[7], c01 = m[5] * m[6] - m[3] * m[8],
-                c02 = m[3] * m[7] - m[4] * m[6];
-    const float id = 1.0f / (m[0] * c00 + m[1] * c01 + m[2] * c02);
-    o[0] = c00 * id;
-    o[1] = (m[2] * m[7] - m[1] * m[8]) * id;
-    o[2] = (m[1] * m[5] - m[2] * m[4]) * id;
-    o[3] = c01 * id;
-    o[4] = (m[0] * m[8] - m[2] * m[6]) * id;
-    o[5] = (m[2] * m[3] - m[0] * m[5]) * id;
-    o[6] = c02 * id;
-    o[7] = (m[1] * m[6] - m[0] * m[7]) * id;
-    o[8] = (m[0] * m[4] - m[1] * m[3]) * id;
-}
-
-// One block per image: keep the bins of the build while the bound in the
-// header comment holds, else rebuild (and always when forced, when the
-// band's images were rearranged, or while autotuning).
-__global__ void k_skin_decide(const ImgRef *imgs, BandDev *bands, int force) {
-    ImgRef r = imgs[blockIdx.x];
-    BandDev &b = bands[r.band];
-    __shared__ BandParams s_bp;
-    __shared__ ImgScalars s_sc;
-    stage_copy(&s_bp, b.bp);
-    stage_copy(&s_sc, &b.sc[r.img]);
-    __syncthreads();
-    const BandParams *bp = &s_bp;
-    if (bp->skin <= 0.0) return;  // uniform over the block
-    ImgScalars &sc = s_sc;
-    const double *part = b.skin_part + (size_t)r.img * b.atpi;
-    double d = 0.0;
-    for (int t = threadIdx.x; t < b.atpi; t += blockDim.x) d = fmax(d, part[t]);
-    d = block_max_any(d);
-    if (threadIdx.x == 0) {
-        bool rebuild = force || bp->stale || bp->tune_rebuild || sc.builds == 0;
-        if (!rebuild) {
-            // in FP32: M - I = D_b^-1 D - I is small, so its FP32 rounding (~1e-7
-            // absolute) moves the bound by far less than the 1e-5 margins, which
-            // also cover the FP32 list test and displacement
-            float Db[9], D[9], Dbi[9], M[9];
-            for (int k = 0; k < 9; ++k) {
-                Db[k] = (float)sc.Db[k];
-                D[k] = (float)sc.D[k];
-            }
-            inv3f(Db, Dbi);
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j)
-                    M[3 * i + j] = Dbi[3 * i] * D[j] + Dbi[3 * i + 1] * D[3 + j] +
-                                   Dbi[3 * i + 2] * D[6 + j] - (i == j ? 1.0f : 0.0f);
-            const float e = norm2_bound(M) * 1.00001f + 1e-6f;
-            const double bound = bp->rl * (1.0 - 1e-5) * (1.0 - (double)e) -
-                                 2.0 * d * (double)norm2_bound(D) * (1.0 + 1e-5);
-            rebuild = !(bound > bp->rc);
-        }
-        if (rebuild) {
-            bin_geometry(bp, b.nbins_cap, sc.h, sc.omega, false, sc);
-            for (int k = 0; k < 9; ++k) sc.Db[k] = sc.D[k];
-            sc.builds += 1;
-        } else {
-            bin_geometry(bp, b.nbins_cap, sc.h, sc.omega, true, sc);
-        }
-        sc.rebuild = rebuild ? 1 : 0;
-        sc.dmax = d;
-        sc.evals += 1;
-    }
-    __syncthreads();
-    stage_copy(&b.sc[r.img], &s_sc);
-}
 
 // Exclusive scan of the bin counts, in three passes over SCAN_TILE-bin
 // tiles: tile sums, a scan of the tile sums per image, and a block-wide scan
@@ -666,9 +666,9 @@ __global__ void k_cartesian(const ImgRef *imgs, BandDev *bands) {
 // ---- launchers -------------------------------------------------------------
 
 template <typename T>
-void launch_mapback(const ImgRef *imgs, int count, BandDev *bands, cudaStream_t s) {
+void launch_mapback(const ImgRef *imgs, int count, BandDev *bands, int force, cudaStream_t s) {
     if (count <= 0) return;
-    k_mapback<T><<<count, 32, 0, s>>>(imgs, count, bands);
+    k_mapback<T><<<count, 32, 0, s>>>(imgs, count, bands, force);
 }
 template <typename T>
 void launch_bin_assign(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
@@ -679,10 +679,6 @@ template <typename T>
 void launch_skin_check(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
     if (ntiles <= 0) return;
     k_skin_check<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
-}
-void launch_skin_decide(const ImgRef *imgs, int count, BandDev *bands, int force, cudaStream_t s) {
-    if (count <= 0) return;
-    k_skin_decide<<<count, RED_THREADS, 0, s>>>(imgs, bands, force);
 }
 void launch_bin_scan(const ImgRef *imgs, int count, int max_bins, BandDev *bands,
                      cudaStream_t s, int part) {
@@ -711,7 +707,7 @@ void launch_cartesian(const ImgRef *imgs, int count, int max_n, BandDev *bands, 
 }
 
 #define CFNEB_INST(T)                                                                     \
-    template void launch_mapback<T>(const ImgRef *, int, BandDev *, cudaStream_t);       \
+    template void launch_mapback<T>(const ImgRef *, int, BandDev *, int, cudaStream_t);  \
     template void launch_bin_assign<T>(const Tile *, int, BandDev *, cudaStream_t);      \
     template void launch_skin_check<T>(const Tile *, int, BandDev *, cudaStream_t);      \
     template void launch_bin_order<T>(const ImgRef *, int, int, BandDev *, cudaStream_t); \

@@ -356,12 +356,12 @@ __device__ inline void stage_copy(S *dst, const S *src) {
 
 // ---- launchers (defined in the kernel translation units) ---------------
 
+// map-back and, after k_skin_check, the cell-list decision of every image
 template <typename T>
-void launch_mapback(const ImgRef *imgs, int count, BandDev *bands, cudaStream_t s);
+void launch_mapback(const ImgRef *imgs, int count, BandDev *bands, int force, cudaStream_t s);
 // displacement since the last build (per tile) and the per-image decision
 template <typename T>
 void launch_skin_check(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
-void launch_skin_decide(const ImgRef *imgs, int count, BandDev *bands, int force, cudaStream_t s);
 template <typename T>
 void launch_bin_assign(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 // part 0: tile sums, 1: scan of the tile sums, 2: final per-bin scan

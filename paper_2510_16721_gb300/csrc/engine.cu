@@ -47,12 +47,12 @@ struct CudaFail {
     } while (0)
 
 enum KernelId {
-    K_MAPBACK, K_SKIN_CHECK, K_SKIN_DECIDE, K_BIN_ASSIGN, K_BIN_TILESUM, K_BIN_TILESCAN, K_BIN_SCANFILL, K_BIN_SCATTER,
+    K_MAPBACK, K_SKIN_CHECK, K_BIN_ASSIGN, K_BIN_TILESUM, K_BIN_TILESCAN, K_BIN_SCANFILL, K_BIN_SCATTER,
     K_BIN_ORDER, K_LJ, K_TERS_LIST, K_TERS_REVERSE, K_TERS_PARTIALS, K_TERS_GATHER, K_IMAGE_FINALIZE,
     K_BAND_DOTS, K_DOTS_REDUCE, K_NEB_COEF, K_NEB_FORCE, K_FIRE_SCALARS, K_FIRE_UPDATE, K_COUNT
 };
 const char *kKernelNames[K_COUNT] = {
-    "mapback", "skin_check", "skin_decide", "bin_assign", "bin_tilesum", "bin_tilescan", "bin_scanfill", "bin_scatter",
+    "mapback", "skin_check", "bin_assign", "bin_tilesum", "bin_tilescan", "bin_scanfill", "bin_scatter",
     "bin_order", "lj_force", "tersoff_list", "tersoff_reverse", "tersoff_partials", "tersoff_gather",
     "image_finalize", "band_dots", "dots_reduce", "neb_coef", "neb_force", "fire_scalars",
     "fire_update"};
@@ -258,10 +258,10 @@ template <typename T>
 void enqueue_eval_set(const LaunchSet &ls, Launcher &L, bool forces = true) {
     BandDev *d = ls.d_bands;
     cudaStream_t s = ls.s;
-    L.pre(K_MAPBACK); launch_mapback<T>(ls.imgs, ls.nimg, d, s); L.post(K_MAPBACK);
+    // displacements since the last build, then map-back and the list decision
     L.pre(K_SKIN_CHECK); launch_skin_check<T>(ls.atiles, ls.n_atiles, d, s); L.post(K_SKIN_CHECK);
-    L.pre(K_SKIN_DECIDE); launch_skin_decide(ls.imgs, ls.nimg, d, ls.force_rebuild, s);
-    L.post(K_SKIN_DECIDE);
+    L.pre(K_MAPBACK); launch_mapback<T>(ls.imgs, ls.nimg, d, ls.force_rebuild, s);
+    L.post(K_MAPBACK);
     L.pre(K_BIN_ASSIGN); launch_bin_assign<T>(ls.atiles, ls.n_atiles, d, s); L.post(K_BIN_ASSIGN);
     L.pre(K_BIN_TILESUM); launch_bin_scan(ls.imgs, ls.nimg, ls.max_bins, d, s, 0); L.post(K_BIN_TILESUM);
     L.pre(K_BIN_TILESCAN); launch_bin_scan(ls.imgs, ls.nimg, ls.max_bins, d, s, 1); L.post(K_BIN_TILESCAN);
@@ -307,7 +307,7 @@ void enqueue_step_set(const LaunchSet &ls, Launcher &L) {
 }
 
 int launches_in_set(const LaunchSet &ls) {
-    return 9 + (ls.n_lj ? 1 : 0) + (ls.n_ters ? 4 : 0) + 1 + 6;
+    return 8 + (ls.n_lj ? 1 : 0) + (ls.n_ters ? 4 : 0) + 1 + 6;
 }
 
 LaunchSet band_set(cfneb_band *b, const ImgRef *imgs, int nimg, const Tile *atiles, int nat) {
