@@ -137,6 +137,23 @@ def dist_info():
     return ws, rank, local
 
 
+def max_over_ranks(torch, dist, ms):
+    """The job's time: the largest timed duration over the ranks (each rank
+    times its own replica between the same two barriers)."""
+    if dist is None:
+        return ms
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ws, units_per_rank, steps, ms):
+    """Whole-job throughput: the units every rank processed over the job's
+    time (weak scaling: each rank steps its own replica)."""
+    return ws * units_per_rank * steps / (ms / 1e3)
+
+
 def band_inputs(wl, seed=2510):
     import cfneb_inputs as ci
     cfg = ci.tersoff_graphite_hexdiamond(reps=wl["reps"], n_images=wl["n_images"], seed=seed,
@@ -289,14 +306,11 @@ def run_ours(args, wl_name):
              (lb1[0] - lb0[0]) / max(1, lb1[1] - lb0[1]),
              "note": "cell and neighbour lists cover rc + skin and are kept while no pair "
                      "can have crossed into rc; the timed steps include every rebuild"}
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(torch, dist, ms)
     path = band.get_path()
     if not np.all(np.isfinite(path["energies"])):
         raise RuntimeError("non-finite energies after the timed steps")
-    value = ws * n * moving * args.steps / (ms / 1e3)
+    value = job_rate(ws, n * moving, args.steps, ms)
 
     # per-kernel times (events around each launch on the library's stream)
     kp = max(5, min(args.steps, 50))
@@ -454,11 +468,8 @@ def run_batch(args):
     clocks.start()
     ms = time_steps(torch, bt, stream, args.steps, dist)
     clk = clocks.stop()
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * work * args.steps / (ms / 1e3)
+    ms = max_over_ranks(torch, dist, ms)
+    value = job_rate(ws, work, args.steps, ms)
     st = bt.status()
     assert all(s["status"] == 0 for s in st)
     # per-kernel profile
