@@ -611,9 +611,13 @@ def serve_once(g, stream, specs, built, budget, max_steps, lead, drain, window):
     atom_images = sum(len(b[0][0]) * (sp["n_images"] - 2) for sp, b in zip(specs, built))
     by_kind = {}
     for sp, r in zip(specs, res):
-        k = by_kind.setdefault(sp["kind"], {"requests": 0, "converged": 0, "lat": []})
+        k = by_kind.setdefault(sp["kind"], {"requests": 0, "converged": 0, "lat": [],
+                                             "errors": {}})
         k["requests"] += 1
         k["converged"] += int(r["converged"])
+        if r["status"] != 0:
+            name = g.status_string(r["status"])
+            k["errors"][name] = k["errors"].get(name, 0) + 1
         if r["state"] == 2:
             k["lat"].append(r["latency_s"])
     for k in by_kind.values():
