@@ -78,7 +78,14 @@ __device__ void bin_geometry(const BandParams *bp, int nbins_cap, const double *
             w[a] = (float)omega / sqrtf((float)(cx * cx + cy * cy + cz * cz)) * 0.9999f;
         }
         for (int a = 0; a < 3; ++a) {
-            const float q = floorf(w[a] / (float)bp->bin_w);
+            // the innermost axis may be binned finer: the LJ kernel walks it
+            // as contiguous rows, so finer bins there trim the candidate
+            // range without adding rows
+            const float bw = (float)bp->bin_w / (a == 2 ? (float)bp->row_refine : 1.0f);
+            // never so fine that the stencil would need more than
+            // MAX_STENCIL bins per side (coarser bins are always correct)
+            const float q = fminf(floorf(w[a] / bw),
+                                  floorf(w[a] * (float)MAX_STENCIL / (float)rl * 0.9999f));
             nb[a] = q < 1.0f ? 1 : (q > 1024.0f ? 1024 : (int)q);
         }
         // keep within the bin capacity: coarser bins are always correct

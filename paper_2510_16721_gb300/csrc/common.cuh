@@ -125,6 +125,8 @@ struct BandParams {
     int status;
     int stale;           // every image rebuilds at the next evaluation
     int tune_rebuild;    // rebuild at every evaluation (autotuning)
+    int row_refine;      // bins along the innermost axis per bin width (>= 1)
+    int pad_rr;
     TP<float> tpf;       // Tersoff constants in FP32 / FP64 (Tersoff bands)
     TP<double> tpd;
 };

@@ -154,6 +154,7 @@ extern "C" int cfneb_lj_evaluate_noalloc(const double *d_positions, int32_t n_at
     bp.c = (double)n;
     bp.rc = rc;
     bp.bin_w = rc;
+    bp.row_refine = 1;
     bp.ftol = -1.0;
     bp.move_limit = 0;
     bp.filter = 1;
