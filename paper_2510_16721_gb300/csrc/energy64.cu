@@ -81,6 +81,28 @@ __device__ inline void for_neighbours64(const BandDev &b, int img, int t, const 
     }
 }
 
+// sin a on [0, pi/2] in FP64 by its Taylor series to the a^25 term in
+// nested form (truncation below 2e-23 at pi/2)
+__device__ inline double sin_quarter64(double a) {
+    const double a2 = a * a;
+    double p = 1.0;
+    for (int k = 12; k >= 1; --k) p = 1.0 - a2 / (double)((2 * k) * (2 * k + 1)) * p;
+    return a * p;
+}
+
+// b = (1 + (beta zeta)^n)^(-1/2n) with m2n = -1/2n: x = (beta zeta)^n from
+// log and exp; for x < 1e-3 (carbon: x ~ 1e-5) b = exp(m2n log1p(x)) by
+// their series (log1p to x^5: 2e-13 relative at the bound, exp to y^6);
+// otherwise the library power
+__device__ inline double bond_order64(double bz, double n, double m2n) {
+    if (!(bz > 0.0)) return 1.0;
+    const double x = exp(n * log(bz));
+    if (x >= 1e-3) return pow(1.0 + x, m2n);
+    const double L = x * (1.0 - x * (0.5 - x * (1.0 / 3.0 - x * (0.25 - x * 0.2))));
+    const double y = m2n * L;
+    return 1.0 + y * (1.0 + y * (0.5 + y * (1.0 / 6.0 + y * (1.0 / 24.0 + y * (1.0 / 120.0 + y / 720.0)))));
+}
+
 template <typename T>
 __global__ void __launch_bounds__(TILE) k_energy64(const Tile *tiles, BandDev *bands) {
     Tile tl = tiles[blockIdx.x];
@@ -142,25 +164,27 @@ __global__ void __launch_bounds__(TILE) k_energy64(const Tile *tiles, BandDev *b
                 }
             }
             const double pi = 3.14159265358979323846;
-            const double c2 = p.c * p.c, d2 = p.d * p.d;
-            double fc[MAXN_TERSOFF];
+            const double c2d2 = p.c * p.c / (p.d * p.d), d2 = p.d * p.d;
+            const double pi_4D = 0.25 * pi / p.D, m2n = -0.5 / p.n;
+            double fc[MAXN_TERSOFF], ir[MAXN_TERSOFF];
             for (int k = 0; k < cnt; ++k) {
                 const double sk = rd[k] - p.R;
-                const double sn = sin(0.25 * pi * (p.D - sk) / p.D);
+                const double sn = sin_quarter64(pi_4D * (p.D - sk));
                 fc[k] = sk <= -p.D ? 1.0 : (sk >= p.D ? 0.0 : sn * sn);
+                ir[k] = rcp64(rd[k]);
             }
             for (int j = 0; j < cnt; ++j) {
+                if (fc[j] == 0.0) continue;  // beyond R + D
                 double zeta = 0.0;
                 for (int k = 0; k < cnt; ++k) {
                     if (k == j) continue;
-                    const double cs = (rx[j] * rx[k] + ry[j] * ry[k] + rz[j] * rz[k]) /
-                                      (rd[j] * rd[k]);
+                    const double cs = (rx[j] * rx[k] + ry[j] * ry[k] + rz[j] * rz[k]) * ir[j] * ir[k];
                     const double u = p.h - cs;
-                    const double g = 1.0 + c2 * u * u / (d2 * (d2 + u * u));
+                    const double g = 1.0 + c2d2 * u * u * rcp64(d2 + u * u);
                     zeta += fc[k] * g;
                 }
-                const double b_ = zeta > 0.0 ? pow(1.0 + pow(p.beta * zeta, p.n), -0.5 / p.n) : 1.0;
-                U += 0.5 * fc[j] * (p.A * exp(-p.lambda1 * rd[j]) - b_ * p.B * exp(-p.lambda2 * rd[j]));
+                U += 0.5 * fc[j] * (p.A * exp(-p.lambda1 * rd[j]) -
+                                    bond_order64(p.beta * zeta, p.n, m2n) * p.B * exp(-p.lambda2 * rd[j]));
             }
         }
     }
