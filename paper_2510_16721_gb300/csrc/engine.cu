@@ -100,6 +100,7 @@ struct cfneb_band {
     double rl = 0.0;             // list cutoff rc + skin
     std::tuple<int, int, int, int> tune_key{};
     double ftol = -1.0;
+    bool ends_e64 = false;       // the endpoints' FP64 energies are known
     // stream ordering
     cudaStream_t user = nullptr, s = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -438,13 +439,14 @@ void eval_images(cfneb_band *b, const std::vector<int> &imgs) {
 
 // FP64 energies (ImgScalars::E64) of the images' current coordinates:
 // map-back, cell list and the FP64 energy kernel, no forces
-void refine_energies(cfneb_band *b, int first, int count) {
+void refine_energies(cfneb_band *b, const std::vector<int> &imgs) {
     std::vector<ImgRef> im;
     std::vector<Tile> at;
-    for (int i = first; i < first + count; ++i) {
+    for (int i : imgs) {
         im.push_back({0, i});
         for (int t = 0; t < b->dv.atpi; ++t) at.push_back({0, i, t, 0});
     }
+    if (im.empty()) return;
     CK(cudaMemcpyAsync(b->d_scratch_imgs, im.data(), im.size() * sizeof(ImgRef),
                        cudaMemcpyHostToDevice, b->s));
     CK(cudaMemcpyAsync(b->d_scratch_tiles, at.data(), at.size() * sizeof(Tile),
@@ -1448,8 +1450,13 @@ int cfneb_get_path(const cfneb_band *cb, int32_t *n_images, double *positions, d
         if (n_images) *n_images = b->N;
         if (positions || cells || energies) {
             // FP64 energies of the current images (map-back, cell list, energy),
-            // then Cartesian positions R = R~ D from the same map-back
-            refine_energies(b, 0, b->N);
+            // then Cartesian positions R = R~ D from the same map-back; the
+            // endpoints never move, so theirs are computed once
+            std::vector<int> imgs;
+            if (!b->ends_e64) imgs = {0, b->N - 1};
+            for (int i = 1; i < b->N - 1; ++i) imgs.push_back(i);
+            refine_energies(b, imgs);
+            b->ends_e64 = true;
             if (b->precision == CFNEB_MIXED)
                 launch_cartesian<float>(b->d_scratch_imgs, b->N, b->n, b->d_self, b->s);
             else
@@ -1556,7 +1563,7 @@ int cfneb_evaluate(const cfneb_structure *structures, int32_t count,
             enter(b);
             // the endpoints were evaluated at creation: image 0 is S; its
             // reported energy is the FP64 one
-            refine_energies(b, 0, 1);
+            refine_energies(b, {0});
             std::vector<ImgScalars> sc(1);
             CK(cudaMemcpyAsync(sc.data(), b->dv.sc, sizeof(ImgScalars), cudaMemcpyDeviceToHost,
                                b->s));
