@@ -423,8 +423,10 @@ __device__ inline void bin_of(const ImgScalars &sc, const BandParams *bp, const 
             s = 0.0;
             wrap[a] += 1;
         }
+        // any bin index outside [0, nb) (a non-finite coordinate) goes to an
+        // edge bin: the index stays in range whatever the input
         const int q = (int)(s * sc.nb[a]);
-        bi[a] = q >= sc.nb[a] ? sc.nb[a] - 1 : q;
+        bi[a] = q >= sc.nb[a] ? sc.nb[a] - 1 : (q < 0 ? 0 : q);
     }
 }
 __device__ inline void bin_of(const ImgScalars &sc, const BandParams *, const float *X, int *bi,

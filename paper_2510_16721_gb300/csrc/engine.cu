@@ -1337,8 +1337,16 @@ int cfneb_create_band(const cfneb_structure *initial, const cfneb_structure *fin
     if (potential->kind == CFNEB_LJ &&
         (potential->rc <= 0 || potential->sigma <= 0 || potential->eps <= 0))
         return CFNEB_ERR_INVALID_ARG;
-    if (std::fabs(det3(initial->cell)) <= 0 || std::fabs(det3(final_->cell)) <= 0)
+    if (!(std::fabs(det3(initial->cell)) > 0) || !(std::fabs(det3(final_->cell)) > 0))
         return CFNEB_ERR_INVALID_ARG;
+    // finite coordinates and cells only (a non-finite coordinate would reach
+    // the cell list as a meaningless bin)
+    for (const cfneb_structure *S : {initial, final_}) {
+        for (int k = 0; k < 9; ++k)
+            if (!std::isfinite(S->cell[k])) return CFNEB_ERR_INVALID_ARG;
+        for (long long k = 0; k < 3LL * S->n_atoms; ++k)
+            if (!std::isfinite(S->positions[k])) return CFNEB_ERR_INVALID_ARG;
+    }
     cfneb_options opt;
     if (options) opt = *options;
     else cfneb_default_options(&opt);
