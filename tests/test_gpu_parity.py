@@ -383,3 +383,17 @@ def test_tersoff_filter_variant_and_pressure_fp64(g, oracle_mod):
     _compare_state(st, ob, 1e-9)
     for i in range(1, 8):
         assert _rel(st["virials"][i], ob.info[i]["V"]) <= 1e-10
+
+
+def test_diamond_vacancy_hop_fp64(g, oracle_mod):
+    """The serving stream's Tersoff vacancy request (cubic diamond, 63 atoms,
+    unrelaxed endpoints, cell filter on): 10 FP64 steps against the oracle.
+    (Longer runs of this band are chaotic in both implementations: fmax
+    jumps between ~0.5 and ~50 eV/A as atoms cross the narrow cutoff shell.)"""
+    R0, h0, R1, h1 = ci.diamond_vacancy_hop(ci.DIAMOND_A, (2, 2, 2))
+    kw = dict(k=0.1, dt=0.1, cell_filter=True)
+    gb = gpu_band(g, R0, h0, R1, h1, 9, g.tersoff_potential(), **kw)
+    ob = oracle_band(oracle_mod, oracle_mod.Tersoff(), R0, h0, R1, h1, 9, **kw)
+    gb.step(10)
+    ob.step(10)
+    _compare_state(gb.get_state(), ob, 1e-9)
