@@ -45,7 +45,7 @@ WORKLOADS = {
 }
 CPU_SAMPLE_REPS = (6, 4, 3)   # the 576-atom tile the large band is built from
 
-# algorithmic work per kernel launch (see DESIGN.md): FLOPs for the force
+# algorithmic work per kernel launch: FLOPs for the force
 # kernels (useful arithmetic, transcendental functions counted as 1), bytes for
 # the memory-bound ones.  w = dict(pairs, triples, atoms, dof, ts)
 FLOP_MODELS = {

@@ -19,7 +19,7 @@ numpy primitives (matrix products, ``eigh``) as the only library steps:
 * adaptive refinement -- images inserted or removed from the spacing of the
   images in configuration space after NEB iterations (Sec. III).
 
-Readings where the paper is silent or garbled (each also listed in the design doc):
+Readings where the paper is silent or garbled:
 
 1. f^{ij} = dU_i/dr^{ij} - dU_j/dr^{ji} (derivation of Eq. V2).
 2. The rotation-free lattice force carries a factor 1/2:
