@@ -51,6 +51,7 @@ CPU_SAMPLE_REPS = (6, 4, 3)   # the 576-atom tile the large band is built from
 FLOP_MODELS = {
     "tersoff_partials": lambda w: 65.0 * w["pairs"] + 89.0 * w["triples"],
     "lj_force": lambda w: 40.0 * w["pairs"],
+    "lj_force_cells": lambda w: 40.0 * w["pairs"],
 }
 BYTE_MODELS = {
     "tersoff_gather": lambda w: w["pairs"] * (8 + 6 * w["ts"]) + w["atoms"] * (8 + 3 * w["ts"]),
@@ -501,7 +502,8 @@ def run_batch(args):
                 "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % peak_src}
     roof.update({"kernel": dom, "kernel_ms": dom_ms, "share": prof[dom][0] / total,
                  "traffic": traffic_for(dom), "work_per_launch": {"pairs": pairs, "atoms": work}})
-    launches = None
+    # launches of the profiled batch steps (every kernel, one launch each)
+    launches = int(round(sum(v[1] for v in prof.values()) / kp * args.steps))
     bt.destroy()
     for b in bands:
         b.destroy()
@@ -562,7 +564,7 @@ def run_batch(args):
                        "parallelism": "replicas x%d" % ws},
             "roofline": roof, "kernel_share": {k: round(v[0] / total, 4)
                                                for k, v in prof.items() if v[1]},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 16 * args.steps, "clocks": clk,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "fp64_plain": fp64, "create_s": t_create}
     print(json.dumps(line))
     if dist is not None:

@@ -122,7 +122,11 @@ typedef struct {
                                  bound from the largest displacement and the
                                  cell change since the build); 0 rebuilds at
                                  every evaluation; < 0 selects the default
-                                 (Tersoff 0.15, LJ 0).  At most rc.          */
+                                 (Tersoff 0.15, LJ 0.12 rc).  At most rc.
+                                 LJ bands with a skin and at most 2^17 atoms
+                                 keep per-atom neighbour lists; other LJ
+                                 bands walk the cell list at every
+                                 evaluation.                                 */
 } cfneb_options;
 
 /* Fill *opt with the defaults: k 0.1, climb on, FP64, FIRE dt 0.1,

@@ -30,6 +30,7 @@ constexpr int RTILE = TILE * RPT;   // rows per row tile (band vector kernels)
 constexpr int MAXN_TERSOFF = 16;    // Tersoff list capacity per atom (entries within rl)
 constexpr int NPART = 12;           // doubles per tile partial record
 constexpr int MAX_STENCIL = 7;      // |delta| <= 7 bins per axis
+constexpr int LJ_LIST_MAX_ATOMS = 1 << 17;  // LJ list entries index 17-bit slots
 
 // device status bits (BandParams::status)
 enum : int {
@@ -157,9 +158,12 @@ struct BandDev {
     void *ref_X;         // [ncap][n] x 4 T: R~ at the build (atom order)
     int *atom_wrap;      // [ncap][n][3]: floor(s) at the build
     double *skin_part;   // [ncap][atpi]: per-tile max displacement
-    // Tersoff per-slot neighbour data
+    // per-slot neighbour lists: Tersoff (slot, code) pairs of MAXN_TERSOFF
+    // entries, or LJ packed entries of lj_cap (0: the LJ kernel walks the
+    // cell list directly)
+    int lj_cap;
     int *nbr_cnt;        // [ncap][n]
-    int *nbr_slot;       // [ncap][MAXN][n]
+    int *nbr_slot;       // [ncap][MAXN or lj_cap][n]
     int *nbr_code;       // [ncap][MAXN][n]
     unsigned char *nbr_rev;  // [ncap][MAXN][n]: entry of j's list pointing back (255: none)
     void *nbr_P;         // [ncap][3*MAXN][n] of T
@@ -375,6 +379,10 @@ void launch_bin_order(const ImgRef *imgs, int count, int max_bins, BandDev *band
                       cudaStream_t s);
 template <typename T>
 void launch_lj(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
+template <typename T>
+void launch_lj_list(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
+template <typename T>
+void launch_lj_nbr(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 template <typename T>
 void launch_tersoff_list(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 template <typename T>

@@ -49,13 +49,14 @@ struct CudaFail {
 enum KernelId {
     K_MAPBACK, K_SKIN_CHECK, K_BIN_ASSIGN, K_BIN_TILESUM, K_BIN_TILESCAN, K_BIN_SCANFILL, K_BIN_SCATTER,
     K_BIN_ORDER, K_LJ, K_TERS_LIST, K_TERS_REVERSE, K_TERS_PARTIALS, K_TERS_GATHER, K_IMAGE_FINALIZE,
-    K_BAND_DOTS, K_DOTS_REDUCE, K_NEB_COEF, K_NEB_FORCE, K_FIRE_SCALARS, K_FIRE_UPDATE, K_COUNT
+    K_BAND_DOTS, K_DOTS_REDUCE, K_NEB_COEF, K_NEB_FORCE, K_FIRE_SCALARS, K_FIRE_UPDATE, K_LJ_LIST,
+    K_LJ_CELLS, K_COUNT
 };
 const char *kKernelNames[K_COUNT] = {
     "mapback", "skin_check", "bin_assign", "bin_tilesum", "bin_tilescan", "bin_scanfill", "bin_scatter",
     "bin_order", "lj_force", "tersoff_list", "tersoff_reverse", "tersoff_partials", "tersoff_gather",
     "image_finalize", "band_dots", "dots_reduce", "neb_coef", "neb_force", "fire_scalars",
-    "fire_update"};
+    "fire_update", "lj_list", "lj_force_cells"};
 
 const double kTersoff1988C[11] = {1393.6, 346.74, 3.4879, 2.2119, 1.5724e-7, 0.72751,
                                   38049.0, 4.3484, -0.57058, 1.95, 0.15};
@@ -224,8 +225,10 @@ struct LaunchSet {
     int nimg = 0;
     const Tile *atiles = nullptr;        // atom tiles of every listed image
     int n_atiles = 0;
-    const Tile *atiles_lj = nullptr;     // the LJ bands' atom tiles
+    const Tile *atiles_lj = nullptr;     // atom tiles of the LJ bands with a neighbour list
     int n_lj = 0;
+    const Tile *atiles_ljc = nullptr;    // atom tiles of the LJ bands without one
+    int n_ljc = 0;
     const Tile *atiles_ters = nullptr;   // the Tersoff bands' atom tiles
     int n_ters = 0;
     const Tile *rtiles = nullptr;        // row tiles
@@ -269,8 +272,11 @@ void enqueue_eval_set(const LaunchSet &ls, Launcher &L, bool forces = true) {
     L.pre(K_BIN_SCANFILL); launch_bin_scan(ls.imgs, ls.nimg, ls.max_bins, d, s, 2); L.post(K_BIN_SCANFILL);
     L.pre(K_BIN_SCATTER); launch_bin_scatter(ls.atiles, ls.n_atiles, d, s); L.post(K_BIN_SCATTER);
     L.pre(K_BIN_ORDER); launch_bin_order<T>(ls.imgs, ls.nimg, ls.max_bins, d, s); L.post(K_BIN_ORDER);
-    // the Tersoff list indexes cell-list slots: it is rebuilt with every
+    // the neighbour lists index cell-list slots: they are rebuilt with every
     // cell list, also by an energy-only evaluation
+    if (ls.n_lj) {
+        L.pre(K_LJ_LIST); launch_lj_list<T>(ls.atiles_lj, ls.n_lj, d, s); L.post(K_LJ_LIST);
+    }
     if (ls.n_ters) {
         L.pre(K_TERS_LIST); launch_tersoff_list<T>(ls.atiles_ters, ls.n_ters, d, s);
         L.post(K_TERS_LIST);
@@ -282,7 +288,10 @@ void enqueue_eval_set(const LaunchSet &ls, Launcher &L, bool forces = true) {
         return;
     }
     if (ls.n_lj) {
-        L.pre(K_LJ); launch_lj<T>(ls.atiles_lj, ls.n_lj, d, s); L.post(K_LJ);
+        L.pre(K_LJ); launch_lj_nbr<T>(ls.atiles_lj, ls.n_lj, d, s); L.post(K_LJ);
+    }
+    if (ls.n_ljc) {
+        L.pre(K_LJ_CELLS); launch_lj<T>(ls.atiles_ljc, ls.n_ljc, d, s); L.post(K_LJ_CELLS);
     }
     if (ls.n_ters) {
         L.pre(K_TERS_PARTIALS); launch_tersoff_partials<T>(ls.atiles_ters, ls.n_ters, d, s);
@@ -308,7 +317,7 @@ void enqueue_step_set(const LaunchSet &ls, Launcher &L) {
 }
 
 int launches_in_set(const LaunchSet &ls) {
-    return 8 + (ls.n_lj ? 1 : 0) + (ls.n_ters ? 4 : 0) + 1 + 6;
+    return 8 + (ls.n_lj ? 2 : 0) + (ls.n_ljc ? 1 : 0) + (ls.n_ters ? 4 : 0) + 1 + 6;
 }
 
 LaunchSet band_set(cfneb_band *b, const ImgRef *imgs, int nimg, const Tile *atiles, int nat) {
@@ -319,9 +328,12 @@ LaunchSet band_set(cfneb_band *b, const ImgRef *imgs, int nimg, const Tile *atil
     ls.nimg = nimg;
     ls.atiles = atiles;
     ls.n_atiles = nat;
-    if (b->kind == CFNEB_LJ) {
+    if (b->kind == CFNEB_LJ && b->dv.lj_cap > 0) {
         ls.atiles_lj = atiles;
         ls.n_lj = nat;
+    } else if (b->kind == CFNEB_LJ) {
+        ls.atiles_ljc = atiles;
+        ls.n_ljc = nat;
     } else {
         ls.atiles_ters = atiles;
         ls.n_ters = nat;
@@ -706,9 +718,10 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
     }
     // neighbour-list skin: the caller's, or 0.15 A for Tersoff (carbon's
     // second neighbours, 2.46-2.52 A, stay outside R + D + skin, so the lists
-    // keep their 3-4 entries) and none for LJ (its force kernel walks the
-    // cell list directly)
-    const double skin = opt->skin >= 0.0 ? opt->skin : (pot->kind == CFNEB_TERSOFF ? 0.15 : 0.0);
+    // keep their 3-4 entries) and 0.12 rc for LJ (0.3 sigma at rc = 2.5
+    // sigma: the list holds ~1.4 candidates per pair inside rc, against ~3.4
+    // for a walk of half-cutoff bins)
+    const double skin = opt->skin >= 0.0 ? opt->skin : (pot->kind == CFNEB_TERSOFF ? 0.15 : 0.12 * rc);
     const double rl = rc + skin;
     b->rl = rl;
     // bin width: the caller's, the cached autotuned one for this class, or rc
@@ -761,6 +774,18 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
         d.ref_X = dalloc(b, na * 4 * b->ts);
         d.atom_wrap = (int *)dalloc(b, na * 3 * sizeof(int));
         d.skin_part = (double *)dalloc(b, nc * d.atpi * sizeof(double));
+    }
+    d.lj_cap = 0;
+    if (pot->kind == CFNEB_LJ && skin > 0.0 && n <= LJ_LIST_MAX_ATOMS) {
+        // list capacity: 1.5 x the entries within rl at the denser endpoint's
+        // mean density, plus 32 (the path never gets much denser than its
+        // ends; an overflow is reported as CFNEB_ERR_NBR_OVERFLOW)
+        const double vmin = std::min(std::fabs(det3(A->cell)), std::fabs(det3(B->cell)));
+        const double expect = n / vmin * 4.0 / 3.0 * 3.14159265358979323846 * rl * rl * rl;
+        d.lj_cap = (int)std::min<double>(std::ceil((1.5 * expect + 32.0) / 8.0) * 8.0, 4096.0);
+        d.nbr_cnt = (int *)dalloc(b, na * sizeof(int));
+        d.nbr_slot = (int *)dalloc(b, na * d.lj_cap * sizeof(int));
+        CK(cudaMemsetAsync(d.nbr_cnt, 0, na * sizeof(int), b->s));
     }
     if (pot->kind == CFNEB_TERSOFF) {
         d.nbr_cnt = (int *)dalloc(b, na * sizeof(int));
@@ -971,7 +996,7 @@ void grow(X **p, size_t *cap, size_t need) {
 void batch_rebuild(cfneb_batch *bt) {
     std::vector<BandDev> dv;
     std::vector<ImgRef> im;
-    std::vector<Tile> all, lj, ters, rows;
+    std::vector<Tile> all, lj, ljc, ters, rows;
     std::vector<int> ids;
     int max_bins = 0;
     for (size_t k = 0; k < bt->bands.size(); ++k) {
@@ -983,7 +1008,8 @@ void batch_rebuild(cfneb_batch *bt) {
             im.push_back({(int)k, i});
             for (int t = 0; t < b->dv.atpi; ++t) {
                 all.push_back({(int)k, i, t, 0});
-                (b->kind == CFNEB_LJ ? lj : ters).push_back({(int)k, i, t, 0});
+                (b->kind != CFNEB_LJ ? ters : b->dv.lj_cap > 0 ? lj : ljc)
+                    .push_back({(int)k, i, t, 0});
             }
             for (int t = 0; t < b->dv.rtpi; ++t) rows.push_back({(int)k, i, t, 0});
         }
@@ -992,6 +1018,7 @@ void batch_rebuild(cfneb_batch *bt) {
     std::vector<Tile> tiles;
     tiles.insert(tiles.end(), all.begin(), all.end());
     tiles.insert(tiles.end(), lj.begin(), lj.end());
+    tiles.insert(tiles.end(), ljc.begin(), ljc.end());
     tiles.insert(tiles.end(), ters.begin(), ters.end());
     tiles.insert(tiles.end(), rows.begin(), rows.end());
     grow(&bt->d_tiles, &bt->cap_tiles, std::max<size_t>(tiles.size(), 1));
@@ -1026,9 +1053,11 @@ void batch_rebuild(cfneb_batch *bt) {
     ls.n_atiles = (int)all.size();
     ls.atiles_lj = bt->d_tiles + all.size();
     ls.n_lj = (int)lj.size();
-    ls.atiles_ters = bt->d_tiles + all.size() + lj.size();
+    ls.atiles_ljc = bt->d_tiles + all.size() + lj.size();
+    ls.n_ljc = (int)ljc.size();
+    ls.atiles_ters = bt->d_tiles + all.size() + lj.size() + ljc.size();
     ls.n_ters = (int)ters.size();
-    ls.rtiles = bt->d_tiles + all.size() + lj.size() + ters.size();
+    ls.rtiles = bt->d_tiles + all.size() + lj.size() + ljc.size() + ters.size();
     ls.n_rtiles = (int)rows.size();
     ls.band_ids = bt->d_ids;
     ls.nbands = (int)ids.size();

@@ -152,3 +152,62 @@ def test_invalid_skin_is_rejected(g, skin):
     R0, h0, R1, h1 = cfg["endpoints"]
     with pytest.raises(g.CfnebError):
         gpu_band(g, R0, h0, R1, h1, 5, g.tersoff_potential(), k=0.1, dt=0.1, skin=skin)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_lj_neighbour_list_and_cell_walk_match(g, oracle_mod, precision):
+    """LJ bands with a skin keep per-atom neighbour lists (entries inside rc
+    first, the skin shell after them); with skin 0 the force kernel walks
+    the cell list.  A strained 4x4x4 vacancy band (255 atoms, cell filter
+    on) through 12 steps on both paths: FP64 states within 1e-9 of the
+    oracle, mixed forces at the stored configuration within 1e-4 eps/sigma
+    of it and within 1e-4 of each other (both paths form the same FP32 pair
+    vectors; only the summation order differs)."""
+    R0, h0, R1, h1 = ci.lj_vacancy_hop(ci.LJ_A, (4, 4, 4))
+    h1s = ci.strained_cell(h1, 9, 0.02)
+    R1 = ci.affine(R1, h1, h1s)
+    kw = dict(k=1.0, dt=0.01, cell_filter=True, precision=precision)
+    lists = gpu_band(g, R0, h0, R1, h1s, 7, g.lj_potential(), **kw)
+    walk = gpu_band(g, R0, h0, R1, h1s, 7, g.lj_potential(), skin=0.0, **kw)
+    assert lists.list_stats()[2] == pytest.approx(0.3)
+    if precision == 0:
+        ob = oracle_band(oracle_mod, oracle_mod.LJ(), R0, h0, R1, h1s, 7, k=1.0, dt=0.01,
+                         cell_filter=True)
+        for _ in range(3):
+            lists.step(4)
+            walk.step(4)
+            ob.step(4)
+            _compare_state(lists.get_state(), ob, 1e-9)
+            _compare_state(walk.get_state(), ob, 1e-9)
+    else:
+        lists.step(12)
+        walk.step(12)
+        sl, sw = lists.get_state(), walk.get_state()
+        lists.step(1)
+        walk.step(1)
+        fl, fw = lists.get_state()["F"], walk.get_state()["F"]
+        img = oracle_mod.AtomicImage(oracle_mod.LJ(), h0, len(R0), True)
+        for i in range(1, 6):
+            _, Fo, _ = img(sl["X"][i])
+            assert np.max(np.abs(fl[i] - Fo)) <= 1e-4, i
+            _, Fo, _ = img(sw["X"][i])
+            assert np.max(np.abs(fw[i] - Fo)) <= 1e-4, i
+    b, e, _ = lists.list_stats()
+    assert b < e                      # lists kept between builds
+    b, e, _ = walk.list_stats()
+    assert b == e
+
+
+def test_lj_neighbour_list_overflow_is_reported(g):
+    """The list capacity follows the endpoints' mean density.  256 atoms at
+    FCC density packed into one corner of a 20 sigma box have ~86 entries
+    within rc + skin but a capacity of 40: the list kernel caps its writes
+    and the band reports the overflow."""
+    R = ci.fcc(ci.LJ_A, 4, 4, 4)[0] + 1.0
+    h = np.eye(3) * 20.0
+    R1 = R.copy()
+    R1[0] += 0.05
+    with pytest.raises(g.CfnebError) as e:
+        gb = gpu_band(g, R, h, R1, h, 5, g.lj_potential(), k=1.0, dt=0.01)
+        gb.step(1)
+    assert e.value.status == g.ERR_NBR_OVERFLOW
