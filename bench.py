@@ -508,22 +508,24 @@ def run_batch(args):
     for b in bands:
         b.destroy()
     # plain FP64, one band per launch: every band stepped on its own
-    k64 = max(3, args.steps // 5)
-    b64 = [make_lj_band(g, c, g.FP64, stream) for c in bcs]
-    for b in b64:
-        b.step(2)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for b in b64:
-        b.step(k64)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms64 = e0.elapsed_time(e1)
-    fp64 = {"value": work * k64 / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64 / k64,
-            "steps": k64, "mode": "FP64, one band per launch (each band's own graph)"}
-    for b in b64:
-        b.destroy()
+    fp64 = None
+    if not args.no_fp64:
+        k64 = max(3, args.steps // 5)
+        b64 = [make_lj_band(g, c, g.FP64, stream) for c in bcs]
+        for b in b64:
+            b.step(2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for b in b64:
+            b.step(k64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        fp64 = {"value": work * k64 / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64 / k64,
+                "steps": k64, "mode": "FP64, one band per launch (each band's own graph)"}
+        for b in b64:
+            b.destroy()
     # end to end: create from host arrays, K batch steps, every path read back
     torch.cuda.synchronize()
     t0 = time.perf_counter()

@@ -106,12 +106,7 @@ __global__ void __launch_bounds__(TILE) k_band_dots(const Tile *tiles, BandDev *
             }
         }
     }
-    double tot[5];
-    block_sum_t<5, T>(acc, tot);
-    if (threadIdx.x == 0) {
-        double *part = b.row_part + ((size_t)tl.img * b.rtpi + tl.t) * NPART;
-        for (int k = 0; k < 5; ++k) part[k] = tot[k];
-    }
+    block_sum_store<5, T>(acc, b.row_part + ((size_t)tl.img * b.rtpi + tl.t) * NPART);
 }
 
 // one block per image: sum the row-tile partials of the five dots
@@ -215,22 +210,19 @@ __global__ void __launch_bounds__(TILE) k_neb_force(const Tile *tiles, BandDev *
             acc[3] = fmax(acc[3], ff);
         }
     }
-    double tot[3];
     T three[3] = {acc[0], acc[1], acc[2]};
-    block_sum_t<3, T>(three, tot);
-    // block max of the row norms
-    __shared__ double smax[TILE / 32];
-    double m = warp_max((double)acc[3]);
+    double *part = b.row_part + ((size_t)tl.img * b.rtpi + tl.t) * NPART;
+    block_sum_store<3, T>(three, part + 5);
+    // block max of the row norms, in T (a max is exact in any precision)
+    __shared__ T smax[TILE / 32];
+    T m = acc[3];
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double mx = 0.0;
+        T mx = (T)0;
         for (int q = 0; q < TILE / 32; ++q) mx = fmax(mx, smax[q]);
-        double *part = b.row_part + ((size_t)tl.img * b.rtpi + tl.t) * NPART;
-        part[5] = tot[0];
-        part[6] = tot[1];
-        part[7] = tot[2];
-        part[8] = mx;
+        part[8] = (double)mx;
     }
 }
 

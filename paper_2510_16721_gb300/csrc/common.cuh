@@ -305,6 +305,30 @@ __device__ inline void block_sum_t(T (&v)[K], double *out) {
     __syncthreads();
 }
 
+// As block_sum_t, but the totals go straight to dst[0..K-1]: lane k of warp
+// 0 sums value k across the warps, in the same order (so the same bits), and
+// the FP64 additions take K/32 warp instructions instead of K in thread 0
+// (an FP64 instruction occupies a warp's FP64 pipe for ~64 cycles here).
+template <int K, typename T>
+__device__ inline void block_sum_store(T (&v)[K], double *dst) {
+    static_assert(K <= 32, "one lane per value");
+    __shared__ T red[TILE / 32][K > 0 ? K : 1];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        T s = v[k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[w][k] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0.0;
+        for (int q = 0; q < TILE / 32; ++q) s += (double)red[q][threadIdx.x];
+        dst[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
 // Sum K per-thread values over a block of any multiple of 32 threads (up to
 // 1024) in FP64, fixed order (a warp butterfly within each warp, then one
 // across the warp totals); thread 0 receives the totals.  Butterflies keep

@@ -16,12 +16,10 @@
 
 namespace cfneb {
 
-template <typename T>
-__device__ inline T rcp(T x);
-template <>
-__device__ inline float rcp<float>(float x) { return __frcp_rn(x); }
-template <>
-__device__ inline double rcp<double>(double x) { return 1.0 / x; }
+// sigma^2 / r^2: FP32 by the fast division intrinsic (2 ulp: ~1e-6 of a
+// pair force, far inside the mixed path's 1e-4 force tolerance), FP64 exact
+__device__ inline float lj_sr2(float sig2, float r2) { return __fdividef(sig2, r2); }
+__device__ inline double lj_sr2(double sig2, double r2) { return sig2 / r2; }
 
 // Per-thread LJ accumulators: force on atom i, energy sum, virial, pair count
 template <typename T>
@@ -29,23 +27,23 @@ struct LJAcc {
     T fx = 0, fy = 0, fz = 0, e = 0;
     T v00 = 0, v01 = 0, v02 = 0, v11 = 0, v12 = 0, v22 = 0;
     int cnt = 0;
-    __device__ inline void pair(T rx, T ry, T rz, T sig2, T eps24) {
-        const T r2 = rx * rx + ry * ry + rz * rz;
-        const T ir2 = rcp<T>(r2);
-        const T sr2 = sig2 * ir2;
+    // pair vector (rx, ry, rz) with |r|^2 = r2; c24 = 24 eps / sigma^2
+    __device__ inline void pair(T rx, T ry, T rz, T r2, T sig2, T c24) {
+        const T sr2 = lj_sr2(sig2, r2);
         const T sr6 = sr2 * sr2 * sr2;
         // phi'(r)/r = 24 eps (sr6 - 2 sr6^2) / r^2
-        const T fr = eps24 * sr6 * ((T)1 - (T)2 * sr6) * ir2;
-        fx += fr * rx;
-        fy += fr * ry;
-        fz += fr * rz;
+        const T fr = c24 * sr2 * sr6 * ((T)1 - (T)2 * sr6);
+        const T frx = fr * rx, fry = fr * ry, frz = fr * rz;
+        fx += frx;
+        fy += fry;
+        fz += frz;
         e += sr6 * (sr6 - (T)1);
-        v00 += fr * rx * rx;
-        v01 += fr * rx * ry;
-        v02 += fr * rx * rz;
-        v11 += fr * ry * ry;
-        v12 += fr * ry * rz;
-        v22 += fr * rz * rz;
+        v00 += frx * rx;
+        v01 += frx * ry;
+        v02 += frx * rz;
+        v11 += fry * ry;
+        v12 += fry * rz;
+        v22 += frz * rz;
         ++cnt;
     }
 };
@@ -64,6 +62,8 @@ __device__ inline int axis_code(int d, int t, int m, int nb) {
 // i2 in bits 27-31 (i_a the axis codes).  The list path therefore needs
 // n <= 2^17 atoms per image.
 constexpr int LJ_AXIS = 30;
+// entries the list force kernel takes per iteration (lists are padded to it)
+constexpr int LJ_UNROLL = 4;
 __device__ inline uint32_t lj_entry(int q, int i01, int i2) {
     return (uint32_t)q | ((uint32_t)i01 << 17) | ((uint32_t)i2 << 27);
 }
@@ -135,14 +135,23 @@ __device__ inline void lj_walk(const typename Vec4<T>::type *off, const int *sta
     }
 }
 
-// Per-block staging of an image's bin geometry
+// Per-block staging of an image's bin geometry and the LJ constants in T
 template <typename T>
 struct LJGeom {
     T bv[9], dh[9], D[9];
+    T rc2, sig2, c24, e4, ephi;   // rc^2, sigma^2, 24 eps / sigma^2, 4 eps, phi(rc)
     int nb[3], m[3];
 };
 template <typename T>
-__device__ inline void lj_stage(LJGeom<T> &g, const ImgScalars &sc) {
+__device__ inline void lj_stage(LJGeom<T> &g, const ImgScalars &sc, const BandParams &bp) {
+    if (threadIdx.x == 0) {
+        const LJParams p = *(const LJParams *)bp.pot;
+        g.rc2 = (T)(p.rc * p.rc);
+        g.sig2 = (T)(p.sigma * p.sigma);
+        g.c24 = (T)(24.0 * p.eps / (p.sigma * p.sigma));
+        g.e4 = (T)(4.0 * p.eps);
+        g.ephi = (T)p.ephi_c;
+    }
     if (threadIdx.x < 9) {
         g.bv[threadIdx.x] = (T)sc.bv[threadIdx.x];
         g.dh[threadIdx.x] = (T)sc.dh[threadIdx.x];
@@ -157,8 +166,8 @@ __device__ inline void lj_stage(LJGeom<T> &g, const ImgScalars &sc) {
 // Writes the generalised atom force F D^T of slot t (row vector times D^T)
 // and the tile's energy, virial and pair-count partials.
 template <typename T>
-__device__ inline void lj_finish(const LJAcc<T> &A, const LJParams &p, const LJGeom<T> &g,
-                                 BandDev &b, const Tile &tl, int t, bool active) {
+__device__ inline void lj_finish(const LJAcc<T> &A, const LJGeom<T> &g, BandDev &b,
+                                 const Tile &tl, int t, bool active) {
     if (active) {
         const T g0 = A.fx * g.D[0] + A.fy * g.D[1] + A.fz * g.D[2];
         const T g1 = A.fx * g.D[3] + A.fy * g.D[4] + A.fz * g.D[5];
@@ -169,26 +178,19 @@ __device__ inline void lj_finish(const LJAcc<T> &A, const LJParams &p, const LJG
         F[1] = g1;
         F[2] = g2;
     }
-    // U_i = 1/2 sum_j [4 eps (sr12 - sr6) - phi(rc)];  V = -1/2 sum r (x) f
-    T acc[8];
-    acc[0] = (T)0.5 * ((T)(4.0 * p.eps) * A.e - (T)p.ephi_c * (T)A.cnt);
+    // U_i = 1/2 sum_j [4 eps (sr12 - sr6) - phi(rc)];  V = -1/2 sum r (x) f,
+    // written as the symmetric virial in row-major order
+    T acc[12];
+    acc[0] = (T)0.5 * (g.e4 * A.e - g.ephi * (T)A.cnt);
     acc[1] = (T)(-0.5) * A.v00;
-    acc[2] = (T)(-0.5) * A.v01;
-    acc[3] = (T)(-0.5) * A.v02;
-    acc[4] = (T)(-0.5) * A.v11;
-    acc[5] = (T)(-0.5) * A.v12;
-    acc[6] = (T)(-0.5) * A.v22;
-    acc[7] = (T)A.cnt;
-    double r8[8];
-    block_sum_t<8, T>(acc, r8);
-    // symmetric virial, row-major
-    const double tot[11] = {r8[0], r8[1], r8[2], r8[3], r8[2], r8[4], r8[5],
-                            r8[3], r8[5], r8[6], r8[7]};
-    if (threadIdx.x == 0) {
-        double *part = b.atom_part + ((size_t)tl.img * b.atpi + tl.t) * NPART;
-        for (int k = 0; k < 11; ++k) part[k] = tot[k];
-        part[11] = 0.0;
-    }
+    acc[2] = acc[4] = (T)(-0.5) * A.v01;
+    acc[3] = acc[7] = (T)(-0.5) * A.v02;
+    acc[5] = (T)(-0.5) * A.v11;
+    acc[6] = acc[8] = (T)(-0.5) * A.v12;
+    acc[9] = (T)(-0.5) * A.v22;
+    acc[10] = (T)A.cnt;
+    acc[11] = (T)0;
+    block_sum_store<12, T>(acc, b.atom_part + ((size_t)tl.img * b.atpi + tl.t) * NPART);
 }
 
 // Direct path (bands without a neighbour list: no skin, or more atoms per
@@ -201,16 +203,15 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 8 : 4) k_lj(const Tile 
     BandDev &b = bands[tl.band];
     if (b.lj_cap > 0) return;  // uniform over the block: the list path runs
     const ImgScalars &sc = b.sc[tl.img];
-    const LJParams p = *(const LJParams *)b.bp->pot;
     __shared__ LJGeom<T> g;
-    lj_stage(g, sc);
+    lj_stage(g, sc, *b.bp);
     __syncthreads();
     const int n = b.n;
     const int t = tl.t * TILE + threadIdx.x;
     const size_t base = (size_t)tl.img * n;
     const T4 *off = (const T4 *)b.slot_off + base;
     const int *start = b.bin_start + (size_t)tl.img * (b.nbins_cap + 1);
-    const T rc2 = (T)(p.rc * p.rc), sig2 = (T)(p.sigma * p.sigma), eps24 = (T)(24.0 * p.eps);
+    const T rc2 = g.rc2, sig2 = g.sig2, c24 = g.c24;
     LJAcc<T> A;
     if (t < n) {
         const T4 oi = off[t];
@@ -218,10 +219,10 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 8 : 4) k_lj(const Tile 
                    [&](int, T ux, T uy, T uz, int, int) {
                        const T r2 = ux * ux + uy * uy + uz * uz;
                        // r2 == 0 only for the atom itself at zero shift
-                       if (r2 < rc2 && r2 > (T)0) A.pair(ux, uy, uz, sig2, eps24);
+                       if (r2 < rc2 && r2 > (T)0) A.pair(ux, uy, uz, r2, sig2, c24);
                    });
     }
-    lj_finish(A, p, g, b, tl, t, t < n);
+    lj_finish(A, g, b, tl, t, t < n);
 }
 
 // Neighbour list of a rebuilt image (bands with a skin): one thread per atom
@@ -237,9 +238,8 @@ __global__ void __launch_bounds__(TILE) k_lj_list(const Tile *tiles, BandDev *ba
     BandDev &b = bands[tl.band];
     const ImgScalars &sc = b.sc[tl.img];
     if (b.lj_cap == 0 || !sc.rebuild) return;  // uniform over the block
-    const LJParams p = *(const LJParams *)b.bp->pot;
     __shared__ LJGeom<T> g;
-    lj_stage(g, sc);
+    lj_stage(g, sc, *b.bp);
     __syncthreads();
     const int n = b.n, cap = b.lj_cap;
     const int t = tl.t * TILE + threadIdx.x;
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(TILE) k_lj_list(const Tile *tiles, BandDev *ba
     const T4 *off = (const T4 *)b.slot_off + base;
     const int *start = b.bin_start + (size_t)tl.img * (b.nbins_cap + 1);
     uint32_t *L = (uint32_t *)b.nbr_slot + (size_t)tl.img * cap * n + t;
-    const T rc2 = (T)(p.rc * p.rc);
+    const T rc2 = g.rc2;
     // a 1e-5 relative margin over rl^2: the list-reuse test leaves the same
     const T screen = (T)(b.bp->rl * b.bp->rl) * (T)1.00001;
     // the atom itself: slot t at zero offset and wrap
@@ -273,16 +273,21 @@ __global__ void __launch_bounds__(TILE) k_lj_list(const Tile *tiles, BandDev *ba
         b.nbr_cnt[base + t] = 0;
         return;
     }
-    // the shell block [cap - nsh, cap) moves down behind the inner entries
+    // the shell block [cap - nsh, cap) moves down behind the inner entries,
+    // and the atom itself pads the list to a whole number of LJ_UNROLL
+    // entries (cap is a multiple of 8; the pair term skips r = 0)
     for (int k = 0; k < nsh; ++k) L[(size_t)(nin + k) * n] = L[(size_t)(cap - nsh + k) * n];
-    b.nbr_cnt[base + t] = total;
+    const int padded = (total + LJ_UNROLL - 1) / LJ_UNROLL * LJ_UNROLL;
+    for (int k = total; k < padded; ++k) L[(size_t)k * n] = self;
+    b.nbr_cnt[base + t] = padded;
 }
 
 // List path: F_i, U_i and the virial from slot t's list entries.  The pair
 // vector of an entry is (o_j - o_i) + c with c the displacement of the
 // bin centres and wrap, c = C01[i0 + LJ_AXIS i1] + C2[i2] from per-axis
 // tables of the image's current bin vectors built by each block in shared
-// memory.  Entries are taken three at a time with their loads issued first.
+// memory.  Entries are taken LJ_UNROLL at a time (lists are padded to a
+// multiple of it), every load of a group issued before its arithmetic.
 template <typename T>
 __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 8 : 4) k_lj_nbr(const Tile *tiles, BandDev *bands) {
     using T4 = typename Vec4<T>::type;
@@ -290,11 +295,10 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 8 : 4) k_lj_nbr(const T
     BandDev &b = bands[tl.band];
     if (b.lj_cap == 0) return;  // uniform over the block: the direct path runs
     const ImgScalars &sc = b.sc[tl.img];
-    const LJParams p = *(const LJParams *)b.bp->pot;
     __shared__ LJGeom<T> g;
     __shared__ T4 s_c01[LJ_AXIS * LJ_AXIS];
     __shared__ T4 s_c2[32];
-    lj_stage(g, sc);
+    lj_stage(g, sc, *b.bp);
     __syncthreads();
     {
         const int L0 = 2 * (2 * g.m[0] + 1), L1 = 2 * (2 * g.m[1] + 1), L2 = 2 * (2 * g.m[2] + 1);
@@ -326,34 +330,32 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 8 : 4) k_lj_nbr(const T
     const int t = tl.t * TILE + threadIdx.x;
     const size_t base = (size_t)tl.img * n;
     const T4 *off = (const T4 *)b.slot_off + base;
-    const T rc2 = (T)(p.rc * p.rc), sig2 = (T)(p.sigma * p.sigma), eps24 = (T)(24.0 * p.eps);
+    const T rc2 = g.rc2, sig2 = g.sig2, c24 = g.c24;
     LJAcc<T> A;
     if (t < n) {
         const uint32_t *L = (const uint32_t *)b.nbr_slot + (size_t)tl.img * cap * n + t;
-        const int cnt = b.nbr_cnt[base + t];
+        const int cnt = b.nbr_cnt[base + t];  // a multiple of LJ_UNROLL
         const T4 oi = off[t];
-        // padding entries point at the atom itself (r2 = 0: no term)
-        const uint32_t self = lj_entry(t, 2 * g.m[0] + LJ_AXIS * 2 * g.m[1], 2 * g.m[2]);
-        constexpr int U = 3;
-        for (int k0 = 0; k0 < cnt; k0 += U) {
-            uint32_t e[U];
+        for (int k = 0; k < cnt; k += LJ_UNROLL, L += (size_t)LJ_UNROLL * n) {
+            uint32_t e[LJ_UNROLL];
 #pragma unroll
-            for (int u = 0; u < U; ++u) e[u] = k0 + u < cnt ? L[(size_t)(k0 + u) * n] : self;
-            T4 oj[U];
+            for (int u = 0; u < LJ_UNROLL; ++u) e[u] = L[(size_t)u * n];
+            T4 oj[LJ_UNROLL];
 #pragma unroll
-            for (int u = 0; u < U; ++u) oj[u] = off[e[u] & 0x1FFFFu];
+            for (int u = 0; u < LJ_UNROLL; ++u) oj[u] = off[e[u] & 0x1FFFFu];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
+            for (int u = 0; u < LJ_UNROLL; ++u) {
                 const T4 a = s_c01[(e[u] >> 17) & 1023u], c = s_c2[e[u] >> 27];
                 const T ux = (oj[u].x - oi.x) + (a.x + c.x);
                 const T uy = (oj[u].y - oi.y) + (a.y + c.y);
                 const T uz = (oj[u].z - oi.z) + (a.z + c.z);
                 const T r2 = ux * ux + uy * uy + uz * uz;
-                if (r2 < rc2 && r2 > (T)0) A.pair(ux, uy, uz, sig2, eps24);
+                // r2 == 0: a padding entry (the atom itself)
+                if (r2 < rc2 && r2 > (T)0) A.pair(ux, uy, uz, r2, sig2, c24);
             }
         }
     }
-    lj_finish(A, p, g, b, tl, t, t < n);
+    lj_finish(A, g, b, tl, t, t < n);
 }
 
 template <typename T>

@@ -450,12 +450,7 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 7 : 1) k_ters_partials(
     for (int k = 0; k < 9; ++k) acc[1 + k] = vir[k];
     acc[10] = (T)nin;
     acc[11] = (T)(nin * (nin - 1));
-    double tot[12];
-    block_sum_t<12, T>(acc, tot);
-    if (threadIdx.x == 0) {
-        double *part = b.atom_part + ((size_t)tl.img * b.atpi + tl.t) * NPART;
-        for (int k = 0; k < 12; ++k) part[k] = tot[k];
-    }
+    block_sum_store<12, T>(acc, b.atom_part + ((size_t)tl.img * b.atpi + tl.t) * NPART);
 }
 
 // Reverse entries of a rebuilt list: for entry k of slot t (neighbour slot
