@@ -287,9 +287,12 @@ __global__ void __launch_bounds__(TILE) k_lj_list(const Tile *tiles, BandDev *ba
 // bin centres and wrap, c = C01[i0 + LJ_AXIS i1] + C2[i2] from per-axis
 // tables of the image's current bin vectors built by each block in shared
 // memory.  Entries are taken LJ_UNROLL at a time (lists are padded to a
-// multiple of it), every load of a group issued before its arithmetic.
+// multiple of it): a group's offsets are gathered and the next group's
+// entries loaded before the group's arithmetic, so a list load's latency
+// overlaps a whole group of pair terms (7 blocks per SM leave the registers
+// for it: measured faster than 8 without the overlap).
 template <typename T>
-__global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 8 : 4) k_lj_nbr(const Tile *tiles, BandDev *bands) {
+__global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 7 : 4) k_lj_nbr(const Tile *tiles, BandDev *bands) {
     using T4 = typename Vec4<T>::type;
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
@@ -336,13 +339,18 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 8 : 4) k_lj_nbr(const T
         const uint32_t *L = (const uint32_t *)b.nbr_slot + (size_t)tl.img * cap * n + t;
         const int cnt = b.nbr_cnt[base + t];  // a multiple of LJ_UNROLL
         const T4 oi = off[t];
-        for (int k = 0; k < cnt; k += LJ_UNROLL, L += (size_t)LJ_UNROLL * n) {
-            uint32_t e[LJ_UNROLL];
+        uint32_t e[LJ_UNROLL];  // the current group's entries
 #pragma unroll
-            for (int u = 0; u < LJ_UNROLL; ++u) e[u] = L[(size_t)u * n];
+        for (int u = 0; u < LJ_UNROLL; ++u) e[u] = cnt > 0 ? L[(size_t)u * n] : 0u;
+        for (int k = 0; k < cnt; k += LJ_UNROLL) {
+            L += (size_t)LJ_UNROLL * n;
             T4 oj[LJ_UNROLL];
 #pragma unroll
             for (int u = 0; u < LJ_UNROLL; ++u) oj[u] = off[e[u] & 0x1FFFFu];
+            uint32_t en[LJ_UNROLL];
+            const bool more = k + LJ_UNROLL < cnt;
+#pragma unroll
+            for (int u = 0; u < LJ_UNROLL; ++u) en[u] = more ? L[(size_t)u * n] : 0u;
 #pragma unroll
             for (int u = 0; u < LJ_UNROLL; ++u) {
                 const T4 a = s_c01[(e[u] >> 17) & 1023u], c = s_c2[e[u] >> 27];
@@ -353,6 +361,8 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 8 : 4) k_lj_nbr(const T
                 // r2 == 0: a padding entry (the atom itself)
                 if (r2 < rc2 && r2 > (T)0) A.pair(ux, uy, uz, r2, sig2, c24);
             }
+#pragma unroll
+            for (int u = 0; u < LJ_UNROLL; ++u) e[u] = en[u];
         }
     }
     lj_finish(A, g, b, tl, t, t < n);
