@@ -249,8 +249,9 @@ def run_reference(args, wl_name):
 
 def traffic_for(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summaries
-    (profiles/*.md rows "| kernel | source.cu | sha256_16 | bytes |"), or
-    None when the kernel's source changed since the capture."""
+    (profiles/*.md rows "| kernel | source.cu | sha256_16 | bytes |", the
+    hash over the source file followed by common.cuh), or None when either
+    changed since the capture."""
     import glob
     import hashlib
     for md in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
@@ -259,9 +260,10 @@ def traffic_for(kernel):
                 cells = [c.strip() for c in line.strip().strip("|").split("|")]
                 if len(cells) != 4 or cells[0] != kernel or not cells[1].endswith(".cu"):
                     continue
-                src = os.path.join(ROOT, "paper_2510_16721_gb300", "csrc", cells[1])
-                with open(src, "rb") as s:
-                    h = hashlib.sha256(s.read()).hexdigest()[:16]
+                csrc = os.path.join(ROOT, "paper_2510_16721_gb300", "csrc")
+                with open(os.path.join(csrc, cells[1]), "rb") as s, \
+                        open(os.path.join(csrc, "common.cuh"), "rb") as c:
+                    h = hashlib.sha256(s.read() + c.read()).hexdigest()[:16]
                 if h != cells[2]:
                     return None
                 try:

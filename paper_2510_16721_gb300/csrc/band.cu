@@ -182,8 +182,11 @@ __global__ void __launch_bounds__(TILE) k_neb_force(const Tile *tiles, BandDev *
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
     T acc[4] = {0, 0, 0, 0};  // F.v, F.F, v.v, largest row |F|^2 (fmax)
-    const ImgScalars &sc = b.sc[tl.img];
-    const T ca = (T)sc.coef[0], cb = (T)sc.coef[1];
+    // coefficients in T, converted once per block
+    __shared__ T s_coef[2];
+    if (threadIdx.x < 2) s_coef[threadIdx.x] = (T)b.sc[tl.img].coef[threadIdx.x];
+    __syncthreads();
+    const T ca = s_coef[0], cb = s_coef[1];
     const size_t stride = (size_t)b.rows * 3;
     const size_t o0 = tl.img * stride + ((size_t)tl.t * RTILE + threadIdx.x) * 3;
     const T *__restrict__ X0 = (const T *)b.X + o0;
@@ -307,8 +310,17 @@ __global__ void __launch_bounds__(TILE) k_fire_update(const Tile *tiles, BandDev
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
     const BandParams *bp = b.bp;
-    if (!bp->move) return;
-    const T cv = (T)bp->cv, cf = (T)bp->cf, dt = (T)bp->dt, ms = (T)bp->maxstep;
+    if (!bp->move) return;  // uniform over the block
+    // FIRE scalars in T, converted once per block
+    __shared__ T s_k[4];
+    if (threadIdx.x == 0) {
+        s_k[0] = (T)bp->cv;
+        s_k[1] = (T)bp->cf;
+        s_k[2] = (T)bp->dt;
+        s_k[3] = (T)bp->maxstep;
+    }
+    __syncthreads();
+    const T cv = s_k[0], cf = s_k[1], dt = s_k[2], ms = s_k[3];
     const size_t o0 = (tl.img * (size_t)b.rows + (size_t)tl.t * RTILE + threadIdx.x) * 3;
     T *__restrict__ X = (T *)b.X + o0;
     T *__restrict__ V = (T *)b.v + o0;

@@ -118,6 +118,7 @@ __device__ void bin_geometry(const BandParams *bp, int nbins_cap, const double *
         for (int c = 0; c < 3; ++c) {
             const double v = q * rint(h[3 * a + c] * inb[a] * iq);
             sc.bv[3 * a + c] = v;
+            sc.bvf[3 * a + c] = (float)v;
             sc.dh[3 * a + c] = h[3 * a + c] - nb[a] * v;
         }
     }
@@ -398,7 +399,7 @@ __device__ inline void refresh_offset(const ImgScalars &sc, const BandParams *, 
         F2 K = {0.0f, 0.0f};
         for (int a = 0; a < 3; ++a) {
             K = f2_add(K, f2_mul((float)wr[a], hh[3 * a + c], hl[3 * a + c]));
-            K = f2_add(K, f2_mul((float)bi[a] + 0.5f, (float)sc.bv[3 * a + c], 0.0f));
+            K = f2_add(K, f2_mul((float)bi[a] + 0.5f, sc.bvf[3 * a + c], 0.0f));
         }
         const F2 d = f2_add(R, {-K.hi, -K.lo});
         off[0][c] = d.hi;
@@ -486,7 +487,7 @@ __global__ void __launch_bounds__(TILE) k_bin_assign(const Tile *tiles, BandDev 
     refresh_offset(sc, bp, Xi, wrap, bi, o, lo);
     ((T4 *)b.atom_off)[ai] = o;
     ((T4 *)b.atom_off_lo)[ai] = lo;
-    if (bp->skin > 0.0) {  // reference state of the build
+    if (b.ref_X) {  // a skin: reference state of the build
         T4 x;
         x.x = Xi[0];
         x.y = Xi[1];
@@ -503,7 +504,7 @@ __global__ void __launch_bounds__(TILE) k_skin_check(const Tile *tiles, BandDev 
     using T4 = typename Vec4<T>::type;
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
-    if (b.bp->skin <= 0.0) return;  // uniform over the block
+    if (!b.ref_X) return;  // no skin (uniform over the block)
     const int i = tl.t * TILE + threadIdx.x;
     T d2 = (T)0;
     if (i < b.n) {

@@ -60,6 +60,7 @@ struct ImgScalars {
     long long builds;    // cell-list builds of this image slot
     long long evals;     // evaluations of this image slot
     float dfl[45];       // FP32: D hi, D lo, h hi, h lo (pairs), h0^-1 (cell list)
+    float bvf[9];        // bv in FP32 (exact: bv has at most 20 significant bits)
     int nb[3];           // bins per axis
     int m[3];            // stencil half width per axis
     int nbins;

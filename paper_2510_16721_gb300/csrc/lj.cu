@@ -140,6 +140,7 @@ template <typename T>
 struct LJGeom {
     T bv[9], dh[9], D[9];
     T rc2, sig2, c24, e4, ephi;   // rc^2, sigma^2, 24 eps / sigma^2, 4 eps, phi(rc)
+    T screen;                     // list screen: rl^2 with a 1e-5 relative margin
     int nb[3], m[3];
 };
 template <typename T>
@@ -151,6 +152,8 @@ __device__ inline void lj_stage(LJGeom<T> &g, const ImgScalars &sc, const BandPa
         g.c24 = (T)(24.0 * p.eps / (p.sigma * p.sigma));
         g.e4 = (T)(4.0 * p.eps);
         g.ephi = (T)p.ephi_c;
+        // the list-reuse test leaves the same 1e-5 relative margin
+        g.screen = (T)(bp.rl * bp.rl) * (T)1.00001;
     }
     if (threadIdx.x < 9) {
         g.bv[threadIdx.x] = (T)sc.bv[threadIdx.x];
@@ -248,9 +251,7 @@ __global__ void __launch_bounds__(TILE) k_lj_list(const Tile *tiles, BandDev *ba
     const T4 *off = (const T4 *)b.slot_off + base;
     const int *start = b.bin_start + (size_t)tl.img * (b.nbins_cap + 1);
     uint32_t *L = (uint32_t *)b.nbr_slot + (size_t)tl.img * cap * n + t;
-    const T rc2 = g.rc2;
-    // a 1e-5 relative margin over rl^2: the list-reuse test leaves the same
-    const T screen = (T)(b.bp->rl * b.bp->rl) * (T)1.00001;
+    const T rc2 = g.rc2, screen = g.screen;
     // the atom itself: slot t at zero offset and wrap
     const uint32_t self =
         lj_entry(t, 2 * g.m[0] + LJ_AXIS * 2 * g.m[1], 2 * g.m[2]);

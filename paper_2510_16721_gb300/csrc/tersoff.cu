@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(TILE) k_ters_list(const Tile *tiles, BandDev *
     BandDev &b = bands[tl.band];
     const ImgScalars &sc = b.sc[tl.img];
     if (!sc.rebuild) return;  // uniform over the block
-    __shared__ T s_bv[9], s_dh[9];
+    __shared__ T s_bv[9], s_dh[9], s_rl2;
     __shared__ int s_nb[3], s_m[3];
     if (threadIdx.x < 9) {
         s_bv[threadIdx.x] = (T)sc.bv[threadIdx.x];
@@ -362,12 +362,15 @@ __global__ void __launch_bounds__(TILE) k_ters_list(const Tile *tiles, BandDev *
         s_nb[threadIdx.x] = sc.nb[threadIdx.x];
         s_m[threadIdx.x] = sc.m[threadIdx.x];
     }
+    if (threadIdx.x == 0) {  // FP64 work once per block, not per thread
+        const double rl = b.bp->rl > 0.0 ? b.bp->rl : b.bp->rc;
+        s_rl2 = (T)(rl * rl);
+    }
     __syncthreads();
     const int n = b.n;
     const int t = tl.t * TILE + threadIdx.x;
     if (t >= n) return;
-    const double rl = b.bp->rl > 0.0 ? b.bp->rl : b.bp->rc;
-    const int total = ters_collect_list<T>((T)(rl * rl), b, tl.img, t, s_bv, s_dh, s_nb, s_m);
+    const int total = ters_collect_list<T>(s_rl2, b, tl.img, t, s_bv, s_dh, s_nb, s_m);
     b.nbr_cnt[(size_t)tl.img * n + t] = total < MAXN_TERSOFF ? total : MAXN_TERSOFF;
     if (total > MAXN_TERSOFF) atomicOr(&b.bp->status, ST_NBR_OVERFLOW);
 }
@@ -487,10 +490,14 @@ template <typename T>
 __global__ void __launch_bounds__(TILE) k_ters_gather(const Tile *tiles, BandDev *bands) {
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
+    // D in T, converted once per block (a conversion from FP64 is an FP64
+    // instruction: per thread they would dominate this short kernel)
+    __shared__ T s_D[9];
+    if (threadIdx.x < 9) s_D[threadIdx.x] = (T)b.sc[tl.img].D[threadIdx.x];
+    __syncthreads();
     const int n = b.n;
     const int t = tl.t * TILE + threadIdx.x;
     if (t >= n) return;
-    const ImgScalars &sc = b.sc[tl.img];
     const size_t base = (size_t)tl.img * n;
     const int *nslot = b.nbr_slot + (size_t)tl.img * MAXN_TERSOFF * n;
     const unsigned char *nrev = b.nbr_rev + (size_t)tl.img * MAXN_TERSOFF * n;
@@ -530,9 +537,9 @@ __global__ void __launch_bounds__(TILE) k_ters_gather(const Tile *tiles, BandDev
             fz -= nP[(size_t)(3 * r + 2) * n + q];
         }
     }
-    const T g0 = fx * (T)sc.D[0] + fy * (T)sc.D[1] + fz * (T)sc.D[2];
-    const T g1 = fx * (T)sc.D[3] + fy * (T)sc.D[4] + fz * (T)sc.D[5];
-    const T g2 = fx * (T)sc.D[6] + fy * (T)sc.D[7] + fz * (T)sc.D[8];
+    const T g0 = fx * s_D[0] + fy * s_D[1] + fz * s_D[2];
+    const T g1 = fx * s_D[3] + fy * s_D[4] + fz * s_D[5];
+    const T g2 = fx * s_D[6] + fy * s_D[7] + fz * s_D[8];
     const int atom = b.slot_atom[base + t];
     T *F = (T *)b.F + ((size_t)tl.img * b.rows + atom) * 3;
     F[0] = g0;
