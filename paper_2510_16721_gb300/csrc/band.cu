@@ -29,56 +29,41 @@ template <typename T>
 __global__ void k_image_finalize(const ImgRef *imgs, BandDev *bands) {
     ImgRef r = imgs[blockIdx.x];
     BandDev &b = bands[r.band];
-    __shared__ BandParams s_bp;
-    __shared__ ImgScalars s_sc;
-    stage_copy(&s_bp, b.bp);
-    stage_copy(&s_sc, &b.sc[r.img]);  // read-only copy; results go to global
-    const BandParams *bp = &s_bp;
+    const BandParams *bp = b.bp;
     ImgScalars &sc = b.sc[r.img];
-    const ImgScalars &sci = s_sc;
-    const double *part = b.atom_part + (size_t)r.img * b.atpi * NPART;
-    double v[12], s[12];
-    for (int k = 0; k < 12; ++k) v[k] = 0.0;
-    for (int t = threadIdx.x; t < b.atpi; t += blockDim.x)
-        for (int k = 0; k < 12; ++k) v[k] += part[(size_t)t * NPART + k];
-    block_sum_any<12>(v, s);
-    if (threadIdx.x != 0) return;
-    sc.pairs = s[10];
-    sc.triples = s[11];
-    double U = s[0];
-    double V[9];
-    for (int k = 0; k < 9; ++k) V[k] = s[1 + k];
-    double E = U;
-    if (bp->pressure != 0.0) {
-        E += bp->pressure * sci.omega;
-        for (int a = 0; a < 3; ++a) V[4 * a] -= bp->pressure * sci.omega;
+    // U, V (9), pairs, triples: tile partials summed in FP64, fixed order
+    __shared__ double s_tot[12];
+    const double tk =
+        block_sum_records<12, 16>(b.atom_part + (size_t)r.img * b.atpi * NPART, NPART, b.atpi);
+    if (threadIdx.x < 12) s_tot[threadIdx.x] = tk;
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
+    // warp 0: the 3x3 work lane-parallel (lane l holds entry (l / 3, l % 3))
+    const Lane3 p;
+    const int lane = threadIdx.x;
+    const double P = bp->pressure, omega = sc.omega;
+    double V = s_tot[1 + p.l];
+    if (P != 0.0 && p.i == p.j) V -= P * omega;
+    if (lane == 0) {
+        sc.pairs = s_tot[10];
+        sc.triples = s_tot[11];
+        sc.U = s_tot[0];
+        sc.E = P != 0.0 ? s_tot[0] + P * omega : s_tot[0];
     }
-    sc.U = U;
-    sc.E = E;
-    for (int k = 0; k < 9; ++k) sc.V[k] = V[k];
-    double Phi[9];
-    if (!bp->filter) {
-        for (int k = 0; k < 9; ++k) Phi[k] = 0.0;
-    } else {
-        const double *Di = sci.Dinv;
-        double DiT[9];
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j) DiT[3 * i + j] = Di[3 * j + i];
-        double tmp[9];
+    if (lane < 9) sc.V[lane] = V;
+    double Phi = 0.0;
+    if (bp->filter) {
+        const double Di = sc.Dinv[p.l];
+        const double DiT = ltrans(Di, p);
         if (bp->variant == 0) {
-            double Vs[9];
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) Vs[3 * i + j] = 0.5 * (V[3 * i + j] + V[3 * j + i]);
-            matmul3(DiT, Vs, tmp);
-            matmul3(tmp, Di, Phi);
-            for (int k = 0; k < 9; ++k) Phi[k] *= 0.5 / bp->c;
+            const double Vs = 0.5 * (V + ltrans(V, p));
+            Phi = lmul(lmul(DiT, Vs, p), Di, p) * (0.5 * rcp64(bp->c));
         } else {
-            matmul3(DiT, V, Phi);
-            for (int k = 0; k < 9; ++k) Phi[k] /= bp->c;
+            Phi = lmul(DiT, V, p) * rcp64(bp->c);
         }
     }
     T *F = (T *)b.F + ((size_t)r.img * b.rows + b.n) * 3;
-    for (int k = 0; k < 9; ++k) F[k] = (T)Phi[k];
+    if (lane < 9) F[lane] = (T)Phi;
 }
 
 template <typename T>
@@ -113,13 +98,9 @@ __global__ void __launch_bounds__(TILE) k_band_dots(const Tile *tiles, BandDev *
 __global__ void k_dots_reduce(const ImgRef *imgs, BandDev *bands) {
     ImgRef r = imgs[blockIdx.x];
     BandDev &b = bands[r.band];
-    const double *part = b.row_part + (size_t)r.img * b.rtpi * NPART;
-    double v[5] = {0, 0, 0, 0, 0}, s[5];
-    for (int t = threadIdx.x; t < b.rtpi; t += blockDim.x)
-        for (int k = 0; k < 5; ++k) v[k] += part[(size_t)t * NPART + k];
-    block_sum_any<5>(v, s);
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 5; ++k) b.sc[r.img].dots[k] = s[k];
+    const double tk =
+        block_sum_records<5, 16>(b.row_part + (size_t)r.img * b.rtpi * NPART, NPART, b.rtpi);
+    if (threadIdx.x < 5) b.sc[r.img].dots[threadIdx.x] = tk;
 }
 
 // one block (one thread per image) per band
@@ -289,18 +270,28 @@ __global__ void k_fire_scalars(const int *band_ids, BandDev *bands) {
     // thread, then a fixed-order block sum
     const int nt = (N - 2) * b.rtpi;
     const double *part0 = b.row_part + (size_t)b.rtpi * NPART;
-    double v[3] = {0, 0, 0}, tot[4];
-    double m = 0.0;
-    for (int q = threadIdx.x; q < nt; q += blockDim.x) {
-        const double *p = part0 + (size_t)q * NPART;
-        v[0] += p[5];
-        v[1] += p[6];
-        v[2] += p[7];
-        m = fmax(m, p[8]);
+    // F.v, F.F, v.v summed, the largest row |F|^2 taken, each over 32 fixed
+    // strided subsets and then in subset order (few FP64 instructions)
+    constexpr int G = 32;
+    __shared__ double s_part[G * 4], s_tot[4];
+    if (threadIdx.x < 4 * G) {
+        const int k = threadIdx.x % 4, g = threadIdx.x / 4;
+        double v = 0.0;
+        for (int q = g; q < nt; q += G) {
+            const double x = part0[(size_t)q * NPART + 5 + k];
+            v = k == 3 ? fmax(v, x) : v + x;
+        }
+        s_part[g * 4 + k] = v;
     }
-    block_sum_any<3>(v, tot);
-    tot[3] = block_max_any(m);
-    if (threadIdx.x == 0) fire_logic(&s_bp, tot);
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        const int k = threadIdx.x;
+        double v = 0.0;
+        for (int g = 0; g < G; ++g) v = k == 3 ? fmax(v, s_part[g * 4 + k]) : v + s_part[g * 4 + k];
+        s_tot[k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) fire_logic(&s_bp, s_tot);
     __syncthreads();
     stage_copy(b.bp, &s_bp);
 }

@@ -197,39 +197,6 @@ __device__ void skin_decide_one(const BandParams *bp, int nbins_cap, ImgScalars 
     sc.evals += 1;
 }
 
-// ---- lane-parallel 3x3 algebra for the map-back -------------------------
-//
-// One warp per image: lane l holds entry (i, j) = (l / 3, l % 3) of each
-// 3x3 matrix (lanes 9..31 mirror lane l % 9; their results are unused).  A
-// product is then 6 shuffles and a chain of 3 FP64 operations per lane
-// instead of 27 dependent-heavy operations in one thread: the map-back is on
-// the critical path of every step and FP64 latency (~64 cycles) dominates it.
-struct Lane3 {
-    int l, i, j;
-    __device__ Lane3() : l((int)(threadIdx.x & 31) % 9), i(l / 3), j(l % 3) {}
-    __device__ double eye() const { return i == j ? 1.0 : 0.0; }
-};
-__device__ inline double lget(double a, int src) { return __shfl_sync(0xffffffffu, a, src); }
-// (A B)_ij = sum_k A_ik B_kj
-__device__ inline double lmul(double a, double b, const Lane3 &p) {
-    const double a0 = lget(a, 3 * p.i), a1 = lget(a, 3 * p.i + 1), a2 = lget(a, 3 * p.i + 2);
-    const double b0 = lget(b, p.j), b1 = lget(b, 3 + p.j), b2 = lget(b, 6 + p.j);
-    return fma(a2, b2, fma(a1, b1, a0 * b0));
-}
-__device__ inline double ltrans(double a, const Lane3 &p) { return lget(a, 3 * p.j + p.i); }
-// cofactor C_ij = A_{i+1,j+1} A_{i+2,j+2} - A_{i+1,j+2} A_{i+2,j+1}
-__device__ inline double lcof(double a, const Lane3 &p) {
-    const int i1 = (p.i + 1) % 3, i2 = (p.i + 2) % 3, j1 = (p.j + 1) % 3, j2 = (p.j + 2) % 3;
-    const double p11 = lget(a, 3 * i1 + j1), p22 = lget(a, 3 * i2 + j2);
-    const double p12 = lget(a, 3 * i1 + j2), p21 = lget(a, 3 * i2 + j1);
-    return fma(p11, p22, -(p12 * p21));
-}
-// det A = sum_j A_0j C_0j, in every lane
-__device__ inline double ldet(double a, double c) {
-    const double t = a * c;
-    return lget(t, 0) + lget(t, 1) + lget(t, 2);
-}
-
 // Map-back of one image per warp: B = X_lat / c, D = B^(1/2) (rotation-free,
 // coupled Newton-Schulz as in the header comment) or D = X_lat / c
 // (deformation gradient), then h = h0 D, h^-1 = D^-1 h0^-1 and
@@ -302,12 +269,15 @@ __global__ void __launch_bounds__(32) k_mapback(const ImgRef *imgs, int count, B
     const double h = lmul(bp->h0[p.l], D, p);
     const double hinv = lmul(Di, bp->h0inv[p.l], p);  // (h0 D)^-1 = D^-1 h0^-1
     const double omega = fabs(ldet(h, lcof(h, p)));
-    // largest displacement since the last build (skin > 0)
+    // largest displacement since the last build (skin > 0), in FP32 (a max
+    // is exact in any precision)
     double dmax = 0.0;
-    if (bp->skin > 0.0) {
-        const double *part = b.skin_part + (size_t)r.img * b.atpi;
-        for (int t = lane; t < b.atpi; t += 32) dmax = fmax(dmax, part[t]);
-        dmax = warp_max(dmax);
+    if (b.skin_part) {
+        const float *part = b.skin_part + (size_t)r.img * b.atpi;
+        float m = 0.0f;
+        for (int t = lane; t < b.atpi; t += 32) m = fmaxf(m, part[t]);
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        dmax = (double)m;
     }
     if (lane < 9) {
         sc.D[lane] = D;
@@ -520,7 +490,8 @@ __global__ void __launch_bounds__(TILE) k_skin_check(const Tile *tiles, BandDev 
     if (threadIdx.x == 0) {
         T m = wmax[0];
         for (int q = 1; q < TILE / 32; ++q) m = fmax(m, wmax[q]);
-        b.skin_part[(size_t)tl.img * b.atpi + tl.t] = sqrt64((double)m);
+        // FP32, rounded up: the reuse test never sees a displacement too small
+        b.skin_part[(size_t)tl.img * b.atpi + tl.t] = __fsqrt_ru(to_float_ru(m));
     }
 }
 
@@ -619,15 +590,17 @@ __global__ void __launch_bounds__(1024) k_bin_scanfill(const ImgRef *imgs, BandD
     }
 }
 
-__global__ void __launch_bounds__(TILE) k_bin_scatter(const Tile *tiles, BandDev *bands) {
-    Tile tl = tiles[blockIdx.x];
-    BandDev &b = bands[tl.band];
-    if (!b.sc[tl.img].rebuild) return;
-    int i = tl.t * TILE + threadIdx.x;
-    if (i >= b.n) return;
-    size_t ai = (size_t)tl.img * b.n + i;
-    const int *start = b.bin_start + (size_t)tl.img * (b.nbins_cap + 1);
-    b.slot_unsorted[(size_t)tl.img * b.n + start[b.atom_bin[ai]] + b.atom_rank[ai]] = i;
+__global__ void __launch_bounds__(TILE) k_bin_scatter(const Tile *tiles, int ntiles, BandDev *bands) {
+    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        const Tile tl = tiles[k];
+        BandDev &b = bands[tl.band];
+        if (!b.sc[tl.img].rebuild) continue;
+        const int i = tl.t * TILE + threadIdx.x;
+        if (i >= b.n) continue;
+        const size_t ai = (size_t)tl.img * b.n + i;
+        const int *start = b.bin_start + (size_t)tl.img * (b.nbins_cap + 1);
+        b.slot_unsorted[(size_t)tl.img * b.n + start[b.atom_bin[ai]] + b.atom_rank[ai]] = i;
+    }
 }
 
 // Threads stride over the bins: order each bin's atoms by atom index and
@@ -700,7 +673,7 @@ void launch_bin_scan(const ImgRef *imgs, int count, int max_bins, BandDev *bands
 }
 void launch_bin_scatter(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
     if (ntiles <= 0) return;
-    k_bin_scatter<<<ntiles, TILE, 0, s>>>(tiles, bands);
+    k_bin_scatter<<<ntiles < GATED_GRID ? ntiles : GATED_GRID, TILE, 0, s>>>(tiles, ntiles, bands);
 }
 template <typename T>
 void launch_bin_order(const ImgRef *imgs, int count, int max_bins, BandDev *bands,

@@ -31,6 +31,10 @@ constexpr int MAXN_TERSOFF = 16;    // Tersoff list capacity per atom (entries w
 constexpr int NPART = 12;           // doubles per tile partial record
 constexpr int MAX_STENCIL = 7;      // |delta| <= 7 bins per axis
 constexpr int LJ_LIST_MAX_ATOMS = 1 << 17;  // LJ list entries index 17-bit slots
+// Grid of the kernels that only do work for images rebuilding their lists:
+// a fixed grid strides over the tiles, so a step in which most images keep
+// their lists costs a few reads per block instead of a block per tile.
+constexpr int GATED_GRID = 152 * 8;
 
 // device status bits (BandParams::status)
 enum : int {
@@ -158,7 +162,7 @@ struct BandDev {
     // neighbour-list reuse: positions and periodic wraps at the last build
     void *ref_X;         // [ncap][n] x 4 T: R~ at the build (atom order)
     int *atom_wrap;      // [ncap][n][3]: floor(s) at the build
-    double *skin_part;   // [ncap][atpi]: per-tile max displacement
+    float *skin_part;    // [ncap][atpi]: per-tile max displacement
     // per-slot neighbour lists: Tersoff (slot, code) pairs of MAXN_TERSOFF
     // entries, or LJ packed entries of lj_cap (0: the LJ kernel walks the
     // cell list directly)
@@ -247,6 +251,9 @@ __host__ __device__ inline int neg_code(int code) {
     return pack_code(-d0, -d1, -d2);
 }
 
+__device__ inline float to_float_ru(float x) { return x; }
+__device__ inline float to_float_ru(double x) { return __double2float_ru(x); }
+
 // deterministic warp sum (fixed butterfly)
 __device__ inline double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -255,6 +262,65 @@ __device__ inline double warp_sum(double v) {
 __device__ inline double warp_max(double v) {
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
+}
+
+// ---- lane-parallel 3x3 algebra (map-back, lattice force) -------------------
+//
+// One warp per image: lane l holds entry (i, j) = (l / 3, l % 3) of each
+// 3x3 matrix (lanes 9..31 mirror lane l % 9; their results are unused).  A
+// product is then 6 shuffles and a chain of 3 FP64 operations per lane
+// instead of 27 dependent-heavy operations in one thread: the map-back is on
+// the critical path of every step and FP64 latency (~64 cycles) dominates it.
+struct Lane3 {
+    int l, i, j;
+    __device__ Lane3() : l((int)(threadIdx.x & 31) % 9), i(l / 3), j(l % 3) {}
+    __device__ double eye() const { return i == j ? 1.0 : 0.0; }
+};
+__device__ inline double lget(double a, int src) { return __shfl_sync(0xffffffffu, a, src); }
+// (A B)_ij = sum_k A_ik B_kj
+__device__ inline double lmul(double a, double b, const Lane3 &p) {
+    const double a0 = lget(a, 3 * p.i), a1 = lget(a, 3 * p.i + 1), a2 = lget(a, 3 * p.i + 2);
+    const double b0 = lget(b, p.j), b1 = lget(b, 3 + p.j), b2 = lget(b, 6 + p.j);
+    return fma(a2, b2, fma(a1, b1, a0 * b0));
+}
+__device__ inline double ltrans(double a, const Lane3 &p) { return lget(a, 3 * p.j + p.i); }
+// cofactor C_ij = A_{i+1,j+1} A_{i+2,j+2} - A_{i+1,j+2} A_{i+2,j+1}
+__device__ inline double lcof(double a, const Lane3 &p) {
+    const int i1 = (p.i + 1) % 3, i2 = (p.i + 2) % 3, j1 = (p.j + 1) % 3, j2 = (p.j + 2) % 3;
+    const double p11 = lget(a, 3 * i1 + j1), p22 = lget(a, 3 * i2 + j2);
+    const double p12 = lget(a, 3 * i1 + j2), p21 = lget(a, 3 * i2 + j1);
+    return fma(p11, p22, -(p12 * p21));
+}
+// det A = sum_j A_0j C_0j, in every lane
+__device__ inline double ldet(double a, double c) {
+    const double t = a * c;
+    return lget(t, 0) + lget(t, 1) + lget(t, 2);
+}
+
+// FP64 sums of K values over `count` records (value k of record q at
+// rec[q * stride + k]) in a fixed order that needs few FP64 instructions (an
+// FP64 instruction occupies a warp's FP64 pipe for ~64 cycles here, so
+// butterflies over many warps cost more than the sums themselves): thread
+// k + K g (g < G) adds value k of records g, g + G, g + 2G, ... in turn, and
+// thread k (< K) then adds the G partial sums in order and returns total k.
+// Needs blockDim.x >= K G; every thread of the block must call it.
+template <int K, int G>
+__device__ inline double block_sum_records(const double *rec, int stride, int count) {
+    __shared__ double s_part[G * K];
+    const int tid = threadIdx.x;
+    if (tid < K * G) {
+        const int k = tid % K, g = tid / K;
+        double v = 0.0;
+#pragma unroll 4
+        for (int q = g; q < count; q += G) v += rec[(size_t)q * stride + k];
+        s_part[g * K + k] = v;
+    }
+    __syncthreads();
+    double tot = 0.0;
+    if (tid < K)
+        for (int g = 0; g < G; ++g) tot += s_part[g * K + tid];
+    __syncthreads();
+    return tot;
 }
 
 // Sum K per-thread values over a TILE-thread block in FP64 (fixed order);

@@ -773,7 +773,7 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
     if (skin > 0.0) {
         d.ref_X = dalloc(b, na * 4 * b->ts);
         d.atom_wrap = (int *)dalloc(b, na * 3 * sizeof(int));
-        d.skin_part = (double *)dalloc(b, nc * d.atpi * sizeof(double));
+        d.skin_part = (float *)dalloc(b, nc * d.atpi * sizeof(float));
     }
     d.lj_cap = 0;
     if (pot->kind == CFNEB_LJ && skin > 0.0 && n <= LJ_LIST_MAX_ATOMS) {

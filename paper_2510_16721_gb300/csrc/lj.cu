@@ -235,18 +235,9 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 8 : 4) k_lj(const Tile 
 // on which entries have a pair term.  Images that keep their cell list keep
 // their list too.
 template <typename T>
-__global__ void __launch_bounds__(TILE) k_lj_list(const Tile *tiles, BandDev *bands) {
+__device__ inline void lj_list_atom(BandDev &b, const Tile &tl, const LJGeom<T> &g, int t) {
     using T4 = typename Vec4<T>::type;
-    Tile tl = tiles[blockIdx.x];
-    BandDev &b = bands[tl.band];
-    const ImgScalars &sc = b.sc[tl.img];
-    if (b.lj_cap == 0 || !sc.rebuild) return;  // uniform over the block
-    __shared__ LJGeom<T> g;
-    lj_stage(g, sc, *b.bp);
-    __syncthreads();
     const int n = b.n, cap = b.lj_cap;
-    const int t = tl.t * TILE + threadIdx.x;
-    if (t >= n) return;
     const size_t base = (size_t)tl.img * n;
     const T4 *off = (const T4 *)b.slot_off + base;
     const int *start = b.bin_start + (size_t)tl.img * (b.nbins_cap + 1);
@@ -281,6 +272,22 @@ __global__ void __launch_bounds__(TILE) k_lj_list(const Tile *tiles, BandDev *ba
     const int padded = (total + LJ_UNROLL - 1) / LJ_UNROLL * LJ_UNROLL;
     for (int k = total; k < padded; ++k) L[(size_t)k * n] = self;
     b.nbr_cnt[base + t] = padded;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_lj_list(const Tile *tiles, int ntiles, BandDev *bands) {
+    __shared__ LJGeom<T> g;
+    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        const Tile tl = tiles[k];
+        BandDev &b = bands[tl.band];
+        const ImgScalars &sc = b.sc[tl.img];
+        if (b.lj_cap == 0 || !sc.rebuild) continue;  // uniform over the block
+        lj_stage(g, sc, *b.bp);
+        __syncthreads();
+        const int t = tl.t * TILE + threadIdx.x;
+        if (t < b.n) lj_list_atom<T>(b, tl, g, t);
+        __syncthreads();  // g is restaged for the next tile
+    }
 }
 
 // List path: F_i, U_i and the virial from slot t's list entries.  The pair
@@ -377,7 +384,10 @@ void launch_lj(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
 template <typename T>
 void launch_lj_list(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
     if (ntiles <= 0) return;
-    k_lj_list<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
+    // a block per tile: a build walks ~370 candidates per atom, and in a
+    // batch of many bands a large share of the images rebuilds at a time
+    // (a capped grid was measured slower here)
+    k_lj_list<T><<<ntiles, TILE, 0, s>>>(tiles, ntiles, bands);
 }
 template <typename T>
 void launch_lj_nbr(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {

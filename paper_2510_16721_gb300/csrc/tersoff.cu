@@ -347,32 +347,36 @@ __device__ inline void ters_site(const TP<T> &q, int cnt, const Nbr<T> &nb, T *n
 // coalesced as [entry][atom].  Images that keep their cell list keep their
 // list too.
 template <typename T>
-__global__ void __launch_bounds__(TILE) k_ters_list(const Tile *tiles, BandDev *bands) {
-    Tile tl = tiles[blockIdx.x];
-    BandDev &b = bands[tl.band];
-    const ImgScalars &sc = b.sc[tl.img];
-    if (!sc.rebuild) return;  // uniform over the block
+__global__ void __launch_bounds__(TILE) k_ters_list(const Tile *tiles, int ntiles, BandDev *bands) {
     __shared__ T s_bv[9], s_dh[9], s_rl2;
     __shared__ int s_nb[3], s_m[3];
-    if (threadIdx.x < 9) {
-        s_bv[threadIdx.x] = (T)sc.bv[threadIdx.x];
-        s_dh[threadIdx.x] = (T)sc.dh[threadIdx.x];
+    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        const Tile tl = tiles[k];
+        BandDev &b = bands[tl.band];
+        const ImgScalars &sc = b.sc[tl.img];
+        if (!sc.rebuild) continue;  // uniform over the block
+        if (threadIdx.x < 9) {
+            s_bv[threadIdx.x] = (T)sc.bv[threadIdx.x];
+            s_dh[threadIdx.x] = (T)sc.dh[threadIdx.x];
+        }
+        if (threadIdx.x < 3) {
+            s_nb[threadIdx.x] = sc.nb[threadIdx.x];
+            s_m[threadIdx.x] = sc.m[threadIdx.x];
+        }
+        if (threadIdx.x == 0) {  // FP64 work once per block, not per thread
+            const double rl = b.bp->rl > 0.0 ? b.bp->rl : b.bp->rc;
+            s_rl2 = (T)(rl * rl);
+        }
+        __syncthreads();
+        const int n = b.n;
+        const int t = tl.t * TILE + threadIdx.x;
+        if (t < n) {
+            const int total = ters_collect_list<T>(s_rl2, b, tl.img, t, s_bv, s_dh, s_nb, s_m);
+            b.nbr_cnt[(size_t)tl.img * n + t] = total < MAXN_TERSOFF ? total : MAXN_TERSOFF;
+            if (total > MAXN_TERSOFF) atomicOr(&b.bp->status, ST_NBR_OVERFLOW);
+        }
+        __syncthreads();  // the staged geometry is rewritten for the next tile
     }
-    if (threadIdx.x < 3) {
-        s_nb[threadIdx.x] = sc.nb[threadIdx.x];
-        s_m[threadIdx.x] = sc.m[threadIdx.x];
-    }
-    if (threadIdx.x == 0) {  // FP64 work once per block, not per thread
-        const double rl = b.bp->rl > 0.0 ? b.bp->rl : b.bp->rc;
-        s_rl2 = (T)(rl * rl);
-    }
-    __syncthreads();
-    const int n = b.n;
-    const int t = tl.t * TILE + threadIdx.x;
-    if (t >= n) return;
-    const int total = ters_collect_list<T>(s_rl2, b, tl.img, t, s_bv, s_dh, s_nb, s_m);
-    b.nbr_cnt[(size_t)tl.img * n + t] = total < MAXN_TERSOFF ? total : MAXN_TERSOFF;
-    if (total > MAXN_TERSOFF) atomicOr(&b.bp->status, ST_NBR_OVERFLOW);
 }
 
 // pair vectors of the list entries of slot t from the current offsets, into
@@ -460,13 +464,8 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 7 : 1) k_ters_partials(
 // qs, stencil code c), the entry of qs's list that points back to t under
 // -c, so that the force gather needs no search.
 template <typename T>
-__global__ void __launch_bounds__(TILE) k_ters_reverse(const Tile *tiles, BandDev *bands) {
-    Tile tl = tiles[blockIdx.x];
-    BandDev &b = bands[tl.band];
-    if (!b.sc[tl.img].rebuild) return;
+__device__ inline void ters_reverse_atom(BandDev &b, const Tile &tl, int t) {
     const int n = b.n;
-    const int t = tl.t * TILE + threadIdx.x;
-    if (t >= n) return;
     const size_t base = (size_t)tl.img * n;
     const int *nslot = b.nbr_slot + (size_t)tl.img * MAXN_TERSOFF * n;
     const int *ncode = b.nbr_code + (size_t)tl.img * MAXN_TERSOFF * n;
@@ -483,6 +482,17 @@ __global__ void __launch_bounds__(TILE) k_ters_reverse(const Tile *tiles, BandDe
                 break;
             }
         nrev[(size_t)k * n + t] = (unsigned char)r;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_ters_reverse(const Tile *tiles, int ntiles, BandDev *bands) {
+    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        const Tile tl = tiles[k];
+        BandDev &b = bands[tl.band];
+        if (!b.sc[tl.img].rebuild) continue;
+        const int t = tl.t * TILE + threadIdx.x;
+        if (t < b.n) ters_reverse_atom<T>(b, tl, t);
     }
 }
 
@@ -550,12 +560,13 @@ __global__ void __launch_bounds__(TILE) k_ters_gather(const Tile *tiles, BandDev
 template <typename T>
 void launch_tersoff_list(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
     if (ntiles <= 0) return;
-    k_ters_list<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
+    k_ters_list<T><<<ntiles < GATED_GRID ? ntiles : GATED_GRID, TILE, 0, s>>>(tiles, ntiles, bands);
 }
 template <typename T>
 void launch_tersoff_reverse(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
     if (ntiles <= 0) return;
-    k_ters_reverse<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
+    k_ters_reverse<T><<<ntiles < GATED_GRID ? ntiles : GATED_GRID, TILE, 0, s>>>(tiles, ntiles,
+                                                                                 bands);
 }
 template <typename T>
 void launch_tersoff_partials(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
