@@ -263,6 +263,17 @@ __device__ inline int ters_collect_list(T rl2, const BandDev &b, int img, int t,
 
 // Site energy U_i, partials P_ij (written to the list) and the site virial
 // of slot t from its cnt neighbour records (r^ij and s = r - R filled in).
+//
+// cos theta_jk, g and dg/dcos are symmetric in (j, k), so the angular work
+// runs over unordered pairs j < k, each evaluated once per pass:
+//   pass 1: zeta_j += fC_k g_jk and zeta_k += fC_j g_jk;
+//   pass 2, per j: b_ij, the radial term of P_ij and pref_j = 1/2 fC_j f_A,j
+//     db_ij/dzeta_ij (zeta parks in the P_x field, pref in the s field);
+//   pass 3: with S = dg_jk (pref_j fC_k + pref_k fC_j),
+//     P_ij += S dcos/dr^ij + pref_k dfC_j g_jk r^ij / r_ij,
+//     P_ik += S dcos/dr^ik + pref_j dfC_k g_jk r^ik / r_ik
+//   (the j-as-bond and k-as-bond terms of dU_i together).  A pair with an
+// entry beyond R + D (fC = dfC = 0) contributes nothing and is skipped.
 template <typename T>
 __device__ inline void ters_site(const TP<T> &q, int cnt, const Nbr<T> &nb, T *nP, int n, int t,
                                  T &U, T (&vir)[9]) {
@@ -272,23 +283,36 @@ __device__ inline void ters_site(const TP<T> &q, int cnt, const Nbr<T> &nb, T *n
         nb(NB_FC, j) = fc;
         nb(NB_DFC, j) = dfc;
         nb(NB_IR, j) = M<T>::rcp(q.R + nb(NB_SR, j));  // 1 / r
-        nb(NB_PX, j) = nb(NB_PY, j) = nb(NB_PZ, j) = (T)0;
+        nb(NB_PX, j) = (T)0;                             // zeta_ij
     }
+    // pass 1: zeta
     for (int j = 0; j < cnt; ++j) {
-        const T fcj = nb(NB_FC, j), dfcj = nb(NB_DFC, j);
-        if (fcj == (T)0 && dfcj == (T)0) continue;  // beyond R + D: no terms
-        const T xj = nb(NB_RX, j), yj = nb(NB_RY, j), zj = nb(NB_RZ, j), sj_ = nb(NB_SR, j);
-        const T irj = nb(NB_IR, j);
-        // zeta_ij and the bond order
-        T zeta = 0;
-        for (int k = 0; k < cnt; ++k) {
-            if (k == j) continue;
+        const T fcj = nb(NB_FC, j);
+        if (fcj == (T)0 && nb(NB_DFC, j) == (T)0) continue;
+        const T xj = nb(NB_RX, j), yj = nb(NB_RY, j), zj = nb(NB_RZ, j), irj = nb(NB_IR, j);
+        T zj_acc = 0;
+        for (int k = j + 1; k < cnt; ++k) {
+            const T fck = nb(NB_FC, k);
+            if (fck == (T)0 && nb(NB_DFC, k) == (T)0) continue;
             const T cs = (xj * nb(NB_RX, k) + yj * nb(NB_RY, k) + zj * nb(NB_RZ, k)) * irj *
                          nb(NB_IR, k);
             T g, dg;
             gfun(q, cs, g, dg);
-            zeta += nb(NB_FC, k) * g;
+            zj_acc += fck * g;
+            nb(NB_PX, k) += fcj * g;
         }
+        nb(NB_PX, j) += zj_acc;
+    }
+    // pass 2: bond orders, energy, radial terms, prefactors
+    for (int j = 0; j < cnt; ++j) {
+        const T fcj = nb(NB_FC, j), dfcj = nb(NB_DFC, j);
+        const T xj = nb(NB_RX, j), yj = nb(NB_RY, j), zj = nb(NB_RZ, j);
+        if (fcj == (T)0 && dfcj == (T)0) {  // beyond R + D: no terms
+            nb(NB_SR, j) = (T)0;
+            nb(NB_PX, j) = nb(NB_PY, j) = nb(NB_PZ, j) = (T)0;
+            continue;
+        }
+        const T zeta = nb(NB_PX, j), sj_ = nb(NB_SR, j), irj = nb(NB_IR, j);
         T bij = (T)1, dbij = (T)0;
         if (zeta > (T)0) {
             const T x = M<T>::ex(q.n * M<T>::lg(q.beta * zeta));
@@ -300,28 +324,39 @@ __device__ inline void ters_site(const TP<T> &q, int cnt, const Nbr<T> &nb, T *n
         const T dfr = -q.l1 * fr, dfa = -q.l2 * fa;
         U += (T)0.5 * fcj * (fr + bij * fa);
         const T radial = (T)0.5 * (dfcj * (fr + bij * fa) + fcj * (dfr + bij * dfa)) * irj;
-        T Pxj = radial * xj, Pyj = radial * yj, Pzj = radial * zj;
-        const T pref = (T)0.5 * fcj * fa * dbij;
-        if (pref != (T)0) {
-            for (int k = 0; k < cnt; ++k) {
-                if (k == j) continue;
-                const T xk = nb(NB_RX, k), yk = nb(NB_RY, k), zk = nb(NB_RZ, k);
-                const T irk = nb(NB_IR, k);
-                const T ijk = irj * irk;
-                const T cs = (xj * xk + yj * yk + zj * zk) * ijk;
-                T g, dg;
-                gfun(q, cs, g, dg);
-                // d cos / d r^ij and d cos / d r^ik
-                const T aj = cs * irj * irj, ak = cs * irk * irk;
-                const T sj = pref * nb(NB_FC, k) * dg;
-                Pxj += sj * (xk * ijk - aj * xj);
-                Pyj += sj * (yk * ijk - aj * yj);
-                Pzj += sj * (zk * ijk - aj * zj);
-                const T rkk = pref * nb(NB_DFC, k) * g * irk;
-                nb(NB_PX, k) += rkk * xk + sj * (xj * ijk - ak * xk);
-                nb(NB_PY, k) += rkk * yk + sj * (yj * ijk - ak * yk);
-                nb(NB_PZ, k) += rkk * zk + sj * (zj * ijk - ak * zk);
-            }
+        nb(NB_SR, j) = (T)0.5 * fcj * fa * dbij;  // pref_j
+        nb(NB_PX, j) = radial * xj;
+        nb(NB_PY, j) = radial * yj;
+        nb(NB_PZ, j) = radial * zj;
+    }
+    // pass 3: angular terms
+    for (int j = 0; j < cnt; ++j) {
+        const T fcj = nb(NB_FC, j), dfcj = nb(NB_DFC, j);
+        if (fcj == (T)0 && dfcj == (T)0) continue;
+        const T xj = nb(NB_RX, j), yj = nb(NB_RY, j), zj = nb(NB_RZ, j);
+        const T irj = nb(NB_IR, j), prefj = nb(NB_SR, j);
+        T Pxj = 0, Pyj = 0, Pzj = 0;
+        for (int k = j + 1; k < cnt; ++k) {
+            const T fck = nb(NB_FC, k), dfck = nb(NB_DFC, k);
+            if (fck == (T)0 && dfck == (T)0) continue;
+            const T prefk = nb(NB_SR, k);
+            if (prefj == (T)0 && prefk == (T)0) continue;
+            const T xk = nb(NB_RX, k), yk = nb(NB_RY, k), zk = nb(NB_RZ, k);
+            const T irk = nb(NB_IR, k);
+            const T ijk = irj * irk;
+            const T cs = (xj * xk + yj * yk + zj * zk) * ijk;
+            T g, dg;
+            gfun(q, cs, g, dg);
+            // dcos/dr^ij = r^ik/(r_ij r_ik) - cos r^ij/r_ij^2 (and j <-> k)
+            const T aj = cs * irj * irj, ak = cs * irk * irk;
+            const T S = dg * (prefj * fck + prefk * fcj);
+            const T rj = prefk * dfcj * g * irj, rk = prefj * dfck * g * irk;
+            Pxj += S * (xk * ijk - aj * xj) + rj * xj;
+            Pyj += S * (yk * ijk - aj * yj) + rj * yj;
+            Pzj += S * (zk * ijk - aj * zj) + rj * zj;
+            nb(NB_PX, k) += S * (xj * ijk - ak * xk) + rk * xk;
+            nb(NB_PY, k) += S * (yj * ijk - ak * yk) + rk * yk;
+            nb(NB_PZ, k) += S * (zj * ijk - ak * zk) + rk * zk;
         }
         nb(NB_PX, j) += Pxj;
         nb(NB_PY, j) += Pyj;
