@@ -171,7 +171,7 @@ struct BandDev {
     int *nbr_slot;       // [ncap][MAXN or lj_cap][n]
     int *nbr_code;       // [ncap][MAXN][n]
     unsigned char *nbr_rev;  // [ncap][MAXN][n]: entry of j's list pointing back (255: none)
-    void *nbr_P;         // [ncap][3*MAXN][n] of T
+    void *nbr_P;         // [ncap][MAXN][n] x 4 T: partials (x, y, z, pad)
     // partial sums
     double *atom_part;   // [ncap][atpi][NPART]
     double *row_part;    // [ncap][rtpi][NPART]

@@ -792,7 +792,7 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
         d.nbr_slot = (int *)dalloc(b, na * MAXN_TERSOFF * sizeof(int));
         d.nbr_code = (int *)dalloc(b, na * MAXN_TERSOFF * sizeof(int));
         d.nbr_rev = (unsigned char *)dalloc(b, na * MAXN_TERSOFF);
-        d.nbr_P = dalloc(b, na * 3 * MAXN_TERSOFF * b->ts);
+        d.nbr_P = dalloc(b, na * 4 * MAXN_TERSOFF * b->ts);
     }
     d.atom_part = (double *)dalloc(b, nc * d.atpi * NPART * sizeof(double));
     d.row_part = (double *)dalloc(b, nc * d.rtpi * NPART * sizeof(double));

@@ -52,6 +52,9 @@ template <> struct M<float> {
     static __device__ float sn(float x) { return sinf(x); }
     // correctly rounded reciprocal: a short sequence, unlike a full divide
     static __device__ float rcp(float x) { return __frcp_rn(x); }
+    // the fast division intrinsic (2 ulp) where only relative accuracy of a
+    // factor matters (1/r of directions, the angular function)
+    static __device__ float rcpf(float x) { return __fdividef(1.0f, x); }
 };
 template <> struct M<double> {
     static __device__ double ex(double x) { return exp(x); }
@@ -60,6 +63,7 @@ template <> struct M<double> {
     static __device__ double sq(double x) { return sqrt(x); }
     static __device__ double sn(double x) { return sin(x); }
     static __device__ double rcp(double x) { return 1.0 / x; }
+    static __device__ double rcpf(double x) { return 1.0 / x; }
 };
 
 __device__ inline float mul_rn(float a, float b) { return __fmul_rn(a, b); }
@@ -135,7 +139,7 @@ __device__ inline void cutoff(const TP<T> &q, T s, T &fc, T &dfc) {
 template <typename T>
 __device__ inline void gfun(const TP<T> &q, T cs, T &g, T &dg) {
     const T u = q.h - cs;
-    const T inv = M<T>::rcp(q.d2 + u * u);
+    const T inv = M<T>::rcpf(q.d2 + u * u);
     g = (T)1 + q.c2d2 * u * u * inv;
     dg = -(T)2 * q.c2 * u * inv * inv;
 }
@@ -275,14 +279,14 @@ __device__ inline int ters_collect_list(T rl2, const BandDev &b, int img, int t,
 //   (the j-as-bond and k-as-bond terms of dU_i together).  A pair with an
 // entry beyond R + D (fC = dfC = 0) contributes nothing and is skipped.
 template <typename T>
-__device__ inline void ters_site(const TP<T> &q, int cnt, const Nbr<T> &nb, T *nP, int n, int t,
-                                 T &U, T (&vir)[9]) {
+__device__ inline void ters_site(const TP<T> &q, int cnt, const Nbr<T> &nb,
+                                 typename Vec4<T>::type *nP, int n, int t, T &U, T (&vir)[9]) {
     for (int j = 0; j < cnt; ++j) {
         T fc, dfc;
         cutoff(q, nb(NB_SR, j), fc, dfc);
         nb(NB_FC, j) = fc;
         nb(NB_DFC, j) = dfc;
-        nb(NB_IR, j) = M<T>::rcp(q.R + nb(NB_SR, j));  // 1 / r
+        nb(NB_IR, j) = M<T>::rcpf(q.R + nb(NB_SR, j));  // 1 / r
         nb(NB_PX, j) = (T)0;                             // zeta_ij
     }
     // pass 1: zeta
@@ -365,9 +369,12 @@ __device__ inline void ters_site(const TP<T> &q, int cnt, const Nbr<T> &nb, T *n
     for (int j = 0; j < cnt; ++j) {
         const T Px = nb(NB_PX, j), Py = nb(NB_PY, j), Pz = nb(NB_PZ, j);
         const T rx = nb(NB_RX, j), ry = nb(NB_RY, j), rz = nb(NB_RZ, j);
-        nP[(size_t)(3 * j + 0) * n + t] = Px;
-        nP[(size_t)(3 * j + 1) * n + t] = Py;
-        nP[(size_t)(3 * j + 2) * n + t] = Pz;
+        typename Vec4<T>::type pv;
+        pv.x = Px;
+        pv.y = Py;
+        pv.z = Pz;
+        pv.w = (T)0;
+        nP[(size_t)j * n + t] = pv;  // one vector store; one vector gather later
         // V_mn -= r_m P_n
         vir[0] -= rx * Px; vir[1] -= rx * Py; vir[2] -= rx * Pz;
         vir[3] -= ry * Px; vir[4] -= ry * Py; vir[5] -= ry * Pz;
@@ -468,7 +475,8 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 7 : 1) k_ters_partials(
     const int n = b.n;
     const int t = tl.t * TILE + threadIdx.x;
     const size_t base = (size_t)tl.img * n;
-    T *nP = (T *)b.nbr_P + (size_t)tl.img * 3 * MAXN_TERSOFF * n;
+    typename Vec4<T>::type *nP =
+        (typename Vec4<T>::type *)b.nbr_P + (size_t)tl.img * MAXN_TERSOFF * n;
     int nin = 0;
     T U = 0;
     T vir[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -546,7 +554,8 @@ __global__ void __launch_bounds__(TILE) k_ters_gather(const Tile *tiles, BandDev
     const size_t base = (size_t)tl.img * n;
     const int *nslot = b.nbr_slot + (size_t)tl.img * MAXN_TERSOFF * n;
     const unsigned char *nrev = b.nbr_rev + (size_t)tl.img * MAXN_TERSOFF * n;
-    const T *nP = (const T *)b.nbr_P + (size_t)tl.img * 3 * MAXN_TERSOFF * n;
+    using T4 = typename Vec4<T>::type;
+    const T4 *nP = (const T4 *)b.nbr_P + (size_t)tl.img * MAXN_TERSOFF * n;
     T fx = 0, fy = 0, fz = 0;
     const int cnt = b.nbr_cnt[base + t];
     // f^ij = P_ij - P_ji, in list order; the first GK entries with every
@@ -561,25 +570,29 @@ __global__ void __launch_bounds__(TILE) k_ters_gather(const Tile *tiles, BandDev
 #pragma unroll
     for (int k = 0; k < GK; ++k) {
         if (k >= cnt) break;
-        fx += nP[(size_t)(3 * k + 0) * n + t];
-        fy += nP[(size_t)(3 * k + 1) * n + t];
-        fz += nP[(size_t)(3 * k + 2) * n + t];
+        const T4 a = nP[(size_t)k * n + t];
+        fx += a.x;
+        fy += a.y;
+        fz += a.z;
         if (k2[k] != 255) {
-            fx -= nP[(size_t)(3 * k2[k] + 0) * n + qs[k]];
-            fy -= nP[(size_t)(3 * k2[k] + 1) * n + qs[k]];
-            fz -= nP[(size_t)(3 * k2[k] + 2) * n + qs[k]];
+            const T4 r = nP[(size_t)k2[k] * n + qs[k]];
+            fx -= r.x;
+            fy -= r.y;
+            fz -= r.z;
         }
     }
     for (int k = GK; k < cnt; ++k) {
-        fx += nP[(size_t)(3 * k + 0) * n + t];
-        fy += nP[(size_t)(3 * k + 1) * n + t];
-        fz += nP[(size_t)(3 * k + 2) * n + t];
+        const T4 a = nP[(size_t)k * n + t];
+        fx += a.x;
+        fy += a.y;
+        fz += a.z;
         const int q = nslot[(size_t)k * n + t];
         const int r = nrev[(size_t)k * n + t];
         if (r != 255) {
-            fx -= nP[(size_t)(3 * r + 0) * n + q];
-            fy -= nP[(size_t)(3 * r + 1) * n + q];
-            fz -= nP[(size_t)(3 * r + 2) * n + q];
+            const T4 p = nP[(size_t)r * n + q];
+            fx -= p.x;
+            fy -= p.y;
+            fz -= p.z;
         }
     }
     const T g0 = fx * s_D[0] + fy * s_D[1] + fz * s_D[2];
