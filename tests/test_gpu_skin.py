@@ -211,3 +211,28 @@ def test_lj_neighbour_list_overflow_is_reported(g):
         gb = gpu_band(g, R, h, R1, h, 5, g.lj_potential(), k=1.0, dt=0.01)
         gb.step(1)
     assert e.value.status == g.ERR_NBR_OVERFLOW
+
+
+@pytest.mark.parametrize("reps,lists", [((20, 20, 20), True), ((33, 33, 33), False)])
+def test_large_lj_band_sampled_forces(g, oracle_mod, reps, lists):
+    """Full-size LJ vacancy bands: 31,999 atoms (the largest band of the
+    64-band batch) keep neighbour lists; 143,747 atoms exceed what a list
+    entry can index (2^17 slots) and walk the cell list.  After 6 mixed
+    steps, forces of an interior image at its stored configuration against
+    the brute-force oracle on 48 sampled atoms (1e-4 eps/sigma), and the
+    FP64 band's first evaluation at 1e-10."""
+    R0, h0, R1, h1 = ci.lj_vacancy_hop(ci.LJ_A, reps)
+    for prec, tol, nstep in ((g.MIXED, 1e-4, 6), (g.FP64, 1e-10, 0)):
+        gb = gpu_band(g, R0, h0, R1, h1, 5, g.lj_potential(), k=1.0, dt=0.01,
+                      cell_filter=False, precision=prec)
+        assert gb.launches_per_step() == (17 if lists else 16)
+        gb.step(nstep)
+        st = gb.get_state()
+        gb.step(1)
+        F = gb.get_state()["F"][2][: len(R0)]
+        X = st["X"][2][: len(R0)]
+        idx = np.random.default_rng(7).choice(len(R0), 48, replace=False)
+        Fo = oracle_mod.LJ().forces_sampled(X, h0, idx)
+        err = np.max(np.abs(F[idx] - Fo))
+        assert err <= (tol if prec == g.MIXED else tol * max(1.0, np.max(np.abs(Fo)))), err
+        gb.destroy()
