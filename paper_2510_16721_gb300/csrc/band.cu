@@ -34,7 +34,7 @@ __global__ void k_image_finalize(const ImgRef *imgs, BandDev *bands) {
     // U, V (9), pairs, triples: tile partials summed in FP64, fixed order
     __shared__ double s_tot[12];
     const double tk =
-        block_sum_records<12, 16>(b.atom_part + (size_t)r.img * b.atpi * NPART, NPART, b.atpi);
+        block_sum_records<12, 21>(b.atom_part + (size_t)r.img * b.atpi * NPART, NPART, b.atpi);
     if (threadIdx.x < 12) s_tot[threadIdx.x] = tk;
     __syncthreads();
     if (threadIdx.x >= 32) return;
@@ -277,6 +277,7 @@ __global__ void k_fire_scalars(const int *band_ids, BandDev *bands) {
     if (threadIdx.x < 4 * G) {
         const int k = threadIdx.x % 4, g = threadIdx.x / 4;
         double v = 0.0;
+#pragma unroll 8
         for (int q = g; q < nt; q += G) {
             const double x = part0[(size_t)q * NPART + 5 + k];
             v = k == 3 ? fmax(v, x) : v + x;

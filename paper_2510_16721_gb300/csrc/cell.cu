@@ -56,73 +56,71 @@ namespace cfneb {
 // Gershgorin row bound (>= lambda_max), and det B / g^2 (<= lambda_min).
 // The products run lane-parallel (k_mapback).
 
-// Bin grid of an image with cell h: with keep_grid false the bin counts
-// nb and stencil half widths m are chosen from the perpendicular widths and
-// the list cutoff; with keep_grid true they stay as built and only the bin
-// vectors follow the cell.
-__device__ void bin_geometry(const BandParams *bp, int nbins_cap, const double *h, double omega,
-                             bool keep_grid, ImgScalars &sc) {
+// Bin grid of an image with cell h (one thread): the bin counts nb and
+// stencil half widths m from the perpendicular widths and the list cutoff.
+// Between rebuilds the grid stays as built and only the bin vectors follow
+// the cell (bin_vectors_warp).
+__device__ void bin_grid(const BandParams *bp, int nbins_cap, const double *h, double omega,
+                         ImgScalars &sc) {
     const double rl = bp->rl > 0.0 ? bp->rl : bp->rc;
     int nb[3];
     float w[3];
-    if (keep_grid) {
-        for (int a = 0; a < 3; ++a) nb[a] = sc.nb[a];
-    } else {
-        // perpendicular widths w_a = Omega / |h_b x h_c| (only choose the bin
-        // grid: FP32, shaded down by 1e-4 so the stencil is never too narrow,
-        // also for atoms binned in FP32)
-        for (int a = 0; a < 3; ++a) {
-            const double *u = h + 3 * ((a + 1) % 3), *v = h + 3 * ((a + 2) % 3);
-            const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2],
-                         cz = u[0] * v[1] - u[1] * v[0];
-            w[a] = (float)omega / sqrtf((float)(cx * cx + cy * cy + cz * cz)) * 0.9999f;
-        }
-        for (int a = 0; a < 3; ++a) {
-            // the innermost axis may be binned finer: the LJ kernel walks it
-            // as contiguous rows, so finer bins there trim the candidate
-            // range without adding rows
-            const float bw = (float)bp->bin_w / (a == 2 ? (float)bp->row_refine : 1.0f);
-            // never so fine that the stencil would need more than
-            // MAX_STENCIL bins per side (coarser bins are always correct)
-            const float q = fminf(floorf(w[a] / bw),
-                                  floorf(w[a] * (float)MAX_STENCIL / (float)rl * 0.9999f));
-            nb[a] = q < 1.0f ? 1 : (q > 1024.0f ? 1024 : (int)q);
-        }
-        // keep within the bin capacity: coarser bins are always correct
-        while ((long long)nb[0] * nb[1] * nb[2] > nbins_cap) {
-            int a = (nb[0] >= nb[1] && nb[0] >= nb[2]) ? 0 : (nb[1] >= nb[2] ? 1 : 2);
-            nb[a] -= 1;
-        }
-    }
-    // bin vectors on a grid of q = 2^(e - 19), 2^e >= max |h_a / nb_a|: every
-    // sum of three products delta_a bv_a (|delta| <= 7) is then exact in
-    // FP32; dh = h - nb bv carries the (sub-1e-4 A) quantisation to the
-    // periodic wrap
-    double inb[3];
-    for (int a = 0; a < 3; ++a) inb[a] = rcp64((double)nb[a]);
-    // only the binade of max |h_a / nb_a| matters; found in FP32, it can be
-    // one binade low by an ulp, and then |bv| <= (2^19 + 1) q: three terms
-    // |delta| <= 7 still sum below 2^24 q, exact in FP32
-    float bmax = 0.0f;
-    for (int a = 0; a < 3; ++a)
-        for (int c = 0; c < 3; ++c) bmax = fmaxf(bmax, fabsf((float)h[3 * a + c] / (float)nb[a]));
-    const int e = ilogbf(bmax) + 1 - 19;
-    const double q = ldexp(1.0, e), iq = ldexp(1.0, -e);  // exact powers of two
+    // perpendicular widths w_a = Omega / |h_b x h_c| (only choose the bin
+    // grid: FP32, shaded down by 1e-4 so the stencil is never too narrow,
+    // also for atoms binned in FP32)
     for (int a = 0; a < 3; ++a) {
-        if (!keep_grid) {
-            const float bw = w[a] / nb[a];
-            const int m = (int)ceilf((float)rl / bw);
-            sc.m[a] = m < 1 ? 1 : (m > MAX_STENCIL ? MAX_STENCIL : m);
-            sc.nb[a] = nb[a];
-        }
-        for (int c = 0; c < 3; ++c) {
-            const double v = q * rint(h[3 * a + c] * inb[a] * iq);
-            sc.bv[3 * a + c] = v;
-            sc.bvf[3 * a + c] = (float)v;
-            sc.dh[3 * a + c] = h[3 * a + c] - nb[a] * v;
-        }
+        const double *u = h + 3 * ((a + 1) % 3), *v = h + 3 * ((a + 2) % 3);
+        const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2],
+                     cz = u[0] * v[1] - u[1] * v[0];
+        w[a] = (float)omega / sqrtf((float)(cx * cx + cy * cy + cz * cz)) * 0.9999f;
+    }
+    for (int a = 0; a < 3; ++a) {
+        // the innermost axis may be binned finer: the LJ kernel walks it
+        // as contiguous rows, so finer bins there trim the candidate
+        // range without adding rows
+        const float bw = (float)bp->bin_w / (a == 2 ? (float)bp->row_refine : 1.0f);
+        // never so fine that the stencil would need more than
+        // MAX_STENCIL bins per side (coarser bins are always correct)
+        const float q = fminf(floorf(w[a] / bw),
+                              floorf(w[a] * (float)MAX_STENCIL / (float)rl * 0.9999f));
+        nb[a] = q < 1.0f ? 1 : (q > 1024.0f ? 1024 : (int)q);
+    }
+    // keep within the bin capacity: coarser bins are always correct
+    while ((long long)nb[0] * nb[1] * nb[2] > nbins_cap) {
+        int a = (nb[0] >= nb[1] && nb[0] >= nb[2]) ? 0 : (nb[1] >= nb[2] ? 1 : 2);
+        nb[a] -= 1;
+    }
+    for (int a = 0; a < 3; ++a) {
+        const float bw = w[a] / nb[a];
+        const int m = (int)ceilf((float)rl / bw);
+        sc.m[a] = m < 1 ? 1 : (m > MAX_STENCIL ? MAX_STENCIL : m);
+        sc.nb[a] = nb[a];
     }
     sc.nbins = nb[0] * nb[1] * nb[2];
+}
+
+// Bin vectors of the image's grid for its current cell, one entry per lane
+// (lanes 0..8; the whole warp calls): bv_a on a grid of q = 2^(e - 19),
+// 2^e >= max |h_a / nb_a|, so every sum of three products delta_a bv_a
+// (|delta| <= 7) is exact in FP32; dh = h - nb bv carries the (sub-1e-4 A)
+// quantisation to the periodic wrap.  Only the binade of max |h_a / nb_a|
+// matters; found in FP32 it can be one binade low by an ulp, and then
+// |bv| <= (2^19 + 1) q: three terms |delta| <= 7 still sum below 2^24 q.
+__device__ void bin_vectors_warp(ImgScalars &sc) {
+    const int lane = threadIdx.x & 31;
+    const int l = lane < 9 ? lane : 0, a = l / 3;
+    const int nba = sc.nb[a];
+    const double h = sc.h[l];
+    float bmax = lane < 9 ? fabsf((float)h / (float)nba) : 0.0f;
+    for (int o = 16; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+    const int e = ilogbf(bmax) + 1 - 19;
+    const double q = ldexp(1.0, e), iq = ldexp(1.0, -e);  // exact powers of two
+    const double v = q * rint(h * rcp64((double)nba) * iq);
+    if (lane < 9) {
+        sc.bv[l] = v;
+        sc.bvf[l] = (float)v;
+        sc.dh[l] = h - nba * v;
+    }
 }
 
 // upper bound of the spectral norm of a 3x3 matrix: the smaller of the
@@ -186,11 +184,9 @@ __device__ void skin_decide_one(const BandParams *bp, int nbins_cap, ImgScalars 
         rebuild = !(bound > bp->rc);
     }
     if (rebuild) {
-        bin_geometry(bp, nbins_cap, sc.h, sc.omega, false, sc);
+        bin_grid(bp, nbins_cap, sc.h, sc.omega, sc);
         for (int k = 0; k < 9; ++k) sc.Db[k] = sc.D[k];
         sc.builds += 1;
-    } else {
-        bin_geometry(bp, nbins_cap, sc.h, sc.omega, true, sc);
     }
     sc.rebuild = rebuild ? 1 : 0;
     sc.dmax = d;
@@ -297,7 +293,7 @@ __global__ void __launch_bounds__(32) k_mapback(const ImgRef *imgs, int count, B
         sc.omega = omega;
         if (bp->skin <= 0.0) {
             // no skin: the cell list is rebuilt at every evaluation
-            bin_geometry(bp, b.nbins_cap, sc.h, omega, false, sc);
+            bin_grid(bp, b.nbins_cap, sc.h, omega, sc);
             sc.rebuild = 1;
             sc.builds += 1;
             sc.evals += 1;
@@ -305,6 +301,8 @@ __global__ void __launch_bounds__(32) k_mapback(const ImgRef *imgs, int count, B
             skin_decide_one(bp, b.nbins_cap, sc, dmax, force);
         }
     }
+    __syncwarp();
+    bin_vectors_warp(sc);  // lane-parallel: the grid (new or kept) follows the cell
     __syncwarp();
     stage_copy(&b.sc[r.img], &s_sc);
 }

@@ -311,7 +311,7 @@ __device__ inline double block_sum_records(const double *rec, int stride, int co
     if (tid < K * G) {
         const int k = tid % K, g = tid / K;
         double v = 0.0;
-#pragma unroll 4
+#pragma unroll 8
         for (int q = g; q < count; q += G) v += rec[(size_t)q * stride + k];
         s_part[g * K + k] = v;
     }
