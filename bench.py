@@ -407,9 +407,11 @@ def run_ours(args, wl_name):
     return 0
 
 
-def make_lj_band(g, bc, precision, stream):
+def make_lj_band(g, bc, precision, stream, skin=None):
     R0, h0, R1, h1 = bc["endpoints"]
     opt = g.default_options()
+    if skin is not None:
+        opt.skin = skin
     opt.k_spring = bc["k"]
     opt.climb = 1
     opt.precision = precision
@@ -459,7 +461,7 @@ def run_batch(args):
     stream = torch.cuda.current_stream()
     work = sum(len(c["endpoints"][0]) * (c["n_images"] - 2) for c in bcs)
     t_create = time.perf_counter()
-    bands = [make_lj_band(g, c, g.MIXED, stream) for c in bcs]
+    bands = [make_lj_band(g, c, g.MIXED, stream, args.skin) for c in bcs]
     bt = g.Batch(g.MIXED, stream=stream)
     for b in bands:
         bt.add(b)
@@ -469,8 +471,13 @@ def run_batch(args):
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
+    lb0 = [b.list_stats() for b in bands]
     ms = time_steps(torch, bt, stream, args.steps, dist)
     clk = clocks.stop()
+    lb1 = [b.list_stats() for b in bands]
+    lists = {"skin": lb1[0][2], "builds_per_image_step":
+             sum(b1[0] - b0[0] for b0, b1 in zip(lb0, lb1)) /
+             max(1, sum(b1[1] - b0[1] for b0, b1 in zip(lb0, lb1)))}
     ms = max_over_ranks(torch, dist, ms)
     value = job_rate(ws, work, args.steps, ms)
     st = bt.status()
@@ -569,7 +576,7 @@ def run_batch(args):
             "roofline": roof, "kernel_share": {k: round(v[0] / total, 4)
                                                for k, v in prof.items() if v[1]},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "fp64_plain": fp64, "create_s": t_create}
+            "fp64_plain": fp64, "create_s": t_create, "lists": lists}
     print(json.dumps(line))
     if dist is not None:
         dist.barrier()
@@ -717,6 +724,8 @@ def main():
                     choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--skin", type=float, default=None,
+                    help="neighbour-list skin of the LJ batch bands (default: the library's)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--serve-window", type=float, default=30.0)
     ap.add_argument("--serve-max-steps", type=int, default=3000)
