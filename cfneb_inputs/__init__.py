@@ -324,3 +324,14 @@ def build_request(spec):
     if spec["kind"] == "tersoff_graphite_hexdiamond":
         return graphite_hexdiamond_path(spec["reps"]), "tersoff"
     return diamond_vacancy_hop(DIAMOND_A, spec["reps"]), "tersoff"
+
+
+def nep_weights(seed=2510, scale=0.3):
+    """Synthetic weights for the NEP-style potential (no trained model is
+    available): N(0, scale^2) entries in the order the potential reads them
+    (radial and angular basis coefficients, hidden-layer weights and biases,
+    output weights and bias), from numpy's PCG64 with the given seed.  The
+    count follows the fixed sizes K = 6, NR = 4, NA = 2, L = 4, H = 16."""
+    K, NR, NA, L, H = 6, 4, 2, 4, 16
+    n = NR * K + NA * K + H * (NR + NA * L) + H + H + 1
+    return np.random.default_rng(seed).normal(0.0, scale, n)

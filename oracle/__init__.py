@@ -17,6 +17,7 @@ from .cfneb import (LJ, Tersoff, TERSOFF_C1988, ROTFREE_B, DEFGRAD_D, NotSPD,  #
                     generalized_force, AtomicImage, upwind_tangent, climbing_index,
                     neb_forces, Fire, row_fmax, Band, interpolate, unwrap_final, make_band,
                     relax_single)
+from .nep import NEP  # noqa: F401
 
 
 def build():
