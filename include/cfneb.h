@@ -64,6 +64,10 @@ extern "C" {
 /* ---- enums ------------------------------------------------------------- */
 #define CFNEB_LJ 0
 #define CFNEB_TERSOFF 1
+#define CFNEB_NEP 2
+/* NEP-style potential: Chebyshev basis size 6, 4 radial and 2 angular
+ * functions, Legendre orders 1..4, 16 hidden units: 261 weights. */
+#define CFNEB_NEP_N_WEIGHTS 261
 
 #define CFNEB_ROTFREE_B 0   /* lattice coordinate B = D D^T (Sec. II.C end)   */
 #define CFNEB_DEFGRAD_D 1   /* lattice coordinate D = h0^-1 h (Sec. II.C)     */
@@ -83,7 +87,7 @@ typedef struct {
 } cfneb_structure;
 
 typedef struct {
-    int32_t kind;             /* CFNEB_LJ or CFNEB_TERSOFF                   */
+    int32_t kind;             /* CFNEB_LJ, CFNEB_TERSOFF or CFNEB_NEP        */
     /* Lennard-Jones: phi = 4 eps [(sigma/r)^12 - (sigma/r)^6], cut at rc,
        minus phi(rc) when shift_energy != 0                                  */
     double eps, sigma, rc;
@@ -91,6 +95,20 @@ typedef struct {
     /* Tersoff (1988 form, lambda3 = 0): A, B, lambda1, lambda2, beta, n, c,
        d, h, R, D.  All zero selects Tersoff's 1988 carbon parameters.       */
     double tersoff[11];
+    /* NEP-style descriptor + neural-network site energy (single species;
+       the neuroevolution potential of the paper's examples, Sec. IV, with
+       caller-given weights): f_c(r) = (1 + cos(pi r / rc)) / 2; radial
+       basis f_k = (T_k(x) + 1)/2 f_c, x = 2 (r/rc - 1)^2 - 1, k < 6;
+       g^R_n = sum_k cR[n][k] f_k (n < 4), g^A_n = sum_k cA[n][k] f_k
+       (n < 2); descriptors q_n = sum_j g^R_n(r_ij) and q_nl = sum_jk
+       g^A_n(r_ij) g^A_n(r_ik) P_l(cos theta_jk), l = 1..4 (order q_0..q_3,
+       q_01..q_04, q_11..q_14); U_i = sum_h w1[h] tanh(sum_d W0[h][d] q_d -
+       b0[h]) - b1.  nep_weights: CFNEB_NEP_N_WEIGHTS doubles in the order
+       cR (4x6), cA (2x6), W0 (16x12), b0 (16), w1 (16), b1; copied at
+       creation.  nep_rc: the cutoff (> 0; the neighbour lists hold at most
+       16 entries within nep_rc + skin).                                    */
+    const double *nep_weights;
+    double nep_rc;
 } cfneb_potential;
 
 typedef struct {

@@ -32,6 +32,8 @@ ERR_STATE = -10
 
 LJ = 0
 TERSOFF = 1
+NEP = 2
+NEP_N_WEIGHTS = 261
 ROTFREE_B = 0
 DEFGRAD_D = 1
 FP64 = 0
@@ -66,7 +68,8 @@ class Structure(ctypes.Structure):
 class Potential(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("eps", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("rc", ctypes.c_double), ("shift_energy", ctypes.c_int32),
-                ("tersoff", ctypes.c_double * 11)]
+                ("tersoff", ctypes.c_double * 11),
+                ("nep_weights", ctypes.POINTER(ctypes.c_double)), ("nep_rc", ctypes.c_double)]
 
 
 class CellFilter(ctypes.Structure):
@@ -197,6 +200,20 @@ def make_structure(R, h, keep):
 def lj_potential(eps=1.0, sigma=1.0, rc=2.5, shift=True):
     p = Potential()
     p.kind, p.eps, p.sigma, p.rc, p.shift_energy = LJ, eps, sigma, rc, int(bool(shift))
+    return p
+
+
+def nep_potential(weights, rc=2.1):
+    """NEP-style descriptor + network potential (cfneb.h): weights in the
+    order cR, cA, W0, b0, w1, b1 (NEP_N_WEIGHTS doubles), cutoff rc."""
+    w = np.ascontiguousarray(weights, dtype=np.float64).ravel()
+    if w.size != NEP_N_WEIGHTS:
+        raise ValueError("expected %d weights, got %d" % (NEP_N_WEIGHTS, w.size))
+    p = Potential()
+    p.kind = NEP
+    p.nep_weights = _dptr(w)
+    p.nep_rc = float(rc)
+    p._keep = w  # the array the pointer refers to lives as long as p
     return p
 
 

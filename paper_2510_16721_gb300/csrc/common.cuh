@@ -30,6 +30,15 @@ constexpr int RTILE = TILE * RPT;   // rows per row tile (band vector kernels)
 constexpr int MAXN_TERSOFF = 16;    // Tersoff list capacity per atom (entries within rl)
 constexpr int NPART = 12;           // doubles per tile partial record
 constexpr int MAX_STENCIL = 7;      // |delta| <= 7 bins per axis
+// NEP-style potential: Chebyshev basis size, radial and angular functions,
+// largest Legendre order, hidden units; descriptor and weight counts
+constexpr int NEP_K = 6, NEP_NR = 4, NEP_NA = 2, NEP_L = 4, NEP_H = 16;
+constexpr int NEP_ND = NEP_NR + NEP_NA * NEP_L;
+constexpr int NEP_NW = NEP_NR * NEP_K + NEP_NA * NEP_K + NEP_H * NEP_ND + 2 * NEP_H + 1;
+// offsets of cR, cA, W0, b0, w1, b1 in the flat weight array
+constexpr int NEP_OCR = 0, NEP_OCA = NEP_NR * NEP_K, NEP_OW0 = NEP_OCA + NEP_NA * NEP_K,
+              NEP_OB0 = NEP_OW0 + NEP_H * NEP_ND, NEP_OW1 = NEP_OB0 + NEP_H,
+              NEP_OB1 = NEP_OW1 + NEP_H;
 constexpr int LJ_LIST_MAX_ATOMS = 1 << 17;  // LJ list entries index 17-bit slots
 // Grid of the kernels that only do work for images rebuilding their lists:
 // a fixed grid strides over the tiles, so a step in which most images keep
@@ -171,6 +180,8 @@ struct BandDev {
     int *nbr_slot;       // [ncap][MAXN or lj_cap][n]
     int *nbr_code;       // [ncap][MAXN][n]
     unsigned char *nbr_rev;  // [ncap][MAXN][n]: entry of j's list pointing back (255: none)
+    const double *nep_w;     // NEP weights [NEP_NW] in FP64 and FP32 (NEP bands)
+    const float *nep_wf;
     void *nbr_P;         // [ncap][MAXN][n] x 4 T: partials (x, y, z, pad)
     // partial sums
     double *atom_part;   // [ncap][atpi][NPART]
@@ -480,6 +491,8 @@ template <typename T>
 void launch_tersoff_reverse(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 template <typename T>
 void launch_tersoff_partials(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
+template <typename T>
+void launch_nep_partials(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 template <typename T>
 void launch_tersoff_gather(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 template <typename T>

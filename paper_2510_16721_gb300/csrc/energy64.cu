@@ -8,8 +8,8 @@
 // the energy -- and only the energy -- in FP64 from the cell list of the
 // configuration being reported: pair vectors from the two-term offsets (exact
 // positions), bin displacements and wrap corrections in FP64, then the
-// Lennard-Jones or Tersoff energy of Sec. II.B's per-atom split summed over
-// atoms in FP64.  Used by cfneb_get_path and cfneb_evaluate, never inside a
+// Lennard-Jones, Tersoff or NEP-style energy of Sec. II.B's per-atom split
+// summed over atoms in FP64.  Used by cfneb_get_path and cfneb_evaluate, never inside a
 // relaxation step.
 //
 // FP64 arithmetic is scarce on this GPU, so it is spent on the terms only:
@@ -103,6 +103,52 @@ __device__ inline double bond_order64(double bz, double n, double m2n) {
     return 1.0 + y * (1.0 + y * (0.5 + y * (1.0 / 6.0 + y * (1.0 / 24.0 + y * (1.0 / 120.0 + y / 720.0)))));
 }
 
+// FP64 pair vectors of the neighbour-list entries of slot t within rc
+// (periodic images included, the atom itself excluded); returns their count
+template <typename T>
+__device__ inline int list_vectors64(const BandDev &b, int img, int t, const ImgScalars &sc,
+                                     double rc, double *rx, double *ry, double *rz, double *rd) {
+    using T4 = typename Vec4<T>::type;
+    const size_t base = (size_t)img * b.n;
+    const T4 *off = (const T4 *)b.slot_off + base;
+    const T4 *offl = (const T4 *)b.slot_off_lo + base;
+    const int *nslot = b.nbr_slot + (size_t)img * MAXN_TERSOFF * b.n;
+    const int *ncode = b.nbr_code + (size_t)img * MAXN_TERSOFF * b.n;
+    const int ne = b.nbr_cnt[base + t];
+    const int bin = b.slot_bin[base + t];
+    const int nb1 = sc.nb[1], nb2 = sc.nb[2];
+    const int bb[3] = {bin / (nb1 * nb2), (bin / nb2) % nb1, bin % nb2};
+    const T4 oi = off[t], oil = offl[t];
+    int cnt = 0;
+    for (int e = 0; e < ne; ++e) {
+        const int q = nslot[(size_t)e * b.n + t];
+        const int code = ncode[(size_t)e * b.n + t];
+        const int dd[3] = {(code & 31) - 16, ((code >> 5) & 31) - 16, ((code >> 10) & 31) - 16};
+        int tt[3];
+        for (int a = 0; a < 3; ++a) {
+            int w = bb[a] + dd[a];
+            tt[a] = 0;
+            while (w < 0) { w += sc.nb[a]; --tt[a]; }
+            while (w >= sc.nb[a]) { w -= sc.nb[a]; ++tt[a]; }
+        }
+        double c[3];
+        for (int k = 0; k < 3; ++k)
+            c[k] = dd[0] * sc.bv[k] + dd[1] * sc.bv[3 + k] + dd[2] * sc.bv[6 + k] +
+                   tt[0] * sc.dh[k] + tt[1] * sc.dh[3 + k] + tt[2] * sc.dh[6 + k];
+        double r[3];
+        pair_vec64<T>(oi, oil, off[q], offl[q], c, r);
+        const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        if (r2 < rc * rc && r2 > 0.0) {
+            rx[cnt] = r[0];
+            ry[cnt] = r[1];
+            rz[cnt] = r[2];
+            rd[cnt] = sqrt(r2);
+            ++cnt;
+        }
+    }
+    return cnt;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(TILE) k_energy64(const Tile *tiles, BandDev *bands) {
     Tile tl = tiles[blockIdx.x];
@@ -119,50 +165,11 @@ __global__ void __launch_bounds__(TILE) k_energy64(const Tile *tiles, BandDev *b
                 const double sr6 = s2 * s2 * s2 / (r2 * r2 * r2);
                 U += 0.5 * (4.0 * p.eps * (sr6 * sr6 - sr6) - p.ephi_c);
             });
-        } else {
+        } else if (bp->kind == 1) {
             const TersoffParams p = *(const TersoffParams *)bp->pot;
             const double rc = p.R + p.D;
             double rx[MAXN_TERSOFF], ry[MAXN_TERSOFF], rz[MAXN_TERSOFF], rd[MAXN_TERSOFF];
-            int cnt = 0;
-            // the neighbour list (within rc + skin) of slot t
-            using T4 = typename Vec4<T>::type;
-            const size_t base = (size_t)tl.img * b.n;
-            const T4 *off = (const T4 *)b.slot_off + base;
-            const T4 *offl = (const T4 *)b.slot_off_lo + base;
-            const int *nslot = b.nbr_slot + (size_t)tl.img * MAXN_TERSOFF * b.n;
-            const int *ncode = b.nbr_code + (size_t)tl.img * MAXN_TERSOFF * b.n;
-            const int ne = b.nbr_cnt[base + t];
-            const int bin = b.slot_bin[base + t];
-            const int nb1 = sc.nb[1], nb2 = sc.nb[2];
-            const int bb[3] = {bin / (nb1 * nb2), (bin / nb2) % nb1, bin % nb2};
-            const T4 oi = off[t], oil = offl[t];
-            for (int e = 0; e < ne; ++e) {
-                const int q = nslot[(size_t)e * b.n + t];
-                const int code = ncode[(size_t)e * b.n + t];
-                const int dd[3] = {(code & 31) - 16, ((code >> 5) & 31) - 16,
-                                   ((code >> 10) & 31) - 16};
-                int tt[3];
-                for (int a = 0; a < 3; ++a) {
-                    int w = bb[a] + dd[a];
-                    tt[a] = 0;
-                    while (w < 0) { w += sc.nb[a]; --tt[a]; }
-                    while (w >= sc.nb[a]) { w -= sc.nb[a]; ++tt[a]; }
-                }
-                double c[3];
-                for (int k = 0; k < 3; ++k)
-                    c[k] = dd[0] * sc.bv[k] + dd[1] * sc.bv[3 + k] + dd[2] * sc.bv[6 + k] +
-                           tt[0] * sc.dh[k] + tt[1] * sc.dh[3 + k] + tt[2] * sc.dh[6 + k];
-                double r[3];
-                pair_vec64<T>(oi, oil, off[q], offl[q], c, r);
-                const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-                if (r2 < rc * rc && r2 > 0.0) {
-                    rx[cnt] = r[0];
-                    ry[cnt] = r[1];
-                    rz[cnt] = r[2];
-                    rd[cnt] = sqrt(r2);
-                    ++cnt;
-                }
-            }
+            const int cnt = list_vectors64<T>(b, tl.img, t, sc, rc, rx, ry, rz, rd);
             const double pi = 3.14159265358979323846;
             const double c2d2 = p.c * p.c / (p.d * p.d), d2 = p.d * p.d;
             const double pi_4D = 0.25 * pi / p.D, m2n = -0.5 / p.n;
@@ -186,6 +193,50 @@ __global__ void __launch_bounds__(TILE) k_energy64(const Tile *tiles, BandDev *b
                 U += 0.5 * fc[j] * (p.A * exp(-p.lambda1 * rd[j]) -
                                     bond_order64(p.beta * zeta, p.n, m2n) * p.B * exp(-p.lambda2 * rd[j]));
             }
+        } else {
+            // NEP-style site energy (descriptors and network as in the force
+            // kernel), in FP64 from the list's pair vectors
+            const double rc = bp->pot[0];
+            double rx[MAXN_TERSOFF], ry[MAXN_TERSOFF], rz[MAXN_TERSOFF], rd[MAXN_TERSOFF];
+            const int cnt = list_vectors64<T>(b, tl.img, t, sc, rc, rx, ry, rz, rd);
+            const double *w = b.nep_w;
+            double qd[NEP_ND], gA[MAXN_TERSOFF][NEP_NA];
+            for (int d = 0; d < NEP_ND; ++d) qd[d] = 0.0;
+            for (int j = 0; j < cnt; ++j) {
+                const double fcj = 0.5 * (1.0 + cospi(rd[j] / rc));
+                const double x = 2.0 * (rd[j] / rc - 1.0) * (rd[j] / rc - 1.0) - 1.0;
+                double f[NEP_K], t0 = 1.0, t1 = x;
+                f[0] = fcj;
+                f[1] = 0.5 * (x + 1.0) * fcj;
+                for (int k = 2; k < NEP_K; ++k) {
+                    const double t2 = 2.0 * x * t1 - t0;
+                    f[k] = 0.5 * (t2 + 1.0) * fcj;
+                    t0 = t1;
+                    t1 = t2;
+                }
+                for (int m = 0; m < NEP_NR; ++m)
+                    for (int k = 0; k < NEP_K; ++k) qd[m] += w[NEP_OCR + m * NEP_K + k] * f[k];
+                for (int m = 0; m < NEP_NA; ++m) {
+                    gA[j][m] = 0.0;
+                    for (int k = 0; k < NEP_K; ++k) gA[j][m] += w[NEP_OCA + m * NEP_K + k] * f[k];
+                }
+            }
+            for (int j = 0; j < cnt; ++j)
+                for (int k = 0; k < cnt; ++k) {
+                    const double c = (rx[j] * rx[k] + ry[j] * ry[k] + rz[j] * rz[k]) / (rd[j] * rd[k]);
+                    const double P[4] = {c, 1.5 * c * c - 0.5, (2.5 * c * c - 1.5) * c,
+                                         (4.375 * c * c - 3.75) * c * c + 0.375};
+                    for (int m = 0; m < NEP_NA; ++m)
+                        for (int l = 0; l < NEP_L; ++l)
+                            qd[NEP_NR + m * NEP_L + l] += gA[j][m] * gA[k][m] * (j == k ? 1.0 : P[l]);
+                }
+            double Ui = -w[NEP_OB1];
+            for (int h = 0; h < NEP_H; ++h) {
+                double a = -w[NEP_OB0 + h];
+                for (int d = 0; d < NEP_ND; ++d) a += w[NEP_OW0 + h * NEP_ND + d] * qd[d];
+                Ui += w[NEP_OW1 + h] * tanh(a);
+            }
+            U += Ui;
         }
     }
     double acc[1] = {U};

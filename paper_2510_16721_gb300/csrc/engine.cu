@@ -46,17 +46,19 @@ struct CudaFail {
         }                                                                                \
     } while (0)
 
+static_assert(NEP_NW == CFNEB_NEP_N_WEIGHTS, "NEP weight count of the header and kernels");
+
 enum KernelId {
     K_MAPBACK, K_SKIN_CHECK, K_BIN_ASSIGN, K_BIN_TILESUM, K_BIN_TILESCAN, K_BIN_SCANFILL, K_BIN_SCATTER,
     K_BIN_ORDER, K_LJ, K_TERS_LIST, K_TERS_REVERSE, K_TERS_PARTIALS, K_TERS_GATHER, K_IMAGE_FINALIZE,
     K_BAND_DOTS, K_DOTS_REDUCE, K_NEB_COEF, K_NEB_FORCE, K_FIRE_SCALARS, K_FIRE_UPDATE, K_LJ_LIST,
-    K_LJ_CELLS, K_COUNT
+    K_LJ_CELLS, K_NEP_PARTIALS, K_COUNT
 };
 const char *kKernelNames[K_COUNT] = {
     "mapback", "skin_check", "bin_assign", "bin_tilesum", "bin_tilescan", "bin_scanfill", "bin_scatter",
     "bin_order", "lj_force", "tersoff_list", "tersoff_reverse", "tersoff_partials", "tersoff_gather",
     "image_finalize", "band_dots", "dots_reduce", "neb_coef", "neb_force", "fire_scalars",
-    "fire_update", "lj_list", "lj_force_cells"};
+    "fire_update", "lj_list", "lj_force_cells", "nep_partials"};
 
 const double kTersoff1988C[11] = {1393.6, 346.74, 3.4879, 2.2119, 1.5724e-7, 0.72751,
                                   38049.0, 4.3484, -0.57058, 1.95, 0.15};
@@ -231,6 +233,8 @@ struct LaunchSet {
     int n_ljc = 0;
     const Tile *atiles_ters = nullptr;   // the Tersoff bands' atom tiles
     int n_ters = 0;
+    const Tile *atiles_nep = nullptr;    // the NEP bands' atom tiles
+    int n_nep = 0;
     const Tile *rtiles = nullptr;        // row tiles
     int n_rtiles = 0;
     const int *band_ids = nullptr;
@@ -283,6 +287,13 @@ void enqueue_eval_set(const LaunchSet &ls, Launcher &L, bool forces = true) {
         L.pre(K_TERS_REVERSE); launch_tersoff_reverse<T>(ls.atiles_ters, ls.n_ters, d, s);
         L.post(K_TERS_REVERSE);
     }
+    // NEP bands use the same many-body lists
+    if (ls.n_nep) {
+        L.pre(K_TERS_LIST); launch_tersoff_list<T>(ls.atiles_nep, ls.n_nep, d, s);
+        L.post(K_TERS_LIST);
+        L.pre(K_TERS_REVERSE); launch_tersoff_reverse<T>(ls.atiles_nep, ls.n_nep, d, s);
+        L.post(K_TERS_REVERSE);
+    }
     if (!forces) {
         launch_energy64<T>(ls.atiles, ls.n_atiles, ls.imgs, ls.nimg, d, s);
         return;
@@ -297,6 +308,12 @@ void enqueue_eval_set(const LaunchSet &ls, Launcher &L, bool forces = true) {
         L.pre(K_TERS_PARTIALS); launch_tersoff_partials<T>(ls.atiles_ters, ls.n_ters, d, s);
         L.post(K_TERS_PARTIALS);
         L.pre(K_TERS_GATHER); launch_tersoff_gather<T>(ls.atiles_ters, ls.n_ters, d, s);
+        L.post(K_TERS_GATHER);
+    }
+    if (ls.n_nep) {
+        L.pre(K_NEP_PARTIALS); launch_nep_partials<T>(ls.atiles_nep, ls.n_nep, d, s);
+        L.post(K_NEP_PARTIALS);
+        L.pre(K_TERS_GATHER); launch_tersoff_gather<T>(ls.atiles_nep, ls.n_nep, d, s);
         L.post(K_TERS_GATHER);
     }
     L.pre(K_IMAGE_FINALIZE); launch_image_finalize<T>(ls.imgs, ls.nimg, d, s); L.post(K_IMAGE_FINALIZE);
@@ -317,7 +334,8 @@ void enqueue_step_set(const LaunchSet &ls, Launcher &L) {
 }
 
 int launches_in_set(const LaunchSet &ls) {
-    return 8 + (ls.n_lj ? 2 : 0) + (ls.n_ljc ? 1 : 0) + (ls.n_ters ? 4 : 0) + 1 + 6;
+    return 8 + (ls.n_lj ? 2 : 0) + (ls.n_ljc ? 1 : 0) + (ls.n_ters ? 4 : 0) + (ls.n_nep ? 4 : 0) +
+           1 + 6;
 }
 
 LaunchSet band_set(cfneb_band *b, const ImgRef *imgs, int nimg, const Tile *atiles, int nat) {
@@ -334,6 +352,9 @@ LaunchSet band_set(cfneb_band *b, const ImgRef *imgs, int nimg, const Tile *atil
     } else if (b->kind == CFNEB_LJ) {
         ls.atiles_ljc = atiles;
         ls.n_ljc = nat;
+    } else if (b->kind == CFNEB_NEP) {
+        ls.atiles_nep = atiles;
+        ls.n_nep = nat;
     } else {
         ls.atiles_ters = atiles;
         ls.n_ters = nat;
@@ -704,6 +725,19 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
         P.pot[1] = sig;
         P.pot[2] = rc;
         P.pot[3] = pot->shift_energy ? 4.0 * eps * (sr6 * sr6 - sr6) : 0.0;
+    } else if (pot->kind == CFNEB_NEP) {
+        rc = pot->nep_rc;
+        P.pot[0] = rc;
+        // the many-body list and pair-vector code reads R (here rc) from the
+        // Tersoff constant block: s = r - rc
+        TersoffParams tp;
+        std::memset(&tp, 0, sizeof(tp));
+        tp.R = rc;
+        tp.D = 1.0;
+        tp.d = 1.0;
+        tp.n = 1.0;
+        P.tpf.load(tp);
+        P.tpd.load(tp);
     } else {
         bool zero = true;
         for (int k = 0; k < 11; ++k) zero = zero && pot->tersoff[k] == 0.0;
@@ -721,7 +755,7 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
     // keep their 3-4 entries) and 0.12 rc for LJ (0.3 sigma at rc = 2.5
     // sigma: the list holds ~1.4 candidates per pair inside rc, against ~3.4
     // for a walk of half-cutoff bins)
-    const double skin = opt->skin >= 0.0 ? opt->skin : (pot->kind == CFNEB_TERSOFF ? 0.15 : 0.12 * rc);
+    const double skin = opt->skin >= 0.0 ? opt->skin : (pot->kind == CFNEB_LJ ? 0.12 * rc : 0.15);
     const double rl = rc + skin;
     b->rl = rl;
     // bin width: the caller's, the cached autotuned one for this class, or rc
@@ -787,7 +821,18 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
         d.nbr_slot = (int *)dalloc(b, na * d.lj_cap * sizeof(int));
         CK(cudaMemsetAsync(d.nbr_cnt, 0, na * sizeof(int), b->s));
     }
-    if (pot->kind == CFNEB_TERSOFF) {
+    if (pot->kind == CFNEB_NEP) {
+        double *w = (double *)dalloc(b, NEP_NW * (sizeof(double) + sizeof(float)));
+        float *wf = (float *)(w + NEP_NW);
+        float hf[NEP_NW];
+        for (int k = 0; k < NEP_NW; ++k) hf[k] = (float)pot->nep_weights[k];
+        CK(cudaMemcpyAsync(w, pot->nep_weights, NEP_NW * sizeof(double), cudaMemcpyHostToDevice, b->s));
+        CK(cudaMemcpyAsync(wf, hf, NEP_NW * sizeof(float), cudaMemcpyHostToDevice, b->s));
+        CK(cudaStreamSynchronize(b->s));  // hf is a stack array
+        d.nep_w = w;
+        d.nep_wf = wf;
+    }
+    if (pot->kind == CFNEB_TERSOFF || pot->kind == CFNEB_NEP) {
         d.nbr_cnt = (int *)dalloc(b, na * sizeof(int));
         d.nbr_slot = (int *)dalloc(b, na * MAXN_TERSOFF * sizeof(int));
         d.nbr_code = (int *)dalloc(b, na * MAXN_TERSOFF * sizeof(int));
@@ -996,7 +1041,7 @@ void grow(X **p, size_t *cap, size_t need) {
 void batch_rebuild(cfneb_batch *bt) {
     std::vector<BandDev> dv;
     std::vector<ImgRef> im;
-    std::vector<Tile> all, lj, ljc, ters, rows;
+    std::vector<Tile> all, lj, ljc, ters, nep, rows;
     std::vector<int> ids;
     int max_bins = 0;
     for (size_t k = 0; k < bt->bands.size(); ++k) {
@@ -1008,7 +1053,7 @@ void batch_rebuild(cfneb_batch *bt) {
             im.push_back({(int)k, i});
             for (int t = 0; t < b->dv.atpi; ++t) {
                 all.push_back({(int)k, i, t, 0});
-                (b->kind != CFNEB_LJ ? ters : b->dv.lj_cap > 0 ? lj : ljc)
+                (b->kind == CFNEB_NEP ? nep : b->kind != CFNEB_LJ ? ters : b->dv.lj_cap > 0 ? lj : ljc)
                     .push_back({(int)k, i, t, 0});
             }
             for (int t = 0; t < b->dv.rtpi; ++t) rows.push_back({(int)k, i, t, 0});
@@ -1020,6 +1065,7 @@ void batch_rebuild(cfneb_batch *bt) {
     tiles.insert(tiles.end(), lj.begin(), lj.end());
     tiles.insert(tiles.end(), ljc.begin(), ljc.end());
     tiles.insert(tiles.end(), ters.begin(), ters.end());
+    tiles.insert(tiles.end(), nep.begin(), nep.end());
     tiles.insert(tiles.end(), rows.begin(), rows.end());
     grow(&bt->d_tiles, &bt->cap_tiles, std::max<size_t>(tiles.size(), 1));
     grow(&bt->d_imgs, &bt->cap_imgs, std::max<size_t>(im.size(), 1));
@@ -1057,7 +1103,9 @@ void batch_rebuild(cfneb_batch *bt) {
     ls.n_ljc = (int)ljc.size();
     ls.atiles_ters = bt->d_tiles + all.size() + lj.size() + ljc.size();
     ls.n_ters = (int)ters.size();
-    ls.rtiles = bt->d_tiles + all.size() + lj.size() + ljc.size() + ters.size();
+    ls.atiles_nep = bt->d_tiles + all.size() + lj.size() + ljc.size() + ters.size();
+    ls.n_nep = (int)nep.size();
+    ls.rtiles = bt->d_tiles + all.size() + lj.size() + ljc.size() + ters.size() + nep.size();
     ls.n_rtiles = (int)rows.size();
     ls.band_ids = bt->d_ids;
     ls.nbands = (int)ids.size();
@@ -1173,6 +1221,7 @@ struct Request {
     double h0[9], h1[9];
     int n = 0, n_images = 0;
     cfneb_potential pot{};
+    std::vector<double> nep_w;  // the request's own copy of NEP weights
     cfneb_cell_filter filt{};
     cfneb_options opt{};
     double fmax = 0.0;
@@ -1240,6 +1289,7 @@ void server_admit(cfneb_server *sv) {
         std::memcpy(A.cell, r.h0, sizeof(r.h0));
         std::memcpy(B.cell, r.h1, sizeof(r.h1));
         cfneb_band *b = nullptr;
+        if (r.pot.kind == CFNEB_NEP) r.pot.nep_weights = r.nep_w.data();
         int st = cfneb_create_band(&A, &B, r.n_images, &r.pot, &r.filt, &r.opt, sv->user, &b);
         if (st != CFNEB_OK) {  // cannot be built at all: retire with the error
             r.status = st;
@@ -1361,8 +1411,16 @@ int cfneb_create_band(const cfneb_structure *initial, const cfneb_structure *fin
     if (initial->types)
         for (int i = 1; i < initial->n_atoms; ++i)
             if (initial->types[i] != initial->types[0]) return CFNEB_ERR_INVALID_ARG;
-    if (potential->kind != CFNEB_LJ && potential->kind != CFNEB_TERSOFF)
+    if (potential->kind != CFNEB_LJ && potential->kind != CFNEB_TERSOFF &&
+        potential->kind != CFNEB_NEP)
         return CFNEB_ERR_INVALID_ARG;
+    if (potential->kind == CFNEB_NEP) {
+        if (!potential->nep_weights || !(potential->nep_rc > 0.0) ||
+            !std::isfinite(potential->nep_rc))
+            return CFNEB_ERR_INVALID_ARG;
+        for (int k = 0; k < NEP_NW; ++k)
+            if (!std::isfinite(potential->nep_weights[k])) return CFNEB_ERR_INVALID_ARG;
+    }
     if (potential->kind == CFNEB_LJ &&
         (potential->rc <= 0 || potential->sigma <= 0 || potential->eps <= 0))
         return CFNEB_ERR_INVALID_ARG;
@@ -1385,7 +1443,7 @@ int cfneb_create_band(const cfneb_structure *initial, const cfneb_structure *fin
     if (opt.bin_scale != 0 && opt.bin_scale < 0.25) return CFNEB_ERR_INVALID_ARG;
     {
         // a skin (< 0: the default) of at most the potential's cutoff
-        double rcut = potential->rc;
+        double rcut = potential->kind == CFNEB_NEP ? potential->nep_rc : potential->rc;
         if (potential->kind == CFNEB_TERSOFF) {
             const bool dflt = std::all_of(potential->tersoff, potential->tersoff + 11,
                                           [](double v) { return v == 0.0; });
@@ -1857,6 +1915,11 @@ int cfneb_server_submit(cfneb_server *sv, const cfneb_structure *initial,
     std::memcpy(r.h1, final_->cell, sizeof(r.h1));
     r.n_images = n_images;
     r.pot = *potential;
+    if (potential->kind == CFNEB_NEP) {
+        if (!potential->nep_weights) return CFNEB_ERR_INVALID_ARG;
+        r.nep_w.assign(potential->nep_weights, potential->nep_weights + NEP_NW);
+        r.pot.nep_weights = nullptr;  // set to the copy when the band is made
+    }
     r.filt = cell_filter ? *cell_filter : cfneb_cell_filter{1, CFNEB_ROTFREE_B, 0.0, 0.0};
     r.opt = *options;
     r.fmax = fmax;
