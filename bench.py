@@ -38,12 +38,17 @@ WORKLOADS = {
                                               precision="mixed", n_max=24),
     "tersoff_graphite_hexdiamond_576": dict(kind="tersoff", reps=(6, 4, 3), n_images=9,
                                             precision="fp64", n_max=9),
+    # the same band under the NEP-style descriptor + network potential
+    # (synthetic weights, cutoff 2.1 A)
+    "nep_graphite_hexdiamond_98304": dict(kind="tersoff", potential="nep", reps=(32, 24, 16),
+                                          n_images=12, precision="mixed", n_max=24),
     # 64 LJ vacancy / divacancy bands, 256..32768 atoms log-uniform, 5..15
     # images, +-2% end strain, cell filter on, one batch (one launch per kernel)
     "lj_batch64": dict(kind="lj_batch", n_bands=64, precision="mixed"),
     "serve_poisson20": dict(kind="serve", rate=20.0, precision="mixed", budget_gb=150.0),
 }
 CPU_SAMPLE_REPS = (6, 4, 3)   # the 576-atom tile the large band is built from
+NEP_SEED, NEP_RC = 3, 2.1     # synthetic NEP-style weights and cutoff
 
 # algorithmic work per kernel launch: FLOPs for the force
 # kernels (useful arithmetic, transcendental functions counted as 1), bytes for
@@ -52,6 +57,11 @@ FLOP_MODELS = {
     "tersoff_partials": lambda w: 65.0 * w["pairs"] + 89.0 * w["triples"],
     "lj_force": lambda w: 40.0 * w["pairs"],
     "lj_force_cells": lambda w: 40.0 * w["pairs"],
+    # NEP-style: per entry the basis and its derivative twice, radial and
+    # angular functions, partial and virial (~200); per ordered neighbour
+    # pair half of the unordered pair's descriptor and derivative work
+    # (~60); per atom the network forward and backward (~870)
+    "nep_partials": lambda w: 200.0 * w["pairs"] + 60.0 * w["triples"] + 870.0 * w["atoms"],
 }
 BYTE_MODELS = {
     "tersoff_gather": lambda w: w["pairs"] * (8 + 6 * w["ts"]) + w["atoms"] * (8 + 3 * w["ts"]),
@@ -174,8 +184,15 @@ def make_band(g, wl, cfg, stream, precision=None):
     opt.maxstep = 0.2
     opt.n_max = wl["n_max"]
     cf = g.CellFilter(1, g.ROTFREE_B, 0.0, 0.0)
-    return g.create_band((R0, h0), (R1, h1), wl["n_images"], g.tersoff_potential(), cf, opt,
+    pot = (g.nep_potential(ci_nep_weights(), NEP_RC) if wl.get("potential") == "nep"
+           else g.tersoff_potential())
+    return g.create_band((R0, h0), (R1, h1), wl["n_images"], pot, cf, opt,
                          stream=stream, noise=cfg["noise"])
+
+
+def ci_nep_weights():
+    import cfneb_inputs as ci
+    return ci.nep_weights(NEP_SEED)
 
 
 def time_steps(torch, band, stream, k, dist=None):
@@ -204,7 +221,9 @@ def cpu_oracle_rate(wl, seconds=12.0, steps=None, warmup=0):
     cfg = ci.tersoff_graphite_hexdiamond(reps=CPU_SAMPLE_REPS, n_images=wl["n_images"],
                                          seed=2510)
     R0, h0, R1, h1 = cfg["endpoints"]
-    band = oracle.make_band(oracle.Tersoff(), R0, h0, R1, h1, wl["n_images"], k=cfg["k"],
+    pot = (oracle.NEP(ci.nep_weights(NEP_SEED), rc=NEP_RC) if wl.get("potential") == "nep"
+           else oracle.Tersoff())
+    band = oracle.make_band(pot, R0, h0, R1, h1, wl["n_images"], k=cfg["k"],
                             climb=True, cell_filter=True,
                             fire=oracle.Fire(dt=cfg["dt"], dt_max=10 * cfg["dt"]),
                             noise=cfg["noise"])
@@ -223,9 +242,11 @@ def cpu_oracle_rate(wl, seconds=12.0, steps=None, warmup=0):
     n = len(R0)
     moving = wl["n_images"] - 2
     return {"value": n * moving * n_done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d-atom tile of the same graphite->hex-diamond Tersoff band, %d images "
+            "sample": "%d-atom tile of the same graphite->hex-diamond %s band, %d images "
                       "(%d moving), %d FP64 steps in %.1f s, one thread; brute-force O(n^2) "
-                      "periodic neighbour search" % (n, wl["n_images"], moving, n_done, el),
+                      "periodic neighbour search" % (n, "NEP-style" if wl.get("potential") == "nep"
+                                                     else "Tersoff", wl["n_images"], moving,
+                                                     n_done, el),
             "steps": n_done, "seconds": el}
 
 
@@ -396,7 +417,10 @@ def run_ours(args, wl_name):
             "data": "synthetic",
             "config": {"workload": wl_name, "atoms": n, "images": wl["n_images"],
                        "moving_images": moving, "precision": wl["precision"],
-                       "potential": "Tersoff 1988 C", "cell_filter": "rotation-free (B)",
+                       "potential": ("NEP-style descriptors + network, synthetic weights "
+                                     "(seed %d), rc %.1f A" % (NEP_SEED, NEP_RC)
+                                     if wl.get("potential") == "nep" else "Tersoff 1988 C"),
+                       "cell_filter": "rotation-free (B)",
                        "l2": "working set > 129 MB L2, no flush", "graph": "CUDA graph per step",
                        "parallelism": "replicas x%d" % ws},
             "roofline": roof, "kernel_share": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
