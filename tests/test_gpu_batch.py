@@ -39,6 +39,10 @@ def _make(g, which, precision, **kw):
         h1s = ci.strained_cell(h1, 5, 0.02)
         return gpu_band(g, R0, h0, ci.affine(R1, h1, h1s), h1s, 5, g.lj_potential(), k=1.0,
                         dt=0.01, cell_filter=True, precision=precision, **kw)
+    if which == "nep96":  # the NEP-style potential on a 96-atom carbon path
+        R0, h0, R1, h1 = ci.graphite_hexdiamond_path((3, 2, 2))
+        return gpu_band(g, R0, h0, R1, h1, 7, g.nep_potential(ci.nep_weights(3), 2.1), k=0.1,
+                        dt=0.05, cell_filter=True, precision=precision, **kw)
     cfg = ci.tersoff_graphite_hexdiamond()
     R0, h0, R1, h1 = cfg["endpoints"]
     return gpu_band(g, R0, h0, R1, h1, 9, g.tersoff_potential(), k=0.1, dt=0.1,
@@ -54,7 +58,7 @@ def _same(a, b):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_batch_equals_alone_bitwise(g, precision):
-    names = ["lj31", "lj255", "ters576"]
+    names = ["lj31", "lj255", "ters576", "nep96"]
     batched = [_make(g, w, precision) for w in names]
     alone = [_make(g, w, precision) for w in names]
     bt = g.Batch(precision)
@@ -66,7 +70,7 @@ def test_batch_equals_alone_bitwise(g, precision):
     for a, b in zip(batched, alone):
         _same(a, b)
     st = bt.status()
-    assert [s["steps"] for s in st] == [12, 12, 12]
+    assert [s["steps"] for s in st] == [12, 12, 12, 12]
     bt.destroy()
 
 

@@ -81,3 +81,27 @@ def test_request_larger_than_budget_is_refused(g):
     r = sv.result(rid)
     assert r["state"] == 2 and r["status"] == g.ERR_HBM_BUDGET
     sv.destroy()
+
+
+def test_server_keeps_its_own_copy_of_nep_weights(g):
+    """A queued NEP-style request: the caller's weight array is overwritten
+    right after submission; the served band still runs on the submitted
+    weights (the same steps, barrier and status as the band alone)."""
+    R0, h0, R1, h1 = ci.graphite_hexdiamond_path((3, 2, 2))
+    w = ci.nep_weights(3)
+    o = g.default_options()
+    o.k_spring, o.dt, o.dt_max, o.precision, o.n_max = 0.1, 0.05, 0.5, g.FP64, 7
+    cf = g.CellFilter(1, g.ROTFREE_B, 0.0, 0.0)
+    sv = g.Server(g.FP64)
+    pot = g.nep_potential(w.copy(), 2.1)
+    rid = sv.submit((R0, h0), (R1, h1), 7, pot, cf, o, 1e-6, 40, arrival_s=0.0)
+    pot._keep[:] = np.nan  # the array the submitted pointer refers to
+    assert sv.run(until_s=60.0)
+    r = sv.result(rid)
+    assert r["state"] == 2 and r["status"] == 0 and r["steps"] == 40
+    alone = g.create_band((R0, h0), (R1, h1), 7, g.nep_potential(w, 2.1), cf, o)
+    alone.relax(1e-6, 40)
+    E = alone.get_path()["energies"]
+    assert r["barrier"] == pytest.approx(E.max() - E[0], rel=1e-12, abs=1e-12)
+    sv.destroy()
+    alone.destroy()
