@@ -9,7 +9,7 @@
  *   - cell-list build over all periodic images of every atom (the per-atom
  *     energy of Sec. II.B, Eq. U, depends on the neighbours of i in the
  *     periodic crystal);
- *   - Lennard-Jones or Tersoff energy, forces and virial
+ *   - Lennard-Jones, Tersoff or NEP-style energy, forces and virial
  *     V = -1/2 sum_ij r^ij (x) f^ij (Sec. II.B, Eqs. V, V2);
  *   - cell filter, forward map: atom rows F D^T and lattice rows
  *     1/2 D^-T V D^-1 / c (Sec. II.C; the 1/2 makes the lattice force the
@@ -36,7 +36,8 @@
  *     library orders its own work after the work already queued on that
  *     stream, and work queued on it later runs after the library's.  A band
  *     is not thread safe.
- *   - Units: LJ in reduced units (eps, sigma); Tersoff in eV and Angstrom.
+ *   - Units: LJ in reduced units (eps, sigma); Tersoff and NEP-style in eV
+ *     and Angstrom.
  */
 #ifndef CFNEB_H
 #define CFNEB_H
@@ -57,7 +58,7 @@ extern "C" {
 #define CFNEB_ERR_CUDA (-5)          /* a CUDA runtime call failed             */
 #define CFNEB_ERR_NONFINITE (-6)     /* NaN/Inf in forces, energies or state   */
 #define CFNEB_ERR_NOT_SPD (-7)       /* lattice coordinate B lost positivity   */
-#define CFNEB_ERR_NBR_OVERFLOW (-8)  /* more Tersoff neighbours than capacity  */
+#define CFNEB_ERR_NBR_OVERFLOW (-8)  /* more list neighbours than capacity    */
 #define CFNEB_ERR_TIMEOUT (-9)       /* a bounded device wait gave up          */
 #define CFNEB_ERR_STATE (-10)        /* call not valid in the current state    */
 
@@ -140,7 +141,8 @@ typedef struct {
                                  bound from the largest displacement and the
                                  cell change since the build); 0 rebuilds at
                                  every evaluation; < 0 selects the default
-                                 (Tersoff 0.15, LJ 0.12 rc).  At most rc.
+                                 (Tersoff and NEP-style 0.15, LJ 0.12 rc).
+                                 At most rc.
                                  LJ bands with a skin and at most 2^17 atoms
                                  keep per-atom neighbour lists; other LJ
                                  bands walk the cell list at every
@@ -236,7 +238,8 @@ int cfneb_evaluate(const cfneb_structure *structures, int32_t count,
  * mixed), the whole step is one captured CUDA graph, and each band keeps its
  * own FIRE state, convergence test and refinement.  Results of a band do not
  * depend on the other members (reductions use fixed per-band slots).
- * Members must share the precision; LJ and Tersoff bands may be mixed.
+ * Members must share the precision; LJ, Tersoff and NEP-style bands may be
+ * mixed.
  * While a band is a member its work is queued on the batch's stream; the
  * band calls above stay valid on it.  The batch does not own its bands. */
 typedef struct cfneb_batch cfneb_batch;
@@ -328,7 +331,7 @@ int cfneb_server_destroy(cfneb_server *server);
  * precision, atom count and density buckets).  Bands created later with
  * options.bin_scale = 0 in a cached class start with the cached width.
  * Bands created with bin_scale = 0 reserve bins for the finest candidate;
- * untuned classes start at 0.5 (LJ) or 1.0 (Tersoff).
+ * untuned classes start at 0.5 (LJ) or 1.0 (Tersoff, NEP-style).
  * *best_scale receives the chosen width / cutoff.  Synchronises. */
 int cfneb_autotune(cfneb_band *band, int32_t steps, double *best_scale);
 
@@ -351,7 +354,7 @@ const char *cfneb_kernel_name(int32_t kernel_id);
 /* Work counters of the last evaluation of the interior images, summed over
  * them: *pairs = neighbour entries (i, j, shift) inside the cutoff,
  * *triples = ordered pairs of distinct neighbour entries of one atom (the
- * three-body terms of Tersoff; 0 for LJ).  Used to turn kernel times into
+ * three-body terms of Tersoff and NEP-style; 0 for LJ).  Used to turn kernel times into
  * arithmetic rates.  Synchronises. */
 int cfneb_get_work(const cfneb_band *band, double *pairs, double *triples);
 
