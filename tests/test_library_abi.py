@@ -61,3 +61,43 @@ def test_host_only_calls(libmod):
 def test_sources_target_sm103a_only():
     from paper_2510_16721_gb300 import _build
     assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_nep_arguments_are_validated_on_the_host(libmod):
+    """A NEP-style potential with a wrong weight count, non-finite weights,
+    a missing weight array or a non-positive cutoff is rejected before any
+    CUDA call."""
+    import ctypes
+
+    import numpy as np
+
+    import cfneb_inputs as ci
+    g = libmod
+    with pytest.raises(ValueError):
+        g.nep_potential(np.zeros(5), 2.1)
+    R0, h0, R1, h1 = ci.graphite_hexdiamond_path((2, 2, 1))
+    keep = []
+    A = g.make_structure(R0, h0, keep)
+    B = g.make_structure(R1, h1, keep)
+    opt = g.default_options()
+    out = ctypes.c_void_p()
+    bad = []
+    w = ci.nep_weights(3)
+    w[10] = np.inf
+    bad.append(g.nep_potential(w, 2.1))
+    bad.append(g.nep_potential(ci.nep_weights(3), 0.0))
+    bad.append(g.nep_potential(ci.nep_weights(3), float("nan")))
+    p = g.Potential()
+    p.kind, p.nep_rc = g.NEP, 2.1
+    bad.append(p)
+    for pot in bad:
+        st = g.lib().cfneb_create_band(ctypes.byref(A), ctypes.byref(B), 5, ctypes.byref(pot),
+                                       None, ctypes.byref(opt), None, ctypes.byref(out))
+        assert st == g.ERR_INVALID_ARG
+    # control: valid arguments pass the host checks (and then need a device)
+    import torch
+    if not torch.cuda.is_available():
+        good = g.nep_potential(ci.nep_weights(3), 2.1)
+        st = g.lib().cfneb_create_band(ctypes.byref(A), ctypes.byref(B), 5, ctypes.byref(good),
+                                       None, ctypes.byref(opt), None, ctypes.byref(out))
+        assert st != g.ERR_INVALID_ARG and st < 0
