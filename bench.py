@@ -74,6 +74,29 @@ BYTE_MODELS = {
 }
 
 
+def kernel_rooflines(prof, w, peaks, peak_src, sm_max):
+    """Roofline of every kernel with a work model, from the per-kernel
+    CUDA-event profile (mean launch time; short kernels include their launch
+    latency there).  Kernels that only work on list rebuilds are left out:
+    their models count every atom."""
+    rebuild_only = ("bin_scatter", "bin_order")
+    out = {}
+    for k, (ms, cnt) in prof.items():
+        if not cnt or k in rebuild_only:
+            continue
+        t = ms / cnt * 1e-3
+        if k in FLOP_MODELS:
+            ach = FLOP_MODELS[k](w) / t / 1e12
+            peak = fp32_peak_tflops(sm_max)
+            out[k] = {"bound": "alu", "achieved": ach, "unit": "TFLOP/s", "frac": ach / peak,
+                      "ms": ms / cnt}
+        elif k in BYTE_MODELS:
+            ach = BYTE_MODELS[k](w) / t / 1e9
+            out[k] = {"bound": "hbm", "achieved": ach, "unit": "GB/s",
+                      "frac": ach / peaks["hbm_gbs"], "ms": ms / cnt}
+    return out
+
+
 def fp32_peak_tflops(sm_mhz=2070.0):
     """152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x clock."""
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -370,6 +393,7 @@ def run_ours(args, wl_name):
                  "work_per_launch": {"pairs": pairs, "triples": triples, "atoms": n * moving}})
     launches = band.launches_per_step() * args.steps
     kernel_share = {k: round(v[0] / total, 4) for k, v in prof.items() if v[1]}
+    roofs = kernel_rooflines(prof, w, peaks, peak_src, (clk or {}).get("sm_max_mhz") or 2070.0)
     band.destroy()
     del band
 
@@ -424,7 +448,8 @@ def run_ours(args, wl_name):
                        "l2": "working set > 129 MB L2, no flush", "graph": "CUDA graph per step",
                        "parallelism": "replicas x%d" % ws},
             "roofline": roof, "kernel_share": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clk, "fp64_plain": fp64, "lists": lists}
+            "gpu_launches": launches, "clocks": clk, "fp64_plain": fp64, "lists": lists,
+            "rooflines": roofs}
     print(json.dumps(line))
     if dist is not None:
         dist.barrier()
@@ -535,6 +560,7 @@ def run_batch(args):
                 "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % peak_src}
     roof.update({"kernel": dom, "kernel_ms": dom_ms, "share": prof[dom][0] / total,
                  "traffic": traffic_for(dom), "work_per_launch": {"pairs": pairs, "atoms": work}})
+    roofs = kernel_rooflines(prof, w, peaks, peak_src, (clk or {}).get("sm_max_mhz") or 2070.0)
     # launches of the profiled batch steps (every kernel, one launch each)
     launches = int(round(sum(v[1] for v in prof.values()) / kp * args.steps))
     bt.destroy()
@@ -600,7 +626,7 @@ def run_batch(args):
             "roofline": roof, "kernel_share": {k: round(v[0] / total, 4)
                                                for k, v in prof.items() if v[1]},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "fp64_plain": fp64, "create_s": t_create, "lists": lists}
+            "fp64_plain": fp64, "create_s": t_create, "lists": lists, "rooflines": roofs}
     print(json.dumps(line))
     if dist is not None:
         dist.barrier()
