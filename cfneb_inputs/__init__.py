@@ -174,9 +174,26 @@ def tersoff_endpoint_cells():
             np.array(d["R_hexdiamond"]), np.array(d["h_hexdiamond"]))
 
 
+def unwrap_cell(R_init, h_init, R_final, h_final):
+    """Final positions of a matched cell (same atom order), each shifted by
+    the lattice vector of the final cell that brings its fractional
+    coordinate nearest to the initial one, within the cell itself."""
+    s0 = np.asarray(R_init) @ np.linalg.inv(h_init)
+    s1 = np.asarray(R_final) @ np.linalg.inv(h_final)
+    return (s1 - np.round(s1 - s0)) @ h_final
+
+
 def graphite_hexdiamond_path(reps):
-    """Endpoints of the graphite -> hexagonal-diamond band at a tiling."""
+    """Endpoints of the graphite -> hexagonal-diamond band at a tiling.
+
+    The matched final cell is unwrapped against the initial one in the
+    8-atom cell before both are tiled, so that every tile carries the same
+    per-atom displacement.  (Unwrapping after tiling would send an atom whose
+    target wrapped across the 8-atom cell boundary to the site in its own
+    tile, 2.9 A through the layer, instead of the neighbouring tile's site
+    1.46 A away.)"""
     Rg, hg, Rd, hd = tersoff_endpoint_cells()
+    Rd = unwrap_cell(Rg, hg, Rd, hd)
     R0, h0 = tile(Rg, hg, reps)
     R1, h1 = tile(Rd, hd, reps)
     return R0, h0, R1, h1
