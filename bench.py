@@ -68,10 +68,22 @@ BYTE_MODELS = {
     "bin_assign": lambda w: w["atoms"] * (7 * w["ts"] + 16),
     "bin_scatter": lambda w: w["atoms"] * 16,
     "bin_order": lambda w: w["atoms"] * (16 + 8 * w["ts"]),
-    "band_dots": lambda w: w["dof"] * 4 * w["ts"],
-    "neb_force": lambda w: w["dof"] * 6 * w["ts"],
+    # pass 1 reads X_{i-1}, X_i, X_{i+1}, F, v; pass 2 reads X_{i-1}, X_i,
+    # X_{i+1}, F and writes f_NEB; pass 3 reads X, v, f_NEB, writes X, v
+    "band_dots": lambda w: w["dof"] * 5 * w["ts"],
+    "neb_force": lambda w: w["dof"] * 5 * w["ts"],
     "fire_update": lambda w: w["dof"] * 5 * w["ts"],
 }
+# the band phase (passes 1-3) against the minimum traffic of a step's NEB
+# projection and FIRE move: 108 B per moving atom-image in FP32 (read X, v,
+# F and write X, v, 60 B; the neighbour images' X for the tangents, 24 B;
+# the re-reads of three passes, 24 B), doubled for FP64 vectors
+BAND_PHASE = ("band_dots", "neb_force", "fire_update")
+BAND_PHASE_BYTES = lambda w: w["atoms"] * 108.0 * (w["ts"] / 4)
+# the force kernel's useful work by the per-entry / per-triple model of the
+# method's arithmetic: 30 flops and 2 exponentials per neighbour entry,
+# 60 flops per ordered triple (zeta and its derivatives)
+SURVEY_FLOPS = {"tersoff_partials": lambda w: 32.0 * w["pairs"] + 60.0 * w["triples"]}
 
 
 def kernel_rooflines(prof, w, peaks, peak_src, sm_max):
@@ -94,12 +106,29 @@ def kernel_rooflines(prof, w, peaks, peak_src, sm_max):
             ach = BYTE_MODELS[k](w) / t / 1e9
             out[k] = {"bound": "hbm", "achieved": ach, "unit": "GB/s",
                       "frac": ach / peaks["hbm_gbs"], "ms": ms / cnt}
+    if all(prof.get(k, (0, 0))[1] for k in BAND_PHASE):
+        t = sum(prof[k][0] / prof[k][1] for k in BAND_PHASE) * 1e-3
+        ach = BAND_PHASE_BYTES(w) / t / 1e9
+        out["band_phase"] = {"bound": "hbm", "achieved": ach, "unit": "GB/s",
+                             "frac": ach / peaks["hbm_gbs"], "ms": t * 1e3,
+                             "model": "108 B per moving atom-image (FP32), passes 1-3"}
     return out
 
 
+def sm_count():
+    """Streaming multiprocessors of the current device (152 on a GB300)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    except Exception:
+        pass
+    return 152
+
+
 def fp32_peak_tflops(sm_mhz=2070.0):
-    """152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    """SMs x 128 FP32 lanes x 2 FLOP (FMA) x clock."""
+    return sm_count() * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 def measured_peaks():
@@ -237,8 +266,45 @@ def time_steps(torch, band, stream, k, dist=None):
     return start.elapsed_time(end)
 
 
-def cpu_oracle_rate(wl, seconds=12.0, steps=None, warmup=0):
-    """Oracle (FP64 CPU) atom·steps/s on the 576-atom tile of the same band."""
+def host_cpu():
+    """(logical cores available to this process, CPU model string)."""
+    import os
+    import platform
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu part", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    if k == "model name":
+                        break
+    except OSError:
+        pass
+    return int(cores or 1), "%s (%s)" % (model, platform.machine())
+
+
+def oracle_step_on(band, pool):
+    """One oracle step with the interior images' energies and forces
+    evaluated concurrently on the pool's threads (the oracle's C potential
+    runs without the interpreter lock), then the oracle's own NEB force and
+    FIRE move.  The arithmetic is the oracle's: only which core evaluates
+    which image differs."""
+    fn = band.image_fn
+    xs = [band.X[i] for i in range(1, band.N - 1)]
+    done = dict(zip(map(id, xs), pool.map(fn, xs)))
+    band.image_fn = lambda X: done.pop(id(X)) if id(X) in done else fn(X)
+    try:
+        band.compute()
+    finally:
+        band.image_fn = fn
+    band.update()
+
+
+def cpu_oracle_rate(wl, seconds=12.0, steps=None, warmup=0, threads=1):
+    """Oracle (FP64 CPU) atom·steps/s on the 576-atom tile of the same band,
+    on `threads` host cores (images in parallel)."""
     import oracle
     import cfneb_inputs as ci
     cfg = ci.tersoff_graphite_hexdiamond(reps=CPU_SAMPLE_REPS, n_images=wl["n_images"],
@@ -250,26 +316,39 @@ def cpu_oracle_rate(wl, seconds=12.0, steps=None, warmup=0):
                             climb=True, cell_filter=True,
                             fire=oracle.Fire(dt=cfg["dt"], dt_max=10 * cfg["dt"]),
                             noise=cfg["noise"])
+    import concurrent.futures
+    pool = concurrent.futures.ThreadPoolExecutor(max_workers=threads) if threads > 1 else None
+
+    def one():
+        if pool is None:
+            band.step(1)
+        else:
+            oracle_step_on(band, pool)
+
     for _ in range(warmup):
-        band.step(1)
+        one()
     n_done = 0
     t0 = time.perf_counter()
     while True:
-        band.step(1)
+        one()
         n_done += 1
         el = time.perf_counter() - t0
         if steps is not None and n_done >= steps:
             break
         if steps is None and el >= seconds:
             break
+    if pool is not None:
+        pool.shutdown()
     n = len(R0)
     moving = wl["n_images"] - 2
-    return {"value": n * moving * n_done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+    _, model = host_cpu()
+    return {"value": n * moving * n_done / el, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "%d-atom tile of the same graphite->hex-diamond %s band, %d images "
-                      "(%d moving), %d FP64 steps in %.1f s, one thread; brute-force O(n^2) "
-                      "periodic neighbour search" % (n, "NEP-style" if wl.get("potential") == "nep"
-                                                     else "Tersoff", wl["n_images"], moving,
-                                                     n_done, el),
+                      "(%d moving), %d FP64 steps in %.1f s on %d thread%s of %s (images in "
+                      "parallel); brute-force O(n^2) periodic neighbour search"
+                      % (n, "NEP-style" if wl.get("potential") == "nep" else "Tersoff",
+                         wl["n_images"], moving, n_done, el, threads, "" if threads == 1 else "s",
+                         model),
             "steps": n_done, "seconds": el}
 
 
@@ -278,7 +357,9 @@ def run_reference(args, wl_name):
     if ws > 1 and rank != 0:
         return 0
     wl = WORKLOADS[wl_name]
-    res = cpu_oracle_rate(wl, steps=max(1, args.steps), warmup=args.warmup)
+    cores, _ = host_cpu()
+    res = cpu_oracle_rate(wl, steps=max(1, args.steps), warmup=args.warmup,
+                          threads=min(cores, wl["n_images"] - 2))
     line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * res["seconds"] / res["steps"], "higher_is_better": True,
@@ -379,7 +460,13 @@ def run_ours(args, wl_name):
         peak = fp32_peak_tflops(sm_max)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x %.0f MHz" % sm_max}
+                "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 (FMA) x %.0f MHz"
+                               % (sm_count(), sm_max)}
+        if dom in SURVEY_FLOPS:
+            a2 = SURVEY_FLOPS[dom](w) / (dom_ms * 1e-3) / 1e12
+            roof["frac_method_model"] = {"achieved": a2, "frac": a2 / peak,
+                                         "model": "32 flops per neighbour entry (2 exp as 1 "
+                                                  "each) + 60 per ordered triple"}
     else:
         model = BYTE_MODELS.get(dom)
         byts = model(w) if model else None
@@ -431,8 +518,12 @@ def run_ours(args, wl_name):
         return 0
     cpu = None
     if not args.no_cpu_baseline:
-        res = cpu_oracle_rate(wl, seconds=args.cpu_seconds)
+        cores, _ = host_cpu()
+        res = cpu_oracle_rate(wl, seconds=args.cpu_seconds,
+                              threads=min(cores, wl["n_images"] - 2))
         cpu = {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        res1 = cpu_oracle_rate(wl, seconds=max(2.0, args.cpu_seconds / 4), threads=1)
+        cpu["one_core"] = {"value": res1["value"], "sample": res1["sample"]}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -469,7 +560,9 @@ def make_lj_band(g, bc, precision, stream, skin=None):
     opt.maxstep = 0.2
     opt.n_max = bc["n_images"]
     opt.bin_scale = 0.0
-    cf = g.CellFilter(1, g.ROTFREE_B, 0.0, 0.0)
+    # lattice scale J = Omega0^(1/3) n^(1/6): the lattice rows relax at the
+    # atoms' pace at every size (c = n leaves them ever softer)
+    cf = g.CellFilter(1, g.ROTFREE_B, g.CELL_FACTOR_J, 0.0)
     return g.create_band((R0, h0), (R1, h1), bc["n_images"], g.lj_potential(), cf, opt,
                          stream=stream)
 
@@ -480,7 +573,7 @@ def cpu_oracle_lj_rate(bcs, seconds):
     bc = min(bcs, key=lambda c: len(c["endpoints"][0]))
     R0, h0, R1, h1 = bc["endpoints"]
     band = oracle.make_band(oracle.LJ(), R0, h0, R1, h1, bc["n_images"], k=bc["k"], climb=True,
-                            cell_filter=True, fire=oracle.Fire(dt=bc["dt"]))
+                            cell_filter=True, c="J", fire=oracle.Fire(dt=bc["dt"]))
     n_done, t0 = 0, time.perf_counter()
     while time.perf_counter() - t0 < seconds or n_done == 0:
         band.step(1)
@@ -550,7 +643,8 @@ def run_batch(args):
         peak = fp32_peak_tflops(sm_max)
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x %.0f MHz" % sm_max}
+                "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 (FMA) x %.0f MHz"
+                               % (sm_count(), sm_max)}
     else:
         byts = BYTE_MODELS[dom](w) if dom in BYTE_MODELS else None
         ach = byts / (dom_ms * 1e-3) / 1e9 if byts else None
@@ -651,12 +745,16 @@ def serve_once(g, stream, specs, built, budget, max_steps, lead, drain, window):
     summarise latencies (retirement - arrival) and served throughput."""
     import numpy as np
     pots = {"lj": g.lj_potential(), "tersoff": g.tersoff_potential()}
-    cf = g.CellFilter(1, g.ROTFREE_B, 0.0, 0.0)
+    # LJ bands take the lattice scale J = Omega0^(1/3) n^(1/6) (their
+    # lattice rows then relax at the atoms' pace); the carbon bands keep
+    # c = n (with J their stiff lattice rows need a smaller FIRE step)
+    cfs = {"lj": g.CellFilter(1, g.ROTFREE_B, g.CELL_FACTOR_J, 0.0),
+           "tersoff": g.CellFilter(1, g.ROTFREE_B, 0.0, 0.0)}
     sv = g.Server(g.MIXED, budget_bytes=budget, stream=stream)
     t0 = time.perf_counter()
     ids = []
     for sp, ((R0, h0, R1, h1), pot) in zip(specs, built):
-        ids.append(sv.submit((R0, h0), (R1, h1), sp["n_images"], pots[pot], cf,
+        ids.append(sv.submit((R0, h0), (R1, h1), sp["n_images"], pots[pot], cfs[pot],
                              _serve_options(g, sp, g.MIXED), sp["fmax"], max_steps,
                              lead + sp["arrival"]))
     t_sub = time.perf_counter() - t0

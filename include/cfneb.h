@@ -58,7 +58,8 @@ extern "C" {
 #define CFNEB_ERR_CUDA (-5)          /* a CUDA runtime call failed             */
 #define CFNEB_ERR_NONFINITE (-6)     /* NaN/Inf in forces, energies or state   */
 #define CFNEB_ERR_NOT_SPD (-7)       /* lattice coordinate B lost positivity   */
-#define CFNEB_ERR_NBR_OVERFLOW (-8)  /* more list neighbours than capacity    */
+#define CFNEB_ERR_NBR_OVERFLOW (-8)  /* more list neighbours than capacity, or a
+                                        cell narrower than (rc + skin) / 7     */
 #define CFNEB_ERR_TIMEOUT (-9)       /* a bounded device wait gave up          */
 #define CFNEB_ERR_STATE (-10)        /* call not valid in the current state    */
 
@@ -69,6 +70,13 @@ extern "C" {
 /* NEP-style potential: Chebyshev basis size 6, 4 radial and 2 angular
  * functions, Legendre orders 1..4, 16 hidden units: 261 weights. */
 #define CFNEB_NEP_N_WEIGHTS 261
+
+/* cell_factor value selecting the scale J = Omega0^(1/3) n^(1/6) of the
+ * generalized solid-state NEB (Sheppard et al. 2012): the lattice rows then
+ * have the stiffness per unit of X of the atom rows at any n, where c = n
+ * makes them ever softer (slower to relax) as n grows (Sec. II.C leaves the
+ * scale open) */
+#define CFNEB_CELL_FACTOR_J (-1.0)
 
 #define CFNEB_ROTFREE_B 0   /* lattice coordinate B = D D^T (Sec. II.C end)   */
 #define CFNEB_DEFGRAD_D 1   /* lattice coordinate D = h0^-1 h (Sec. II.C)     */
@@ -115,7 +123,10 @@ typedef struct {
 typedef struct {
     int32_t enabled;          /* 0: fixed cell (h = h0 for every image)      */
     int32_t variant;          /* CFNEB_ROTFREE_B (default) or CFNEB_DEFGRAD_D */
-    double cell_factor;       /* c in X_lat = c B; <= 0 selects n_atoms      */
+    double cell_factor;       /* c in X_lat = c B (> 0); CFNEB_CELL_FACTOR_J
+                                 selects J = Omega0^(1/3) n^(1/6) (Omega0 the
+                                 initial cell's volume); other values <= 0
+                                 select n_atoms                              */
     double pressure;          /* external pressure P: H = U + P Omega        */
 } cfneb_cell_filter;
 
@@ -219,6 +230,28 @@ int cfneb_get_path(const cfneb_band *band, int32_t *n_images, double *positions,
  * Synchronises. */
 int cfneb_get_state(const cfneb_band *band, double *X, double *F, double *Fneb,
                     double *virials, double *fire, int32_t *climbing_index);
+
+/* Restore the generalised coordinates of every image (a checkpoint taken
+ * with cfneb_get_state; Sec. II.C coordinates X = (R~, c B)).  X holds
+ * N x (n+3) x 3 doubles for the band's current image count N, endpoints
+ * included; values are rounded to the band's storage precision.  FIRE is
+ * reset (v = 0, dt = dt0), the endpoints are evaluated again and every
+ * image rebuilds its cell and neighbour lists at the next evaluation.
+ * Errors: INVALID_ARG (NULL or a non-finite entry), NOT_SPD (an endpoint's
+ * lattice rows), CUDA.  Synchronises. */
+int cfneb_set_state(cfneb_band *band, const double *X);
+
+/* Per-image scalars of the last step (Sec. II.A): energies[N] the
+ * energies (U + P Omega) the step's tangent and climbing image used (in the
+ * mixed path from FP32 site energies summed in FP64; cfneb_get_path reports
+ * FP64 energies); dots[N x 10] for the interior images |dX+|^2, |dX-|^2,
+ * dX+.dX-, F.dX+, F.dX-, F.F, F.v, v.v, dX+.v, dX-.v (dX+ = X_{i+1} - X_i,
+ * dX- = X_i - X_{i-1}, F the generalised force, v the FIRE velocity before
+ * the move); coef[N x 2] the a, b with f_NEB = F + a dX+ + b dX-.
+ * Endpoint entries are 0 (their energy is reported).  Any pointer may be
+ * NULL.  Synchronises. */
+int cfneb_get_image_scalars(const cfneb_band *band, double *energies, double *dots,
+                            double *coef);
 
 /* Release the band and its device memory. */
 int cfneb_destroy_band(cfneb_band *band);
@@ -372,10 +405,11 @@ int cfneb_get_list_stats(const cfneb_band *band, int64_t *builds, int64_t *evalu
 int cfneb_launches_per_step(const cfneb_band *band, int32_t *launches);
 
 /* ---- evaluation without device allocation --------------------------------
- * The paper has no counterpart to this entry point; it serves callers that
- * cannot call cudaMalloc: code running while a CUDA graph is captured on its
- * stream, allocators that own all of a process's device memory (a caching
- * pool or a fixed arena), services that must not allocate once serving.
+ * The paper has no counterpart to this entry point.  It serves callers that
+ * cannot call cudaMalloc: processes whose allocator owns all of the device
+ * memory (a framework's caching pool, a fixed arena sized at start-up), and
+ * services that must not allocate once serving (an allocation can fail or
+ * stall at any time).
  *
  * Lennard-Jones energy, forces and virial (FP64, the same kernels and
  * results as cfneb_evaluate with CFNEB_FP64) of one periodic structure of
@@ -389,14 +423,18 @@ int cfneb_launches_per_step(const cfneb_band *band, int32_t *launches);
  *   d_forces     DEVICE pointer to n_atoms x 3 doubles, or NULL
  *   d_virial     DEVICE pointer to 9 doubles, or NULL
  *   cuda_stream  the stream the work is queued on (NULL = legacy default)
- * Returns without waiting; the outputs are valid once the stream reaches
- * this point.  n_atoms above the maximum, a NULL position or cell pointer,
- * or a singular cell return CFNEB_ERR_INVALID_ARG before any GPU work.
- * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  Every
- * call shares the one array and leaves its contents behind (the counts that
- * must start at zero are cleared by each call), so calls that overlap on the
- * GPU -- other streams, or unsynchronised host threads -- race. */
+ * Waits for the stream and returns the status the kernels raised:
+ * CFNEB_ERR_NONFINITE for a non-finite energy (overlapping atoms).
+ * n_atoms above the maximum, a NULL position or cell pointer, a
+ * non-finite cell entry or eps, sigma, rc, a singular cell, or a cell
+ * narrower than rc / 7 along a lattice direction (the cell list reaches 7
+ * bins to each side) return CFNEB_ERR_INVALID_ARG before any GPU work.
+ * The array's device address is looked up, and kept, once per CUDA context
+ * (the first call in a context, with that context current, does it).
+ * Every call shares the one array and leaves its contents behind (the
+ * counts that must start at zero are cleared by each call), so calls that
+ * overlap on the GPU -- other streams, or unsynchronised host threads --
+ * race. */
 #define CFNEB_NOALLOC_MAX_ATOMS 32768
 int cfneb_lj_evaluate_noalloc(const double *d_positions, int32_t n_atoms, const double *cell,
                               double eps, double sigma, double rc, int32_t shift_energy,

@@ -30,7 +30,10 @@ Readings where the paper is silent or garbled:
 3. h0 is the cell of the initial endpoint, shared by every image.
 4. D is recovered from B as the symmetric positive square root.
 5. The lattice coordinate is scaled: X_lat = c B, F_lat = Phi / c,
-   c = number of atoms unless given.
+   c = number of atoms unless given; c = "J" selects J = Omega0^(1/3) n^(1/6)
+   (the scale of the generalized solid-state NEB, Omega0 the initial cell's
+   volume), which keeps the lattice rows' stiffness per unit of X at that of
+   the atom rows for any n.
 6. B is stored as 9 entries (a symmetric 3x3 block of 3 "atoms").
 7. The virial is symmetrised in the rotation-free filter.
 8. Tangent: Henkelman-Jonsson upwind rule (exact ties fall to the energy
@@ -461,6 +464,8 @@ def make_band(pot, R0, h0, R1, h1, n_images, k=0.1, climb=True, cell_filter=True
     h1 = np.asarray(h1, dtype=np.float64)
     R1 = unwrap_final(R0, h0, R1, h1)
     n = R0.shape[0]
+    if c == "J":  # J = Omega0^(1/3) n^(1/6) (generalized solid-state NEB scale)
+        c = abs(np.linalg.det(h0)) ** (1.0 / 3.0) * n ** (1.0 / 6.0)
     c = float(n) if c is None or c <= 0 else float(c)
     if not cell_filter:
         h1 = h0

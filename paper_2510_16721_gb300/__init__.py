@@ -36,6 +36,7 @@ NEP = 2
 NEP_N_WEIGHTS = 261
 ROTFREE_B = 0
 DEFGRAD_D = 1
+CELL_FACTOR_J = -1.0
 FP64 = 0
 MIXED = 1
 
@@ -43,6 +44,7 @@ MIXED = 1
 EXPORTS = [
     "cfneb_default_options", "cfneb_create_band", "cfneb_step", "cfneb_relax",
     "cfneb_insert_image", "cfneb_delete_image", "cfneb_get_path", "cfneb_get_state",
+    "cfneb_set_state", "cfneb_get_image_scalars",
     "cfneb_destroy_band", "cfneb_evaluate", "cfneb_profile", "cfneb_profile_read",
     "cfneb_kernel_count", "cfneb_kernel_name", "cfneb_launches_per_step",
     "cfneb_status_string", "cfneb_get_work", "cfneb_get_list_stats", "cfneb_lj_evaluate_noalloc",
@@ -112,6 +114,8 @@ def lib():
             "cfneb_delete_image": ([vp, i32], ctypes.c_int),
             "cfneb_get_path": ([vp, P(i32), dp, dp, dp, dp], ctypes.c_int),
             "cfneb_get_state": ([vp, dp, dp, dp, dp, dp, P(i32)], ctypes.c_int),
+            "cfneb_set_state": ([vp, dp], ctypes.c_int),
+            "cfneb_get_image_scalars": ([vp, dp, dp, dp], ctypes.c_int),
             "cfneb_destroy_band": ([vp], ctypes.c_int),
             "cfneb_evaluate": ([P(Structure), i32, P(Potential), i32, vp, dp, dp, dp],
                                ctypes.c_int),
@@ -295,6 +299,25 @@ class Band:
         return dict(X=X, F=F, Fneb=Fn, virials=V, dt=fire[0], alpha=fire[1], n_pos=int(fire[2]),
                     steps=int(fire[3]), ci=int(ci.value))
 
+    def set_state(self, X):
+        """cfneb_set_state: every image's generalised coordinates from X
+        (N x (n+3) x 3); FIRE reset, endpoints evaluated again."""
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        if X.shape != (self.n_images, self.n_atoms + 3, 3):
+            raise ValueError("X must have shape (N, n+3, 3)")
+        _check(lib().cfneb_set_state(self._h, _dptr(X)), "cfneb_set_state")
+
+    def image_scalars(self):
+        """cfneb_get_image_scalars: step energies (N), the ten dots (N x 10)
+        and the f_NEB coefficients (N x 2) of the last step."""
+        N = self.n_images
+        E = np.zeros(N)
+        dots = np.zeros((N, 10))
+        coef = np.zeros((N, 2))
+        _check(lib().cfneb_get_image_scalars(self._h, _dptr(E), _dptr(dots), _dptr(coef)),
+               "cfneb_get_image_scalars")
+        return dict(E=E, dots=dots, coef=coef)
+
     def profile(self, enable=True):
         return _check(lib().cfneb_profile(self._h, int(bool(enable))), "cfneb_profile")
 
@@ -432,6 +455,25 @@ class Batch:
         _check(lib().cfneb_batch_bytes(self._h, ctypes.byref(u), ctypes.byref(b)),
                "cfneb_batch_bytes")
         return int(u.value), int(b.value)
+
+    def set_state(self, X):
+        """cfneb_set_state: every image's generalised coordinates from X
+        (N x (n+3) x 3); FIRE reset, endpoints evaluated again."""
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        if X.shape != (self.n_images, self.n_atoms + 3, 3):
+            raise ValueError("X must have shape (N, n+3, 3)")
+        _check(lib().cfneb_set_state(self._h, _dptr(X)), "cfneb_set_state")
+
+    def image_scalars(self):
+        """cfneb_get_image_scalars: step energies (N), the ten dots (N x 10)
+        and the f_NEB coefficients (N x 2) of the last step."""
+        N = self.n_images
+        E = np.zeros(N)
+        dots = np.zeros((N, 10))
+        coef = np.zeros((N, 2))
+        _check(lib().cfneb_get_image_scalars(self._h, _dptr(E), _dptr(dots), _dptr(coef)),
+               "cfneb_get_image_scalars")
+        return dict(E=E, dots=dots, coef=coef)
 
     def profile(self, enable=True):
         return _check(lib().cfneb_batch_profile(self._h, int(bool(enable))), "cfneb_batch_profile")

@@ -6,21 +6,26 @@
 //                   generalised force: (1/c) 1/2 D^-T V_sym D^-1 for the
 //                   rotation-free filter, (1/c) D^-T V for the deformation
 //                   gradient (Sec. II.C).
-// k_band_dots       per row tile: |dX+|^2, |dX-|^2, dX+.dX-, F.dX+, F.dX- in
-//                   FP64 (dX+ = X_{i+1} - X_i, dX- = X_i - X_{i-1}).
-// k_dots_reduce     sums those tile partials per image (one block per image).
-// k_neb_coef        per band: climbing image, upwind tangent weights and the
-//                   two coefficients with f_NEB = F + a dX+ + b dX-.  Since
-//                   tau = w+ dX+ + w- dX-, |tau| and F.tau follow from the five
-//                   dots, and the projection f - (f.t)t + k(|dX+|-|dX-|) t
-//                   (Sec. II.A; climbing image f - 2 (f.t) t) becomes two
-//                   scalars per image.
-// k_neb_force       writes f_NEB and per-tile FIRE sums F.v, F.F, v.v and the
-//                   largest row norm (fmax).
-// k_fire_scalars    per band: convergence test, FIRE decision (Bitzek et al.
-//                   2006, band-global power P = F.v) and the new dt, alpha.
-// k_fire_update     v <- cv v + cf F; v += dt F; dX = dt v clamped per row to
-//                   maxstep; X += dX (interior images only).
+// The band phase of a step is three passes over the row tiles of the
+// interior images:
+// k_band_dots       pass 1: per tile, ten dots with compensated
+//                   accumulation (|dX+|^2, |dX-|^2, dX+.dX-, F.dX+, F.dX-,
+//                   F.F, F.v, v.v, dX+.v, dX-.v; dX+ = X_{i+1} - X_i,
+//                   dX- = X_i - X_{i-1}); the last tile of an image sums the
+//                   image's tiles in FP64 and computes the image's upwind
+//                   tangent weights, the two coefficients of
+//                   f_NEB = F + a dX+ + b dX- (Sec. II.A; the climbing image
+//                   is the argmax of the energies, final before this pass)
+//                   and its FIRE terms F_NEB.v, |F_NEB|^2, |v|^2 from the dots.
+// k_neb_force       pass 2: writes f_NEB and takes the largest row norm; the
+//                   last tile of a band sums the images' FIRE terms, runs the
+//                   convergence test and the FIRE decision (Bitzek et al.
+//                   2006, band-global power).
+// k_fire_update     pass 3: v <- cv v + cf F; v += dt F; dX = dt v clamped
+//                   per row to maxstep; X += dX (interior images only).
+// "Last" blocks are found with completion counters (a fence, then an atomic
+// increment); the sums they form read the other blocks' records in a fixed
+// order, so results do not depend on block scheduling.
 #include "common.cuh"
 
 namespace cfneb {
@@ -66,152 +71,232 @@ __global__ void k_image_finalize(const ImgRef *imgs, BandDev *bands) {
     if (lane < 9) F[lane] = (T)Phi;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(TILE) k_band_dots(const Tile *tiles, BandDev *bands) {
-    Tile tl = tiles[blockIdx.x];
-    BandDev &b = bands[tl.band];
-    T acc[5] = {0, 0, 0, 0, 0};
-    const size_t stride = (size_t)b.rows * 3;
-    const size_t o0 = tl.img * stride + ((size_t)tl.t * RTILE + threadIdx.x) * 3;
-    const T *__restrict__ X0 = (const T *)b.X + o0;
-    const T *__restrict__ F0 = (const T *)b.F + o0;
-    const int nrow = b.rows - tl.t * RTILE - (int)threadIdx.x;
+// ---- band pass 1: the ten dot products of every interior image ------------
+//
+// Row sums in T, accumulated across rows with Knuth's two-sum (FP32: the
+// running sum is carried as an unevaluated pair s + c, so the error of a
+// thread's total is the rounding of each row's 3-term product sum,
+// |err| <= 2^-23 sum_rows sum_c |a_c b_c|, with no growth in the row count);
+// the warp butterfly adds pairs the same way and the block total is formed
+// in FP64 from the pairs.  FP64 bands accumulate plainly in FP64.
+template <typename T> struct Acc;
+template <> struct Acc<float> {
+    float s = 0.0f, c = 0.0f;
+    __device__ void add(float p) {
+        const float t = __fadd_rn(s, p), z = __fsub_rn(t, s);
+        c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z)));
+        s = t;
+    }
+    __device__ void add(const Acc &o) {  // pair + pair
+        add(o.s);
+        c = __fadd_rn(c, o.c);
+    }
+    __device__ void shfl_xor(int o) {
+        Acc q;
+        q.s = __shfl_xor_sync(0xffffffffu, s, o);
+        q.c = __shfl_xor_sync(0xffffffffu, c, o);
+        add(q);
+    }
+    __device__ double value() const { return (double)s + (double)c; }
+};
+template <> struct Acc<double> {
+    double s = 0.0;
+    __device__ void add(double p) { s += p; }
+    __device__ void add(const Acc &o) { s += o.s; }
+    __device__ void shfl_xor(int o) { s += __shfl_xor_sync(0xffffffffu, s, o); }
+    __device__ double value() const { return s; }
+};
+
+// Block totals of K accumulators (fixed order: warp butterfly, then warps
+// 0..3 in turn); lane k < K of warp 0 stores total k to dst[k] in FP64.
+template <int K, typename T>
+__device__ inline void block_acc_store(Acc<T> (&a)[K], double *dst) {
+    static_assert(K <= 32, "one lane per value");
+    __shared__ Acc<T> red[RTHREADS / 32][K];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-        if (k * TILE < nrow) {
-            const T *x0 = X0 + k * TILE * 3, *f = F0 + k * TILE * 3;
-            for (int c = 0; c < 3; ++c) {
-                const T a = x0[c];
-                const T dp = x0[stride + c] - a, dm = a - x0[c - (long long)stride], fc = f[c];
-                acc[0] += dp * dp;
-                acc[1] += dm * dm;
-                acc[2] += dp * dm;
-                acc[3] += fc * dp;
-                acc[4] += fc * dm;
-            }
-        }
-    }
-    block_sum_store<5, T>(acc, b.row_part + ((size_t)tl.img * b.rtpi + tl.t) * NPART);
-}
-
-// one block per image: sum the row-tile partials of the five dots
-__global__ void k_dots_reduce(const ImgRef *imgs, BandDev *bands) {
-    ImgRef r = imgs[blockIdx.x];
-    BandDev &b = bands[r.band];
-    const double tk =
-        block_sum_records<5, 16>(b.row_part + (size_t)r.img * b.rtpi * NPART, NPART, b.rtpi);
-    if (threadIdx.x < 5) b.sc[r.img].dots[threadIdx.x] = tk;
-}
-
-// one block (one thread per image) per band
-__global__ void k_neb_coef(const int *band_ids, BandDev *bands) {
-    BandDev &b = bands[band_ids[blockIdx.x]];
-    BandParams *bp = b.bp;
-    const int N = bp->N;
-    __shared__ int s_ci;
-    if (threadIdx.x == 0) {
-        int ci = -1;
-        if (bp->climb) {
-            double best = 0.0;
-            for (int i = 1; i < N - 1; ++i)
-                if (ci < 0 || b.sc[i].E > best) {
-                    best = b.sc[i].E;
-                    ci = i;
-                }
-        }
-        s_ci = ci;
-        bp->ci = ci;
+    for (int k = 0; k < K; ++k) {
+        for (int o = 16; o > 0; o >>= 1) a[k].shfl_xor(o);
+        if (lane == 0) red[w][k] = a[k];
     }
     __syncthreads();
-    for (int i = 1 + threadIdx.x; i < N - 1; i += blockDim.x) {
-        const ImgScalars &sc = b.sc[i];
-        const double Em = b.sc[i - 1].E, E0 = sc.E, Ep = b.sc[i + 1].E;
-        double wp, wm;
-        if (Ep > E0 && E0 > Em) {
-            wp = 1.0; wm = 0.0;
-        } else if (Ep < E0 && E0 < Em) {
-            wp = 0.0; wm = 1.0;
-        } else {
-            const double a = fabs(Ep - E0), c = fabs(Em - E0);
-            const double dmax = fmax(a, c), dmin = fmin(a, c);
-            if (dmax == 0.0) {
-                wp = 1.0; wm = 1.0;
-            } else if (Ep > Em) {
-                wp = dmax; wm = dmin;
-            } else {
-                wp = dmin; wm = dmax;
-            }
-        }
-        const double pp = sc.dots[0], mm = sc.dots[1], pm = sc.dots[2];
-        const double fp = sc.dots[3], fm = sc.dots[4];
-        const double tt = wp * wp * pp + 2.0 * wp * wm * pm + wm * wm * mm;
-        const double tn = sqrt(tt);
-        const double ft = (wp * fp + wm * fm) / tn;  // F . tau_hat
-        double gamma;
-        if (i == s_ci) {
-            gamma = -2.0 * ft;
-        } else {
-            gamma = bp->k * (sqrt(pp) - sqrt(mm)) - ft;
-        }
-        b.sc[i].coef[0] = gamma * wp / tn;
-        b.sc[i].coef[1] = gamma * wm / tn;
+    if (threadIdx.x < K) {
+        Acc<T> t = red[0][threadIdx.x];
+        for (int q = 1; q < RTHREADS / 32; ++q) t.add(red[q][threadIdx.x]);
+        dst[threadIdx.x] = t.value();
+        __threadfence();  // visible to the block that finishes the image
     }
+    __syncthreads();
 }
 
-template <typename T>
-__global__ void __launch_bounds__(TILE) k_neb_force(const Tile *tiles, BandDev *bands) {
+// FP64 sums of K values over `count` records like block_sum_records, with
+// loads that bypass L1 (the records were written by other blocks of the
+// running kernel).
+template <int K, int G>
+__device__ inline double block_sum_records_cg(const double *rec, int stride, int count) {
+    __shared__ double s_part[G * K];
+    const int tid = threadIdx.x;
+    if (tid < K * G) {
+        const int k = tid % K, g = tid / K;
+        double v = 0.0;
+        for (int q = g; q < count; q += G) v += __ldcg(rec + (size_t)q * stride + k);
+        s_part[g * K + k] = v;
+    }
+    __syncthreads();
+    double tot = 0.0;
+    if (tid < K)
+        for (int g = 0; g < G; ++g) tot += s_part[g * K + tid];
+    __syncthreads();
+    return tot;
+}
+
+// true in every thread of the one block that arrives last (counter reaches
+// total); that block also resets the counter for the next launch
+__device__ inline bool last_arrival(unsigned int *counter, unsigned int total) {
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int prev = atomicAdd(counter, 1u);
+        s_last = prev + 1u == total;
+        if (s_last) *counter = 0u;
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last != 0;
+}
+
+// Climbing image of a band: argmax of the step energies over the interior
+// images, lowest index on ties (the energies are final before pass 1).
+__device__ inline int climbing_image(const BandDev &b) {
+    const BandParams *bp = b.bp;
+    if (!bp->climb) return -1;
+    const int N = bp->N;
+    int ci = -1;
+    double best = 0.0;
+    for (int i = 1; i < N - 1; ++i) {
+        const double e = b.sc[i].E;
+        if (ci < 0 || e > best) {
+            best = e;
+            ci = i;
+        }
+    }
+    return ci;
+}
+
+// One image, after its dots: upwind tangent weights and the two
+// coefficients with f_NEB = F + a dX+ + b dX-.  Since tau = w+ dX+ + w- dX-,
+// |tau| and F.tau follow from five dots, and the projection
+// f - (f.t)t + k(|dX+| - |dX-|) t (Sec. II.A; climbing image f - 2 (f.t) t)
+// is two scalars per image.  The image's FIRE terms follow from the other
+// five dots without a pass over f_NEB:
+//   F_NEB.v = F.v + a dX+.v + b dX-.v,
+//   |F_NEB|^2 = F.F + a^2 |dX+|^2 + b^2 |dX-|^2 + 2a F.dX+ + 2b F.dX-
+//               + 2ab dX+.dX-.
+__device__ inline void image_coef(BandDev &b, int i, int ci, const double *d) {
+    const BandParams *bp = b.bp;
+    ImgScalars &sc = b.sc[i];
+    const double Em = b.sc[i - 1].E, E0 = sc.E, Ep = b.sc[i + 1].E;
+    double wp, wm;
+    if (Ep > E0 && E0 > Em) {
+        wp = 1.0; wm = 0.0;
+    } else if (Ep < E0 && E0 < Em) {
+        wp = 0.0; wm = 1.0;
+    } else {
+        const double a = fabs(Ep - E0), c = fabs(Em - E0);
+        const double dmax = fmax(a, c), dmin = fmin(a, c);
+        if (dmax == 0.0) {
+            wp = 1.0; wm = 1.0;
+        } else if (Ep > Em) {
+            wp = dmax; wm = dmin;
+        } else {
+            wp = dmin; wm = dmax;
+        }
+    }
+    const double pp = d[0], mm = d[1], pm = d[2], fp = d[3], fm = d[4];
+    const double tt = wp * wp * pp + 2.0 * wp * wm * pm + wm * wm * mm;
+    const double tn = sqrt(tt);
+    const double ft = (wp * fp + wm * fm) / tn;  // F . tau_hat
+    const double gamma = i == ci ? -2.0 * ft : bp->k * (sqrt(pp) - sqrt(mm)) - ft;
+    const double a = gamma * wp / tn, bb = gamma * wm / tn;
+    sc.coef[0] = a;
+    sc.coef[1] = bb;
+    sc.fire[0] = d[6] + a * d[8] + bb * d[9];
+    sc.fire[1] = d[5] + a * a * pp + bb * bb * mm + 2.0 * a * fp + 2.0 * bb * fm +
+                 2.0 * a * bb * pm;
+    sc.fire[2] = d[7];
+}
+
+// Pass 1 over the row tiles of the interior images: the ten dots of each
+// tile into the tile's partial record; with FUSE, the last tile of an image
+// sums the image's records (fixed order) into its dots, and the last image
+// of a band computes the band's NEB coefficients and FIRE sums.
+template <typename T, bool FUSE>
+__global__ void __launch_bounds__(RTHREADS, sizeof(T) == 4 ? 4 : 2) k_band_dots(const Tile *tiles, BandDev *bands) {
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
-    T acc[4] = {0, 0, 0, 0};  // F.v, F.F, v.v, largest row |F|^2 (fmax)
-    // coefficients in T, converted once per block
-    __shared__ T s_coef[2];
-    if (threadIdx.x < 2) s_coef[threadIdx.x] = (T)b.sc[tl.img].coef[threadIdx.x];
-    __syncthreads();
-    const T ca = s_coef[0], cb = s_coef[1];
+    Acc<T> acc[10];
     const size_t stride = (size_t)b.rows * 3;
     const size_t o0 = tl.img * stride + ((size_t)tl.t * RTILE + threadIdx.x) * 3;
     const T *__restrict__ X0 = (const T *)b.X + o0;
     const T *__restrict__ F0 = (const T *)b.F + o0;
     const T *__restrict__ V0 = (const T *)b.v + o0;
-    T *__restrict__ G0 = (T *)b.Fneb + o0;
     const int nrow = b.rows - tl.t * RTILE - (int)threadIdx.x;
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
-        if (k * TILE < nrow) {
-            const size_t q = (size_t)k * TILE * 3;
-            T ff = 0;
+        if (k * RTHREADS < nrow) {
+            const T *x0 = X0 + k * RTHREADS * 3, *f = F0 + k * RTHREADS * 3,
+                    *v = V0 + k * RTHREADS * 3;
+            T r[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
             for (int c = 0; c < 3; ++c) {
-                const T a = X0[q + c];
-                const T g = F0[q + c] + ca * (X0[q + stride + c] - a) +
-                            cb * (a - X0[q + c - stride]);
-                const T vc = V0[q + c];
-                G0[q + c] = g;
-                acc[0] += g * vc;
-                ff += g * g;
-                acc[2] += vc * vc;
+                const T a = x0[c];
+                const T dp = x0[stride + c] - a, dm = a - x0[c - (long long)stride];
+                const T fc = f[c], vc = v[c];
+                r[0] = fma(dp, dp, r[0]);
+                r[1] = fma(dm, dm, r[1]);
+                r[2] = fma(dp, dm, r[2]);
+                r[3] = fma(fc, dp, r[3]);
+                r[4] = fma(fc, dm, r[4]);
+                r[5] = fma(fc, fc, r[5]);
+                r[6] = fma(fc, vc, r[6]);
+                r[7] = fma(vc, vc, r[7]);
+                r[8] = fma(dp, vc, r[8]);
+                r[9] = fma(dm, vc, r[9]);
             }
-            acc[1] += ff;
-            acc[3] = fmax(acc[3], ff);
+#pragma unroll
+            for (int q = 0; q < 10; ++q) acc[q].add(r[q]);
         }
     }
-    T three[3] = {acc[0], acc[1], acc[2]};
     double *part = b.row_part + ((size_t)tl.img * b.rtpi + tl.t) * NPART;
-    block_sum_store<3, T>(three, part + 5);
-    // block max of the row norms, in T (a max is exact in any precision)
-    __shared__ T smax[TILE / 32];
-    T m = acc[3];
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = m;
+    block_acc_store<10, T>(acc, part);
+    if (!FUSE) return;
+    ImgScalars &sc = b.sc[tl.img];
+    if (!last_arrival(&sc.done, (unsigned)b.rtpi)) return;
+    const double tk = block_sum_records_cg<10, 12>(
+        b.row_part + (size_t)tl.img * b.rtpi * NPART, NPART, b.rtpi);
+    __shared__ double s_d[10];
+    if (threadIdx.x < 10) {
+        sc.dots[threadIdx.x] = tk;
+        s_d[threadIdx.x] = tk;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        T mx = (T)0;
-        for (int q = 0; q < TILE / 32; ++q) mx = fmax(mx, smax[q]);
-        part[8] = (double)mx;
+        const int ci = climbing_image(b);
+        if (tl.img == 1) b.bp->ci = ci;
+        image_coef(b, tl.img, ci, s_d);
     }
 }
 
-// one block per band; the threads sum the tile partials of every interior
-// image, thread 0 runs the FIRE logic
+// one block per image: sum the row-tile partials of the ten dots (spacings
+// for the refinement check, outside the step)
+__global__ void k_dots_reduce(const ImgRef *imgs, BandDev *bands) {
+    ImgRef r = imgs[blockIdx.x];
+    BandDev &b = bands[r.band];
+    const double tk =
+        block_sum_records<10, 12>(b.row_part + (size_t)r.img * b.rtpi * NPART, NPART, b.rtpi);
+    if (threadIdx.x < 10) b.sc[r.img].dots[threadIdx.x] = tk;
+}
+
 // convergence test and FIRE decision on the band's parameters
 __device__ inline void fire_logic(BandParams *bp, const double *tot) {
     bp->stale = 0;  // every image of the band has rebuilt its cell list
@@ -258,47 +343,72 @@ __device__ inline void fire_logic(BandParams *bp, const double *tot) {
     bp->steps += 1;
 }
 
-__global__ void k_fire_scalars(const int *band_ids, BandDev *bands) {
-    BandDev &b = bands[band_ids[blockIdx.x]];
-    // the band's parameters are staged in shared memory, updated by thread 0
-    // and written back (no other kernel touches them meanwhile)
-    __shared__ BandParams s_bp;
-    stage_copy(&s_bp, b.bp);
+__device__ inline void atomic_max_nonneg(unsigned long long *bits, double v) {
+    atomicMax(bits, (unsigned long long)__double_as_longlong(v));
+}
+
+// Pass 2: f_NEB rows (written for the state read-back and the move) and the
+// largest row norm; the last tile of the band runs the convergence test and
+// the FIRE decision on the sums of pass 1.
+template <typename T>
+__global__ void __launch_bounds__(RTHREADS, 4) k_neb_force(const Tile *tiles, BandDev *bands) {
+    Tile tl = tiles[blockIdx.x];
+    BandDev &b = bands[tl.band];
+    // coefficients in T, converted once per block
+    __shared__ T s_coef[2];
+    if (threadIdx.x < 2) s_coef[threadIdx.x] = (T)b.sc[tl.img].coef[threadIdx.x];
     __syncthreads();
-    const int N = s_bp.N;
-    // the row-tile partials of images 1..N-2, one fixed strided subset per
-    // thread, then a fixed-order block sum
-    const int nt = (N - 2) * b.rtpi;
-    const double *part0 = b.row_part + (size_t)b.rtpi * NPART;
-    // F.v, F.F, v.v summed, the largest row |F|^2 taken, each over 32 fixed
-    // strided subsets and then in subset order (few FP64 instructions)
-    constexpr int G = 32;
-    __shared__ double s_part[G * 4], s_tot[4];
-    if (threadIdx.x < 4 * G) {
-        const int k = threadIdx.x % 4, g = threadIdx.x / 4;
-        double v = 0.0;
-#pragma unroll 8
-        for (int q = g; q < nt; q += G) {
-            const double x = part0[(size_t)q * NPART + 5 + k];
-            v = k == 3 ? fmax(v, x) : v + x;
+    const T ca = s_coef[0], cb = s_coef[1];
+    const size_t stride = (size_t)b.rows * 3;
+    const size_t o0 = tl.img * stride + ((size_t)tl.t * RTILE + threadIdx.x) * 3;
+    const T *__restrict__ X0 = (const T *)b.X + o0;
+    const T *__restrict__ F0 = (const T *)b.F + o0;
+    T *__restrict__ G0 = (T *)b.Fneb + o0;
+    const int nrow = b.rows - tl.t * RTILE - (int)threadIdx.x;
+    T mx = 0;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        if (k * RTHREADS < nrow) {
+            const size_t q = (size_t)k * RTHREADS * 3;
+            T ff = 0;
+            for (int c = 0; c < 3; ++c) {
+                const T a = X0[q + c];
+                const T g = F0[q + c] + ca * (X0[q + stride + c] - a) +
+                            cb * (a - X0[q + c - stride]);
+                G0[q + c] = g;
+                ff = fma(g, g, ff);
+            }
+            mx = fmax(mx, ff);
         }
-        s_part[g * 4 + k] = v;
     }
+    // block max of the row norms (a max is exact in any precision)
+    __shared__ T smax[RTHREADS / 32];
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = mx;
     __syncthreads();
-    if (threadIdx.x < 4) {
-        const int k = threadIdx.x;
+    BandParams *bp = b.bp;
+    if (threadIdx.x == 0) {
+        T m = (T)0;
+        for (int q = 0; q < RTHREADS / 32; ++q) m = fmax(m, smax[q]);
+        atomic_max_nonneg(&bp->fmax2_bits, (double)m);
+    }
+    if (!last_arrival(&bp->done_b, (unsigned)((bp->N - 2) * b.rtpi))) return;
+    // the band's FIRE sums over the interior images, in image order
+    __shared__ double s_tot[4];
+    if (threadIdx.x < 3) {
         double v = 0.0;
-        for (int g = 0; g < G; ++g) v = k == 3 ? fmax(v, s_part[g * 4 + k]) : v + s_part[g * 4 + k];
-        s_tot[k] = v;
+        for (int i = 1; i < bp->N - 1; ++i) v += b.sc[i].fire[threadIdx.x];
+        s_tot[threadIdx.x] = v;
     }
     __syncthreads();
-    if (threadIdx.x == 0) fire_logic(&s_bp, s_tot);
-    __syncthreads();
-    stage_copy(b.bp, &s_bp);
+    if (threadIdx.x == 0) {
+        s_tot[3] = __longlong_as_double((long long)atomicExch(&bp->fmax2_bits, 0ull));
+        fire_logic(bp, s_tot);
+    }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(TILE) k_fire_update(const Tile *tiles, BandDev *bands) {
+__global__ void __launch_bounds__(RTHREADS, sizeof(T) == 4 ? 4 : 2) k_fire_update(const Tile *tiles, BandDev *bands) {
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
     const BandParams *bp = b.bp;
@@ -317,26 +427,26 @@ __global__ void __launch_bounds__(TILE) k_fire_update(const Tile *tiles, BandDev
     T *__restrict__ X = (T *)b.X + o0;
     T *__restrict__ V = (T *)b.v + o0;
     const T *__restrict__ Fn = (const T *)b.Fneb + o0;
-    const int nrow = b.rows - tl.t * RTILE - (int)threadIdx.x;  // rows k * TILE < nrow exist
-    // all loads first (rows of one thread are TILE apart: independent)
+    const int nrow = b.rows - tl.t * RTILE - (int)threadIdx.x;  // rows k * RTHREADS < nrow exist
+    // all loads first (rows of one thread are RTHREADS apart: independent)
     T xr[RPT][3], vr[RPT][3], fr[RPT][3];
 #pragma unroll
     for (int k = 0; k < RPT; ++k)
-        if (k * TILE < nrow)
+        if (k * RTHREADS < nrow)
             for (int c = 0; c < 3; ++c) {
-                xr[k][c] = X[k * TILE * 3 + c];
-                vr[k][c] = V[k * TILE * 3 + c];
-                fr[k][c] = Fn[k * TILE * 3 + c];
+                xr[k][c] = X[k * RTHREADS * 3 + c];
+                vr[k][c] = V[k * RTHREADS * 3 + c];
+                fr[k][c] = Fn[k * RTHREADS * 3 + c];
             }
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
-        if (k * TILE >= nrow) break;
+        if (k * RTHREADS >= nrow) break;
         T dx[3];
         T n2 = 0;
         for (int c = 0; c < 3; ++c) {
             T vc = cv * vr[k][c] + cf * fr[k][c];
             vc += dt * fr[k][c];
-            V[k * TILE * 3 + c] = vc;
+            V[k * RTHREADS * 3 + c] = vc;
             dx[c] = dt * vc;
             n2 += dx[c] * dx[c];
         }
@@ -344,7 +454,7 @@ __global__ void __launch_bounds__(TILE) k_fire_update(const Tile *tiles, BandDev
             const T s = ms / sqrt(n2);
             for (int c = 0; c < 3; ++c) dx[c] *= s;
         }
-        for (int c = 0; c < 3; ++c) X[k * TILE * 3 + c] = xr[k][c] + dx[c];
+        for (int c = 0; c < 3; ++c) X[k * RTHREADS * 3 + c] = xr[k][c] + dx[c];
     }
 }
 
@@ -462,32 +572,31 @@ void launch_image_finalize(const ImgRef *imgs, int count, BandDev *bands, cudaSt
     if (count <= 0) return;
     k_image_finalize<T><<<count, RED_THREADS, 0, s>>>(imgs, bands);
 }
+// pass 1 of the step (fused: per-image dots, NEB coefficients, FIRE sums)
 template <typename T>
 void launch_band_dots(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
     if (ntiles <= 0) return;
-    k_band_dots<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
+    k_band_dots<T, true><<<ntiles, RTHREADS, 0, s>>>(tiles, bands);
+}
+// the dots alone (into the tile records; k_dots_reduce sums them per image)
+template <typename T>
+void launch_band_dots_only(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    k_band_dots<T, false><<<ntiles, RTHREADS, 0, s>>>(tiles, bands);
 }
 void launch_dots_reduce(const ImgRef *imgs, int count, BandDev *bands, cudaStream_t s) {
     if (count <= 0) return;
     k_dots_reduce<<<count, RED_THREADS, 0, s>>>(imgs, bands);
 }
-void launch_neb_coef(const int *band_ids, int nbands, BandDev *bands, cudaStream_t s) {
-    if (nbands <= 0) return;
-    k_neb_coef<<<nbands, 32, 0, s>>>(band_ids, bands);
-}
 template <typename T>
 void launch_neb_force(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
     if (ntiles <= 0) return;
-    k_neb_force<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
-}
-void launch_fire_scalars(const int *band_ids, int nbands, BandDev *bands, cudaStream_t s) {
-    if (nbands <= 0) return;
-    k_fire_scalars<<<nbands, 1024, 0, s>>>(band_ids, bands);
+    k_neb_force<T><<<ntiles, RTHREADS, 0, s>>>(tiles, bands);
 }
 template <typename T>
 void launch_fire_update(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
     if (ntiles <= 0) return;
-    k_fire_update<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
+    k_fire_update<T><<<ntiles, RTHREADS, 0, s>>>(tiles, bands);
 }
 template <typename T>
 void launch_midpoint(BandDev *band, int img, int rows, cudaStream_t s) {
@@ -499,6 +608,7 @@ void launch_midpoint(BandDev *band, int img, int rows, cudaStream_t s) {
 #define CFNEB_INST(T)                                                                       \
     template void launch_image_finalize<T>(const ImgRef *, int, BandDev *, cudaStream_t);   \
     template void launch_band_dots<T>(const Tile *, int, BandDev *, cudaStream_t);          \
+    template void launch_band_dots_only<T>(const Tile *, int, BandDev *, cudaStream_t);     \
     template void launch_neb_force<T>(const Tile *, int, BandDev *, cudaStream_t);          \
     template void launch_fire_update<T>(const Tile *, int, BandDev *, cudaStream_t);        \
     template void launch_midpoint<T>(BandDev *, int, int, cudaStream_t);                  \

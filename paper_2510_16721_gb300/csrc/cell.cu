@@ -93,6 +93,9 @@ __device__ void bin_grid(const BandParams *bp, int nbins_cap, const double *h, d
     for (int a = 0; a < 3; ++a) {
         const float bw = w[a] / nb[a];
         const int m = (int)ceilf((float)rl / bw);
+        // a cell narrower than rl / MAX_STENCIL: periodic images beyond the
+        // stencil would be missed
+        if (m > MAX_STENCIL) atomicOr(const_cast<int *>(&bp->status), ST_NBR_OVERFLOW);
         sc.m[a] = m < 1 ? 1 : (m > MAX_STENCIL ? MAX_STENCIL : m);
         sc.nb[a] = nb[a];
     }
@@ -671,7 +674,7 @@ void launch_bin_scan(const ImgRef *imgs, int count, int max_bins, BandDev *bands
 }
 void launch_bin_scatter(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
     if (ntiles <= 0) return;
-    k_bin_scatter<<<ntiles < GATED_GRID ? ntiles : GATED_GRID, TILE, 0, s>>>(tiles, ntiles, bands);
+    k_bin_scatter<<<ntiles < gated_grid() ? ntiles : gated_grid(), TILE, 0, s>>>(tiles, ntiles, bands);
 }
 template <typename T>
 void launch_bin_order(const ImgRef *imgs, int count, int max_bins, BandDev *bands,

@@ -24,9 +24,10 @@
 
 namespace cfneb {
 
-constexpr int TILE = 128;           // rows per tile = threads per block
-constexpr int RPT = 8;              // rows per thread of the row-tile kernels
-constexpr int RTILE = TILE * RPT;   // rows per row tile (band vector kernels)
+constexpr int TILE = 128;           // atoms per atom tile = threads per block
+constexpr int RTHREADS = 256;       // threads per block of the row-tile kernels
+constexpr int RPT = 4;              // rows per thread of the row-tile kernels
+constexpr int RTILE = RTHREADS * RPT;  // rows per row tile (band vector kernels)
 constexpr int MAXN_TERSOFF = 16;    // Tersoff list capacity per atom (entries within rl)
 constexpr int NPART = 12;           // doubles per tile partial record
 constexpr int MAX_STENCIL = 7;      // |delta| <= 7 bins per axis
@@ -41,9 +42,22 @@ constexpr int NEP_OCR = 0, NEP_OCA = NEP_NR * NEP_K, NEP_OW0 = NEP_OCA + NEP_NA 
               NEP_OB1 = NEP_OW1 + NEP_H;
 constexpr int LJ_LIST_MAX_ATOMS = 1 << 17;  // LJ list entries index 17-bit slots
 // Grid of the kernels that only do work for images rebuilding their lists:
-// a fixed grid strides over the tiles, so a step in which most images keep
-// their lists costs a few reads per block instead of a block per tile.
-constexpr int GATED_GRID = 152 * 8;
+// a fixed grid (8 blocks per SM of the current device) strides over the
+// tiles, so a step in which most images keep their lists costs a few reads
+// per block instead of a block per tile.
+inline int gated_grid() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152 * 8;
+    if (!cached[dev]) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            sms <= 0)
+            sms = 152;
+        cached[dev] = sms * 8;
+    }
+    return cached[dev];
+}
 
 // device status bits (BandParams::status)
 enum : int {
@@ -64,8 +78,10 @@ struct ImgScalars {
     double bv[9];        // bin edge vectors, row a = h_a / nb_a rounded to T
     double dh[9];        // wrap correction, row a = h_a - nb_a bv_a
     double omega;        // |det h|
-    double dots[5];      // |dX+|^2, |dX-|^2, dX+.dX-, F.dX+, F.dX-
+    double dots[10];     // |dX+|^2, |dX-|^2, dX+.dX-, F.dX+, F.dX-, F.F, F.v,
+                         // v.v, dX+.v, dX-.v (band pass 1)
     double coef[2];      // f_NEB = F + coef[0] dX+ + coef[1] dX-
+    double fire[3];      // this image's F_NEB.v, |F_NEB|^2, |v|^2
     double pairs;        // neighbour entries inside the cutoff (last evaluation)
     double triples;      // ordered neighbour pairs (j, k != j) of the atoms (Tersoff)
     double Db[9];        // D when the cell list was last built (skin test)
@@ -78,6 +94,8 @@ struct ImgScalars {
     int m[3];            // stencil half width per axis
     int nbins;
     int rebuild;         // this evaluation rebuilds the cell list
+    unsigned int done;   // row tiles of this image finished in band pass 1
+    int pad_done;
 };
 
 struct TersoffParams {
@@ -142,6 +160,11 @@ struct BandParams {
     int tune_rebuild;    // rebuild at every evaluation (autotuning)
     int row_refine;      // bins along the innermost axis per bin width (>= 1)
     int pad_rr;
+    // completion counter of band pass 2 (zero between launches; the last
+    // block of the band resets it) and the running fmax^2 as the bits of a
+    // non-negative double (ordered like the values)
+    unsigned int done_b, pad_done;
+    unsigned long long fmax2_bits;
     TP<float> tpf;       // Tersoff constants in FP32 / FP64 (Tersoff bands)
     TP<double> tpd;
 };
@@ -407,6 +430,40 @@ __device__ inline void block_sum_store(T (&v)[K], double *dst) {
     __syncthreads();
 }
 
+// As block_sum_store for K <= 16 values, with a transposing warp reduction:
+// at each butterfly level a lane keeps half of its values and adds the
+// partner's copy of that half (16 shuffles in all instead of 5 per value),
+// so lane l ends with the warp total of value l >> 1.  Fixed order; the
+// totals go to dst[0..K-1] in FP64 (across the warps, in warp order).
+template <int K, typename T>
+__device__ inline void block_sum_store_tr(const T (&v)[K], double *dst) {
+    static_assert(K <= 16, "values are padded to 16");
+    __shared__ T red[TILE / 32][16];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T a[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[k] = k < K ? v[k] : (T)0;
+#pragma unroll
+    for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < h; ++k) {
+            const T send = hi ? a[k] : a[k + h];
+            const T keep = hi ? a[k + h] : a[k];
+            a[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
+    if ((lane & 1) == 0) red[w][lane >> 1] = a[0];
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0.0;
+        for (int q = 0; q < TILE / 32; ++q) s += (double)red[q][threadIdx.x];
+        dst[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
 // Sum K per-thread values over a block of any multiple of 32 threads (up to
 // 1024) in FP64, fixed order (a warp butterfly within each warp, then one
 // across the warp totals); thread 0 receives the totals.  Butterflies keep
@@ -497,13 +554,16 @@ template <typename T>
 void launch_tersoff_gather(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 template <typename T>
 void launch_image_finalize(const ImgRef *imgs, int count, BandDev *bands, cudaStream_t s);
+// band pass 1 (dots, then per image and per band the NEB coefficients and
+// FIRE sums), pass 2 (f_NEB, fmax, FIRE decision); the dots alone and their
+// per-image sums (spacings of the refinement check)
 template <typename T>
 void launch_band_dots(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
-void launch_dots_reduce(const ImgRef *imgs, int count, BandDev *bands, cudaStream_t s);
-void launch_neb_coef(const int *band_ids, int nbands, BandDev *bands, cudaStream_t s);
 template <typename T>
 void launch_neb_force(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
-void launch_fire_scalars(const int *band_ids, int nbands, BandDev *bands, cudaStream_t s);
+template <typename T>
+void launch_band_dots_only(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
+void launch_dots_reduce(const ImgRef *imgs, int count, BandDev *bands, cudaStream_t s);
 template <typename T>
 void launch_fire_update(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 template <typename T>

@@ -171,6 +171,16 @@ void widths(const double *h, double *w) {
     }
 }
 
+// every perpendicular width of h is at least rl / MAX_STENCIL (with a
+// margin for the FP32 bin arithmetic)
+bool stencil_reaches(const double *h, double rl) {
+    double w[3];
+    widths(h, w);
+    for (int a = 0; a < 3; ++a)
+        if (!(rl < MAX_STENCIL * w[a] * 0.999)) return false;
+    return true;
+}
+
 int bins_for(const double *h, double bw) {
     double w[3];
     widths(h, w);
@@ -325,17 +335,14 @@ void enqueue_step_set(const LaunchSet &ls, Launcher &L) {
     cudaStream_t s = ls.s;
     enqueue_eval_set<T>(ls, L);
     L.pre(K_BAND_DOTS); launch_band_dots<T>(ls.rtiles, ls.n_rtiles, d, s); L.post(K_BAND_DOTS);
-    L.pre(K_DOTS_REDUCE); launch_dots_reduce(ls.imgs, ls.nimg, d, s); L.post(K_DOTS_REDUCE);
-    L.pre(K_NEB_COEF); launch_neb_coef(ls.band_ids, ls.nbands, d, s); L.post(K_NEB_COEF);
     L.pre(K_NEB_FORCE); launch_neb_force<T>(ls.rtiles, ls.n_rtiles, d, s); L.post(K_NEB_FORCE);
-    L.pre(K_FIRE_SCALARS); launch_fire_scalars(ls.band_ids, ls.nbands, d, s); L.post(K_FIRE_SCALARS);
     L.pre(K_FIRE_UPDATE); launch_fire_update<T>(ls.rtiles, ls.n_rtiles, d, s);
     L.post(K_FIRE_UPDATE);
 }
 
 int launches_in_set(const LaunchSet &ls) {
     return 8 + (ls.n_lj ? 2 : 0) + (ls.n_ljc ? 1 : 0) + (ls.n_ters ? 4 : 0) + (ls.n_nep ? 4 : 0) +
-           1 + 6;
+           1 + 3;
 }
 
 LaunchSet band_set(cfneb_band *b, const ImgRef *imgs, int nimg, const Tile *atiles, int nat) {
@@ -589,11 +596,11 @@ void spacings(cfneb_band *b, std::vector<double> &ell) {
     CK(cudaMemcpyAsync(b->d_scratch_tiles, rt.data(), rt.size() * sizeof(Tile),
                        cudaMemcpyHostToDevice, b->s));
     if (b->precision == CFNEB_MIXED)
-        launch_band_dots<float>(b->d_scratch_tiles + b->dv.rtpi, (int)rt.size() - b->dv.rtpi,
-                                b->d_self, b->s);
+        launch_band_dots_only<float>(b->d_scratch_tiles + b->dv.rtpi,
+                                     (int)rt.size() - b->dv.rtpi, b->d_self, b->s);
     else
-        launch_band_dots<double>(b->d_scratch_tiles + b->dv.rtpi, (int)rt.size() - b->dv.rtpi,
-                                 b->d_self, b->s);
+        launch_band_dots_only<double>(b->d_scratch_tiles + b->dv.rtpi,
+                                      (int)rt.size() - b->dv.rtpi, b->d_self, b->s);
     launch_dots_reduce(b->d_scratch_imgs + 1, (int)im.size() - 1, b->d_self, b->s);
     CK(cudaGetLastError());
     std::vector<ImgScalars> sc(b->N);
@@ -705,7 +712,15 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
     b->kind = pot->kind;
     b->filt = cf ? *cf : cfneb_cell_filter{1, CFNEB_ROTFREE_B, 0.0, 0.0};
     std::memcpy(b->h0, A->cell, sizeof(b->h0));
-    b->c = b->filt.cell_factor > 0 ? b->filt.cell_factor : (double)b->n;
+    // lattice scale: the caller's c, or J = Omega0^(1/3) n^(1/6) (the scale
+    // of the generalized solid-state NEB: it keeps the lattice rows'
+    // stiffness per unit of X independent of n), or n_atoms
+    if (b->filt.cell_factor > 0)
+        b->c = b->filt.cell_factor;
+    else if (b->filt.cell_factor == CFNEB_CELL_FACTOR_J)
+        b->c = std::cbrt(std::fabs(det3(A->cell))) * std::pow((double)b->n, 1.0 / 6.0);
+    else
+        b->c = (double)b->n;
     CK(cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
@@ -758,6 +773,12 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
     const double skin = opt->skin >= 0.0 ? opt->skin : (pot->kind == CFNEB_LJ ? 0.12 * rc : 0.15);
     const double rl = rc + skin;
     b->rl = rl;
+    // the cell list reaches MAX_STENCIL bins to each side: both end cells
+    // must be at least rl / MAX_STENCIL wide along every lattice direction
+    if (!stencil_reaches(A->cell, rl) || (cf && cf->enabled && !stencil_reaches(B->cell, rl))) {
+        *err = CFNEB_ERR_INVALID_ARG;
+        return b;
+    }
     // bin width: the caller's, the cached autotuned one for this class, or rc
     const double dens = (double)b->n / std::fabs(det3(A->cell)) * rc * rc * rc;
     b->tune_key = std::make_tuple(pot->kind, opt->precision,
@@ -1619,6 +1640,61 @@ int cfneb_get_state(const cfneb_band *cb, double *X, double *F, double *Fneb, do
         if (climbing_index) *climbing_index = b->h_bp->ci;
         leave(b);
         return status_from_bits(b->h_bp->status);
+    } catch (CudaFail &) {
+        return CFNEB_ERR_CUDA;
+    }
+}
+
+int cfneb_set_state(cfneb_band *b, const double *X) {
+    if (!b || !X) return CFNEB_ERR_INVALID_ARG;
+    const size_t per = (size_t)b->dv.rows * 3;
+    for (size_t i = 0; i < (size_t)b->N * per; ++i)
+        if (!std::isfinite(X[i])) return CFNEB_ERR_INVALID_ARG;
+    try {
+        enter(b);
+        const size_t cnt = (size_t)b->N * per;
+        const double *src = X;
+        char *dst = (char *)b->dv.X;
+        if (b->ts == 4) {
+            std::vector<float> tmp(cnt);
+            for (size_t i = 0; i < cnt; ++i) tmp[i] = (float)src[i];
+            CK(cudaMemcpyAsync(dst, tmp.data(), cnt * sizeof(float), cudaMemcpyHostToDevice,
+                               b->s));
+            CK(cudaStreamSynchronize(b->s));
+        } else {
+            CK(cudaMemcpyAsync(dst, src, cnt * sizeof(double), cudaMemcpyHostToDevice, b->s));
+            CK(cudaStreamSynchronize(b->s));
+        }
+        fire_reset(b);
+        eval_images(b, {0, b->N - 1});  // the endpoints' energies and forces
+        b->ends_e64 = false;            // their FP64 energies are re-taken when reported
+        read_params(b);
+        leave(b);
+        return status_from_bits(b->h_bp->status);
+    } catch (CudaFail &) {
+        return CFNEB_ERR_CUDA;
+    }
+}
+
+int cfneb_get_image_scalars(const cfneb_band *cb, double *energies, double *dots, double *coef) {
+    cfneb_band *b = const_cast<cfneb_band *>(cb);
+    if (!b) return CFNEB_ERR_INVALID_ARG;
+    try {
+        enter(b);
+        std::vector<ImgScalars> sc(b->N);
+        CK(cudaMemcpyAsync(sc.data(), b->dv.sc, b->N * sizeof(ImgScalars),
+                           cudaMemcpyDeviceToHost, b->s));
+        CK(cudaStreamSynchronize(b->s));
+        for (int i = 0; i < b->N; ++i) {
+            const bool inner = i > 0 && i < b->N - 1;
+            if (energies) energies[i] = sc[i].E;
+            for (int k = 0; k < 10; ++k)
+                if (dots) dots[10 * i + k] = inner ? sc[i].dots[k] : 0.0;
+            for (int k = 0; k < 2; ++k)
+                if (coef) coef[2 * i + k] = inner ? sc[i].coef[k] : 0.0;
+        }
+        leave(b);
+        return CFNEB_OK;
     } catch (CudaFail &) {
         return CFNEB_ERR_CUDA;
     }

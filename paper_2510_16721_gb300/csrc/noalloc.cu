@@ -1,14 +1,15 @@
 // Lennard-Jones evaluation of one structure without any device allocation.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured on its stream, allocators that own all device memory of a
-// process (a framework's caching pool, a fixed arena sized at start-up),
-// and long-running services that must not allocate once they are serving.
-// This entry point runs the library's existing FP64 evaluation kernels (set-up,
-// map-back, cell list, LJ forces, per-image finalize) on scratch memory that
-// lives in one file-scope __device__ array, and copies the results into the
-// caller's device buffers.  The caller passes inputs and outputs; nothing is
-// allocated or freed, here or in any library routine it calls.
+// Some callers cannot call cudaMalloc: allocators that own all device memory
+// of a process (a framework's caching pool, a fixed arena sized at
+// start-up) leave nothing for a library to take, and long-running services
+// must not allocate once they are serving (an allocation can fail or stall
+// at any time).  This entry point runs the library's existing FP64
+// evaluation kernels (set-up, map-back, cell list, LJ forces, per-image
+// finalize) on scratch memory that lives in one file-scope __device__
+// array, and copies the results into the caller's device buffers.  The
+// caller passes inputs and outputs; nothing is allocated or freed, here or
+// in any library routine it calls.
 //
 // The array is every loading GPU's for the lifetime of the process and is
 // shared by every call: calls that overlap on the GPU (different streams, or
@@ -16,7 +17,10 @@
 // cleared at the start of each call.
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
+
+#include <cuda.h>
 
 #include "../../include/cfneb.h"
 #include "common.cuh"
@@ -88,8 +92,47 @@ __global__ void k_noalloc_init(BandDev dv, BandParams bp, H1 cell, int ntiles) {
     for (int k = tid; k < NA_MAX_BINS; k += gridDim.x * blockDim.x) cnt[k] = 0;
 }
 
+// The device address of the array belongs to the CUDA context the module is
+// loaded in (a cudaDeviceReset or a context of the caller's own makes a new
+// one), so it is looked up once per context and cached under the context's
+// process-unique id (cuCtxGetId; the driver functions are reached through
+// the runtime's entry-point query, so no driver library is linked).
 std::mutex g_mu;
-unsigned char *g_base[256];  // device address of the array, per device
+std::map<unsigned long long, unsigned char *> g_base;
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+
+// the array's device address in the current context, or nullptr
+unsigned char *scratch_base() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_ctx_current || !g_ctx_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault,
+                                             &q1) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) !=
+                cudaSuccess ||
+            q2 != cudaDriverEntryPointSuccess)
+            return nullptr;
+        g_ctx_current = (CtxGetCurrentFn)f1;
+        g_ctx_id = (CtxGetIdFn)f2;
+    }
+    // make the runtime bind the device's context to this thread first
+    if (cudaFree(nullptr) != cudaSuccess) return nullptr;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx || g_ctx_id(ctx, &id) != CUDA_SUCCESS)
+        return nullptr;
+    auto it = g_base.find(id);
+    if (it != g_base.end()) return it->second;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return nullptr;
+    g_base[id] = (unsigned char *)p;
+    return (unsigned char *)p;
+}
 
 }  // namespace
 
@@ -99,22 +142,28 @@ extern "C" int cfneb_lj_evaluate_noalloc(const double *d_positions, int32_t n_at
                                          double *d_forces, double *d_virial, void *cuda_stream) {
     if (!d_positions || !cell || n_atoms <= 0) return CFNEB_ERR_INVALID_ARG;
     if (n_atoms > NA_MAX_ATOMS) return CFNEB_ERR_INVALID_ARG;
-    if (!(eps > 0) || !(sigma > 0) || !(rc > 0)) return CFNEB_ERR_INVALID_ARG;
+    for (int k = 0; k < 9; ++k)
+        if (!std::isfinite(cell[k])) return CFNEB_ERR_INVALID_ARG;
+    if (!std::isfinite(eps) || !std::isfinite(sigma) || !std::isfinite(rc) || !(eps > 0) ||
+        !(sigma > 0) || !(rc > 0))
+        return CFNEB_ERR_INVALID_ARG;
     if (!(std::fabs(det3(cell)) > 0)) return CFNEB_ERR_INVALID_ARG;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return CFNEB_ERR_CUDA;
-    // once per device, with that device current: the device address of the
-    // array (host code may not use the symbol itself as a pointer)
-    unsigned char *base = nullptr;
+    // the cell list reaches MAX_STENCIL bins to each side: every lattice
+    // direction must be at least rc / MAX_STENCIL wide
     {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_base[dev]) {
-            void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return CFNEB_ERR_CUDA;
-            g_base[dev] = (unsigned char *)p;
+        const double vol = std::fabs(det3(cell));
+        for (int a = 0; a < 3; ++a) {
+            const double *u = cell + 3 * ((a + 1) % 3), *v = cell + 3 * ((a + 2) % 3);
+            const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2],
+                         cz = u[0] * v[1] - u[1] * v[0];
+            const double w = vol / std::sqrt(cx * cx + cy * cy + cz * cz);
+            if (!(rc < MAX_STENCIL * w * 0.999)) return CFNEB_ERR_INVALID_ARG;
         }
-        base = g_base[dev];
     }
+    // the device address of the array in the current context (host code
+    // may not use the symbol itself as a pointer)
+    unsigned char *base = scratch_base();
+    if (!base) return CFNEB_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const int n = n_atoms;
     BandDev dv;
@@ -200,5 +249,19 @@ extern "C" int cfneb_lj_evaluate_noalloc(const double *d_positions, int32_t n_at
     if (d_forces && cudaMemcpyAsync(d_forces, base + O_F, (size_t)n * 3 * sizeof(double),
                                     cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return CFNEB_ERR_CUDA;
+    // the status word the kernels raise, and the energy (a non-finite
+    // energy marks overlapping atoms): read back once the work is done
+    int bits = 0;
+    double e = 0.0;
+    const BandParams *d_bp = (const BandParams *)(base + O_PARAMS);
+    if (cudaMemcpyAsync(&bits, &d_bp->status, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(&e, &sc0->E, sizeof(double), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return CFNEB_ERR_CUDA;
+    if (bits & ST_NONFINITE || !std::isfinite(e)) return CFNEB_ERR_NONFINITE;
+    if (bits & ST_NOT_SPD) return CFNEB_ERR_NOT_SPD;
+    if (bits & ST_NBR_OVERFLOW) return CFNEB_ERR_NBR_OVERFLOW;
     return CFNEB_OK;
 }

@@ -450,20 +450,184 @@ __device__ inline void ters_load(const TP<T> &q, const BandDev &b, int img, int 
     }
 }
 
-// One thread per atom.  Each thread's neighbour records (pair vector, s,
-// cutoff values, partials) sit in shared memory, strided by the block size
-// so that the threads of a warp hit distinct banks; an atom with more list
-// entries than the shared slots keeps them in local memory.
+// ---- register-resident site computation (FP32 path) -------------------------
+//
+// Carbon atoms hold 3 (graphite) or 4 (diamond) list entries within R + D +
+// skin, 5 or more only in compressed intermediates.  For up to RMAX entries
+// the records live in registers: every loop below is unrolled over RMAX with
+// the entry index known at compile time, and the angular values (cos, g,
+// dg/dcos) of each unordered pair are kept from the zeta pass for the force
+// pass instead of being evaluated twice.  Atoms with more entries take the
+// record path above (ters_site on a local array).  The arithmetic is that of
+// ters_site term by term.
+constexpr int RMAX = 4;
+constexpr int RPAIRS = RMAX * (RMAX - 1) / 2;
+
 template <typename T>
-__global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 7 : 1) k_ters_partials(const Tile *tiles, BandDev *bands) {
-    constexpr int NS = NShared<T>::value;
+__device__ inline void ters_load_reg(const TP<T> &q, const BandDev &b, int img, int t, int cnt,
+                                     const T *s_bv, const T *s_dh, const int *s_nb,
+                                     T (&rx)[RMAX], T (&ry)[RMAX], T (&rz)[RMAX],
+                                     T (&sr)[RMAX]) {
+    using T4 = typename Vec4<T>::type;
+    const int n = b.n;
+    const size_t base = (size_t)img * n;
+    const T4 *off = (const T4 *)b.slot_off + base;
+    const T4 *offl = (const T4 *)b.slot_off_lo + base;
+    const int *nslot = b.nbr_slot + (size_t)img * MAXN_TERSOFF * n;
+    const int *ncode = b.nbr_code + (size_t)img * MAXN_TERSOFF * n;
+    const int bin = b.slot_bin[base + t];
+    const int nb12 = s_nb[1] * s_nb[2];
+    const int b0 = bin / nb12, rem = bin - b0 * nb12;
+    const int b1 = rem / s_nb[2], b2 = rem - b1 * s_nb[2];
+    const T4 oi = off[t], oil = offl[t];
+    int qs[RMAX], code[RMAX];
+#pragma unroll
+    for (int k = 0; k < RMAX; ++k) {
+        qs[k] = k < cnt ? nslot[(size_t)k * n + t] : t;
+        code[k] = k < cnt ? ncode[(size_t)k * n + t] : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < RMAX; ++k) {
+        if (k < cnt) {
+            ters_pair<T>(q, oi, oil, off[qs[k]], offl[qs[k]], code[k], b0, b1, b2, s_bv, s_dh,
+                         s_nb, rx[k], ry[k], rz[k], sr[k]);
+        } else {
+            rx[k] = ry[k] = rz[k] = (T)0;
+            sr[k] = q.D + q.D;  // beyond R + D: no terms
+        }
+    }
+}
+
+template <typename T>
+__device__ inline void ters_site_reg(const TP<T> &q, const T (&rx)[RMAX], const T (&ry)[RMAX],
+                                     const T (&rz)[RMAX], const T (&sr)[RMAX],
+                                     typename Vec4<T>::type *nP, int cnt, int n, int t, T &U,
+                                     T (&vir)[9]) {
+    T fc[RMAX], dfc[RMAX], ir[RMAX], zeta[RMAX];
+    bool act[RMAX];
+#pragma unroll
+    for (int j = 0; j < RMAX; ++j) {
+        cutoff(q, sr[j], fc[j], dfc[j]);
+        act[j] = !(fc[j] == (T)0 && dfc[j] == (T)0);
+        ir[j] = M<T>::rcpf(q.R + sr[j]);
+        zeta[j] = (T)0;
+    }
+    // pass 1: zeta over unordered pairs; cos, g, dg kept per pair
+    T pc[RPAIRS], pg[RPAIRS], pdg[RPAIRS];
+    {
+        int p = 0;
+#pragma unroll
+        for (int j = 0; j < RMAX; ++j) {
+            T zj_acc = 0;
+#pragma unroll
+            for (int k = j + 1; k < RMAX; ++k, ++p) {
+                pc[p] = pg[p] = pdg[p] = (T)0;
+                if (act[j] && act[k]) {
+                    const T cs = (rx[j] * rx[k] + ry[j] * ry[k] + rz[j] * rz[k]) * ir[j] * ir[k];
+                    T g, dg;
+                    gfun(q, cs, g, dg);
+                    pc[p] = cs;
+                    pg[p] = g;
+                    pdg[p] = dg;
+                    zj_acc += fc[k] * g;
+                    zeta[k] += fc[j] * g;
+                }
+            }
+            zeta[j] += zj_acc;
+        }
+    }
+    // pass 2: bond orders, energy, radial terms, prefactors
+    T pref[RMAX], Px[RMAX], Py[RMAX], Pz[RMAX];
+#pragma unroll
+    for (int j = 0; j < RMAX; ++j) {
+        pref[j] = Px[j] = Py[j] = Pz[j] = (T)0;
+        if (act[j]) {
+            const T z = zeta[j], s = sr[j];
+            T bij = (T)1, dbij = (T)0;
+            if (z > (T)0) {
+                const T x = M<T>::ex(q.n * M<T>::lg(q.beta * z));
+                if (x < (T)(1.0 / 1024.0)) {
+                    // (1 + x)^(-1/2n) by its series: log1p(x) to x^4 and
+                    // exp(-u) to u^3 (truncation below 1e-13 relative)
+                    const T l = x * ((T)1 - x * ((T)0.5 - x * ((T)(1.0 / 3.0) - x * (T)0.25)));
+                    const T u = q.inv2n * l;
+                    bij = (T)1 - u * ((T)1 - u * ((T)0.5 - u * (T)(1.0 / 6.0)));
+                } else {
+                    bij = M<T>::ex(-q.inv2n * M<T>::l1p(x));
+                }
+                dbij = (T)(-0.5) * bij * x / (((T)1 + x) * z);
+            }
+            const T fr = q.AeR * M<T>::ex(-q.l1 * s);
+            const T fa = -q.BeR * M<T>::ex(-q.l2 * s);
+            const T dfr = -q.l1 * fr, dfa = -q.l2 * fa;
+            U += (T)0.5 * fc[j] * (fr + bij * fa);
+            const T radial = (T)0.5 * (dfc[j] * (fr + bij * fa) + fc[j] * (dfr + bij * dfa)) * ir[j];
+            pref[j] = (T)0.5 * fc[j] * fa * dbij;
+            Px[j] = radial * rx[j];
+            Py[j] = radial * ry[j];
+            Pz[j] = radial * rz[j];
+        }
+    }
+    // pass 3: angular terms, both bonds of each unordered pair at once
+    {
+        int p = 0;
+#pragma unroll
+        for (int j = 0; j < RMAX; ++j) {
+            T Pxj = 0, Pyj = 0, Pzj = 0;
+#pragma unroll
+            for (int k = j + 1; k < RMAX; ++k, ++p) {
+                if (act[j] && act[k] && (pref[j] != (T)0 || pref[k] != (T)0)) {
+                    const T ijk = ir[j] * ir[k];
+                    const T cs = pc[p], g = pg[p], dg = pdg[p];
+                    const T aj = cs * ir[j] * ir[j], ak = cs * ir[k] * ir[k];
+                    const T S = dg * (pref[j] * fc[k] + pref[k] * fc[j]);
+                    const T rj = pref[k] * dfc[j] * g * ir[j], rk = pref[j] * dfc[k] * g * ir[k];
+                    Pxj += S * (rx[k] * ijk - aj * rx[j]) + rj * rx[j];
+                    Pyj += S * (ry[k] * ijk - aj * ry[j]) + rj * ry[j];
+                    Pzj += S * (rz[k] * ijk - aj * rz[j]) + rj * rz[j];
+                    Px[k] += S * (rx[j] * ijk - ak * rx[k]) + rk * rx[k];
+                    Py[k] += S * (ry[j] * ijk - ak * ry[k]) + rk * ry[k];
+                    Pz[k] += S * (rz[j] * ijk - ak * rz[k]) + rk * rz[k];
+                }
+            }
+            Px[j] += Pxj;
+            Py[j] += Pyj;
+            Pz[j] += Pzj;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < RMAX; ++j) {
+        if (j < cnt) {
+            typename Vec4<T>::type pv;
+            pv.x = Px[j];
+            pv.y = Py[j];
+            pv.z = Pz[j];
+            pv.w = (T)0;
+            nP[(size_t)j * n + t] = pv;
+            // V_mn -= r_m P_n
+            vir[0] -= rx[j] * Px[j]; vir[1] -= rx[j] * Py[j]; vir[2] -= rx[j] * Pz[j];
+            vir[3] -= ry[j] * Px[j]; vir[4] -= ry[j] * Py[j]; vir[5] -= ry[j] * Pz[j];
+            vir[6] -= rz[j] * Px[j]; vir[7] -= rz[j] * Py[j]; vir[8] -= rz[j] * Pz[j];
+        }
+    }
+}
+
+// One thread per atom.  FP32: the records of an atom with at most RMAX list
+// entries live in registers (ters_site_reg); more entries take a local
+// array.  FP64: the records sit in shared memory, strided by the block size
+// so that the threads of a warp hit distinct banks (local memory beyond
+// NShared entries).
+template <typename T>
+__global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 5 : 1) k_ters_partials(const Tile *tiles, BandDev *bands) {
+    constexpr bool REG = sizeof(T) == 4;
+    constexpr int NS = REG ? 1 : NShared<T>::value;
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
     const ImgScalars &sc = b.sc[tl.img];
     __shared__ T s_bv[9], s_dh[9];
     __shared__ int s_nb[3];
     __shared__ TP<T> s_q;  // per-band constants, staged by the whole block
-    __shared__ T s_rec[NB_FIELDS * NS * TILE];
+    __shared__ T s_rec[REG ? 1 : NB_FIELDS * NS * TILE];
     if (threadIdx.x < 9) {
         s_bv[threadIdx.x] = (T)sc.bv[threadIdx.x];
         s_dh[threadIdx.x] = (T)sc.dh[threadIdx.x];
@@ -482,7 +646,13 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 7 : 1) k_ters_partials(
     T vir[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (t < n) {
         const int cnt = b.nbr_cnt[base + t];
-        if (cnt <= NS) {
+        if (REG && cnt <= RMAX) {
+            T rx[RMAX], ry[RMAX], rz[RMAX], sr[RMAX];
+            ters_load_reg<T>(q, b, tl.img, t, cnt, s_bv, s_dh, s_nb, rx, ry, rz, sr);
+#pragma unroll
+            for (int k = 0; k < RMAX; ++k) nin += k < cnt && sub_rn(sr[k], q.D) < q.Dlo;
+            ters_site_reg<T>(q, rx, ry, rz, sr, nP, cnt, n, t, U, vir);
+        } else if (!REG && cnt <= NS) {
             const Nbr<T> nb{s_rec + threadIdx.x, TILE, NS};
             ters_load<T>(q, b, tl.img, t, cnt, s_bv, s_dh, s_nb, nb);
             for (int k = 0; k < cnt; ++k) nin += sub_rn(nb(NB_SR, k), q.D) < q.Dlo;
@@ -500,7 +670,7 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 7 : 1) k_ters_partials(
     for (int k = 0; k < 9; ++k) acc[1 + k] = vir[k];
     acc[10] = (T)nin;
     acc[11] = (T)(nin * (nin - 1));
-    block_sum_store<12, T>(acc, b.atom_part + ((size_t)tl.img * b.atpi + tl.t) * NPART);
+    block_sum_store_tr<12, T>(acc, b.atom_part + ((size_t)tl.img * b.atpi + tl.t) * NPART);
 }
 
 // Reverse entries of a rebuilt list: for entry k of slot t (neighbour slot
@@ -903,12 +1073,12 @@ __global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 4 : 1) k_nep_partials(c
 template <typename T>
 void launch_tersoff_list(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
     if (ntiles <= 0) return;
-    k_ters_list<T><<<ntiles < GATED_GRID ? ntiles : GATED_GRID, TILE, 0, s>>>(tiles, ntiles, bands);
+    k_ters_list<T><<<ntiles < gated_grid() ? ntiles : gated_grid(), TILE, 0, s>>>(tiles, ntiles, bands);
 }
 template <typename T>
 void launch_tersoff_reverse(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
     if (ntiles <= 0) return;
-    k_ters_reverse<T><<<ntiles < GATED_GRID ? ntiles : GATED_GRID, TILE, 0, s>>>(tiles, ntiles,
+    k_ters_reverse<T><<<ntiles < gated_grid() ? ntiles : gated_grid(), TILE, 0, s>>>(tiles, ntiles,
                                                                                  bands);
 }
 template <typename T>

@@ -64,7 +64,7 @@ def lj_band_case(n_images=7, strain_seed=None):
 def gpu_band(g, R0, h0, R1, h1, n_images, potential, k, dt, maxstep=0.2, climb=True,
              cell_filter=True, precision=0, noise=None, dt_max=None, adaptive=False, n_min=3,
              n_max=None, variant=0, pressure=0.0, bin_scale=0.0, alpha_ins=1.5, alpha_del=0.5,
-             skin=None):
+             skin=None, cell_factor=0.0):
     opt = g.default_options()
     if skin is not None:
         opt.skin = skin
@@ -80,15 +80,15 @@ def gpu_band(g, R0, h0, R1, h1, n_images, potential, k, dt, maxstep=0.2, climb=T
     opt.bin_scale = bin_scale
     opt.alpha_ins = alpha_ins
     opt.alpha_del = alpha_del
-    cf = g.CellFilter(int(cell_filter), variant, 0.0, pressure)
+    cf = g.CellFilter(int(cell_filter), variant, cell_factor, pressure)
     return g.create_band((R0, h0), (R1, h1), n_images, potential, cf, opt, noise=noise)
 
 
 def oracle_band(o, pot, R0, h0, R1, h1, n_images, k, dt, maxstep=0.2, climb=True,
                 cell_filter=True, noise=None, dt_max=None, adaptive=False, n_min=3, n_max=None,
-                variant=0, pressure=0.0, alpha_ins=1.5, alpha_del=0.5):
+                variant=0, pressure=0.0, alpha_ins=1.5, alpha_del=0.5, c=None):
     fire = o.Fire(dt=dt, dt_max=10 * dt if dt_max is None else dt_max, maxstep=maxstep)
-    return o.make_band(pot, R0, h0, R1, h1, n_images, k=k, climb=climb,
+    return o.make_band(pot, R0, h0, R1, h1, n_images, k=k, climb=climb, c=c,
                        cell_filter=cell_filter, fire=fire, noise=noise, adaptive=adaptive,
                        n_min=n_min, n_max=n_images if n_max is None else n_max,
                        variant=variant, pressure=pressure, alpha_ins=alpha_ins,

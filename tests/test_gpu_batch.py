@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import cfneb_inputs as ci
-from _cases import gpu_band, lj_band_case
+from _cases import gpu_band, lj_band_case, oracle_band
 
 pytestmark = pytest.mark.gpu
 
@@ -71,6 +71,52 @@ def test_batch_equals_alone_bitwise(g, precision):
         _same(a, b)
     st = bt.status()
     assert [s["steps"] for s in st] == [12, 12, 12, 12]
+    bt.destroy()
+
+
+def _oracle_of(o, which):
+    if which == "lj31":
+        R0, h0, R1, h1 = lj_band_case()
+        return oracle_band(o, o.LJ(), R0, h0, R1, h1, 7, k=1.0, dt=0.01, cell_filter=False)
+    if which == "lj72":
+        R0, h0, R1, h1 = ci.lj_vacancy_hop(ci.LJ_A, (3, 3, 2))
+        h1s = ci.strained_cell(h1, 3, 0.003)
+        return oracle_band(o, o.LJ(), R0, h0, ci.affine(R1, h1, h1s), h1s, 5, k=1.0, dt=0.01,
+                           cell_filter=True)
+    if which == "lj255":
+        R0, h0, R1, h1 = ci.lj_vacancy_hop(ci.LJ_A, (4, 4, 4), divacancy=True)
+        h1s = ci.strained_cell(h1, 5, 0.02)
+        return oracle_band(o, o.LJ(), R0, h0, ci.affine(R1, h1, h1s), h1s, 5, k=1.0, dt=0.01,
+                           cell_filter=True)
+    cfg = ci.tersoff_graphite_hexdiamond()
+    R0, h0, R1, h1 = cfg["endpoints"]
+    return oracle_band(o, o.Tersoff(), R0, h0, R1, h1, 9, k=0.1, dt=0.1, cell_filter=True,
+                       noise=cfg["noise"])
+
+
+def test_batch_matches_oracle_fp64(g, oracle_mod):
+    """Uneven FP64 bands (31-atom fixed-cell and 72- and 255-atom cell-filter
+    LJ hops, the 576-atom Tersoff carbon band) stepped together in one batch:
+    each band's state after 10 steps is the oracle's at 1e-9."""
+    names = ["lj31", "lj72", "lj255", "ters576"]
+    batched = [_make(g, w, 0) for w in names]
+    bt = g.Batch(0)
+    for b in batched:
+        bt.add(b)
+    bt.step(10)
+    for name, b in zip(names, batched):
+        ob = _oracle_of(oracle_mod, name)
+        ob.step(10)
+        st = b.get_state()
+        assert st["X"].shape[0] == ob.N
+        for i in range(ob.N):
+            d = np.max(np.abs(st["X"][i] - ob.X[i])) / max(1.0, np.max(np.abs(ob.X[i])))
+            assert d <= 1e-9, (name, "X", i, d)
+        for i in range(1, ob.N - 1):
+            Fo = ob.fneb[i - 1].reshape(st["Fneb"][i].shape)
+            d = np.max(np.abs(st["Fneb"][i] - Fo)) / max(1.0, np.max(np.abs(Fo)))
+            assert d <= 1e-9, (name, "Fneb", i, d)
+        assert st["ci"] == ob.ci, name
     bt.destroy()
 
 

@@ -101,3 +101,27 @@ def test_nep_arguments_are_validated_on_the_host(libmod):
         st = g.lib().cfneb_create_band(ctypes.byref(A), ctypes.byref(B), 5, ctypes.byref(good),
                                        None, ctypes.byref(opt), None, ctypes.byref(out))
         assert st != g.ERR_INVALID_ARG and st < 0
+
+
+@pytest.mark.parametrize("case", ["inf_cell", "nan_eps", "inf_rc", "narrow_cell", "singular"])
+def test_noalloc_rejects_invalid_input_before_gpu_work(libmod, case):
+    """cfneb_lj_evaluate_noalloc validates its host arguments first: a
+    non-finite cell entry or potential constant, a singular cell or a cell
+    narrower than rc / 7 along a lattice direction (the cell list reaches 7
+    bins to each side) return INVALID_ARG without touching the device (the
+    device pointers here are never dereferenced)."""
+    import numpy as np
+    h = np.eye(3) * 10.0
+    eps, sigma, rc = 1.0, 1.0, 2.5
+    if case == "inf_cell":
+        h[1, 2] = np.inf
+    elif case == "nan_eps":
+        eps = float("nan")
+    elif case == "inf_rc":
+        rc = float("inf")
+    elif case == "narrow_cell":
+        h[2, 2] = 0.3  # rc / 7 = 0.357
+    else:
+        h[2] = h[1]
+    st = libmod.lj_evaluate_noalloc(16, 4, h, eps, sigma, rc, 1, 0, 0, 0)
+    assert st == libmod.ERR_INVALID_ARG

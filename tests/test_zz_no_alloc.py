@@ -1,13 +1,13 @@
 """The allocation-free entry point, cfneb_lj_evaluate_noalloc.
 
-It exists for callers that cannot allocate device memory (stream capture in
-progress, a process-wide allocator, a service that must not allocate while
-serving): the caller hands in device buffers, the library works in one
+It exists for callers that cannot allocate device memory (a process whose
+allocator owns all of the device memory, a service that must not allocate
+while serving): the caller hands in device buffers, the library works in one
 static device array.  These tests call it through the C ABI with device
 buffers owned by the test and check its output against cfneb_evaluate (the
 allocating entry point) at the FP64 tolerance of the other parity tests,
 on two calls in a row with different structures, so that the second call
-runs on the scratch the first one left behind.
+runs on the scratch the first one left behind, and against the FP64 oracle.
 """
 import numpy as np
 import pytest
@@ -55,6 +55,16 @@ def test_noalloc_matches_evaluate_on_two_calls(env):
         assert abs(E - Er[0]) <= 1e-10 * abs(Er[0])
         assert _rel(F, Fr[0]) <= 1e-10
         assert _rel(V, Vr[0]) <= 1e-10
+
+
+def test_noalloc_matches_oracle(env, oracle_mod):
+    torch, g = env
+    R, h = lj_structures()["triclinic240"]
+    E, F, V = _noalloc(torch, g, R, h)
+    e, Fo, Vo = oracle_mod.LJ(1.0, 1.0, 2.5, True).evaluate(R, h)
+    assert abs(E - np.sum(e)) <= 1e-10 * abs(np.sum(e))
+    assert _rel(F, Fo) <= 1e-10
+    assert _rel(V, Vo) <= 1e-10
 
 
 def test_noalloc_rejects_oversized_input(env):
