@@ -541,6 +541,14 @@ def run_ours(args, wl_name):
             "roofline": roof, "kernel_share": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "fp64_plain": fp64, "lists": lists,
             "rooflines": roofs}
+    if not args.no_batch:
+        # the batched workload (64 uneven LJ bands, one launch per kernel per
+        # step), measured after the main line's numbers are taken
+        bl = batch_line(args, "lj_batch64", 20, 3, None, with_fp64=not args.no_fp64,
+                        with_cpu=False)
+        line["lj_batch64"] = {k: bl[k] for k in ("value", "unit", "ms_per_step", "steps",
+                                                 "warmup", "config", "roofline", "e2e",
+                                                 "fp64_plain", "gpu_launches", "clocks")}
     print(json.dumps(line))
     if dist is not None:
         dist.barrier()
@@ -586,9 +594,7 @@ def cpu_oracle_lj_rate(bcs, seconds):
 
 
 def run_batch(args):
-    import numpy as np
     import torch
-    import cfneb_inputs as ci
     ws, rank, local = dist_info()
     dist = None
     if ws > 1:
@@ -596,9 +602,26 @@ def run_batch(args):
         td.init_process_group("nccl")
         dist = td
     torch.cuda.set_device(local)
+    line = batch_line(args, args.workload, args.steps, args.warmup, dist,
+                      with_fp64=not args.no_fp64, with_cpu=not args.no_cpu_baseline)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+    return 0
+
+
+def batch_line(args, workload, nsteps, warmup, dist, with_fp64=True, with_cpu=True):
+    """The batched workload (64 uneven LJ bands in one batch): timed steps,
+    per-kernel profile and rooflines, end to end, the FP64 one-band-per-launch
+    comparator and the oracle baseline, as one JSON-ready dict."""
+    import numpy as np
+    import torch
+    import cfneb_inputs as ci
+    ws, rank, local = dist_info()
     import paper_2510_16721_gb300 as g
     g.build()
-    wl = WORKLOADS[args.workload]
+    wl = WORKLOADS[workload]
     bcs = ci.lj_batch(seed=4 + rank, n_bands=wl["n_bands"])
     stream = torch.cuda.current_stream()
     work = sum(len(c["endpoints"][0]) * (c["n_images"] - 2) for c in bcs)
@@ -609,23 +632,23 @@ def run_batch(args):
         bt.add(b)
     t_create = time.perf_counter() - t_create
     bt.autotune(4)
-    bt.step(args.warmup)
+    bt.step(warmup)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     lb0 = [b.list_stats() for b in bands]
-    ms = time_steps(torch, bt, stream, args.steps, dist)
+    ms = time_steps(torch, bt, stream, nsteps, dist)
     clk = clocks.stop()
     lb1 = [b.list_stats() for b in bands]
     lists = {"skin": lb1[0][2], "builds_per_image_step":
              sum(b1[0] - b0[0] for b0, b1 in zip(lb0, lb1)) /
              max(1, sum(b1[1] - b0[1] for b0, b1 in zip(lb0, lb1)))}
     ms = max_over_ranks(torch, dist, ms)
-    value = job_rate(ws, work, args.steps, ms)
+    value = job_rate(ws, work, nsteps, ms)
     st = bt.status()
     assert all(s["status"] == 0 for s in st)
     # per-kernel profile
-    kp = max(5, min(args.steps, 20))
+    kp = max(5, min(nsteps, 20))
     bt.profile(True)
     bt.step(kp)
     prof = bt.profile_read()
@@ -656,14 +679,14 @@ def run_batch(args):
                  "traffic": traffic_for(dom), "work_per_launch": {"pairs": pairs, "atoms": work}})
     roofs = kernel_rooflines(prof, w, peaks, peak_src, (clk or {}).get("sm_max_mhz") or 2070.0)
     # launches of the profiled batch steps (every kernel, one launch each)
-    launches = int(round(sum(v[1] for v in prof.values()) / kp * args.steps))
+    launches = int(round(sum(v[1] for v in prof.values()) / kp * nsteps))
     bt.destroy()
     for b in bands:
         b.destroy()
     # plain FP64, one band per launch: every band stepped on its own
     fp64 = None
-    if not args.no_fp64:
-        k64 = max(3, args.steps // 5)
+    if with_fp64:
+        k64 = max(3, nsteps // 5)
         b64 = [make_lj_band(g, c, g.FP64, stream) for c in bcs]
         for b in b64:
             b.step(2)
@@ -686,7 +709,7 @@ def run_batch(args):
     bt2 = g.Batch(g.MIXED, stream=stream)
     for b in b2:
         bt2.add(b)
-    bt2.step(args.steps)
+    bt2.step(nsteps)
     d2h = 0
     for b in b2:
         p = b.get_path()
@@ -697,23 +720,20 @@ def run_batch(args):
     bt2.destroy()
     for b in b2:
         b.destroy()
-    e2e = {"value": ws * work * args.steps / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+    e2e = {"value": ws * work * nsteps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": h2d / nsteps, "d2h_bytes_per_step": d2h / nsteps,
            "seconds": e2e_s, "includes": "creation of all bands, K batch steps, all paths read"}
-    if rank != 0:
-        if dist is not None:
-            dist.barrier()
-        return 0
-    cpu = None if args.no_cpu_baseline else cpu_oracle_lj_rate(bcs, args.cpu_seconds)
+    cpu = cpu_oracle_lj_rate(bcs, args.cpu_seconds) if (with_cpu and rank == 0) else None
     sizes = [len(c["endpoints"][0]) for c in bcs]
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": nsteps,
+            "warmup": warmup, "ms_per_step": ms / nsteps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 pair arithmetic, f64 reductions and 3x3 cell work", "data": "synthetic",
-            "config": {"workload": args.workload, "bands": len(bcs), "atoms_min": min(sizes),
+            "config": {"workload": workload, "bands": len(bcs), "atoms_min": min(sizes),
                        "atoms_max": max(sizes), "atom_images_per_step": work,
                        "precision": "mixed", "potential": "LJ rc 2.5",
-                       "cell_filter": "rotation-free (B)", "bin_width": "autotuned per class",
+                       "cell_filter": "rotation-free (B), lattice scale J",
+                       "bin_width": "autotuned per class",
                        "l2": "working set > 129 MB L2, no flush",
                        "graph": "one CUDA graph per batch step",
                        "parallelism": "replicas x%d" % ws},
@@ -721,10 +741,6 @@ def run_batch(args):
                                                for k, v in prof.items() if v[1]},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "fp64_plain": fp64, "create_s": t_create, "lists": lists, "rooflines": roofs}
-    print(json.dumps(line))
-    if dist is not None:
-        dist.barrier()
-    return 0
 
 
 def _serve_options(g, spec, precision):
@@ -872,6 +888,8 @@ def main():
                     choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="leave the batched LJ workload out of the default line")
     ap.add_argument("--skin", type=float, default=None,
                     help="neighbour-list skin of the LJ batch bands (default: the library's)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

@@ -391,6 +391,14 @@ const char *cfneb_kernel_name(int32_t kernel_id);
  * arithmetic rates.  Synchronises. */
 int cfneb_get_work(const cfneb_band *band, double *pairs, double *triples);
 
+/* The band's tuning: *bin_scale = cell-list bin width / list cutoff and
+ * *blocks_per_sm = resident blocks per SM of the force kernel variant it
+ * launches (FP32 LJ with lists: 5-8, FP32 Tersoff: 4-6; 0 where the
+ * potential or precision has one variant).  cfneb_autotune picks both: the
+ * bin width from timed evaluations with forced rebuilds, then the variant
+ * at that width.  Any output pointer may be NULL.  Reads host state only. */
+int cfneb_get_tuning(const cfneb_band *band, double *bin_scale, int32_t *blocks_per_sm);
+
 /* Cell-list reuse counters summed over the interior image slots since the
  * band was created: *builds = cell-list (and neighbour-list) builds,
  * *evaluations = force evaluations; *skin = the skin in use.  The paper

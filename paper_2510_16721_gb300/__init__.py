@@ -44,7 +44,7 @@ MIXED = 1
 EXPORTS = [
     "cfneb_default_options", "cfneb_create_band", "cfneb_step", "cfneb_relax",
     "cfneb_insert_image", "cfneb_delete_image", "cfneb_get_path", "cfneb_get_state",
-    "cfneb_set_state", "cfneb_get_image_scalars",
+    "cfneb_set_state", "cfneb_get_image_scalars", "cfneb_get_tuning",
     "cfneb_destroy_band", "cfneb_evaluate", "cfneb_profile", "cfneb_profile_read",
     "cfneb_kernel_count", "cfneb_kernel_name", "cfneb_launches_per_step",
     "cfneb_status_string", "cfneb_get_work", "cfneb_get_list_stats", "cfneb_lj_evaluate_noalloc",
@@ -116,6 +116,7 @@ def lib():
             "cfneb_get_state": ([vp, dp, dp, dp, dp, dp, P(i32)], ctypes.c_int),
             "cfneb_set_state": ([vp, dp], ctypes.c_int),
             "cfneb_get_image_scalars": ([vp, dp, dp, dp], ctypes.c_int),
+            "cfneb_get_tuning": ([vp, dp, P(i32)], ctypes.c_int),
             "cfneb_destroy_band": ([vp], ctypes.c_int),
             "cfneb_evaluate": ([P(Structure), i32, P(Potential), i32, vp, dp, dp, dp],
                                ctypes.c_int),
@@ -307,6 +308,13 @@ class Band:
             raise ValueError("X must have shape (N, n+3, 3)")
         _check(lib().cfneb_set_state(self._h, _dptr(X)), "cfneb_set_state")
 
+    def tuning(self):
+        """cfneb_get_tuning: (bin width / list cutoff, force kernel blocks per SM)."""
+        sc, mb = ctypes.c_double(0.0), ctypes.c_int32(0)
+        _check(lib().cfneb_get_tuning(self._h, ctypes.byref(sc), ctypes.byref(mb)),
+               "cfneb_get_tuning")
+        return float(sc.value), int(mb.value)
+
     def image_scalars(self):
         """cfneb_get_image_scalars: step energies (N), the ten dots (N x 10)
         and the f_NEB coefficients (N x 2) of the last step."""
@@ -455,25 +463,6 @@ class Batch:
         _check(lib().cfneb_batch_bytes(self._h, ctypes.byref(u), ctypes.byref(b)),
                "cfneb_batch_bytes")
         return int(u.value), int(b.value)
-
-    def set_state(self, X):
-        """cfneb_set_state: every image's generalised coordinates from X
-        (N x (n+3) x 3); FIRE reset, endpoints evaluated again."""
-        X = np.ascontiguousarray(X, dtype=np.float64)
-        if X.shape != (self.n_images, self.n_atoms + 3, 3):
-            raise ValueError("X must have shape (N, n+3, 3)")
-        _check(lib().cfneb_set_state(self._h, _dptr(X)), "cfneb_set_state")
-
-    def image_scalars(self):
-        """cfneb_get_image_scalars: step energies (N), the ten dots (N x 10)
-        and the f_NEB coefficients (N x 2) of the last step."""
-        N = self.n_images
-        E = np.zeros(N)
-        dots = np.zeros((N, 10))
-        coef = np.zeros((N, 2))
-        _check(lib().cfneb_get_image_scalars(self._h, _dptr(E), _dptr(dots), _dptr(coef)),
-               "cfneb_get_image_scalars")
-        return dict(E=E, dots=dots, coef=coef)
 
     def profile(self, enable=True):
         return _check(lib().cfneb_batch_profile(self._h, int(bool(enable))), "cfneb_batch_profile")

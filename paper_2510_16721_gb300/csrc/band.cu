@@ -231,26 +231,57 @@ __device__ inline void image_coef(BandDev &b, int i, int ci, const double *d) {
 // tile into the tile's partial record; with FUSE, the last tile of an image
 // sums the image's records (fixed order) into its dots, and the last image
 // of a band computes the band's NEB coefficients and FIRE sums.
+// Each thread of a row tile owns 4 consecutive rows: 12 values, loaded and
+// stored with 16-byte vector accesses (the row stride of an image is a
+// multiple of 4 rows, so every thread's first value is 16-byte aligned).
+__device__ inline void ld12(const float *p, float (&v)[12]) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float4 a = q[k];
+        v[4 * k] = a.x; v[4 * k + 1] = a.y; v[4 * k + 2] = a.z; v[4 * k + 3] = a.w;
+    }
+}
+__device__ inline void ld12(const double *p, double (&v)[12]) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const double2 a = q[k];
+        v[2 * k] = a.x; v[2 * k + 1] = a.y;
+    }
+}
+__device__ inline void st12(float *p, const float (&v)[12]) {
+    float4 *q = reinterpret_cast<float4 *>(p);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) q[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+}
+__device__ inline void st12(double *p, const double (&v)[12]) {
+    double2 *q = reinterpret_cast<double2 *>(p);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) q[k] = make_double2(v[2 * k], v[2 * k + 1]);
+}
+
 template <typename T, bool FUSE>
 __global__ void __launch_bounds__(RTHREADS, sizeof(T) == 4 ? 4 : 2) k_band_dots(const Tile *tiles, BandDev *bands) {
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
     Acc<T> acc[10];
     const size_t stride = (size_t)b.rows * 3;
-    const size_t o0 = tl.img * stride + ((size_t)tl.t * RTILE + threadIdx.x) * 3;
-    const T *__restrict__ X0 = (const T *)b.X + o0;
-    const T *__restrict__ F0 = (const T *)b.F + o0;
-    const T *__restrict__ V0 = (const T *)b.v + o0;
-    const int nrow = b.rows - tl.t * RTILE - (int)threadIdx.x;
+    const int r0 = tl.t * RTILE + RPT * (int)threadIdx.x;  // first of this thread's rows
+    if (r0 < b.rows) {
+        const size_t o0 = tl.img * stride + (size_t)r0 * 3;
+        T a[12], xp[12], xm[12], f[12], v[12];
+        ld12((const T *)b.X + o0, a);
+        ld12((const T *)b.X + o0 + stride, xp);
+        ld12((const T *)b.X + o0 - stride, xm);
+        ld12((const T *)b.F + o0, f);
+        ld12((const T *)b.v + o0, v);
 #pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-        if (k * RTHREADS < nrow) {
-            const T *x0 = X0 + k * RTHREADS * 3, *f = F0 + k * RTHREADS * 3,
-                    *v = V0 + k * RTHREADS * 3;
+        for (int q = 0; q < RPT; ++q) {
             T r[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-            for (int c = 0; c < 3; ++c) {
-                const T a = x0[c];
-                const T dp = x0[stride + c] - a, dm = a - x0[c - (long long)stride];
+#pragma unroll
+            for (int c = 3 * q; c < 3 * q + 3; ++c) {
+                const T dp = xp[c] - a[c], dm = a[c] - xm[c];
                 const T fc = f[c], vc = v[c];
                 r[0] = fma(dp, dp, r[0]);
                 r[1] = fma(dm, dm, r[1]);
@@ -264,7 +295,7 @@ __global__ void __launch_bounds__(RTHREADS, sizeof(T) == 4 ? 4 : 2) k_band_dots(
                 r[9] = fma(dm, vc, r[9]);
             }
 #pragma unroll
-            for (int q = 0; q < 10; ++q) acc[q].add(r[q]);
+            for (int k = 0; k < 10; ++k) acc[k].add(r[k]);
         }
     }
     double *part = b.row_part + ((size_t)tl.img * b.rtpi + tl.t) * NPART;
@@ -360,24 +391,22 @@ __global__ void __launch_bounds__(RTHREADS, 4) k_neb_force(const Tile *tiles, Ba
     __syncthreads();
     const T ca = s_coef[0], cb = s_coef[1];
     const size_t stride = (size_t)b.rows * 3;
-    const size_t o0 = tl.img * stride + ((size_t)tl.t * RTILE + threadIdx.x) * 3;
-    const T *__restrict__ X0 = (const T *)b.X + o0;
-    const T *__restrict__ F0 = (const T *)b.F + o0;
-    T *__restrict__ G0 = (T *)b.Fneb + o0;
-    const int nrow = b.rows - tl.t * RTILE - (int)threadIdx.x;
+    const int r0 = tl.t * RTILE + RPT * (int)threadIdx.x;
     T mx = 0;
+    if (r0 < b.rows) {
+        const size_t o0 = tl.img * stride + (size_t)r0 * 3;
+        T a[12], xp[12], xm[12], gv[12];
+        ld12((const T *)b.X + o0, a);
+        ld12((const T *)b.X + o0 + stride, xp);
+        ld12((const T *)b.X + o0 - stride, xm);
+        ld12((const T *)b.F + o0, gv);
 #pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-        if (k * RTHREADS < nrow) {
-            const size_t q = (size_t)k * RTHREADS * 3;
-            T ff = 0;
-            for (int c = 0; c < 3; ++c) {
-                const T a = X0[q + c];
-                const T g = F0[q + c] + ca * (X0[q + stride + c] - a) +
-                            cb * (a - X0[q + c - stride]);
-                G0[q + c] = g;
-                ff = fma(g, g, ff);
-            }
+        for (int c = 0; c < 12; ++c) gv[c] = gv[c] + ca * (xp[c] - a[c]) + cb * (a[c] - xm[c]);
+        st12((T *)b.Fneb + o0, gv);
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const T ff = fma(gv[3 * q + 2], gv[3 * q + 2],
+                             fma(gv[3 * q + 1], gv[3 * q + 1], gv[3 * q] * gv[3 * q]));
             mx = fmax(mx, ff);
         }
     }
@@ -423,39 +452,35 @@ __global__ void __launch_bounds__(RTHREADS, sizeof(T) == 4 ? 4 : 2) k_fire_updat
     }
     __syncthreads();
     const T cv = s_k[0], cf = s_k[1], dt = s_k[2], ms = s_k[3];
-    const size_t o0 = (tl.img * (size_t)b.rows + (size_t)tl.t * RTILE + threadIdx.x) * 3;
-    T *__restrict__ X = (T *)b.X + o0;
-    T *__restrict__ V = (T *)b.v + o0;
-    const T *__restrict__ Fn = (const T *)b.Fneb + o0;
-    const int nrow = b.rows - tl.t * RTILE - (int)threadIdx.x;  // rows k * RTHREADS < nrow exist
-    // all loads first (rows of one thread are RTHREADS apart: independent)
-    T xr[RPT][3], vr[RPT][3], fr[RPT][3];
+    const int r0 = tl.t * RTILE + RPT * (int)threadIdx.x;
+    if (r0 >= b.rows) return;
+    const size_t o0 = (tl.img * (size_t)b.rows + (size_t)r0) * 3;
+    T x[12], v[12], fn[12];
+    ld12((const T *)b.X + o0, x);
+    ld12((const T *)b.v + o0, v);
+    ld12((const T *)b.Fneb + o0, fn);
 #pragma unroll
-    for (int k = 0; k < RPT; ++k)
-        if (k * RTHREADS < nrow)
-            for (int c = 0; c < 3; ++c) {
-                xr[k][c] = X[k * RTHREADS * 3 + c];
-                vr[k][c] = V[k * RTHREADS * 3 + c];
-                fr[k][c] = Fn[k * RTHREADS * 3 + c];
-            }
-#pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-        if (k * RTHREADS >= nrow) break;
+    for (int q = 0; q < RPT; ++q) {
         T dx[3];
         T n2 = 0;
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
-            T vc = cv * vr[k][c] + cf * fr[k][c];
-            vc += dt * fr[k][c];
-            V[k * RTHREADS * 3 + c] = vc;
+            T vc = cv * v[3 * q + c] + cf * fn[3 * q + c];
+            vc += dt * fn[3 * q + c];
+            v[3 * q + c] = vc;
             dx[c] = dt * vc;
             n2 += dx[c] * dx[c];
         }
         if (n2 > ms * ms) {
-            const T s = ms / sqrt(n2);
-            for (int c = 0; c < 3; ++c) dx[c] *= s;
+            const T sc = ms / sqrt(n2);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dx[c] *= sc;
         }
-        for (int c = 0; c < 3; ++c) X[k * RTHREADS * 3 + c] = xr[k][c] + dx[c];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) x[3 * q + c] += dx[c];
     }
+    st12((T *)b.v + o0, v);
+    st12((T *)b.X + o0, x);
 }
 
 // X_img <- 1/2 (X_{img-1} + X_{img+1}) (image insertion; all rows)

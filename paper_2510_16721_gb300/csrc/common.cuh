@@ -26,7 +26,7 @@ namespace cfneb {
 
 constexpr int TILE = 128;           // atoms per atom tile = threads per block
 constexpr int RTHREADS = 256;       // threads per block of the row-tile kernels
-constexpr int RPT = 4;              // rows per thread of the row-tile kernels
+constexpr int RPT = 4;              // consecutive rows per thread of the row-tile kernels
 constexpr int RTILE = RTHREADS * RPT;  // rows per row tile (band vector kernels)
 constexpr int MAXN_TERSOFF = 16;    // Tersoff list capacity per atom (entries within rl)
 constexpr int NPART = 12;           // doubles per tile partial record
@@ -540,14 +540,17 @@ template <typename T>
 void launch_lj(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 template <typename T>
 void launch_lj_list(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
+// minb: resident blocks per SM of the force kernel variant (FP32: 5-8 for
+// LJ, 4-6 for Tersoff; the autotuner picks it)
 template <typename T>
-void launch_lj_nbr(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
+void launch_lj_nbr(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s, int minb);
 template <typename T>
 void launch_tersoff_list(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 template <typename T>
 void launch_tersoff_reverse(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 template <typename T>
-void launch_tersoff_partials(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
+void launch_tersoff_partials(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s,
+                             int minb);
 template <typename T>
 void launch_nep_partials(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 template <typename T>

@@ -65,12 +65,25 @@ const double kTersoff1988C[11] = {1393.6, 346.74, 3.4879, 2.2119, 1.5724e-7, 0.7
 
 // bin width candidates (x cutoff) of the autotuner; the first is the finest
 const double kTuneScales[4] = {0.5, 0.75, 1.0, 1.3};
+// resident blocks per SM of the FP32 force kernels (the register cap of the
+// kernel variant launched): defaults and the autotuner's candidates
+constexpr int kLjMinb = 7, kTersMinb = 5;
+const int kLjMinbs[4] = {5, 6, 7, 8};
+const int kTersMinbs[3] = {4, 5, 6};
 
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, double> g_tune;  // class -> bin width / rc
+std::map<std::tuple<int, int, int, int>, int> g_tune_minb;  // class -> blocks per SM
 
 // untuned default per potential (measured on GB300: LJ at FCC density is
 // fastest with half-cutoff bins, carbon Tersoff with cutoff-wide bins)
+int tuned_minb(const std::tuple<int, int, int, int> &key) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_minb.find(key);
+    if (it != g_tune_minb.end()) return it->second;
+    return 0;  // the kernel's default
+}
+
 double tuned_scale(const std::tuple<int, int, int, int> &key) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
@@ -102,6 +115,7 @@ struct cfneb_band {
     double rc = 0.0;             // potential cutoff
     double rl = 0.0;             // list cutoff rc + skin
     std::tuple<int, int, int, int> tune_key{};
+    int minb = 0;                // force kernel blocks per SM (0: the default)
     double ftol = -1.0;
     bool ends_e64 = false;       // the endpoints' FP64 energies are known
     // stream ordering
@@ -251,6 +265,7 @@ struct LaunchSet {
     int nbands = 0;
     int max_bins = 0;                    // largest nbins_cap among the bands
     int force_rebuild = 0;               // rebuild every listed image's cell list
+    int lj_minb = kLjMinb, ters_minb = kTersMinb;  // force kernel variants
 };
 
 // optional CUDA-event bracketing of every launch (profiling)
@@ -309,13 +324,14 @@ void enqueue_eval_set(const LaunchSet &ls, Launcher &L, bool forces = true) {
         return;
     }
     if (ls.n_lj) {
-        L.pre(K_LJ); launch_lj_nbr<T>(ls.atiles_lj, ls.n_lj, d, s); L.post(K_LJ);
+        L.pre(K_LJ); launch_lj_nbr<T>(ls.atiles_lj, ls.n_lj, d, s, ls.lj_minb); L.post(K_LJ);
     }
     if (ls.n_ljc) {
         L.pre(K_LJ_CELLS); launch_lj<T>(ls.atiles_ljc, ls.n_ljc, d, s); L.post(K_LJ_CELLS);
     }
     if (ls.n_ters) {
-        L.pre(K_TERS_PARTIALS); launch_tersoff_partials<T>(ls.atiles_ters, ls.n_ters, d, s);
+        L.pre(K_TERS_PARTIALS);
+        launch_tersoff_partials<T>(ls.atiles_ters, ls.n_ters, d, s, ls.ters_minb);
         L.post(K_TERS_PARTIALS);
         L.pre(K_TERS_GATHER); launch_tersoff_gather<T>(ls.atiles_ters, ls.n_ters, d, s);
         L.post(K_TERS_GATHER);
@@ -371,6 +387,10 @@ LaunchSet band_set(cfneb_band *b, const ImgRef *imgs, int nimg, const Tile *atil
     ls.band_ids = b->d_band_ids;
     ls.nbands = 1;
     ls.max_bins = b->dv.nbins_cap;
+    if (b->minb > 0) {
+        if (b->kind == CFNEB_LJ) ls.lj_minb = b->minb;
+        if (b->kind == CFNEB_TERSOFF) ls.ters_minb = b->minb;
+    }
     return ls;
 }
 
@@ -785,12 +805,17 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
                                   (int)std::floor(std::log2((double)std::max(1, b->n))),
                                   (int)std::floor(2.0 * std::log2(std::max(dens, 1e-3))));
     double bscale = opt->bin_scale > 0 ? opt->bin_scale : tuned_scale(b->tune_key);
+    b->minb = tuned_minb(b->tune_key);
     double bin_w = rl * bscale;
     b->rc = rc;
     // reserve bins for the finest autotuning candidate when tuning may follow
     const double cap_w = opt->bin_scale > 0 ? bin_w : rl * kTuneScales[0];
     // geometry
-    const int n = b->n, rows = n + 3;
+    // row stride of an image: the n atom rows and 3 lattice rows, padded to a
+    // multiple of 4 rows (12 values) so that every image starts on a 16-byte
+    // boundary and the band kernels load whole rows with vector loads; the
+    // padding rows stay zero in X, F, f_NEB and v
+    const int n = b->n, rows = (n + 3 + 3) / 4 * 4;
     BandDev &d = b->dv;
     d.n = n;
     d.rows = rows;
@@ -808,6 +833,7 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
     d.F = dalloc(b, vec);
     d.Fneb = dalloc(b, vec);
     d.v = dalloc(b, vec);
+    for (void *p : {d.X, d.F, d.Fneb, d.v}) CK(cudaMemsetAsync(p, 0, vec, b->s));
     d.sc = (ImgScalars *)dalloc(b, nc * sizeof(ImgScalars));
     d.bp = (BandParams *)dalloc(b, sizeof(BandParams));
     d.bin_count = (int *)dalloc(b, nc * d.nbins_cap * sizeof(int));
@@ -1000,10 +1026,31 @@ double autotune_band(cfneb_band *b, int steps) {
         }
     }
     set_tune_rebuild(b, 0);
+    // then the force kernel's blocks per SM at that bin width (FP32 LJ with
+    // neighbour lists and Tersoff; steps with list reuse, as the run has)
+    int best_minb = 0;
+    const bool lj_list = b->kind == CFNEB_LJ && b->dv.lj_cap > 0;
+    if (b->precision == CFNEB_MIXED && (lj_list || b->kind == CFNEB_TERSOFF)) {
+        const int *cand = lj_list ? kLjMinbs : kTersMinbs;
+        const int nc = lj_list ? 4 : 3;
+        double bm = 1e300;
+        for (int q = 0; q < nc; ++q) {
+            b->minb = cand[q];
+            b->graph_dirty = true;
+            const double ms = time_bin_w(b, best * b->rl, steps);
+            if (ms < bm) {
+                bm = ms;
+                best_minb = cand[q];
+            }
+        }
+        b->minb = best_minb;
+        b->graph_dirty = true;
+    }
     set_bin_w(b, best * b->rl);
     set_control(b, keep_ftol, keep_limit);
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[b->tune_key] = best;
+    if (best_minb) g_tune_minb[b->tune_key] = best_minb;
     return best;
 }
 
@@ -1015,6 +1062,7 @@ double autotune_band(cfneb_band *b, int steps) {
 
 struct cfneb_batch {
     int precision = 0;
+    int lj_minb = 0, ters_minb = 0;  // force kernel variants (0: the default)
     unsigned long long budget = 0, used = 0;
     cudaStream_t user = nullptr, s = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -1131,6 +1179,8 @@ void batch_rebuild(cfneb_batch *bt) {
     ls.band_ids = bt->d_ids;
     ls.nbands = (int)ids.size();
     ls.max_bins = max_bins;
+    if (bt->lj_minb) ls.lj_minb = bt->lj_minb;
+    if (bt->ters_minb) ls.ters_minb = bt->ters_minb;
     if (bt->gexec) {
         CK(cudaGraphExecDestroy(bt->gexec));
         bt->gexec = nullptr;
@@ -1604,26 +1654,25 @@ int cfneb_get_state(const cfneb_band *cb, double *X, double *F, double *Fneb, do
     if (!b) return CFNEB_ERR_INVALID_ARG;
     try {
         enter(b);
-        const size_t cnt = (size_t)b->N * b->dv.rows * 3;
+        // per image n + 3 rows out of the padded row stride
+        const size_t per = (size_t)(b->n + 3) * 3, stride = (size_t)b->dv.rows * 3;
+        const size_t cnt = (size_t)b->N * stride;
         std::vector<char> tmp(cnt * b->ts);
         auto fetch = [&](void *src, double *dst) {
             if (!dst) return;
             CK(cudaMemcpyAsync(tmp.data(), src, cnt * b->ts, cudaMemcpyDeviceToHost, b->s));
             CK(cudaStreamSynchronize(b->s));
-            if (b->ts == 4) {
-                const float *f = (const float *)tmp.data();
-                for (size_t i = 0; i < cnt; ++i) dst[i] = f[i];
-            } else {
-                std::memcpy(dst, tmp.data(), cnt * sizeof(double));
-            }
+            for (int im = 0; im < b->N; ++im)
+                for (size_t i = 0; i < per; ++i)
+                    dst[im * per + i] = b->ts == 4 ? ((const float *)tmp.data())[im * stride + i]
+                                                   : ((const double *)tmp.data())[im * stride + i];
         };
         fetch(b->dv.X, X);
         fetch(b->dv.F, F);
         fetch(b->dv.Fneb, Fneb);
         if (Fneb) {  // endpoints carry no NEB force
-            std::memset(Fneb, 0, (size_t)b->dv.rows * 3 * sizeof(double));
-            std::memset(Fneb + (size_t)(b->N - 1) * b->dv.rows * 3, 0,
-                        (size_t)b->dv.rows * 3 * sizeof(double));
+            std::memset(Fneb, 0, per * sizeof(double));
+            std::memset(Fneb + (size_t)(b->N - 1) * per, 0, per * sizeof(double));
         }
         std::vector<ImgScalars> sc(b->N);
         CK(cudaMemcpyAsync(sc.data(), b->dv.sc, b->N * sizeof(ImgScalars),
@@ -1647,22 +1696,25 @@ int cfneb_get_state(const cfneb_band *cb, double *X, double *F, double *Fneb, do
 
 int cfneb_set_state(cfneb_band *b, const double *X) {
     if (!b || !X) return CFNEB_ERR_INVALID_ARG;
-    const size_t per = (size_t)b->dv.rows * 3;
+    const size_t per = (size_t)(b->n + 3) * 3, stride = (size_t)b->dv.rows * 3;
     for (size_t i = 0; i < (size_t)b->N * per; ++i)
         if (!std::isfinite(X[i])) return CFNEB_ERR_INVALID_ARG;
     try {
         enter(b);
-        const size_t cnt = (size_t)b->N * per;
-        const double *src = X;
-        char *dst = (char *)b->dv.X;
+        // n + 3 rows per image into the padded row stride (padding stays 0)
+        const size_t cnt = (size_t)b->N * stride;
+        std::vector<double> pad(cnt, 0.0);
+        for (int im = 0; im < b->N; ++im)
+            std::memcpy(pad.data() + im * stride, X + im * per, per * sizeof(double));
         if (b->ts == 4) {
             std::vector<float> tmp(cnt);
-            for (size_t i = 0; i < cnt; ++i) tmp[i] = (float)src[i];
-            CK(cudaMemcpyAsync(dst, tmp.data(), cnt * sizeof(float), cudaMemcpyHostToDevice,
+            for (size_t i = 0; i < cnt; ++i) tmp[i] = (float)pad[i];
+            CK(cudaMemcpyAsync(b->dv.X, tmp.data(), cnt * sizeof(float), cudaMemcpyHostToDevice,
                                b->s));
             CK(cudaStreamSynchronize(b->s));
         } else {
-            CK(cudaMemcpyAsync(dst, src, cnt * sizeof(double), cudaMemcpyHostToDevice, b->s));
+            CK(cudaMemcpyAsync(b->dv.X, pad.data(), cnt * sizeof(double), cudaMemcpyHostToDevice,
+                               b->s));
             CK(cudaStreamSynchronize(b->s));
         }
         fire_reset(b);
@@ -1930,17 +1982,52 @@ int cfneb_autotune(cfneb_band *b, int32_t steps, double *best_scale) {
     }
 }
 
+int cfneb_get_tuning(const cfneb_band *b, double *bin_scale, int32_t *blocks_per_sm) {
+    if (!b) return CFNEB_ERR_INVALID_ARG;
+    if (bin_scale) *bin_scale = b->rl > 0.0 ? b->h_bp->bin_w / b->rl : 0.0;
+    if (blocks_per_sm) {
+        int m = b->minb;
+        if (!m && b->precision == CFNEB_MIXED)
+            m = b->kind == CFNEB_LJ && b->dv.lj_cap > 0 ? kLjMinb
+                : b->kind == CFNEB_TERSOFF ? kTersMinb : 0;
+        *blocks_per_sm = m;
+    }
+    return CFNEB_OK;
+}
+
 int cfneb_batch_autotune(cfneb_batch *bt, int32_t steps) {
     if (!bt || steps <= 0) return CFNEB_ERR_INVALID_ARG;
     try {
         bt_enter(bt);
         std::map<std::tuple<int, int, int, int>, double> done;
+        std::map<std::tuple<int, int, int, int>, int> done_minb;
+        // per class: bin width, then the force kernel's blocks per SM; the
+        // batch launches the variant tuned for its largest member of each
+        // potential (one launch covers every member)
+        long long big_lj = -1, big_ters = -1;
         for (cfneb_band *b : bt->bands) {
             auto it = done.find(b->tune_key);
-            const double sc = it != done.end() ? it->second : autotune_band(b, steps);
-            done[b->tune_key] = sc;
+            double sc;
+            if (it != done.end()) {
+                sc = it->second;
+                b->minb = done_minb[b->tune_key];
+            } else {
+                sc = autotune_band(b, steps);
+                done[b->tune_key] = sc;
+                done_minb[b->tune_key] = b->minb;
+            }
             set_bin_w(b, sc * b->rl);
+            const long long work = (long long)b->n * (b->N - 2);
+            if (b->kind == CFNEB_LJ && b->minb && work > big_lj) {
+                big_lj = work;
+                bt->lj_minb = b->minb;
+            }
+            if (b->kind == CFNEB_TERSOFF && b->minb && work > big_ters) {
+                big_ters = work;
+                bt->ters_minb = b->minb;
+            }
         }
+        bt->dirty = true;
         bt_leave(bt);
         return CFNEB_OK;
     } catch (CudaFail &) {

@@ -299,8 +299,11 @@ __global__ void __launch_bounds__(TILE) k_lj_list(const Tile *tiles, int ntiles,
 // entries loaded before the group's arithmetic, so a list load's latency
 // overlaps a whole group of pair terms (7 blocks per SM leave the registers
 // for it: measured faster than 8 without the overlap).
-template <typename T>
-__global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 7 : 4) k_lj_nbr(const Tile *tiles, BandDev *bands) {
+// MINB: resident blocks per SM the register allocation is held to (the
+// autotuner picks it with the bin width: more blocks hide more gather
+// latency, fewer leave more registers for the look-ahead)
+template <typename T, int MINB>
+__global__ void __launch_bounds__(TILE, MINB) k_lj_nbr(const Tile *tiles, BandDev *bands) {
     using T4 = typename Vec4<T>::type;
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
@@ -390,15 +393,24 @@ void launch_lj_list(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t 
     k_lj_list<T><<<ntiles, TILE, 0, s>>>(tiles, ntiles, bands);
 }
 template <typename T>
-void launch_lj_nbr(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
+void launch_lj_nbr(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s, int minb) {
     if (ntiles <= 0) return;
-    k_lj_nbr<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
+    if (sizeof(T) == 8) {
+        k_lj_nbr<T, 4><<<ntiles, TILE, 0, s>>>(tiles, bands);
+        return;
+    }
+    switch (minb) {
+        case 5: k_lj_nbr<T, 5><<<ntiles, TILE, 0, s>>>(tiles, bands); break;
+        case 6: k_lj_nbr<T, 6><<<ntiles, TILE, 0, s>>>(tiles, bands); break;
+        case 8: k_lj_nbr<T, 8><<<ntiles, TILE, 0, s>>>(tiles, bands); break;
+        default: k_lj_nbr<T, 7><<<ntiles, TILE, 0, s>>>(tiles, bands); break;
+    }
 }
 template void launch_lj<float>(const Tile *, int, BandDev *, cudaStream_t);
 template void launch_lj<double>(const Tile *, int, BandDev *, cudaStream_t);
 template void launch_lj_list<float>(const Tile *, int, BandDev *, cudaStream_t);
 template void launch_lj_list<double>(const Tile *, int, BandDev *, cudaStream_t);
-template void launch_lj_nbr<float>(const Tile *, int, BandDev *, cudaStream_t);
-template void launch_lj_nbr<double>(const Tile *, int, BandDev *, cudaStream_t);
+template void launch_lj_nbr<float>(const Tile *, int, BandDev *, cudaStream_t, int);
+template void launch_lj_nbr<double>(const Tile *, int, BandDev *, cudaStream_t, int);
 
 }  // namespace cfneb

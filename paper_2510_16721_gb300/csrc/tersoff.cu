@@ -617,8 +617,10 @@ __device__ inline void ters_site_reg(const TP<T> &q, const T (&rx)[RMAX], const 
 // array.  FP64: the records sit in shared memory, strided by the block size
 // so that the threads of a warp hit distinct banks (local memory beyond
 // NShared entries).
-template <typename T>
-__global__ void __launch_bounds__(TILE, sizeof(T) == 4 ? 5 : 1) k_ters_partials(const Tile *tiles, BandDev *bands) {
+// MINB: resident blocks per SM the register allocation is held to (FP32;
+// picked by the autotuner with the bin width)
+template <typename T, int MINB>
+__global__ void __launch_bounds__(TILE, MINB) k_ters_partials(const Tile *tiles, BandDev *bands) {
     constexpr bool REG = sizeof(T) == 4;
     constexpr int NS = REG ? 1 : NShared<T>::value;
     Tile tl = tiles[blockIdx.x];
@@ -1082,9 +1084,18 @@ void launch_tersoff_reverse(const Tile *tiles, int ntiles, BandDev *bands, cudaS
                                                                                  bands);
 }
 template <typename T>
-void launch_tersoff_partials(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
+void launch_tersoff_partials(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s,
+                             int minb) {
     if (ntiles <= 0) return;
-    k_ters_partials<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
+    if (sizeof(T) == 8) {
+        k_ters_partials<T, 1><<<ntiles, TILE, 0, s>>>(tiles, bands);
+        return;
+    }
+    switch (minb) {
+        case 4: k_ters_partials<T, 4><<<ntiles, TILE, 0, s>>>(tiles, bands); break;
+        case 6: k_ters_partials<T, 6><<<ntiles, TILE, 0, s>>>(tiles, bands); break;
+        default: k_ters_partials<T, 5><<<ntiles, TILE, 0, s>>>(tiles, bands); break;
+    }
 }
 template <typename T>
 void launch_tersoff_gather(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
@@ -1095,8 +1106,8 @@ template void launch_tersoff_list<float>(const Tile *, int, BandDev *, cudaStrea
 template void launch_tersoff_list<double>(const Tile *, int, BandDev *, cudaStream_t);
 template void launch_tersoff_reverse<float>(const Tile *, int, BandDev *, cudaStream_t);
 template void launch_tersoff_reverse<double>(const Tile *, int, BandDev *, cudaStream_t);
-template void launch_tersoff_partials<float>(const Tile *, int, BandDev *, cudaStream_t);
-template void launch_tersoff_partials<double>(const Tile *, int, BandDev *, cudaStream_t);
+template void launch_tersoff_partials<float>(const Tile *, int, BandDev *, cudaStream_t, int);
+template void launch_tersoff_partials<double>(const Tile *, int, BandDev *, cudaStream_t, int);
 template <typename T>
 void launch_nep_partials(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
     if (ntiles <= 0) return;

@@ -197,3 +197,40 @@ def test_autotune_leaves_state_and_forces(g, oracle_mod):
     for i in (1, 2, 3):
         _, Fo, _ = img(after["X"][i])
         assert np.max(np.abs(st["F"][i] - Fo)) <= 1e-10 * max(1.0, np.max(np.abs(Fo)))
+
+
+def test_autotune_picks_kernel_variant_mixed(g, oracle_mod):
+    """Mixed LJ band with neighbour lists: the autotuner picks the bin width
+    and then the force kernel's blocks per SM among its variants; X and the
+    move count are left alone, and the forces of the chosen variant match
+    the oracle within the mixed tolerance."""
+    b = _make(g, "lj255", 1, bin_scale=0.0)
+    b.step(3)
+    before = b.get_state()
+    best = b.autotune(3)
+    scale, minb = b.tuning()
+    assert best in (0.5, 0.75, 1.0, 1.3) and scale == pytest.approx(best)
+    assert minb in (5, 6, 7, 8)
+    after = b.get_state()
+    np.testing.assert_array_equal(after["X"], before["X"])
+    assert after["steps"] == before["steps"]
+    b.step(1)
+    st = b.get_state()
+    R0, h0, _, _ = ci.lj_vacancy_hop(ci.LJ_A, (4, 4, 4), divacancy=True)
+    img = oracle_mod.AtomicImage(oracle_mod.LJ(), h0, len(R0), True)
+    for i in (1, 2, 3):
+        _, Fo, _ = img(after["X"][i])
+        assert np.max(np.abs(st["F"][i] - Fo)) <= 1e-4
+
+
+def test_batch_autotune_sets_variants(g):
+    bands = [_make(g, w, 1, bin_scale=0.0) for w in ("lj255", "ters576")]
+    bt = g.Batch(1)
+    for b in bands:
+        bt.add(b)
+    bt.autotune(2)
+    assert bands[0].tuning()[1] in (5, 6, 7, 8)
+    assert bands[1].tuning()[1] in (4, 5, 6)
+    bt.step(3)
+    assert all(s["status"] == 0 for s in bt.status())
+    bt.destroy()
