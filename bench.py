@@ -38,6 +38,8 @@ WORKLOADS = {
                                               precision="mixed", n_max=24),
     "tersoff_graphite_hexdiamond_576": dict(kind="tersoff", reps=(6, 4, 3), n_images=9,
                                             precision="fp64", n_max=9),
+    # the 31-atom LJ FCC vacancy hop, fixed cell, FP64 (launch-latency bound)
+    "lj_vacancy_31": dict(kind="lj_small", n_images=7, precision="fp64", n_max=7),
     # the same band under the NEP-style descriptor + network potential
     # (synthetic weights, cutoff 2.1 A)
     "nep_graphite_hexdiamond_98304": dict(kind="tersoff", potential="nep", reps=(32, 24, 16),
@@ -219,6 +221,10 @@ def job_rate(ws, units_per_rank, steps, ms):
 
 def band_inputs(wl, seed=2510):
     import cfneb_inputs as ci
+    if wl["kind"] == "lj_small":
+        cfg = ci.lj_vacancy_31()
+        cfg["noise"] = None
+        return cfg
     cfg = ci.tersoff_graphite_hexdiamond(reps=wl["reps"], n_images=wl["n_images"], seed=seed,
                                          precision=wl["precision"])
     return cfg
@@ -235,9 +241,9 @@ def make_band(g, wl, cfg, stream, precision=None):
     opt.dt_max = 10 * cfg["dt"]
     opt.maxstep = 0.2
     opt.n_max = wl["n_max"]
-    cf = g.CellFilter(1, g.ROTFREE_B, 0.0, 0.0)
+    cf = g.CellFilter(int(cfg.get("cell_filter", True)), g.ROTFREE_B, 0.0, 0.0)
     pot = (g.nep_potential(ci_nep_weights(), NEP_RC) if wl.get("potential") == "nep"
-           else g.tersoff_potential())
+           else g.lj_potential() if wl["kind"] == "lj_small" else g.tersoff_potential())
     return g.create_band((R0, h0), (R1, h1), wl["n_images"], pot, cf, opt,
                          stream=stream, noise=cfg["noise"])
 
@@ -307,13 +313,17 @@ def cpu_oracle_rate(wl, seconds=12.0, steps=None, warmup=0, threads=1):
     on `threads` host cores (images in parallel)."""
     import oracle
     import cfneb_inputs as ci
-    cfg = ci.tersoff_graphite_hexdiamond(reps=CPU_SAMPLE_REPS, n_images=wl["n_images"],
-                                         seed=2510)
+    if wl["kind"] == "lj_small":
+        cfg = band_inputs(wl)
+        pot = oracle.LJ()
+    else:
+        cfg = ci.tersoff_graphite_hexdiamond(reps=CPU_SAMPLE_REPS, n_images=wl["n_images"],
+                                             seed=2510)
+        pot = (oracle.NEP(ci.nep_weights(NEP_SEED), rc=NEP_RC) if wl.get("potential") == "nep"
+               else oracle.Tersoff())
     R0, h0, R1, h1 = cfg["endpoints"]
-    pot = (oracle.NEP(ci.nep_weights(NEP_SEED), rc=NEP_RC) if wl.get("potential") == "nep"
-           else oracle.Tersoff())
     band = oracle.make_band(pot, R0, h0, R1, h1, wl["n_images"], k=cfg["k"],
-                            climb=True, cell_filter=True,
+                            climb=True, cell_filter=cfg.get("cell_filter", True),
                             fire=oracle.Fire(dt=cfg["dt"], dt_max=10 * cfg["dt"]),
                             noise=cfg["noise"])
     import concurrent.futures
@@ -343,10 +353,11 @@ def cpu_oracle_rate(wl, seconds=12.0, steps=None, warmup=0, threads=1):
     moving = wl["n_images"] - 2
     _, model = host_cpu()
     return {"value": n * moving * n_done / el, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": "%d-atom tile of the same graphite->hex-diamond %s band, %d images "
-                      "(%d moving), %d FP64 steps in %.1f s on %d thread%s of %s (images in "
-                      "parallel); brute-force O(n^2) periodic neighbour search"
-                      % (n, "NEP-style" if wl.get("potential") == "nep" else "Tersoff",
+            "sample": "%s, %d images (%d moving), %d FP64 steps in %.1f s on %d thread%s of "
+                      "%s (images in parallel); brute-force O(n^2) periodic neighbour search"
+                      % ("the same %d-atom LJ band" % n if wl["kind"] == "lj_small" else
+                         "%d-atom tile of the same graphite->hex-diamond %s band"
+                         % (n, "NEP-style" if wl.get("potential") == "nep" else "Tersoff"),
                          wl["n_images"], moving, n_done, el, threads, "" if threads == 1 else "s",
                          model),
             "steps": n_done, "seconds": el}
@@ -534,14 +545,17 @@ def run_ours(args, wl_name):
                        "moving_images": moving, "precision": wl["precision"],
                        "potential": ("NEP-style descriptors + network, synthetic weights "
                                      "(seed %d), rc %.1f A" % (NEP_SEED, NEP_RC)
-                                     if wl.get("potential") == "nep" else "Tersoff 1988 C"),
-                       "cell_filter": "rotation-free (B)",
+                                     if wl.get("potential") == "nep" else
+                                     "LJ rc 2.5 sigma, energy-shifted" if wl["kind"] == "lj_small"
+                                     else "Tersoff 1988 C"),
+                       "cell_filter": "off (fixed cell)" if wl["kind"] == "lj_small"
+                       else "rotation-free (B)",
                        "l2": "working set > 129 MB L2, no flush", "graph": "CUDA graph per step",
                        "parallelism": "replicas x%d" % ws},
             "roofline": roof, "kernel_share": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "fp64_plain": fp64, "lists": lists,
             "rooflines": roofs}
-    if not args.no_batch:
+    if not args.no_batch and wl_name == "tersoff_graphite_hexdiamond_98304":
         # the batched workload (64 uneven LJ bands, one launch per kernel per
         # step), measured after the main line's numbers are taken
         bl = batch_line(args, "lj_batch64", 20, 3, None, with_fp64=not args.no_fp64,

@@ -241,6 +241,39 @@ int cfneb_get_state(const cfneb_band *band, double *X, double *F, double *Fneb,
  * lattice rows), CUDA.  Synchronises. */
 int cfneb_set_state(cfneb_band *band, const double *X);
 
+/* ---- image-range shards ----------------------------------------------------
+ * A band of many images can be spread over several devices (or processes)
+ * as contiguous image ranges (the paper's scale, Sec. I and Sec. III: ~100
+ * images of 1e5 atoms).  Each range is a band of its own whose two end
+ * images are ghosts: copies of the neighbouring ranges' boundary images (or
+ * the true endpoints).  One step of the whole band, driven by the caller:
+ *   1. cfneb_shard_evaluate on every range (energies and forces of its
+ *      interior images; energies[N] returned, end images as last set);
+ *   2. exchange: each range's first and last interior image (with
+ *      cfneb_shard_get_image) go to the neighbours' ghosts
+ *      (cfneb_shard_set_ghost);
+ *   3. the climbing image is the argmax of every range's interior energies
+ *      (lowest global index on ties); each range is told its local index,
+ *      or -1;
+ *   4. cfneb_shard_project: f_NEB of the interior images (Sec. II.A) and the
+ *      range's FIRE sums: sums[4] = F_NEB.v, |F_NEB|^2, |v|^2 and the
+ *      largest squared row norm of f_NEB;
+ *   5. the caller sums the first three over the ranges and takes the
+ *      maximum of the fourth (fmax = its square root; converged if below
+ *      the tolerance), then cfneb_shard_move on every range with the same
+ *      global sums: the FIRE decision (identical on every range) and move.
+ * cfneb_shard_enable turns a band into a range (FIRE reset; not for bands in
+ * a batch or with adaptive refinement); set its images first with
+ * cfneb_set_state.  Host pointers; every call synchronises.  Errors:
+ * INVALID_ARG (not a shard, bad index or side, non-finite X), CUDA, and the
+ * band's status bits. */
+int cfneb_shard_enable(cfneb_band *band);
+int cfneb_shard_evaluate(cfneb_band *band, double *energies);
+int cfneb_shard_get_image(const cfneb_band *band, int32_t index, double *X, double *energy);
+int cfneb_shard_set_ghost(cfneb_band *band, int32_t side, const double *X, double energy);
+int cfneb_shard_project(cfneb_band *band, int32_t climbing_index, double *sums);
+int cfneb_shard_move(cfneb_band *band, const double *sums);
+
 /* Per-image scalars of the last step (Sec. II.A): energies[N] the
  * energies (U + P Omega) the step's tangent and climbing image used (in the
  * mixed path from FP32 site energies summed in FP64; cfneb_get_path reports

@@ -223,11 +223,14 @@ def climbing_index(E):
     return 1 + int(np.argmax(inner))
 
 
-def neb_forces(X, E, F, k, climb):
-    """f_NEB for the interior images.  X, F: (N, d); E: (N,)."""
+def neb_forces(X, E, F, k, climb, ci=None):
+    """f_NEB for the interior images.  X, F: (N, d); E: (N,).  ``ci``, when
+    given, names the climbing image instead of the argmax of E (a range of
+    a band whose climbing image lies elsewhere passes -1)."""
     N = X.shape[0]
     out = np.zeros_like(X)
-    ci = climbing_index(E) if climb else -1
+    if ci is None:
+        ci = climbing_index(E) if climb else -1
     for i in range(1, N - 1):
         tau = upwind_tangent(X[i - 1], X[i], X[i + 1], E[i - 1], E[i], E[i + 1])
         that = tau / np.linalg.norm(tau)
@@ -259,20 +262,21 @@ class Fire:
         self.dt, self.alpha, self.n_pos = self.dt0, self.alpha0, 0
         self.fresh = True
 
-    def step(self, F):
+    def step(self, F, sums=None):
         """One FIRE move for the stacked vector F (moving images only).
 
         Returns the displacement dX.  Velocity mixing uses band-global
-        quantities P = F.v, |F|, |v|.
+        quantities P = F.v, |F|^2, |v|^2; ``sums`` = (P, |F|^2, |v|^2), when
+        given, are those of the whole band (F and v here being a part of it).
         """
         if self.v is None or self.v.shape != F.shape:
             self.v = np.zeros_like(F)
             self.fresh = True
         if not self.fresh:
-            P = float(np.sum(F * self.v))
+            P = float(np.sum(F * self.v)) if sums is None else float(sums[0])
             if P > 0.0:
-                fn = np.sqrt(float(np.sum(F * F)))
-                vn = np.sqrt(float(np.sum(self.v * self.v)))
+                fn = np.sqrt(float(np.sum(F * F)) if sums is None else float(sums[1]))
+                vn = np.sqrt(float(np.sum(self.v * self.v)) if sums is None else float(sums[2]))
                 if fn > 0.0:
                     self.v = (1.0 - self.alpha) * self.v + self.alpha * vn * F / fn
                 if self.n_pos > self.n_min:

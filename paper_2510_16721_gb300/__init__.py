@@ -45,6 +45,8 @@ EXPORTS = [
     "cfneb_default_options", "cfneb_create_band", "cfneb_step", "cfneb_relax",
     "cfneb_insert_image", "cfneb_delete_image", "cfneb_get_path", "cfneb_get_state",
     "cfneb_set_state", "cfneb_get_image_scalars", "cfneb_get_tuning",
+    "cfneb_shard_enable", "cfneb_shard_evaluate", "cfneb_shard_get_image", "cfneb_shard_set_ghost",
+    "cfneb_shard_project", "cfneb_shard_move",
     "cfneb_destroy_band", "cfneb_evaluate", "cfneb_profile", "cfneb_profile_read",
     "cfneb_kernel_count", "cfneb_kernel_name", "cfneb_launches_per_step",
     "cfneb_status_string", "cfneb_get_work", "cfneb_get_list_stats", "cfneb_lj_evaluate_noalloc",
@@ -117,6 +119,12 @@ def lib():
             "cfneb_set_state": ([vp, dp], ctypes.c_int),
             "cfneb_get_image_scalars": ([vp, dp, dp, dp], ctypes.c_int),
             "cfneb_get_tuning": ([vp, dp, P(i32)], ctypes.c_int),
+            "cfneb_shard_enable": ([vp], ctypes.c_int),
+            "cfneb_shard_evaluate": ([vp, dp], ctypes.c_int),
+            "cfneb_shard_get_image": ([vp, i32, dp, dp], ctypes.c_int),
+            "cfneb_shard_set_ghost": ([vp, i32, dp, dbl], ctypes.c_int),
+            "cfneb_shard_project": ([vp, i32, dp], ctypes.c_int),
+            "cfneb_shard_move": ([vp, dp], ctypes.c_int),
             "cfneb_destroy_band": ([vp], ctypes.c_int),
             "cfneb_evaluate": ([P(Structure), i32, P(Potential), i32, vp, dp, dp, dp],
                                ctypes.c_int),
@@ -307,6 +315,37 @@ class Band:
         if X.shape != (self.n_images, self.n_atoms + 3, 3):
             raise ValueError("X must have shape (N, n+3, 3)")
         _check(lib().cfneb_set_state(self._h, _dptr(X)), "cfneb_set_state")
+
+    # -- image-range shard (paper_2510_16721_gb300.sharded drives these) --
+    def shard_enable(self):
+        _check(lib().cfneb_shard_enable(self._h), "cfneb_shard_enable")
+
+    def shard_evaluate(self):
+        E = np.zeros(self.n_images)
+        _check(lib().cfneb_shard_evaluate(self._h, _dptr(E)), "cfneb_shard_evaluate")
+        return E
+
+    def shard_get_image(self, index):
+        X = np.zeros((self.n_atoms + 3, 3))
+        e = ctypes.c_double(0.0)
+        _check(lib().cfneb_shard_get_image(self._h, int(index), _dptr(X), ctypes.byref(e)),
+               "cfneb_shard_get_image")
+        return X, float(e.value)
+
+    def shard_set_ghost(self, side, X, energy):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        _check(lib().cfneb_shard_set_ghost(self._h, int(side), _dptr(X), float(energy)),
+               "cfneb_shard_set_ghost")
+
+    def shard_project(self, climbing_index):
+        sums = np.zeros(4)
+        _check(lib().cfneb_shard_project(self._h, int(climbing_index), _dptr(sums)),
+               "cfneb_shard_project")
+        return sums
+
+    def shard_move(self, sums):
+        sums = np.ascontiguousarray(sums, dtype=np.float64)
+        _check(lib().cfneb_shard_move(self._h, _dptr(sums)), "cfneb_shard_move")
 
     def tuning(self):
         """cfneb_get_tuning: (bin width / list cutoff, force kernel blocks per SM)."""

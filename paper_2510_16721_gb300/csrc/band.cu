@@ -138,9 +138,14 @@ __device__ inline double block_sum_records_cg(const double *rec, int stride, int
     const int tid = threadIdx.x;
     if (tid < K * G) {
         const int k = tid % K, g = tid / K;
-        double v = 0.0;
-        for (int q = g; q < count; q += G) v += __ldcg(rec + (size_t)q * stride + k);
-        s_part[g * K + k] = v;
+        double v0 = 0.0, v1 = 0.0;  // two interleaved accumulators
+        int q = g;
+        for (; q + G < count; q += 2 * G) {
+            v0 += __ldcg(rec + (size_t)q * stride + k);
+            v1 += __ldcg(rec + (size_t)(q + G) * stride + k);
+        }
+        if (q < count) v0 += __ldcg(rec + (size_t)q * stride + k);
+        s_part[g * K + k] = v0 + v1;
     }
     __syncthreads();
     double tot = 0.0;
@@ -168,20 +173,32 @@ __device__ inline bool last_arrival(unsigned int *counter, unsigned int total) {
 
 // Climbing image of a band: argmax of the step energies over the interior
 // images, lowest index on ties (the energies are final before pass 1).
-__device__ inline int climbing_image(const BandDev &b) {
+// Called by a whole warp: the lanes load the energies in parallel and a
+// butterfly keeps (larger energy, else lower index), so every lane returns
+// the same index.
+__device__ inline int climbing_image_warp(const BandDev &b) {
     const BandParams *bp = b.bp;
     if (!bp->climb) return -1;
     const int N = bp->N;
-    int ci = -1;
-    double best = 0.0;
-    for (int i = 1; i < N - 1; ++i) {
+    const int lane = threadIdx.x & 31;
+    double best = -INFINITY;
+    int bi = 0x7fffffff;
+    for (int i = 1 + lane; i < N - 1; i += 32) {
         const double e = b.sc[i].E;
-        if (ci < 0 || e > best) {
+        if (e > best) {  // i grows within a lane: ties keep the lower index
             best = e;
-            ci = i;
+            bi = i;
         }
     }
-    return ci;
+    for (int o = 16; o > 0; o >>= 1) {
+        const double e2 = __shfl_xor_sync(0xffffffffu, best, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (e2 > best || (e2 == best && i2 < bi)) {
+            best = e2;
+            bi = i2;
+        }
+    }
+    return bi == 0x7fffffff ? 1 : bi;  // all energies NaN: the first image
 }
 
 // One image, after its dots: upwind tangent weights and the two
@@ -215,10 +232,12 @@ __device__ inline void image_coef(BandDev &b, int i, int ci, const double *d) {
     }
     const double pp = d[0], mm = d[1], pm = d[2], fp = d[3], fm = d[4];
     const double tt = wp * wp * pp + 2.0 * wp * wm * pm + wm * wm * mm;
-    const double tn = sqrt(tt);
-    const double ft = (wp * fp + wm * fm) / tn;  // F . tau_hat
-    const double gamma = i == ci ? -2.0 * ft : bp->k * (sqrt(pp) - sqrt(mm)) - ft;
-    const double a = gamma * wp / tn, bb = gamma * wm / tn;
+    // 1 / |tau| and the spring lengths from FP32-seeded Newton steps (an FP64
+    // divide or square root is a long dependent sequence on this GPU)
+    const double itn = rsqrt64(tt);
+    const double ft = (wp * fp + wm * fm) * itn;  // F . tau_hat
+    const double gamma = i == ci ? -2.0 * ft : bp->k * (sqrt64(pp) - sqrt64(mm)) - ft;
+    const double a = gamma * wp * itn, bb = gamma * wm * itn;
     sc.coef[0] = a;
     sc.coef[1] = bb;
     sc.fire[0] = d[6] + a * d[8] + bb * d[9];
@@ -311,10 +330,12 @@ __global__ void __launch_bounds__(RTHREADS, sizeof(T) == 4 ? 4 : 2) k_band_dots(
         s_d[threadIdx.x] = tk;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const int ci = climbing_image(b);
-        if (tl.img == 1) b.bp->ci = ci;
-        image_coef(b, tl.img, ci, s_d);
+    if (threadIdx.x < 32) {
+        const int ci = b.bp->shard ? b.bp->ci_ext : climbing_image_warp(b);
+        if (threadIdx.x == 0) {
+            if (tl.img == 1) b.bp->ci = ci;
+            image_coef(b, tl.img, ci, s_d);
+        }
     }
 }
 
@@ -332,7 +353,7 @@ __global__ void k_dots_reduce(const ImgRef *imgs, BandDev *bands) {
 __device__ inline void fire_logic(BandParams *bp, const double *tot) {
     bp->stale = 0;  // every image of the band has rebuilt its cell list
     const double P = tot[0], FF = tot[1], VV = tot[2];
-    const double fmax_ = sqrt(tot[3]);
+    const double fmax_ = sqrt64(tot[3]);
     bp->P = P;
     bp->FF = FF;
     bp->VV = VV;
@@ -353,7 +374,7 @@ __device__ inline void fire_logic(BandParams *bp, const double *tot) {
         if (P > 0.0) {
             if (FF > 0.0) {
                 cv = 1.0 - bp->alpha;
-                cf = bp->alpha * sqrt(VV) / sqrt(FF);
+                cf = bp->alpha * sqrt64(VV) * rsqrt64(FF);
             }
             if (bp->npos > 5) {
                 bp->dt = fmin(bp->dt * 1.1, bp->dt_max);
@@ -422,18 +443,42 @@ __global__ void __launch_bounds__(RTHREADS, 4) k_neb_force(const Tile *tiles, Ba
         atomic_max_nonneg(&bp->fmax2_bits, (double)m);
     }
     if (!last_arrival(&bp->done_b, (unsigned)((bp->N - 2) * b.rtpi))) return;
-    // the band's FIRE sums over the interior images, in image order
+    // the band's FIRE sums over the interior images, in image order (the
+    // images' terms loaded in parallel, then added in order)
     __shared__ double s_tot[4];
-    if (threadIdx.x < 3) {
-        double v = 0.0;
-        for (int i = 1; i < bp->N - 1; ++i) v += b.sc[i].fire[threadIdx.x];
-        s_tot[threadIdx.x] = v;
+    __shared__ double s_fire[3][64];
+    const int N = bp->N;
+    for (int base = 1; base < N - 1; base += 64) {
+        const int cnt = min(64, N - 1 - base);
+        if (threadIdx.x < 3 * cnt) {
+            const int k = threadIdx.x / cnt, q = threadIdx.x % cnt;
+            s_fire[k][q] = __ldcg(&b.sc[base + q].fire[k]);
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            double v = base == 1 ? 0.0 : s_tot[threadIdx.x];
+            for (int q = 0; q < cnt; ++q) v += s_fire[threadIdx.x][q];
+            s_tot[threadIdx.x] = v;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     if (threadIdx.x == 0) {
         s_tot[3] = __longlong_as_double((long long)atomicExch(&bp->fmax2_bits, 0ull));
-        fire_logic(bp, s_tot);
+        if (bp->shard) {  // the caller combines the shards' sums
+            bp->P = s_tot[0];
+            bp->FF = s_tot[1];
+            bp->VV = s_tot[2];
+            bp->fmax = s_tot[3];
+        } else {
+            fire_logic(bp, s_tot);
+        }
     }
+}
+
+// the FIRE decision of a shard on the sums of every shard of the band
+__global__ void k_shard_fire(BandDev *band, double P, double FF, double VV, double fmax2) {
+    const double tot[4] = {P, FF, VV, fmax2};
+    fire_logic(band->bp, tot);
 }
 
 template <typename T>
@@ -612,6 +657,10 @@ void launch_band_dots_only(const Tile *tiles, int ntiles, BandDev *bands, cudaSt
 void launch_dots_reduce(const ImgRef *imgs, int count, BandDev *bands, cudaStream_t s) {
     if (count <= 0) return;
     k_dots_reduce<<<count, RED_THREADS, 0, s>>>(imgs, bands);
+}
+void launch_shard_fire(BandDev *band, double P, double FF, double VV, double fmax2,
+                       cudaStream_t s) {
+    k_shard_fire<<<1, 1, 0, s>>>(band, P, FF, VV, fmax2);
 }
 template <typename T>
 void launch_neb_force(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {

@@ -274,6 +274,7 @@ __global__ void __launch_bounds__(32) k_mapback(const ImgRef *imgs, int count, B
     if (b.skin_part) {
         const float *part = b.skin_part + (size_t)r.img * b.atpi;
         float m = 0.0f;
+#pragma unroll 8
         for (int t = lane; t < b.atpi; t += 32) m = fmaxf(m, part[t]);
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         dmax = (double)m;
@@ -357,7 +358,14 @@ __device__ inline F2 f2_add(F2 a, F2 b) {
     return {hi, __fsub_rn(e, __fsub_rn(hi, s))};
 }
 
-__device__ inline void refresh_offset(const ImgScalars &sc, const BandParams *, const float *X,
+// Many-body (Tersoff, NEP-style) bands: the leading part is rounded to a
+// multiple of 2^-20 A (the remainder goes to the low part, exactly), so that
+// the force kernel forms (o_j - o_i) + (bin displacement) exactly with plain
+// FP32 operations: every term sits on the 2^-20 grid (bin vectors on a
+// coarser power-of-two grid) and the sums stay below 2^3 A.
+constexpr float OFF_GRID = 1048576.0f;  // 2^20
+
+__device__ inline void refresh_offset(const ImgScalars &sc, const BandParams *bp, const float *X,
                                       const int *wr, const int *bi, float4 &o, float4 &lo) {
     const float *Dh = sc.dfl, *Dl = sc.dfl + 9, *hh = sc.dfl + 18, *hl = sc.dfl + 27;
     float off[2][3];
@@ -373,8 +381,14 @@ __device__ inline void refresh_offset(const ImgScalars &sc, const BandParams *, 
             K = f2_add(K, f2_mul((float)bi[a] + 0.5f, sc.bvf[3 * a + c], 0.0f));
         }
         const F2 d = f2_add(R, {-K.hi, -K.lo});
-        off[0][c] = d.hi;
-        off[1][c] = d.lo;
+        if (bp->kind != KIND_LJ) {
+            const float q = rintf(d.hi * OFF_GRID) * (1.0f / OFF_GRID);
+            off[0][c] = q;
+            off[1][c] = __fadd_rn(__fsub_rn(d.hi, q), d.lo);  // d.hi - q is exact
+        } else {
+            off[0][c] = d.hi;
+            off[1][c] = d.lo;
+        }
     }
     o = make_float4(off[0][0], off[0][1], off[0][2], (float)bi[2]);
     lo = make_float4(off[1][0], off[1][1], off[1][2], 0.0f);

@@ -59,6 +59,9 @@ inline int gated_grid() {
     return cached[dev];
 }
 
+// potential kinds of BandParams::kind (the values of include/cfneb.h)
+constexpr int KIND_LJ = 0, KIND_TERSOFF = 1, KIND_NEP = 2;
+
 // device status bits (BandParams::status)
 enum : int {
     ST_NOT_SPD = 1,
@@ -165,6 +168,12 @@ struct BandParams {
     // non-negative double (ordered like the values)
     unsigned int done_b, pad_done;
     unsigned long long fmax2_bits;
+    // image-range shard of a band spread over several devices: the end
+    // images are neighbours' images (ghosts), the climbing image comes from
+    // the caller (ci_ext: local index, or -1 for none in this range) and
+    // the FIRE sums of pass 2 are left in P, FF, VV, fmax (squared) for the
+    // caller to combine; the FIRE decision then takes the global sums
+    int shard, ci_ext;
     TP<float> tpf;       // Tersoff constants in FP32 / FP64 (Tersoff bands)
     TP<double> tpd;
 };
@@ -343,11 +352,22 @@ __device__ inline double block_sum_records(const double *rec, int stride, int co
     __shared__ double s_part[G * K];
     const int tid = threadIdx.x;
     if (tid < K * G) {
+        // four interleaved accumulators (records g, g + G, g + 2G, g + 3G go
+        // to accumulators 0..3 in turn): a quarter of the dependent FP64 add
+        // chain, with the loads of each round in flight together
         const int k = tid % K, g = tid / K;
-        double v = 0.0;
-#pragma unroll 8
-        for (int q = g; q < count; q += G) v += rec[(size_t)q * stride + k];
-        s_part[g * K + k] = v;
+        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+        int q = g;
+        for (; q + 3 * G < count; q += 4 * G) {
+            v0 += rec[(size_t)q * stride + k];
+            v1 += rec[(size_t)(q + G) * stride + k];
+            v2 += rec[(size_t)(q + 2 * G) * stride + k];
+            v3 += rec[(size_t)(q + 3 * G) * stride + k];
+        }
+        if (q < count) v0 += rec[(size_t)q * stride + k];
+        if (q + G < count) v1 += rec[(size_t)(q + G) * stride + k];
+        if (q + 2 * G < count) v2 += rec[(size_t)(q + 2 * G) * stride + k];
+        s_part[g * K + k] = (v0 + v1) + (v2 + v3);
     }
     __syncthreads();
     double tot = 0.0;
@@ -516,6 +536,7 @@ __device__ inline void stage_copy(S *dst, const S *src) {
     static_assert(alignof(S) >= 8, "record must be 8-byte aligned for word copies");
     const unsigned long long *s = (const unsigned long long *)src;
     unsigned long long *d = (unsigned long long *)dst;
+#pragma unroll 4
     for (int k = threadIdx.x; k < (int)(sizeof(S) / 8); k += blockDim.x) d[k] = s[k];
 }
 
@@ -567,6 +588,9 @@ void launch_neb_force(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_
 template <typename T>
 void launch_band_dots_only(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 void launch_dots_reduce(const ImgRef *imgs, int count, BandDev *bands, cudaStream_t s);
+// the FIRE decision of a shard on the global sums (P, F.F, v.v, fmax^2)
+void launch_shard_fire(BandDev *band, double P, double FF, double VV, double fmax2,
+                       cudaStream_t s);
 template <typename T>
 void launch_fire_update(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 template <typename T>

@@ -47,6 +47,8 @@ struct CudaFail {
     } while (0)
 
 static_assert(NEP_NW == CFNEB_NEP_N_WEIGHTS, "NEP weight count of the header and kernels");
+static_assert(KIND_LJ == CFNEB_LJ && KIND_TERSOFF == CFNEB_TERSOFF && KIND_NEP == CFNEB_NEP,
+              "potential kinds of the header and kernels");
 
 enum KernelId {
     K_MAPBACK, K_SKIN_CHECK, K_BIN_ASSIGN, K_BIN_TILESUM, K_BIN_TILESCAN, K_BIN_SCANFILL, K_BIN_SCATTER,
@@ -1720,6 +1722,144 @@ int cfneb_set_state(cfneb_band *b, const double *X) {
         fire_reset(b);
         eval_images(b, {0, b->N - 1});  // the endpoints' energies and forces
         b->ends_e64 = false;            // their FP64 energies are re-taken when reported
+        read_params(b);
+        leave(b);
+        return status_from_bits(b->h_bp->status);
+    } catch (CudaFail &) {
+        return CFNEB_ERR_CUDA;
+    }
+}
+
+// ---- image-range shards ---------------------------------------------------
+
+int cfneb_shard_enable(cfneb_band *b) {
+    if (!b || b->batch || b->opt.adaptive) return CFNEB_ERR_INVALID_ARG;
+    try {
+        enter(b);
+        read_params(b);
+        b->h_bp->shard = 1;
+        b->h_bp->ci_ext = -1;
+        b->h_bp->ftol = -1.0;  // the caller tests convergence on the global fmax
+        CK(cudaMemcpyAsync(b->dv.bp, b->h_bp, sizeof(BandParams), cudaMemcpyHostToDevice, b->s));
+        fire_reset(b);
+        leave(b);
+        return CFNEB_OK;
+    } catch (CudaFail &) {
+        return CFNEB_ERR_CUDA;
+    }
+}
+
+int cfneb_shard_evaluate(cfneb_band *b, double *energies) {
+    if (!b || !b->h_bp->shard) return CFNEB_ERR_INVALID_ARG;
+    try {
+        enter(b);
+        Launcher L;
+        const LaunchSet ls = band_step_set(b);
+        if (b->precision == CFNEB_MIXED) enqueue_eval_set<float>(ls, L);
+        else enqueue_eval_set<double>(ls, L);
+        CK(cudaGetLastError());
+        std::vector<ImgScalars> sc(b->N);
+        CK(cudaMemcpyAsync(sc.data(), b->dv.sc, b->N * sizeof(ImgScalars),
+                           cudaMemcpyDeviceToHost, b->s));
+        read_params(b);
+        if (energies)
+            for (int i = 0; i < b->N; ++i) energies[i] = sc[i].E;
+        leave(b);
+        return status_from_bits(b->h_bp->status);
+    } catch (CudaFail &) {
+        return CFNEB_ERR_CUDA;
+    }
+}
+
+int cfneb_shard_set_ghost(cfneb_band *b, int32_t side, const double *X, double energy) {
+    if (!b || !X || (side != 0 && side != 1) || !b->h_bp->shard) return CFNEB_ERR_INVALID_ARG;
+    const size_t per = (size_t)(b->n + 3) * 3;
+    for (size_t i = 0; i < per; ++i)
+        if (!std::isfinite(X[i])) return CFNEB_ERR_INVALID_ARG;
+    try {
+        enter(b);
+        const int img = side == 0 ? 0 : b->N - 1;
+        char *dst = (char *)b->dv.X + (size_t)img * b->dv.rows * 3 * b->ts;
+        std::vector<float> f;
+        if (b->ts == 4) {
+            f.resize(per);
+            for (size_t i = 0; i < per; ++i) f[i] = (float)X[i];
+            CK(cudaMemcpyAsync(dst, f.data(), per * sizeof(float), cudaMemcpyHostToDevice, b->s));
+        } else {
+            CK(cudaMemcpyAsync(dst, X, per * sizeof(double), cudaMemcpyHostToDevice, b->s));
+        }
+        CK(cudaMemcpyAsync(&b->dv.sc[img].E, &energy, sizeof(double), cudaMemcpyHostToDevice,
+                           b->s));
+        CK(cudaStreamSynchronize(b->s));
+        leave(b);
+        return CFNEB_OK;
+    } catch (CudaFail &) {
+        return CFNEB_ERR_CUDA;
+    }
+}
+
+int cfneb_shard_get_image(const cfneb_band *cb, int32_t index, double *X, double *energy) {
+    cfneb_band *b = const_cast<cfneb_band *>(cb);
+    if (!b || index < 0 || index >= b->N) return CFNEB_ERR_INVALID_ARG;
+    try {
+        enter(b);
+        const size_t per = (size_t)(b->n + 3) * 3;
+        const char *src = (const char *)b->dv.X + (size_t)index * b->dv.rows * 3 * b->ts;
+        std::vector<char> tmp(per * b->ts);
+        double e = 0.0;
+        CK(cudaMemcpyAsync(tmp.data(), src, tmp.size(), cudaMemcpyDeviceToHost, b->s));
+        CK(cudaMemcpyAsync(&e, &b->dv.sc[index].E, sizeof(double), cudaMemcpyDeviceToHost, b->s));
+        CK(cudaStreamSynchronize(b->s));
+        if (X)
+            for (size_t i = 0; i < per; ++i)
+                X[i] = b->ts == 4 ? ((const float *)tmp.data())[i] : ((const double *)tmp.data())[i];
+        if (energy) *energy = e;
+        leave(b);
+        return CFNEB_OK;
+    } catch (CudaFail &) {
+        return CFNEB_ERR_CUDA;
+    }
+}
+
+int cfneb_shard_project(cfneb_band *b, int32_t climbing_index, double *sums) {
+    if (!b || !sums || !b->h_bp->shard || climbing_index < -1 || climbing_index == 0 ||
+        climbing_index >= b->N - 1)
+        return CFNEB_ERR_INVALID_ARG;
+    try {
+        enter(b);
+        int ci = climbing_index;
+        CK(cudaMemcpyAsync(&b->dv.bp->ci_ext, &ci, sizeof(int), cudaMemcpyHostToDevice, b->s));
+        const LaunchSet ls = band_step_set(b);
+        if (b->precision == CFNEB_MIXED) {
+            launch_band_dots<float>(ls.rtiles, ls.n_rtiles, ls.d_bands, b->s);
+            launch_neb_force<float>(ls.rtiles, ls.n_rtiles, ls.d_bands, b->s);
+        } else {
+            launch_band_dots<double>(ls.rtiles, ls.n_rtiles, ls.d_bands, b->s);
+            launch_neb_force<double>(ls.rtiles, ls.n_rtiles, ls.d_bands, b->s);
+        }
+        CK(cudaGetLastError());
+        read_params(b);
+        sums[0] = b->h_bp->P;
+        sums[1] = b->h_bp->FF;
+        sums[2] = b->h_bp->VV;
+        sums[3] = b->h_bp->fmax;  // the largest squared row norm
+        leave(b);
+        return CFNEB_OK;
+    } catch (CudaFail &) {
+        return CFNEB_ERR_CUDA;
+    }
+}
+
+int cfneb_shard_move(cfneb_band *b, const double *sums) {
+    if (!b || !sums || !b->h_bp->shard) return CFNEB_ERR_INVALID_ARG;
+    try {
+        enter(b);
+        launch_shard_fire(b->d_self, sums[0], sums[1], sums[2], sums[3], b->s);
+        if (b->precision == CFNEB_MIXED)
+            launch_fire_update<float>(b->d_rtiles, b->n_rtiles, b->d_self, b->s);
+        else
+            launch_fire_update<double>(b->d_rtiles, b->n_rtiles, b->d_self, b->s);
+        CK(cudaGetLastError());
         read_params(b);
         leave(b);
         return status_from_bits(b->h_bp->status);

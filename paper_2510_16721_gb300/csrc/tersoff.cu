@@ -26,11 +26,12 @@
 // bond-order derivative grows like zeta^(n-1) when a neighbour nears R + D,
 // so forces there respond to a distance error d like d^0.46: ~1e-4 eV/A for
 // the 1e-7 A that an FP32 pair vector near 2 A can hold.  Each atom's
-// offset is stored as a leading FP32 part plus the FP32 remainder; a pair
-// vector is formed as (o_j - o_i) + c with Knuth's two-sum keeping the
-// rounding errors (c, the displacement between bin centres, is exact by
-// construction), and s = r - R follows from r^2 - R^2 with FMA-exact
-// squares.  Directions and angles use the leading part; every radial
+// offset is stored as a leading FP32 part on a 2^-20 A grid plus the FP32
+// remainder; a pair vector's leading part (o_j - o_i) + c is then exact in
+// plain FP32 (c, the displacement between bin centres, lies on a coarser
+// power-of-two grid by construction), its low part collects the remainders
+// and the periodic-wrap correction, and s = r - R follows from r^2 - R^2
+// with FMA-exact squares.  (FP64 bands use Knuth's two-sum instead.)  Directions and angles use the leading part; every radial
 // function (f_C, f_R, f_A and derivatives) uses s, accurate to ~1e-12 A.
 // exp(-l r) is evaluated as exp(-l R) exp(-l s).  The cutoff function is
 // written without cancellation: with a = pi (D - s) / 4D and
@@ -187,16 +188,28 @@ __device__ inline void ters_pair(const TP<T> &q, const typename Vec4<T>::type &o
     const T wx = t0 * s_dh[0] + t1 * s_dh[3] + t2 * s_dh[6];
     const T wy = t0 * s_dh[1] + t1 * s_dh[4] + t2 * s_dh[7];
     const T wz = t0 * s_dh[2] + t1 * s_dh[5] + t2 * s_dh[8];
-    T ex1, ey1, ez1, ex2, ey2, ez2;
-    two_sum(oj.x, -oi.x, x, ex1);
-    two_sum(oj.y, -oi.y, y, ey1);
-    two_sum(oj.z, -oi.z, z, ez1);
-    two_sum(x, cx, x, ex2);
-    two_sum(y, cy, y, ey2);
-    two_sum(z, cz, z, ez2);
-    T xl = ((ojl.x - oil.x) + wx) + (ex1 + ex2);
-    T yl = ((ojl.y - oil.y) + wy) + (ey1 + ey2);
-    T zl = ((ojl.z - oil.z) + wz) + (ez1 + ez2);
+    T xl, yl, zl;
+    if (sizeof(T) == 4) {
+        // FP32 offsets of many-body bands lie on a 2^-20 A grid (the offset
+        // refresh rounds them there): (o_j - o_i) + c is exact as it stands
+        x = add_rn(sub_rn(oj.x, oi.x), cx);
+        y = add_rn(sub_rn(oj.y, oi.y), cy);
+        z = add_rn(sub_rn(oj.z, oi.z), cz);
+        xl = add_rn(sub_rn(ojl.x, oil.x), wx);
+        yl = add_rn(sub_rn(ojl.y, oil.y), wy);
+        zl = add_rn(sub_rn(ojl.z, oil.z), wz);
+    } else {
+        T ex1, ey1, ez1, ex2, ey2, ez2;
+        two_sum(oj.x, -oi.x, x, ex1);
+        two_sum(oj.y, -oi.y, y, ey1);
+        two_sum(oj.z, -oi.z, z, ez1);
+        two_sum(x, cx, x, ex2);
+        two_sum(y, cy, y, ey2);
+        two_sum(z, cz, z, ez2);
+        xl = ((ojl.x - oil.x) + wx) + (ex1 + ex2);
+        yl = ((ojl.y - oil.y) + wy) + (ey1 + ey2);
+        zl = ((ojl.z - oil.z) + wz) + (ez1 + ez2);
+    }
     // renormalise: the leading part (used for directions) takes the wrap
     // remainder, the low part keeps the rest
     fast_two_sum(x, xl, x, xl);
