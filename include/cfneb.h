@@ -441,8 +441,9 @@ int cfneb_get_tuning(const cfneb_band *band, double *bin_scale, int32_t *blocks_
 int cfneb_get_list_stats(const cfneb_band *band, int64_t *builds, int64_t *evaluations,
                          double *skin);
 
-/* Number of kernel launches one cfneb_step makes for this band (for
- * launch accounting). */
+/* Number of kernel launches one cfneb_step makes for this band when it
+ * rebuilds cell and neighbour lists (for launch accounting; a step in which
+ * every image keeps its lists skips the 6-7 rebuild kernels). */
 int cfneb_launches_per_step(const cfneb_band *band, int32_t *launches);
 
 /* ---- evaluation without device allocation --------------------------------

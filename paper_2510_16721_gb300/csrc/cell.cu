@@ -714,4 +714,23 @@ CFNEB_INST(float)
 CFNEB_INST(double)
 #undef CFNEB_INST
 
+// Whether any listed image rebuilds its cell list this step: switches the
+// conditional graph node that holds the rebuild kernels (one thread block;
+// the only setter of the condition)
+__global__ void k_any_rebuild(const ImgRef *imgs, int count, BandDev *bands,
+                              cudaGraphConditionalHandle cond) {
+    int any = 0;
+    for (int k = threadIdx.x; k < count; k += blockDim.x) {
+        const ImgRef r = imgs[k];
+        any |= bands[r.band].sc[r.img].rebuild;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) cudaGraphSetConditional(cond, any ? 1u : 0u);
+}
+
+void launch_any_rebuild(const ImgRef *imgs, int count, BandDev *bands,
+                        cudaGraphConditionalHandle cond, cudaStream_t s) {
+    k_any_rebuild<<<1, 256, 0, s>>>(imgs, count, bands, cond);
+}
+
 }  // namespace cfneb

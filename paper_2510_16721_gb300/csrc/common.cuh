@@ -550,6 +550,10 @@ template <typename T>
 void launch_skin_check(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 template <typename T>
 void launch_bin_assign(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
+// sets `cond` (a conditional graph node's handle) to whether any listed
+// image rebuilds its cell list in this step
+void launch_any_rebuild(const ImgRef *imgs, int count, BandDev *bands,
+                        cudaGraphConditionalHandle cond, cudaStream_t s);
 // part 0: tile sums, 1: scan of the tile sums, 2: final per-bin scan
 void launch_bin_scan(const ImgRef *imgs, int count, int max_bins, BandDev *bands,
                      cudaStream_t s, int part);

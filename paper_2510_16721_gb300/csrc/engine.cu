@@ -122,6 +122,7 @@ struct cfneb_band {
     bool ends_e64 = false;       // the endpoints' FP64 energies are known
     // stream ordering
     cudaStream_t user = nullptr, s = nullptr;
+    cudaStream_t s_body = nullptr;   // captures the conditional list-rebuild body
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     // launch tables (device) and their sizes
     Tile *d_atiles = nullptr;    // atom tiles of the interior images
@@ -172,6 +173,7 @@ void free_band(cfneb_band *b) {
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->s) cudaStreamDestroy(b->s);
+    if (b->s_body) cudaStreamDestroy(b->s_body);
     if (b->h_bp) cudaFreeHost(b->h_bp);
     delete b;
 }
@@ -268,6 +270,7 @@ struct LaunchSet {
     int max_bins = 0;                    // largest nbins_cap among the bands
     int force_rebuild = 0;               // rebuild every listed image's cell list
     int lj_minb = kLjMinb, ters_minb = kTersMinb;  // force kernel variants
+    cudaStream_t s_body = nullptr;       // captures the conditional rebuild body
 };
 
 // optional CUDA-event bracketing of every launch (profiling)
@@ -289,15 +292,13 @@ struct Launcher {
     }
 };
 
+// cell-list scan, scatter and order, then the neighbour lists (they index
+// cell-list slots, so they are rebuilt with every cell list, also by an
+// energy-only evaluation); each kernel skips the images that keep theirs
 template <typename T>
-void enqueue_eval_set(const LaunchSet &ls, Launcher &L, bool forces = true) {
+void enqueue_rebuild(const LaunchSet &ls, Launcher &L) {
     BandDev *d = ls.d_bands;
     cudaStream_t s = ls.s;
-    // displacements since the last build, then map-back and the list decision
-    L.pre(K_SKIN_CHECK); launch_skin_check<T>(ls.atiles, ls.n_atiles, d, s); L.post(K_SKIN_CHECK);
-    L.pre(K_MAPBACK); launch_mapback<T>(ls.imgs, ls.nimg, d, ls.force_rebuild, s);
-    L.post(K_MAPBACK);
-    L.pre(K_BIN_ASSIGN); launch_bin_assign<T>(ls.atiles, ls.n_atiles, d, s); L.post(K_BIN_ASSIGN);
     L.pre(K_BIN_TILESUM); launch_bin_scan(ls.imgs, ls.nimg, ls.max_bins, d, s, 0); L.post(K_BIN_TILESUM);
     L.pre(K_BIN_TILESCAN); launch_bin_scan(ls.imgs, ls.nimg, ls.max_bins, d, s, 1); L.post(K_BIN_TILESCAN);
     L.pre(K_BIN_SCANFILL); launch_bin_scan(ls.imgs, ls.nimg, ls.max_bins, d, s, 2); L.post(K_BIN_SCANFILL);
@@ -320,6 +321,57 @@ void enqueue_eval_set(const LaunchSet &ls, Launcher &L, bool forces = true) {
         L.post(K_TERS_LIST);
         L.pre(K_TERS_REVERSE); launch_tersoff_reverse<T>(ls.atiles_nep, ls.n_nep, d, s);
         L.post(K_TERS_REVERSE);
+    }
+}
+
+template <typename T>
+void enqueue_eval_set(const LaunchSet &ls, Launcher &L, bool forces = true) {
+    BandDev *d = ls.d_bands;
+    cudaStream_t s = ls.s;
+    // displacements since the last build, then map-back and the list decision
+    L.pre(K_SKIN_CHECK); launch_skin_check<T>(ls.atiles, ls.n_atiles, d, s); L.post(K_SKIN_CHECK);
+    L.pre(K_MAPBACK); launch_mapback<T>(ls.imgs, ls.nimg, d, ls.force_rebuild, s);
+    L.post(K_MAPBACK);
+    L.pre(K_BIN_ASSIGN); launch_bin_assign<T>(ls.atiles, ls.n_atiles, d, s); L.post(K_BIN_ASSIGN);
+    // the cell-list and neighbour-list rebuild: inside a graph capture it
+    // goes into the body of a conditional node that runs only in steps
+    // where some image rebuilds (most steps keep every list); outside a
+    // capture its kernels run and skip the images that keep their lists
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cst));
+    if (cst == cudaStreamCaptureStatusActive && ls.s_body && !L.prof) {
+        cudaGraph_t graph = nullptr;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &graph, &deps, nullptr, &nd));
+        cudaGraphConditionalHandle cond;
+        CK(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
+        launch_any_rebuild(ls.imgs, ls.nimg, d, cond, s);
+        CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &graph, &deps, nullptr, &nd));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        CK(cudaGraphAddNode(&node, graph, deps, nullptr, nd, &cp));
+        CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
+                                               cudaStreamSetCaptureDependencies));
+        CK(cudaStreamBeginCaptureToGraph(ls.s_body, cp.conditional.phGraph_out[0], nullptr,
+                                         nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        LaunchSet body = ls;
+        body.s = ls.s_body;
+        try {
+            enqueue_rebuild<T>(body, L);
+        } catch (...) {
+            cudaGraph_t tmp = nullptr;
+            cudaStreamEndCapture(ls.s_body, &tmp);
+            throw;
+        }
+        cudaGraph_t tmp = nullptr;
+        CK(cudaStreamEndCapture(ls.s_body, &tmp));
+    } else {
+        enqueue_rebuild<T>(ls, L);
     }
     if (!forces) {
         launch_energy64<T>(ls.atiles, ls.n_atiles, ls.imgs, ls.nimg, d, s);
@@ -358,9 +410,12 @@ void enqueue_step_set(const LaunchSet &ls, Launcher &L) {
     L.post(K_FIRE_UPDATE);
 }
 
+// launches of a step when it rebuilds lists (the graph's conditional node
+// skips the 5 cell-list and 1-2 neighbour-list kernels in other steps); the
+// +1 is the kernel that sets the condition
 int launches_in_set(const LaunchSet &ls) {
     return 8 + (ls.n_lj ? 2 : 0) + (ls.n_ljc ? 1 : 0) + (ls.n_ters ? 4 : 0) + (ls.n_nep ? 4 : 0) +
-           1 + 3;
+           1 + 3 + 1;
 }
 
 LaunchSet band_set(cfneb_band *b, const ImgRef *imgs, int nimg, const Tile *atiles, int nat) {
@@ -389,6 +444,7 @@ LaunchSet band_set(cfneb_band *b, const ImgRef *imgs, int nimg, const Tile *atil
     ls.band_ids = b->d_band_ids;
     ls.nbands = 1;
     ls.max_bins = b->dv.nbins_cap;
+    ls.s_body = b->s_body;
     if (b->minb > 0) {
         if (b->kind == CFNEB_LJ) ls.lj_minb = b->minb;
         if (b->kind == CFNEB_TERSOFF) ls.ters_minb = b->minb;
@@ -744,6 +800,7 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
     else
         b->c = (double)b->n;
     CK(cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&b->s_body, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
     CK(cudaMallocHost((void **)&b->h_bp, sizeof(BandParams)));
@@ -1064,6 +1121,7 @@ double autotune_band(cfneb_band *b, int steps) {
 
 struct cfneb_batch {
     int precision = 0;
+    cudaStream_t s_body = nullptr;   // captures the conditional list-rebuild body
     int lj_minb = 0, ters_minb = 0;  // force kernel variants (0: the default)
     unsigned long long budget = 0, used = 0;
     cudaStream_t user = nullptr, s = nullptr;
@@ -1181,6 +1239,7 @@ void batch_rebuild(cfneb_batch *bt) {
     ls.band_ids = bt->d_ids;
     ls.nbands = (int)ids.size();
     ls.max_bins = max_bins;
+    ls.s_body = bt->s_body;
     if (bt->lj_minb) ls.lj_minb = bt->lj_minb;
     if (bt->ters_minb) ls.ters_minb = bt->ters_minb;
     if (bt->gexec) {
@@ -1276,6 +1335,7 @@ void batch_free(cfneb_batch *bt) {
     if (bt->ev_in) cudaEventDestroy(bt->ev_in);
     if (bt->ev_out) cudaEventDestroy(bt->ev_out);
     if (bt->s) cudaStreamDestroy(bt->s);
+    if (bt->s_body) cudaStreamDestroy(bt->s_body);
     delete bt;
 }
 
@@ -1967,6 +2027,7 @@ int cfneb_batch_create(int32_t precision, uint64_t budget_bytes, void *cuda_stre
     bt->user = (cudaStream_t)cuda_stream;
     try {
         CK(cudaStreamCreateWithFlags(&bt->s, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&bt->s_body, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&bt->ev_in, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&bt->ev_out, cudaEventDisableTiming));
         bt->prof_ev.resize(2 * 64);
