@@ -22,7 +22,9 @@
 //                   convergence test and the FIRE decision (Bitzek et al.
 //                   2006, band-global power).
 // k_fire_update     pass 3: v <- cv v + cf F; v += dt F; dX = dt v clamped
-//                   per row to maxstep; X += dX (interior images only).
+//                   per row to maxstep; X += dX (interior images only); with
+//                   a skin, also each row tile's largest displacement since
+//                   the last list build (the next step's reuse test).
 // "Last" blocks are found with completion counters (a fence, then an atomic
 // increment); the sums they form read the other blocks' records in a fixed
 // order, so results do not depend on block scheduling.
@@ -483,6 +485,7 @@ __global__ void k_shard_fire(BandDev *band, double P, double FF, double VV, doub
 
 template <typename T>
 __global__ void __launch_bounds__(RTHREADS, sizeof(T) == 4 ? 4 : 2) k_fire_update(const Tile *tiles, BandDev *bands) {
+    using T4 = typename Vec4<T>::type;
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
     const BandParams *bp = b.bp;
@@ -498,34 +501,61 @@ __global__ void __launch_bounds__(RTHREADS, sizeof(T) == 4 ? 4 : 2) k_fire_updat
     __syncthreads();
     const T cv = s_k[0], cf = s_k[1], dt = s_k[2], ms = s_k[3];
     const int r0 = tl.t * RTILE + RPT * (int)threadIdx.x;
-    if (r0 >= b.rows) return;
-    const size_t o0 = (tl.img * (size_t)b.rows + (size_t)r0) * 3;
-    T x[12], v[12], fn[12];
-    ld12((const T *)b.X + o0, x);
-    ld12((const T *)b.v + o0, v);
-    ld12((const T *)b.Fneb + o0, fn);
+    T d2 = 0;  // largest squared displacement of this thread's atom rows since the build
+    if (r0 < b.rows) {
+        const size_t o0 = (tl.img * (size_t)b.rows + (size_t)r0) * 3;
+        T x[12], v[12], fn[12];
+        ld12((const T *)b.X + o0, x);
+        ld12((const T *)b.v + o0, v);
+        ld12((const T *)b.Fneb + o0, fn);
 #pragma unroll
-    for (int q = 0; q < RPT; ++q) {
-        T dx[3];
-        T n2 = 0;
+        for (int q = 0; q < RPT; ++q) {
+            T dx[3];
+            T n2 = 0;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            T vc = cv * v[3 * q + c] + cf * fn[3 * q + c];
-            vc += dt * fn[3 * q + c];
-            v[3 * q + c] = vc;
-            dx[c] = dt * vc;
-            n2 += dx[c] * dx[c];
+            for (int c = 0; c < 3; ++c) {
+                T vc = cv * v[3 * q + c] + cf * fn[3 * q + c];
+                vc += dt * fn[3 * q + c];
+                v[3 * q + c] = vc;
+                dx[c] = dt * vc;
+                n2 += dx[c] * dx[c];
+            }
+            if (n2 > ms * ms) {
+                const T sc = ms / sqrt(n2);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) dx[c] *= sc;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) x[3 * q + c] += dx[c];
         }
-        if (n2 > ms * ms) {
-            const T sc = ms / sqrt(n2);
+        st12((T *)b.v + o0, v);
+        st12((T *)b.X + o0, x);
+        if (b.ref_X) {
+            const T4 *ref = (const T4 *)b.ref_X + (size_t)tl.img * b.n;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) dx[c] *= sc;
+            for (int q = 0; q < RPT; ++q) {
+                if (r0 + q < b.n) {
+                    const T4 rf = ref[r0 + q];
+                    const T ex = x[3 * q] - rf.x, ey = x[3 * q + 1] - rf.y,
+                            ez = x[3 * q + 2] - rf.z;
+                    d2 = fmax(d2, ex * ex + ey * ey + ez * ez);
+                }
+            }
         }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) x[3 * q + c] += dx[c];
     }
-    st12((T *)b.v + o0, v);
-    st12((T *)b.X + o0, x);
+    // the row tile's largest displacement for the next evaluation's list
+    // decision (FP32, rounded up: the reuse test never sees one too small)
+    if (b.ref_X) {
+        __shared__ T wmax[RTHREADS / 32];
+        for (int o = 16; o > 0; o >>= 1) d2 = fmax(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = d2;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            T m = wmax[0];
+            for (int q = 1; q < RTHREADS / 32; ++q) m = fmax(m, wmax[q]);
+            b.skin_part[(size_t)tl.img * b.atpi + tl.t] = __fsqrt_ru(to_float_ru(m));
+        }
+    }
 }
 
 // X_img <- 1/2 (X_{img-1} + X_{img+1}) (image insertion; all rows)

@@ -201,7 +201,7 @@ __device__ void skin_decide_one(const BandParams *bp, int nbins_cap, ImgScalars 
 // (deformation gradient), then h = h0 D, h^-1 = D^-1 h0^-1 and
 // Omega = |det h|; then the image's cell-list decision: with no skin a
 // rebuild on the new cell, with a skin the reuse test on the displacements
-// k_skin_check left per tile.  The image record is staged in shared memory,
+// the last move (k_fire_update) left per row tile.  The image record is staged in shared memory,
 // updated and written back whole.
 template <typename T>
 __global__ void __launch_bounds__(32) k_mapback(const ImgRef *imgs, int count, BandDev *bands,
@@ -272,10 +272,11 @@ __global__ void __launch_bounds__(32) k_mapback(const ImgRef *imgs, int count, B
     // is exact in any precision)
     double dmax = 0.0;
     if (b.skin_part) {
+        // per row tile, left by the last move (k_fire_update)
         const float *part = b.skin_part + (size_t)r.img * b.atpi;
         float m = 0.0f;
 #pragma unroll 8
-        for (int t = lane; t < b.atpi; t += 32) m = fmaxf(m, part[t]);
+        for (int t = lane; t < b.rtpi; t += 32) m = fmaxf(m, part[t]);
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         dmax = (double)m;
     }
@@ -483,34 +484,6 @@ __global__ void __launch_bounds__(TILE) k_bin_assign(const Tile *tiles, BandDev 
     }
 }
 
-// Largest displacement |R~ - R~_b| since the build, one value per atom tile.
-template <typename T>
-__global__ void __launch_bounds__(TILE) k_skin_check(const Tile *tiles, BandDev *bands) {
-    using T4 = typename Vec4<T>::type;
-    Tile tl = tiles[blockIdx.x];
-    BandDev &b = bands[tl.band];
-    if (!b.ref_X) return;  // no skin (uniform over the block)
-    const int i = tl.t * TILE + threadIdx.x;
-    T d2 = (T)0;
-    if (i < b.n) {
-        const T *Xi = (const T *)b.X + ((size_t)tl.img * b.rows + i) * 3;
-        const T4 r = ((const T4 *)b.ref_X)[(size_t)tl.img * b.n + i];
-        const T dx = Xi[0] - r.x, dy = Xi[1] - r.y, dz = Xi[2] - r.z;
-        d2 = dx * dx + dy * dy + dz * dz;
-    }
-    for (int o = 16; o > 0; o >>= 1) d2 = fmax(d2, __shfl_xor_sync(0xffffffffu, d2, o));
-    __shared__ T wmax[TILE / 32];
-    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = d2;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        T m = wmax[0];
-        for (int q = 1; q < TILE / 32; ++q) m = fmax(m, wmax[q]);
-        // FP32, rounded up: the reuse test never sees a displacement too small
-        b.skin_part[(size_t)tl.img * b.atpi + tl.t] = __fsqrt_ru(to_float_ru(m));
-    }
-}
-
-
 // Exclusive scan of the bin counts, in three passes over SCAN_TILE-bin
 // tiles: tile sums, a scan of the tile sums per image, and a block-wide scan
 // of each tile offset by its tile prefix.  Integer arithmetic: exact and
@@ -673,11 +646,6 @@ void launch_bin_assign(const Tile *tiles, int ntiles, BandDev *bands, cudaStream
     if (ntiles <= 0) return;
     k_bin_assign<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
 }
-template <typename T>
-void launch_skin_check(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
-    if (ntiles <= 0) return;
-    k_skin_check<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
-}
 void launch_bin_scan(const ImgRef *imgs, int count, int max_bins, BandDev *bands,
                      cudaStream_t s, int part) {
     if (count <= 0 || max_bins <= 0) return;
@@ -707,7 +675,6 @@ void launch_cartesian(const ImgRef *imgs, int count, int max_n, BandDev *bands, 
 #define CFNEB_INST(T)                                                                     \
     template void launch_mapback<T>(const ImgRef *, int, BandDev *, int, cudaStream_t);  \
     template void launch_bin_assign<T>(const Tile *, int, BandDev *, cudaStream_t);      \
-    template void launch_skin_check<T>(const Tile *, int, BandDev *, cudaStream_t);      \
     template void launch_bin_order<T>(const ImgRef *, int, int, BandDev *, cudaStream_t); \
     template void launch_cartesian<T>(const ImgRef *, int, int, BandDev *, cudaStream_t);
 CFNEB_INST(float)

@@ -203,7 +203,7 @@ struct BandDev {
     // neighbour-list reuse: positions and periodic wraps at the last build
     void *ref_X;         // [ncap][n] x 4 T: R~ at the build (atom order)
     int *atom_wrap;      // [ncap][n][3]: floor(s) at the build
-    float *skin_part;    // [ncap][atpi]: per-tile max displacement
+    float *skin_part;    // [ncap][atpi]: per-row-tile max displacement (rtpi used)
     // per-slot neighbour lists: Tersoff (slot, code) pairs of MAXN_TERSOFF
     // entries, or LJ packed entries of lj_cap (0: the LJ kernel walks the
     // cell list directly)
@@ -542,12 +542,10 @@ __device__ inline void stage_copy(S *dst, const S *src) {
 
 // ---- launchers (defined in the kernel translation units) ---------------
 
-// map-back and, after k_skin_check, the cell-list decision of every image
+// map-back and the cell-list decision of every image (the displacements
+// since the last build come from the last move, per row tile)
 template <typename T>
 void launch_mapback(const ImgRef *imgs, int count, BandDev *bands, int force, cudaStream_t s);
-// displacement since the last build (per tile) and the per-image decision
-template <typename T>
-void launch_skin_check(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 template <typename T>
 void launch_bin_assign(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 // sets `cond` (a conditional graph node's handle) to whether any listed

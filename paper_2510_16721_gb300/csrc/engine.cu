@@ -51,13 +51,13 @@ static_assert(KIND_LJ == CFNEB_LJ && KIND_TERSOFF == CFNEB_TERSOFF && KIND_NEP =
               "potential kinds of the header and kernels");
 
 enum KernelId {
-    K_MAPBACK, K_SKIN_CHECK, K_BIN_ASSIGN, K_BIN_TILESUM, K_BIN_TILESCAN, K_BIN_SCANFILL, K_BIN_SCATTER,
+    K_MAPBACK, K_BIN_ASSIGN, K_BIN_TILESUM, K_BIN_TILESCAN, K_BIN_SCANFILL, K_BIN_SCATTER,
     K_BIN_ORDER, K_LJ, K_TERS_LIST, K_TERS_REVERSE, K_TERS_PARTIALS, K_TERS_GATHER, K_IMAGE_FINALIZE,
     K_BAND_DOTS, K_DOTS_REDUCE, K_NEB_COEF, K_NEB_FORCE, K_FIRE_SCALARS, K_FIRE_UPDATE, K_LJ_LIST,
     K_LJ_CELLS, K_NEP_PARTIALS, K_COUNT
 };
 const char *kKernelNames[K_COUNT] = {
-    "mapback", "skin_check", "bin_assign", "bin_tilesum", "bin_tilescan", "bin_scanfill", "bin_scatter",
+    "mapback", "bin_assign", "bin_tilesum", "bin_tilescan", "bin_scanfill", "bin_scatter",
     "bin_order", "lj_force", "tersoff_list", "tersoff_reverse", "tersoff_partials", "tersoff_gather",
     "image_finalize", "band_dots", "dots_reduce", "neb_coef", "neb_force", "fire_scalars",
     "fire_update", "lj_list", "lj_force_cells", "nep_partials"};
@@ -328,8 +328,8 @@ template <typename T>
 void enqueue_eval_set(const LaunchSet &ls, Launcher &L, bool forces = true) {
     BandDev *d = ls.d_bands;
     cudaStream_t s = ls.s;
-    // displacements since the last build, then map-back and the list decision
-    L.pre(K_SKIN_CHECK); launch_skin_check<T>(ls.atiles, ls.n_atiles, d, s); L.post(K_SKIN_CHECK);
+    // the displacements since the last build were taken by the last move
+    // (k_fire_update); then map-back and the list decision
     L.pre(K_MAPBACK); launch_mapback<T>(ls.imgs, ls.nimg, d, ls.force_rebuild, s);
     L.post(K_MAPBACK);
     L.pre(K_BIN_ASSIGN); launch_bin_assign<T>(ls.atiles, ls.n_atiles, d, s); L.post(K_BIN_ASSIGN);
@@ -414,7 +414,7 @@ void enqueue_step_set(const LaunchSet &ls, Launcher &L) {
 // skips the 5 cell-list and 1-2 neighbour-list kernels in other steps); the
 // +1 is the kernel that sets the condition
 int launches_in_set(const LaunchSet &ls) {
-    return 8 + (ls.n_lj ? 2 : 0) + (ls.n_ljc ? 1 : 0) + (ls.n_ters ? 4 : 0) + (ls.n_nep ? 4 : 0) +
+    return 7 + (ls.n_lj ? 2 : 0) + (ls.n_ljc ? 1 : 0) + (ls.n_ters ? 4 : 0) + (ls.n_nep ? 4 : 0) +
            1 + 3 + 1;
 }
 
