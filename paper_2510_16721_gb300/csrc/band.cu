@@ -24,7 +24,9 @@
 // k_fire_update     pass 3: v <- cv v + cf F; v += dt F; dX = dt v clamped
 //                   per row to maxstep; X += dX (interior images only); with
 //                   a skin, also each row tile's largest displacement since
-//                   the last list build (the next step's reuse test).
+//                   the last list build (the next step's reuse test).  One
+//                   warp per image moves its lattice rows and computes the
+//                   new cell for the next map-back, beside the row tiles.
 // "Last" blocks are found with completion counters (a fence, then an atomic
 // increment); the sums they form read the other blocks' records in a fixed
 // order, so results do not depend on block scheduling.
@@ -33,15 +35,15 @@
 namespace cfneb {
 
 template <typename T>
-__global__ void k_image_finalize(const ImgRef *imgs, BandDev *bands) {
+__global__ void __launch_bounds__(FIN_THREADS) k_image_finalize(const ImgRef *imgs, BandDev *bands) {
     ImgRef r = imgs[blockIdx.x];
     BandDev &b = bands[r.band];
     const BandParams *bp = b.bp;
     ImgScalars &sc = b.sc[r.img];
     // U, V (9), pairs, triples: tile partials summed in FP64, fixed order
     __shared__ double s_tot[12];
-    const double tk =
-        block_sum_records<12, 21>(b.atom_part + (size_t)r.img * b.atpi * NPART, NPART, b.atpi);
+    const double tk = block_sum_records_wide<12, 12, FIN_THREADS, false>(
+        b.atom_part + (size_t)r.img * b.atpi * NPART, NPART, b.atpi);
     if (threadIdx.x < 12) s_tot[threadIdx.x] = tk;
     __syncthreads();
     if (threadIdx.x >= 32) return;
@@ -131,32 +133,6 @@ __device__ inline void block_acc_store(Acc<T> (&a)[K], double *dst) {
     __syncthreads();
 }
 
-// FP64 sums of K values over `count` records like block_sum_records, with
-// loads that bypass L1 (the records were written by other blocks of the
-// running kernel).
-template <int K, int G>
-__device__ inline double block_sum_records_cg(const double *rec, int stride, int count) {
-    __shared__ double s_part[G * K];
-    const int tid = threadIdx.x;
-    if (tid < K * G) {
-        const int k = tid % K, g = tid / K;
-        double v0 = 0.0, v1 = 0.0;  // two interleaved accumulators
-        int q = g;
-        for (; q + G < count; q += 2 * G) {
-            v0 += __ldcg(rec + (size_t)q * stride + k);
-            v1 += __ldcg(rec + (size_t)(q + G) * stride + k);
-        }
-        if (q < count) v0 += __ldcg(rec + (size_t)q * stride + k);
-        s_part[g * K + k] = v0 + v1;
-    }
-    __syncthreads();
-    double tot = 0.0;
-    if (tid < K)
-        for (int g = 0; g < G; ++g) tot += s_part[g * K + tid];
-    __syncthreads();
-    return tot;
-}
-
 // true in every thread of the one block that arrives last (counter reaches
 // total); that block also resets the counter for the next launch
 __device__ inline bool last_arrival(unsigned int *counter, unsigned int total) {
@@ -175,18 +151,20 @@ __device__ inline bool last_arrival(unsigned int *counter, unsigned int total) {
 
 // Climbing image of a band: argmax of the step energies over the interior
 // images, lowest index on ties (the energies are final before pass 1).
-// Called by a whole warp: the lanes load the energies in parallel and a
+// Called by a whole warp with e0 = the energy of image 1 + lane (loaded by
+// the caller ahead of other work; -inf where there is no such image): a
 // butterfly keeps (larger energy, else lower index), so every lane returns
 // the same index.
-__device__ inline int climbing_image_warp(const BandDev &b) {
-    const BandParams *bp = b.bp;
-    if (!bp->climb) return -1;
-    const int N = bp->N;
+__device__ inline int climbing_image_warp(const BandDev &b, int N, double e0) {
     const int lane = threadIdx.x & 31;
     double best = -INFINITY;
     int bi = 0x7fffffff;
-    for (int i = 1 + lane; i < N - 1; i += 32) {
-        const double e = b.sc[i].E;
+    if (1 + lane < N - 1 && e0 > best) {  // NaN never wins
+        best = e0;
+        bi = 1 + lane;
+    }
+    for (int i = 33 + lane; i < N - 1; i += 32) {
+        const double e = __ldcg(&b.sc[i].E);
         if (e > best) {  // i grows within a lane: ties keep the lower index
             best = e;
             bi = i;
@@ -212,10 +190,9 @@ __device__ inline int climbing_image_warp(const BandDev &b) {
 //   F_NEB.v = F.v + a dX+.v + b dX-.v,
 //   |F_NEB|^2 = F.F + a^2 |dX+|^2 + b^2 |dX-|^2 + 2a F.dX+ + 2b F.dX-
 //               + 2ab dX+.dX-.
-__device__ inline void image_coef(BandDev &b, int i, int ci, const double *d) {
-    const BandParams *bp = b.bp;
+__device__ inline void image_coef(BandDev &b, int i, int ci, const double *d, double Em,
+                                  double E0, double Ep, double kspring) {
     ImgScalars &sc = b.sc[i];
-    const double Em = b.sc[i - 1].E, E0 = sc.E, Ep = b.sc[i + 1].E;
     double wp, wm;
     if (Ep > E0 && E0 > Em) {
         wp = 1.0; wm = 0.0;
@@ -238,7 +215,7 @@ __device__ inline void image_coef(BandDev &b, int i, int ci, const double *d) {
     // divide or square root is a long dependent sequence on this GPU)
     const double itn = rsqrt64(tt);
     const double ft = (wp * fp + wm * fm) * itn;  // F . tau_hat
-    const double gamma = i == ci ? -2.0 * ft : bp->k * (sqrt64(pp) - sqrt64(mm)) - ft;
+    const double gamma = i == ci ? -2.0 * ft : kspring * (sqrt64(pp) - sqrt64(mm)) - ft;
     const double a = gamma * wp * itn, bb = gamma * wm * itn;
     sc.coef[0] = a;
     sc.coef[1] = bb;
@@ -324,7 +301,24 @@ __global__ void __launch_bounds__(RTHREADS, sizeof(T) == 4 ? 4 : 2) k_band_dots(
     if (!FUSE) return;
     ImgScalars &sc = b.sc[tl.img];
     if (!last_arrival(&sc.done, (unsigned)b.rtpi)) return;
-    const double tk = block_sum_records_cg<10, 12>(
+    // warp 0 loads what the climbing image and the tangent need before the
+    // record sums, so that those loads share the sums' round trip
+    BandParams *bp = b.bp;
+    const int lane = threadIdx.x & 31;
+    double e0 = 0.0, Em = 0.0, E0 = 0.0, Ep = 0.0, kspring = 0.0;
+    int N = 0, climb = 0, shard = 0, ci_ext = -1;
+    if (threadIdx.x < 32) {
+        if (1 + lane < b.ncap) e0 = __ldcg(&b.sc[1 + lane].E);
+        N = bp->N;
+        climb = bp->climb;
+        shard = bp->shard;
+        ci_ext = bp->ci_ext;
+        kspring = bp->k;
+        Em = __ldcg(&b.sc[tl.img - 1].E);
+        E0 = __ldcg(&sc.E);
+        Ep = __ldcg(&b.sc[tl.img + 1].E);
+    }
+    const double tk = block_sum_records_wide<10, 4, RTHREADS, true>(
         b.row_part + (size_t)tl.img * b.rtpi * NPART, NPART, b.rtpi);
     __shared__ double s_d[10];
     if (threadIdx.x < 10) {
@@ -333,10 +327,10 @@ __global__ void __launch_bounds__(RTHREADS, sizeof(T) == 4 ? 4 : 2) k_band_dots(
     }
     __syncthreads();
     if (threadIdx.x < 32) {
-        const int ci = b.bp->shard ? b.bp->ci_ext : climbing_image_warp(b);
+        const int ci = shard ? ci_ext : (climb ? climbing_image_warp(b, N, e0) : -1);
         if (threadIdx.x == 0) {
-            if (tl.img == 1) b.bp->ci = ci;
-            image_coef(b, tl.img, ci, s_d);
+            if (tl.img == 1) bp->ci = ci;
+            image_coef(b, tl.img, ci, s_d, Em, E0, Ep, kspring);
         }
     }
 }
@@ -483,10 +477,89 @@ __global__ void k_shard_fire(BandDev *band, double P, double FF, double VV, doub
     fire_logic(band->bp, tot);
 }
 
+// One row of the move (Bitzek et al. 2006 with the band-global mixing
+// cv, cf): v <- cv v + cf F_NEB; v += dt F_NEB; dX = dt v, scaled down to
+// maxstep in norm; X += dX.  Atom rows and lattice rows take the same step.
 template <typename T>
-__global__ void __launch_bounds__(RTHREADS, sizeof(T) == 4 ? 4 : 2) k_fire_update(const Tile *tiles, BandDev *bands) {
+__device__ inline void fire_row(T *x, T *v, const T *fn, T cv, T cf, T dt, T ms) {
+    T dx[3];
+    T n2 = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        T vc = cv * v[c] + cf * fn[c];
+        vc += dt * fn[c];
+        v[c] = vc;
+        dx[c] = dt * vc;
+        n2 += dx[c] * dx[c];
+    }
+    if (n2 > ms * ms) {
+        const T sc = ms / sqrt(n2);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dx[c] *= sc;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) x[c] += dx[c];
+}
+
+// The three lattice rows of one image, one warp: the move, then the new
+// cell (image_cell_warp) and the bin vectors of the kept grid, so that the
+// next evaluation's map-back finds them ready (cell_fresh) instead of
+// starting its FP64 chain only then.  Runs beside the atom rows' blocks.
+template <typename T>
+__device__ inline void lattice_move_warp(const ImgRef r, BandDev *bands) {
+    BandDev &b = bands[r.band];
+    const BandParams *bp = b.bp;
+    if (!bp->move) return;  // uniform over the warp
+    const int lane = threadIdx.x & 31;
+    const T cv = (T)bp->cv, cf = (T)bp->cf, dt = (T)bp->dt, ms = (T)bp->maxstep;
+    T x[3] = {0, 0, 0};
+    if (lane < 3) {  // lane q moves lattice row n + q
+        const size_t o = ((size_t)r.img * b.rows + b.n + lane) * 3;
+        T v[3], fn[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            x[c] = ((const T *)b.X)[o + c];
+            v[c] = ((const T *)b.v)[o + c];
+            fn[c] = ((const T *)b.Fneb)[o + c];
+        }
+        fire_row(x, v, fn, cv, cf, dt, ms);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            ((T *)b.X)[o + c] = x[c];
+            ((T *)b.v)[o + c] = v[c];
+        }
+    }
+    // entry (l / 3, l % 3), l = lane % 9, of the moved lattice rows
+    const int l = lane % 9;
+    const T a0 = __shfl_sync(0xffffffffu, x[0], l / 3);
+    const T a1 = __shfl_sync(0xffffffffu, x[1], l / 3);
+    const T a2 = __shfl_sync(0xffffffffu, x[2], l / 3);
+    const T xl = l % 3 == 0 ? a0 : (l % 3 == 1 ? a1 : a2);
+    ImgScalars &sc = b.sc[r.img];
+    const bool ok = image_cell_warp(bp, (double)xl, sc);
+    if (!ok && lane == 0) atomicOr(&b.bp->status, ST_NOT_SPD);
+    __syncwarp();
+    bin_vectors_warp(sc);
+    if (lane == 0) {
+        if (bp->skin > 0.0) skin_terms(sc);  // for the next list decision
+        sc.cell_fresh = 1;
+    }
+}
+
+// Pass 3: blocks 0 .. nimg-1 move the lattice rows of imgs[block] (one warp
+// each, scheduled first so that their FP64 cell work overlaps the rest);
+// the other blocks move the atom rows of their row tile, 4 rows a thread,
+// and with a skin record the tile's largest displacement since the last
+// list build.
+template <typename T>
+__global__ void __launch_bounds__(RTHREADS, sizeof(T) == 4 ? 4 : 2)
+    k_fire_update(const Tile *tiles, const ImgRef *imgs, int nimg, BandDev *bands) {
     using T4 = typename Vec4<T>::type;
-    Tile tl = tiles[blockIdx.x];
+    if ((int)blockIdx.x < nimg) {
+        if (threadIdx.x < 32) lattice_move_warp<T>(imgs[blockIdx.x], bands);
+        return;
+    }
+    Tile tl = tiles[blockIdx.x - nimg];
     BandDev &b = bands[tl.band];
     const BandParams *bp = b.bp;
     if (!bp->move) return;  // uniform over the block
@@ -501,40 +574,38 @@ __global__ void __launch_bounds__(RTHREADS, sizeof(T) == 4 ? 4 : 2) k_fire_updat
     __syncthreads();
     const T cv = s_k[0], cf = s_k[1], dt = s_k[2], ms = s_k[3];
     const int r0 = tl.t * RTILE + RPT * (int)threadIdx.x;
+    const int n = b.n;
     T d2 = 0;  // largest squared displacement of this thread's atom rows since the build
-    if (r0 < b.rows) {
+    if (r0 < n) {
+        // rows r0 .. r0 + 3 lie within the padded stride (rows >= n + 3);
+        // only atom rows move here (lattice rows: lattice_move_warp;
+        // padding rows stay zero)
         const size_t o0 = (tl.img * (size_t)b.rows + (size_t)r0) * 3;
         T x[12], v[12], fn[12];
         ld12((const T *)b.X + o0, x);
         ld12((const T *)b.v + o0, v);
         ld12((const T *)b.Fneb + o0, fn);
 #pragma unroll
-        for (int q = 0; q < RPT; ++q) {
-            T dx[3];
-            T n2 = 0;
+        for (int q = 0; q < RPT; ++q)
+            if (r0 + q < n) fire_row(x + 3 * q, v + 3 * q, fn + 3 * q, cv, cf, dt, ms);
+        if (r0 + RPT <= n) {
+            st12((T *)b.v + o0, v);
+            st12((T *)b.X + o0, x);
+        } else {  // the last atom rows of the image: row by row
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                T vc = cv * v[3 * q + c] + cf * fn[3 * q + c];
-                vc += dt * fn[3 * q + c];
-                v[3 * q + c] = vc;
-                dx[c] = dt * vc;
-                n2 += dx[c] * dx[c];
-            }
-            if (n2 > ms * ms) {
-                const T sc = ms / sqrt(n2);
+            for (int q = 0; q < RPT; ++q)
+                if (r0 + q < n)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) dx[c] *= sc;
-            }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) x[3 * q + c] += dx[c];
+                    for (int c = 0; c < 3; ++c) {
+                        ((T *)b.v)[o0 + 3 * q + c] = v[3 * q + c];
+                        ((T *)b.X)[o0 + 3 * q + c] = x[3 * q + c];
+                    }
         }
-        st12((T *)b.v + o0, v);
-        st12((T *)b.X + o0, x);
         if (b.ref_X) {
-            const T4 *ref = (const T4 *)b.ref_X + (size_t)tl.img * b.n;
+            const T4 *ref = (const T4 *)b.ref_X + (size_t)tl.img * n;
 #pragma unroll
             for (int q = 0; q < RPT; ++q) {
-                if (r0 + q < b.n) {
+                if (r0 + q < n) {
                     const T4 rf = ref[r0 + q];
                     const T ex = x[3 * q] - rf.x, ey = x[3 * q + 1] - rf.y,
                             ez = x[3 * q + 2] - rf.z;
@@ -670,7 +741,7 @@ void launch_setup(const double *R0, const double *R1, const double *noise, int n
 template <typename T>
 void launch_image_finalize(const ImgRef *imgs, int count, BandDev *bands, cudaStream_t s) {
     if (count <= 0) return;
-    k_image_finalize<T><<<count, RED_THREADS, 0, s>>>(imgs, bands);
+    k_image_finalize<T><<<count, FIN_THREADS, 0, s>>>(imgs, bands);
 }
 // pass 1 of the step (fused: per-image dots, NEB coefficients, FIRE sums)
 template <typename T>
@@ -698,9 +769,10 @@ void launch_neb_force(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_
     k_neb_force<T><<<ntiles, RTHREADS, 0, s>>>(tiles, bands);
 }
 template <typename T>
-void launch_fire_update(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
-    if (ntiles <= 0) return;
-    k_fire_update<T><<<ntiles, RTHREADS, 0, s>>>(tiles, bands);
+void launch_fire_update(const Tile *tiles, int ntiles, const ImgRef *imgs, int nimg,
+                        BandDev *bands, cudaStream_t s) {
+    if (ntiles + nimg <= 0) return;
+    k_fire_update<T><<<nimg + ntiles, RTHREADS, 0, s>>>(tiles, imgs, nimg, bands);
 }
 template <typename T>
 void launch_midpoint(BandDev *band, int img, int rows, cudaStream_t s) {
@@ -714,7 +786,8 @@ void launch_midpoint(BandDev *band, int img, int rows, cudaStream_t s) {
     template void launch_band_dots<T>(const Tile *, int, BandDev *, cudaStream_t);          \
     template void launch_band_dots_only<T>(const Tile *, int, BandDev *, cudaStream_t);     \
     template void launch_neb_force<T>(const Tile *, int, BandDev *, cudaStream_t);          \
-    template void launch_fire_update<T>(const Tile *, int, BandDev *, cudaStream_t);        \
+    template void launch_fire_update<T>(const Tile *, int, const ImgRef *, int, BandDev *,  \
+                                        cudaStream_t);                                    \
     template void launch_midpoint<T>(BandDev *, int, int, cudaStream_t);                  \
     template void launch_setup<T>(const double *, const double *, const double *, int, int, \
                                   BandDev *, cudaStream_t, const double *);

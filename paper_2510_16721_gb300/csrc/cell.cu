@@ -102,93 +102,28 @@ __device__ void bin_grid(const BandParams *bp, int nbins_cap, const double *h, d
     sc.nbins = nb[0] * nb[1] * nb[2];
 }
 
-// Bin vectors of the image's grid for its current cell, one entry per lane
-// (lanes 0..8; the whole warp calls): bv_a on a grid of q = 2^(e - 19),
-// 2^e >= max |h_a / nb_a|, so every sum of three products delta_a bv_a
-// (|delta| <= 7) is exact in FP32; dh = h - nb bv carries the (sub-1e-4 A)
-// quantisation to the periodic wrap.  Only the binade of max |h_a / nb_a|
-// matters; found in FP32 it can be one binade low by an ulp, and then
-// |bv| <= (2^19 + 1) q: three terms |delta| <= 7 still sum below 2^24 q.
-__device__ void bin_vectors_warp(ImgScalars &sc) {
-    const int lane = threadIdx.x & 31;
-    const int l = lane < 9 ? lane : 0, a = l / 3;
-    const int nba = sc.nb[a];
-    const double h = sc.h[l];
-    float bmax = lane < 9 ? fabsf((float)h / (float)nba) : 0.0f;
-    for (int o = 16; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
-    const int e = ilogbf(bmax) + 1 - 19;
-    const double q = ldexp(1.0, e), iq = ldexp(1.0, -e);  // exact powers of two
-    const double v = q * rint(h * rcp64((double)nba) * iq);
-    if (lane < 9) {
-        sc.bv[l] = v;
-        sc.bvf[l] = (float)v;
-        sc.dh[l] = h - nba * v;
-    }
-}
-
-// upper bound of the spectral norm of a 3x3 matrix: the smaller of the
-// Frobenius norm and sqrt(|A|_1 |A|_inf), in FP32 and raised by 1e-6 to
-// stay a bound
-__device__ inline float norm2_bound(const float *A) {
-    float f = 0.0f, c1 = 0.0f, ci = 0.0f;
-    for (int i = 0; i < 3; ++i) {
-        float rs = 0.0f, cs = 0.0f;
-        for (int j = 0; j < 3; ++j) {
-            f += A[3 * i + j] * A[3 * i + j];
-            rs += fabsf(A[3 * i + j]);
-            cs += fabsf(A[3 * j + i]);
-        }
-        ci = fmaxf(ci, rs);
-        c1 = fmaxf(c1, cs);
-    }
-    return fminf(sqrtf(f), sqrtf(c1 * ci)) * 1.000001f;
-}
-
-// FP32 inverse of a 3x3 matrix (cofactors over the determinant)
-__device__ inline void inv3f(const float *m, float *o) {
-    const float c00 = m[4] * m[8] - m[5] * m[7], c01 = m[5] * m[6] - m[3] * m[8],
-                c02 = m[3] * m[7] - m[4] * m[6];
-    const float id = 1.0f / (m[0] * c00 + m[1] * c01 + m[2] * c02);
-    o[0] = c00 * id;
-    o[1] = (m[2] * m[7] - m[1] * m[8]) * id;
-    o[2] = (m[1] * m[5] - m[2] * m[4]) * id;
-    o[3] = c01 * id;
-    o[4] = (m[0] * m[8] - m[2] * m[6]) * id;
-    o[5] = (m[2] * m[3] - m[0] * m[5]) * id;
-    o[6] = c02 * id;
-    o[7] = (m[1] * m[6] - m[0] * m[7]) * id;
-    o[8] = (m[0] * m[4] - m[1] * m[3]) * id;
-}
-
 // The rebuild decision of one image on its staged record sc (one thread):
 // keep the bins of the build while the bound in the header comment holds,
 // else rebuild (always when forced, when the band's images were rearranged,
-// or while autotuning).  d = the largest displacement since the build.
+// or while autotuning).  d = the largest displacement since the build; the
+// cell's part of the bound (skin_terms) is current in sc.
 __device__ void skin_decide_one(const BandParams *bp, int nbins_cap, ImgScalars &sc, double d,
                                 int force) {
     bool rebuild = force || bp->stale || bp->tune_rebuild || sc.builds == 0;
     if (!rebuild) {
-        // in FP32: M - I = D_b^-1 D - I is small, so its FP32 rounding (~1e-7
-        // absolute) moves the bound by far less than the 1e-5 margins, which
-        // also cover the FP32 list test and displacement
-        float Db[9], D[9], Dbi[9], M[9];
-        for (int k = 0; k < 9; ++k) {
-            Db[k] = (float)sc.Db[k];
-            D[k] = (float)sc.D[k];
-        }
-        inv3f(Db, Dbi);
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j)
-                M[3 * i + j] = Dbi[3 * i] * D[j] + Dbi[3 * i + 1] * D[3 + j] +
-                               Dbi[3 * i + 2] * D[6 + j] - (i == j ? 1.0f : 0.0f);
-        const float e = norm2_bound(M) * 1.00001f + 1e-6f;
-        const double bound = bp->rl * (1.0 - 1e-5) * (1.0 - (double)e) -
-                             2.0 * d * (double)norm2_bound(D) * (1.0 + 1e-5);
+        const double bound = bp->rl * (1.0 - 1e-5) * (1.0 - (double)sc.skin_e) -
+                             2.0 * d * (double)sc.skin_nD * (1.0 + 1e-5);
         rebuild = !(bound > bp->rc);
     }
     if (rebuild) {
         bin_grid(bp, nbins_cap, sc.h, sc.omega, sc);
-        for (int k = 0; k < 9; ++k) sc.Db[k] = sc.D[k];
+        float Db[9];
+        for (int k = 0; k < 9; ++k) {
+            sc.Db[k] = sc.D[k];
+            Db[k] = (float)sc.D[k];
+        }
+        inv3f(Db, sc.Dbif);
+        skin_terms(sc);
         sc.builds += 1;
     }
     sc.rebuild = rebuild ? 1 : 0;
@@ -196,13 +131,14 @@ __device__ void skin_decide_one(const BandParams *bp, int nbins_cap, ImgScalars 
     sc.evals += 1;
 }
 
-// Map-back of one image per warp: B = X_lat / c, D = B^(1/2) (rotation-free,
-// coupled Newton-Schulz as in the header comment) or D = X_lat / c
-// (deformation gradient), then h = h0 D, h^-1 = D^-1 h0^-1 and
-// Omega = |det h|; then the image's cell-list decision: with no skin a
-// rebuild on the new cell, with a skin the reuse test on the displacements
-// the last move (k_fire_update) left per row tile.  The image record is staged in shared memory,
-// updated and written back whole.
+// Map-back of one image per warp and its cell-list decision.  The cell
+// (image_cell_warp: D, h, Omega and the bin vectors) is taken over from the
+// last move when k_fire_update already computed it for the current lattice
+// rows; it is computed here for forced evaluations, after the band's images
+// were rearranged or reloaded (stale) and whenever the move did not leave
+// it.  Then with no skin a rebuild on the new cell, with a skin the reuse
+// test on the displacements the last move left per row tile.  The image
+// record is staged in shared memory, updated and written back whole.
 template <typename T>
 __global__ void __launch_bounds__(32) k_mapback(const ImgRef *imgs, int count, BandDev *bands,
                                                 int force) {
@@ -215,59 +151,13 @@ __global__ void __launch_bounds__(32) k_mapback(const ImgRef *imgs, int count, B
     __syncwarp();
     const BandParams *bp = &s_bp;
     ImgScalars &sc = s_sc;
-    const Lane3 p;
     const int lane = threadIdx.x & 31;
-    const T *Xl = (const T *)b.X + ((size_t)r.img * b.rows + b.n) * 3;
-    double D = p.eye(), Di = p.eye();
-    bool ok = true;
-    if (bp->filter) {
-        const double L = (double)Xl[p.l] * rcp64(bp->c);
-        if (bp->variant == 0) {
-            const double B = 0.5 * (L + ltrans(L, p));
-            const double C = lcof(B, p);
-            const double det = ldet(B, C);
-            // Sylvester's criterion: B00 > 0, the leading 2x2 minor (= C22) > 0, det > 0
-            ok = lget(B, 0) > 0.0 && lget(C, 8) > 0.0 && det > 0.0;
-            if (ok) {
-                // spectrum bracket [det / g^2, g], g = largest Gershgorin row bound
-                const double rs = fabs(lget(B, 3 * p.i)) + fabs(lget(B, 3 * p.i + 1)) +
-                                  fabs(lget(B, 3 * p.i + 2));
-                const double g = fmax(fmax(lget(rs, 0), lget(rs, 3)), lget(rs, 6));
-                const double ig = rcp64(g);
-                const double mu = 0.5 * (g + det * ig * ig);
-                double Y = B * rcp64(mu), Z = p.eye();
-                for (int it = 0; it < 40; ++it) {
-                    const double e = p.eye() - lmul(Z, Y, p);  // I - Z Y
-                    const double Tm = p.eye() + 0.5 * e;       // (3I - Z Y) / 2
-                    float dev = fabsf((float)e);
-                    for (int o = 16; o > 0; o >>= 1)
-                        dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));
-                    const double Y1 = lmul(Y, Tm, p), Z1 = lmul(Tm, Z, p);
-                    Y = Y1;
-                    Z = Z1;
-                    if (dev < 1e-9f) break;  // the last step took it to ~1e-18
-                }
-                const double rmu = sqrt64(mu);
-                D = 0.5 * (Y + ltrans(Y, p)) * rmu;
-                Di = 0.5 * (Z + ltrans(Z, p)) * rcp64(rmu);
-            }
-        } else {
-            const double C = lcof(L, p);
-            const double det = ldet(L, C);
-            ok = det > 0.0;
-            if (ok) {
-                D = L;
-                Di = ltrans(C, p) * rcp64(det);
-            }
-        }
+    const bool fresh = !force && !bp->stale && sc.cell_fresh;
+    if (!fresh) {
+        const T *Xl = (const T *)b.X + ((size_t)r.img * b.rows + b.n) * 3;
+        const bool ok = image_cell_warp(bp, (double)Xl[lane % 9], sc);
+        if (!ok && lane == 0) atomicOr(&b.bp->status, ST_NOT_SPD);
     }
-    if (!ok) {
-        if (lane == 0) atomicOr(&b.bp->status, ST_NOT_SPD);
-        D = Di = p.eye();
-    }
-    const double h = lmul(bp->h0[p.l], D, p);
-    const double hinv = lmul(Di, bp->h0inv[p.l], p);  // (h0 D)^-1 = D^-1 h0^-1
-    const double omega = fabs(ldet(h, lcof(h, p)));
     // largest displacement since the last build (skin > 0), in FP32 (a max
     // is exact in any precision)
     double dmax = 0.0;
@@ -280,25 +170,13 @@ __global__ void __launch_bounds__(32) k_mapback(const ImgRef *imgs, int count, B
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         dmax = (double)m;
     }
-    if (lane < 9) {
-        sc.D[lane] = D;
-        sc.Dinv[lane] = Di;
-        sc.h[lane] = h;
-        sc.hinv[lane] = hinv;
-        // FP32 pairs of D and h and FP32 h0^-1 for the FP32 cell-list path
-        const float Dh = (float)D, hh = (float)h;
-        sc.dfl[lane] = Dh;
-        sc.dfl[9 + lane] = (float)(D - (double)Dh);
-        sc.dfl[18 + lane] = hh;
-        sc.dfl[27 + lane] = (float)(h - (double)hh);
-        sc.dfl[36 + lane] = (float)bp->h0inv[lane];
-    }
     __syncwarp();
     if (lane == 0) {
-        sc.omega = omega;
+        sc.cell_fresh = 1;
+        if (!fresh && bp->skin > 0.0) skin_terms(sc);
         if (bp->skin <= 0.0) {
             // no skin: the cell list is rebuilt at every evaluation
-            bin_grid(bp, b.nbins_cap, sc.h, omega, sc);
+            bin_grid(bp, b.nbins_cap, sc.h, sc.omega, sc);
             sc.rebuild = 1;
             sc.builds += 1;
             sc.evals += 1;
@@ -307,7 +185,9 @@ __global__ void __launch_bounds__(32) k_mapback(const ImgRef *imgs, int count, B
         }
     }
     __syncwarp();
-    bin_vectors_warp(sc);  // lane-parallel: the grid (new or kept) follows the cell
+    // the grid (new or kept) follows the cell; a move that left the cell
+    // also left the bin vectors of the kept grid
+    if (!fresh || sc.rebuild) bin_vectors_warp(sc);
     __syncwarp();
     stage_copy(&b.sc[r.img], &s_sc);
 }
@@ -366,21 +246,34 @@ __device__ inline F2 f2_add(F2 a, F2 b) {
 // coarser power-of-two grid) and the sums stay below 2^3 A.
 constexpr float OFF_GRID = 1048576.0f;  // 2^20
 
+__device__ inline F2 f2_prod(float a, float b) {  // a b exactly
+    const float p = __fmul_rn(a, b);
+    return {p, fmaf(a, b, -p)};
+}
+
+// K = sum_a (wrap_a h_a + (b_a + 1/2) bv_a) is formed as
+// sum_a m_a bv_a + sum_a wrap_a dh_a with m_a = wrap_a nb_a + b_a + 1/2
+// (h_a = nb_a bv_a + dh_a): each m_a bv_a is exact as a pair (bv exact in
+// FP32, m_a a half-integer far below 2^23), the dh terms are tiny and join
+// the low part.
 __device__ inline void refresh_offset(const ImgScalars &sc, const BandParams *bp, const float *X,
                                       const int *wr, const int *bi, float4 &o, float4 &lo) {
-    const float *Dh = sc.dfl, *Dl = sc.dfl + 9, *hh = sc.dfl + 18, *hl = sc.dfl + 27;
+    const float *Dh = sc.dfl, *Dl = sc.dfl + 9;
+    float m[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) m[a] = (float)(wr[a] * sc.nb[a] + bi[a]) + 0.5f;
     float off[2][3];
+#pragma unroll
     for (int c = 0; c < 3; ++c) {
         // R_c = sum_k X_k D_kc (X exact in FP32)
         F2 R = f2_mul(X[0], Dh[c], Dl[c]);
         R = f2_add(R, f2_mul(X[1], Dh[3 + c], Dl[3 + c]));
         R = f2_add(R, f2_mul(X[2], Dh[6 + c], Dl[6 + c]));
-        // K_c = sum_a wrap_a h_ac + (b_a + 1/2) bv_ac
-        F2 K = {0.0f, 0.0f};
-        for (int a = 0; a < 3; ++a) {
-            K = f2_add(K, f2_mul((float)wr[a], hh[3 * a + c], hl[3 * a + c]));
-            K = f2_add(K, f2_mul((float)bi[a] + 0.5f, sc.bvf[3 * a + c], 0.0f));
-        }
+        F2 K = f2_prod(m[0], sc.bvf[c]);
+        K = f2_add(K, f2_prod(m[1], sc.bvf[3 + c]));
+        K = f2_add(K, f2_prod(m[2], sc.bvf[6 + c]));
+        K.lo = fmaf((float)wr[0], sc.dhf[c],
+                    fmaf((float)wr[1], sc.dhf[3 + c], fmaf((float)wr[2], sc.dhf[6 + c], K.lo)));
         const F2 d = f2_add(R, {-K.hi, -K.lo});
         if (bp->kind != KIND_LJ) {
             const float q = rintf(d.hi * OFF_GRID) * (1.0f / OFF_GRID);
@@ -447,10 +340,10 @@ __global__ void __launch_bounds__(TILE) k_bin_assign(const Tile *tiles, BandDev 
         if (t >= b.n) return;
         const size_t st = (size_t)tl.img * b.n + t;
         const int i = b.slot_atom[st];
-        const int bin = b.slot_bin[st];
+        int bi[3];
+        unpack_bin(b.slot_bin[st], bi[0], bi[1], bi[2]);
         const int *wr = b.atom_wrap + ((size_t)tl.img * b.n + i) * 3;
         const T *Xi = (const T *)b.X + ((size_t)tl.img * b.rows + i) * 3;
-        const int bi[3] = {bin / (sc.nb[1] * sc.nb[2]), (bin / sc.nb[2]) % sc.nb[1], bin % sc.nb[2]};
         T4 o, lo;
         refresh_offset(sc, bp, Xi, wr, bi, o, lo);
         ((T4 *)b.slot_off)[st] = o;
@@ -603,16 +496,19 @@ __global__ void k_bin_order(const ImgRef *imgs, BandDev *bands) {
     const int *start = b.bin_start + (size_t)r.img * (b.nbins_cap + 1);
     const size_t base = (size_t)r.img * b.n;
     const int *un = b.slot_unsorted + base;
+    const int nb1 = b.sc[r.img].nb[1], nb2 = b.sc[r.img].nb[2];
     for (int bin = blockIdx.x * blockDim.x + threadIdx.x; bin < nbins;
          bin += gridDim.x * blockDim.x) {
         const int s0 = start[bin], s1 = start[bin + 1];
+        const int b0 = bin / (nb1 * nb2), b1 = (bin / nb2) % nb1;
+        const int pb = pack_bin(b0, b1, bin % nb2);
         for (int p = s0; p < s1; ++p) {
             const int idx = un[p];
             int rk = 0;
             for (int q = s0; q < s1; ++q) rk += (un[q] < idx);
             const int dst = s0 + rk;
             b.slot_atom[base + dst] = idx;
-            b.slot_bin[base + dst] = bin;
+            b.slot_bin[base + dst] = pb;
             b.atom_slot[base + idx] = dst;
             ((T4 *)b.slot_off)[base + dst] = ((const T4 *)b.atom_off)[base + idx];
             ((T4 *)b.slot_off_lo)[base + dst] = ((const T4 *)b.atom_off_lo)[base + idx];

@@ -93,12 +93,16 @@ struct ImgScalars {
     long long evals;     // evaluations of this image slot
     float dfl[45];       // FP32: D hi, D lo, h hi, h lo (pairs), h0^-1 (cell list)
     float bvf[9];        // bv in FP32 (exact: bv has at most 20 significant bits)
+    float dhf[9];        // dh in FP32 (the offset refresh's wrap term)
+    float Dbif[9];       // FP32 inverse of Db (list reuse)
+    float skin_e, skin_nD;  // the cell's part of the reuse bound (skin_terms)
     int nb[3];           // bins per axis
     int m[3];            // stencil half width per axis
     int nbins;
     int rebuild;         // this evaluation rebuilds the cell list
     unsigned int done;   // row tiles of this image finished in band pass 1
-    int pad_done;
+    int cell_fresh;      // D, h, Omega and the bin vectors follow the current
+                         // lattice rows (set by the map-back and by the move)
 };
 
 struct TersoffParams {
@@ -186,6 +190,18 @@ template <> __host__ __device__ inline const TP<double> &tp_of<double>(const Ban
     return p.tpd;
 }
 
+// A bin's three indices in one int, 10 bits each (bin_grid keeps nb_a <=
+// 1024): the kernels that walk a slot's stencil unpack them with shifts
+// instead of dividing the linear index by the grid's extents.
+__host__ __device__ inline int pack_bin(int b0, int b1, int b2) {
+    return b0 | (b1 << 10) | (b2 << 20);
+}
+__host__ __device__ inline void unpack_bin(int p, int &b0, int &b1, int &b2) {
+    b0 = p & 1023;
+    b1 = (p >> 10) & 1023;
+    b2 = p >> 20;
+}
+
 struct BandDev {
     int n, rows, ncap, nbins_cap;
     int atpi, rtpi;      // atom tiles / row tiles per image
@@ -198,6 +214,8 @@ struct BandDev {
     int *bin_tsum;       // [ncap][tsum_cap] scan tile sums / prefixes
     int tsum_cap;
     int *atom_bin, *atom_rank, *slot_unsorted, *slot_atom, *slot_bin, *atom_slot;  // [ncap][n]
+    // (atom_bin: linear bin index; slot_bin: the bin's three indices packed
+    // by pack_bin)
     void *atom_off, *slot_off;   // [ncap][n] x 4 T (x, y, z, pad): offsets, leading part
     void *atom_off_lo, *slot_off_lo;  // [ncap][n] x 4 T: offset - leading part
     // neighbour-list reuse: positions and periodic wraps at the last build
@@ -340,6 +358,159 @@ __device__ inline double ldet(double a, double c) {
     return lget(t, 0) + lget(t, 1) + lget(t, 2);
 }
 
+// The cell of an image from its lattice rows (Sec. II.C), one warp: lane l
+// passes entry (l % 9) / 3, (l % 9) % 3 of X_lat (lanes 9..31 mirror, as
+// for every lane-parallel 3x3 below).  B = X_lat / c and D = B^(1/2), the
+// symmetric root, by the coupled Newton-Schulz iteration (Y -> B^(1/2),
+// Z -> B^(-1/2), B scaled into the iteration's convergence region first),
+// for the rotation-free filter; D = X_lat / c for the deformation gradient;
+// D = I with the filter off.  Then h = h0 D, h^-1 = D^-1 h0^-1 and
+// Omega = |det h|, written with D and D^-1 and their FP32 pairs into sc
+// (lanes 0..8; Omega by lane 0).  Returns false, with D = I, when B (or the
+// deformation gradient) is not positive definite.
+__device__ inline bool image_cell_warp(const BandParams *bp, double xlat, ImgScalars &sc) {
+    const Lane3 p;
+    const int lane = threadIdx.x & 31;
+    double D = p.eye(), Di = p.eye();
+    bool ok = true;
+    if (bp->filter) {
+        const double L = xlat * rcp64(bp->c);
+        if (bp->variant == 0) {
+            const double B = 0.5 * (L + ltrans(L, p));
+            const double C = lcof(B, p);
+            const double det = ldet(B, C);
+            // Sylvester's criterion: B00 > 0, the leading 2x2 minor (= C22) > 0, det > 0
+            ok = lget(B, 0) > 0.0 && lget(C, 8) > 0.0 && det > 0.0;
+            if (ok) {
+                // spectrum bracket [det / g^2, g], g = largest Gershgorin row bound
+                const double rs = fabs(lget(B, 3 * p.i)) + fabs(lget(B, 3 * p.i + 1)) +
+                                  fabs(lget(B, 3 * p.i + 2));
+                const double g = fmax(fmax(lget(rs, 0), lget(rs, 3)), lget(rs, 6));
+                const double ig = rcp64(g);
+                const double mu = 0.5 * (g + det * ig * ig);
+                double Y = B * rcp64(mu), Z = p.eye();
+                for (int it = 0; it < 40; ++it) {
+                    const double e = p.eye() - lmul(Z, Y, p);  // I - Z Y
+                    const double Tm = p.eye() + 0.5 * e;       // (3I - Z Y) / 2
+                    float dev = fabsf((float)e);
+                    for (int o = 16; o > 0; o >>= 1)
+                        dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+                    const double Y1 = lmul(Y, Tm, p), Z1 = lmul(Tm, Z, p);
+                    Y = Y1;
+                    Z = Z1;
+                    if (dev < 1e-9f) break;  // the last step took it to ~1e-18
+                }
+                const double rmu = sqrt64(mu);
+                D = 0.5 * (Y + ltrans(Y, p)) * rmu;
+                Di = 0.5 * (Z + ltrans(Z, p)) * rcp64(rmu);
+            }
+        } else {
+            const double C = lcof(L, p);
+            const double det = ldet(L, C);
+            ok = det > 0.0;
+            if (ok) {
+                D = L;
+                Di = ltrans(C, p) * rcp64(det);
+            }
+        }
+    }
+    if (!ok) D = Di = p.eye();
+    const double h = lmul(bp->h0[p.l], D, p);
+    const double hinv = lmul(Di, bp->h0inv[p.l], p);  // (h0 D)^-1 = D^-1 h0^-1
+    const double omega = fabs(ldet(h, lcof(h, p)));
+    if (lane < 9) {
+        sc.D[lane] = D;
+        sc.Dinv[lane] = Di;
+        sc.h[lane] = h;
+        sc.hinv[lane] = hinv;
+        // FP32 pairs of D and h and FP32 h0^-1 for the FP32 cell-list path
+        const float Dh = (float)D, hh = (float)h;
+        sc.dfl[lane] = Dh;
+        sc.dfl[9 + lane] = (float)(D - (double)Dh);
+        sc.dfl[18 + lane] = hh;
+        sc.dfl[27 + lane] = (float)(h - (double)hh);
+        sc.dfl[36 + lane] = (float)bp->h0inv[lane];
+    }
+    if (lane == 0) sc.omega = omega;
+    return ok;
+}
+
+// Bin vectors of the image's grid for its current cell, one entry per lane
+// (lanes 0..8; the whole warp calls): bv_a on a grid of q = 2^(e - 19),
+// 2^e >= max |h_a / nb_a|, so every sum of three products delta_a bv_a
+// (|delta| <= 7) is exact in FP32; dh = h - nb bv carries the (sub-1e-4 A)
+// quantisation to the periodic wrap.  Only the binade of max |h_a / nb_a|
+// matters; found in FP32 it can be one binade low by an ulp, and then
+// |bv| <= (2^19 + 1) q: three terms |delta| <= 7 still sum below 2^24 q.
+__device__ inline void bin_vectors_warp(ImgScalars &sc) {
+    const int lane = threadIdx.x & 31;
+    const int l = lane < 9 ? lane : 0, a = l / 3;
+    const int nba = sc.nb[a];
+    const double h = sc.h[l];
+    float bmax = lane < 9 ? fabsf((float)h / (float)nba) : 0.0f;
+    for (int o = 16; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+    const int e = ilogbf(bmax) + 1 - 19;
+    const double q = ldexp(1.0, e), iq = ldexp(1.0, -e);  // exact powers of two
+    const double v = q * rint(h * rcp64((double)nba) * iq);
+    if (lane < 9) {
+        sc.bv[l] = v;
+        sc.bvf[l] = (float)v;
+        sc.dh[l] = h - nba * v;
+        sc.dhf[l] = (float)(h - nba * v);
+    }
+}
+
+// upper bound of the spectral norm of a 3x3 matrix: the smaller of the
+// Frobenius norm and sqrt(|A|_1 |A|_inf), in FP32 and raised by 1e-6 to
+// stay a bound
+__device__ inline float norm2_bound(const float *A) {
+    float f = 0.0f, c1 = 0.0f, ci = 0.0f;
+    for (int i = 0; i < 3; ++i) {
+        float rs = 0.0f, cs = 0.0f;
+        for (int j = 0; j < 3; ++j) {
+            f += A[3 * i + j] * A[3 * i + j];
+            rs += fabsf(A[3 * i + j]);
+            cs += fabsf(A[3 * j + i]);
+        }
+        ci = fmaxf(ci, rs);
+        c1 = fmaxf(c1, cs);
+    }
+    return fminf(sqrtf(f), sqrtf(c1 * ci)) * 1.000001f;
+}
+
+// FP32 inverse of a 3x3 matrix (cofactors over the determinant)
+__device__ inline void inv3f(const float *m, float *o) {
+    const float c00 = m[4] * m[8] - m[5] * m[7], c01 = m[5] * m[6] - m[3] * m[8],
+                c02 = m[3] * m[7] - m[4] * m[6];
+    const float id = 1.0f / (m[0] * c00 + m[1] * c01 + m[2] * c02);
+    o[0] = c00 * id;
+    o[1] = (m[2] * m[7] - m[1] * m[8]) * id;
+    o[2] = (m[1] * m[5] - m[2] * m[4]) * id;
+    o[3] = c01 * id;
+    o[4] = (m[0] * m[8] - m[2] * m[6]) * id;
+    o[5] = (m[2] * m[3] - m[0] * m[5]) * id;
+    o[6] = c02 * id;
+    o[7] = (m[1] * m[6] - m[0] * m[7]) * id;
+    o[8] = (m[0] * m[4] - m[1] * m[3]) * id;
+}
+
+// The cell's part of the list-reuse bound (one thread): with M = D_b^-1 D - I
+// (D_b = D at the build), skin_e = |M|_2 bound and skin_nD = |D|_2 bound, in
+// FP32: M - I is small, so its FP32 rounding (~1e-7 absolute) moves the
+// bound by far less than the 1e-5 margins, which also cover the FP32 list
+// test and displacement.  D from its FP32 leading part, D_b^-1 from the
+// build (Dbif).
+__device__ inline void skin_terms(ImgScalars &sc) {
+    const float *D = sc.dfl;
+    float M[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            M[3 * i + j] = sc.Dbif[3 * i] * D[j] + sc.Dbif[3 * i + 1] * D[3 + j] +
+                           sc.Dbif[3 * i + 2] * D[6 + j] - (i == j ? 1.0f : 0.0f);
+    sc.skin_e = norm2_bound(M) * 1.00001f + 1e-6f;
+    sc.skin_nD = norm2_bound(D);
+}
+
 // FP64 sums of K values over `count` records (value k of record q at
 // rec[q * stride + k]) in a fixed order that needs few FP64 instructions (an
 // FP64 instruction occupies a warp's FP64 pipe for ~64 cycles here, so
@@ -373,6 +544,52 @@ __device__ inline double block_sum_records(const double *rec, int stride, int co
     double tot = 0.0;
     if (tid < K)
         for (int g = 0; g < G; ++g) tot += s_part[g * K + tid];
+    __syncthreads();
+    return tot;
+}
+
+// FP64 sums of K values over `count` records like block_sum_records, with
+// the loads in flight together: thread k + K g (g < G = NT / K) loads value
+// k of records g, g + G, ..., g + (U - 1) G at once and adds them in that
+// order (U G records per round trip instead of a chain of four), then the
+// G partial sums are added in H = 8 strided groups and the groups in
+// order.  The FP64 add count is the same; the round trips fall from
+// count / 4G to count / UG.  CG: loads bypass L1 (records written by other
+// blocks of the running kernel).  NT = blockDim.x; every thread calls.
+template <int K, int U, int NT, bool CG>
+__device__ inline double block_sum_records_wide(const double *rec, int stride, int count) {
+    constexpr int G = NT / K, H = 8;
+    static_assert(G >= H, "too few threads for the group sums");
+    __shared__ double s_part[G * K];
+    __shared__ double s_grp[H * K];
+    const int tid = threadIdx.x;
+    if (tid < K * G) {
+        const int k = tid % K, g = tid / K;
+        double v = 0.0;
+        for (int q0 = g; q0 < count; q0 += U * G) {
+            double w[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int q = q0 + u * G;
+                const double *p = rec + (size_t)q * stride + k;
+                w[u] = q < count ? (CG ? __ldcg(p) : *p) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) v += w[u];
+        }
+        s_part[g * K + k] = v;
+    }
+    __syncthreads();
+    if (tid < K * H) {
+        const int k = tid % K, h = tid / K;
+        double v = 0.0;
+        for (int g = h; g < G; g += H) v += s_part[g * K + k];
+        s_grp[h * K + k] = v;
+    }
+    __syncthreads();
+    double tot = 0.0;
+    if (tid < K)
+        for (int h = 0; h < H; ++h) tot += s_grp[h * K + tid];
     __syncthreads();
     return tot;
 }
@@ -525,6 +742,8 @@ __device__ inline double block_max_any(double v) {
 
 // threads of the per-image / per-band reduction kernels
 constexpr int RED_THREADS = 256;
+// threads of the per-image finalize (one block per image: wide record sums)
+constexpr int FIN_THREADS = 1024;
 
 // Copy a record between global and shared memory with all threads of the
 // block (8-byte words).  The per-image and per-band kernels read many fields
@@ -534,10 +753,24 @@ template <typename S>
 __device__ inline void stage_copy(S *dst, const S *src) {
     static_assert(sizeof(S) % 8 == 0, "record size must be a multiple of 8 bytes");
     static_assert(alignof(S) >= 8, "record must be 8-byte aligned for word copies");
+    // every word loaded before the first store (the compiler cannot tell
+    // the shared side from the global one, so interleaved copies would wait
+    // out one round trip per word); PER words per thread cover the record
+    // for any block of at least 32 threads
+    constexpr int NW = (int)(sizeof(S) / 8), PER = (NW + 31) / 32;
     const unsigned long long *s = (const unsigned long long *)src;
     unsigned long long *d = (unsigned long long *)dst;
-#pragma unroll 4
-    for (int k = threadIdx.x; k < (int)(sizeof(S) / 8); k += blockDim.x) d[k] = s[k];
+    unsigned long long w[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = threadIdx.x + k * blockDim.x;
+        w[k] = i < NW ? s[i] : 0ull;
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = threadIdx.x + k * blockDim.x;
+        if (i < NW) d[i] = w[k];
+    }
 }
 
 // ---- launchers (defined in the kernel translation units) ---------------
@@ -594,7 +827,8 @@ void launch_dots_reduce(const ImgRef *imgs, int count, BandDev *bands, cudaStrea
 void launch_shard_fire(BandDev *band, double P, double FF, double VV, double fmax2,
                        cudaStream_t s);
 template <typename T>
-void launch_fire_update(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
+void launch_fire_update(const Tile *tiles, int ntiles, const ImgRef *imgs, int nimg,
+                        BandDev *bands, cudaStream_t s);
 template <typename T>
 void launch_energy64(const Tile *tiles, int ntiles, const ImgRef *imgs, int nimg, BandDev *bands,
                      cudaStream_t s);

@@ -41,9 +41,9 @@ __device__ inline void for_neighbours64(const BandDev &b, int img, int t, const 
     const T4 *off = (const T4 *)b.slot_off + base;
     const T4 *offl = (const T4 *)b.slot_off_lo + base;
     const int *start = b.bin_start + (size_t)img * (b.nbins_cap + 1);
-    const int bin = b.slot_bin[base + t];
     const int nb0 = sc.nb[0], nb1 = sc.nb[1], nb2 = sc.nb[2];
-    const int b0 = bin / (nb1 * nb2), b1 = (bin / nb2) % nb1, b2 = bin % nb2;
+    int b0, b1, b2;
+    unpack_bin(b.slot_bin[base + t], b0, b1, b2);
     const T4 oi = off[t], oil = offl[t];
     // leading-part screen: its error (~1e-6 relative in FP32) is far inside
     // the 1e-3 margin; the FP64 test below decides
@@ -115,9 +115,8 @@ __device__ inline int list_vectors64(const BandDev &b, int img, int t, const Img
     const int *nslot = b.nbr_slot + (size_t)img * MAXN_TERSOFF * b.n;
     const int *ncode = b.nbr_code + (size_t)img * MAXN_TERSOFF * b.n;
     const int ne = b.nbr_cnt[base + t];
-    const int bin = b.slot_bin[base + t];
-    const int nb1 = sc.nb[1], nb2 = sc.nb[2];
-    const int bb[3] = {bin / (nb1 * nb2), (bin / nb2) % nb1, bin % nb2};
+    int bb[3];
+    unpack_bin(b.slot_bin[base + t], bb[0], bb[1], bb[2]);
     const T4 oi = off[t], oil = offl[t];
     int cnt = 0;
     for (int e = 0; e < ne; ++e) {

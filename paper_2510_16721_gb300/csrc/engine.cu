@@ -101,6 +101,26 @@ void batch_mark_dirty(cfneb_batch *bt);
 }
 
 // One band: its device buffers and host-side configuration.
+// A side stream and two events: inside a graph capture, work recorded on
+// the side stream after `a` runs beside the main stream until the main
+// stream waits on `b` (a fork and a join in the captured graph).
+struct Fork {
+    cudaStream_t s = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    void create() {
+        CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+    }
+    void destroy() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+        if (s) cudaStreamDestroy(s);
+        s = nullptr;
+        a = b = nullptr;
+    }
+};
+
 struct cfneb_band {
     int n = 0, N = 0, ncap = 0, precision = 0, kind = 0;
     size_t ts = 8;               // sizeof(T)
@@ -123,6 +143,7 @@ struct cfneb_band {
     // stream ordering
     cudaStream_t user = nullptr, s = nullptr;
     cudaStream_t s_body = nullptr;   // captures the conditional list-rebuild body
+    Fork fork;                       // the finalize beside the force gather (graphs)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     // launch tables (device) and their sizes
     Tile *d_atiles = nullptr;    // atom tiles of the interior images
@@ -132,8 +153,8 @@ struct cfneb_band {
     Tile *d_scratch_tiles = nullptr;   // tables for ad-hoc image sets
     ImgRef *d_scratch_imgs = nullptr;
     int n_atiles = 0, n_rtiles = 0, n_imgs = 0;
-    // graph
-    cudaGraphExec_t gexec = nullptr;
+    // graphs: one step, and GRAPH_STEPS steps
+    cudaGraphExec_t gexec = nullptr, gexec_n = nullptr;
     bool graph_dirty = true;
     // profiling
     bool prof = false;
@@ -169,11 +190,13 @@ void free_band(cfneb_band *b) {
     for (void *p : b->allocs) cudaFree(p);
     b->allocs.clear();
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->gexec_n) cudaGraphExecDestroy(b->gexec_n);
     for (auto e : b->prof_ev) cudaEventDestroy(e);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->s) cudaStreamDestroy(b->s);
     if (b->s_body) cudaStreamDestroy(b->s_body);
+    b->fork.destroy();
     if (b->h_bp) cudaFreeHost(b->h_bp);
     delete b;
 }
@@ -271,6 +294,7 @@ struct LaunchSet {
     int force_rebuild = 0;               // rebuild every listed image's cell list
     int lj_minb = kLjMinb, ters_minb = kTersMinb;  // force kernel variants
     cudaStream_t s_body = nullptr;       // captures the conditional rebuild body
+    const Fork *fork = nullptr;          // side stream and events for the finalize
 };
 
 // optional CUDA-event bracketing of every launch (profiling)
@@ -387,16 +411,38 @@ void enqueue_eval_set(const LaunchSet &ls, Launcher &L, bool forces = true) {
         L.pre(K_TERS_PARTIALS);
         launch_tersoff_partials<T>(ls.atiles_ters, ls.n_ters, d, s, ls.ters_minb);
         L.post(K_TERS_PARTIALS);
-        L.pre(K_TERS_GATHER); launch_tersoff_gather<T>(ls.atiles_ters, ls.n_ters, d, s);
-        L.post(K_TERS_GATHER);
     }
     if (ls.n_nep) {
         L.pre(K_NEP_PARTIALS); launch_nep_partials<T>(ls.atiles_nep, ls.n_nep, d, s);
         L.post(K_NEP_PARTIALS);
+    }
+    // Inside a graph the finalize (tile sums into E and V, the lattice
+    // force) needs only the partials' records, not the gathered atom
+    // forces: it runs on the side stream beside the gathers, joined before
+    // the band passes.
+    CK(cudaStreamIsCapturing(s, &cst));
+    const bool fork = ls.fork && (ls.n_ters || ls.n_nep) && !L.prof &&
+                      cst == cudaStreamCaptureStatusActive;
+    if (fork) {
+        CK(cudaEventRecord(ls.fork->a, s));
+        CK(cudaStreamWaitEvent(ls.fork->s, ls.fork->a, 0));
+        launch_image_finalize<T>(ls.imgs, ls.nimg, d, ls.fork->s);
+        CK(cudaEventRecord(ls.fork->b, ls.fork->s));
+    }
+    if (ls.n_ters) {
+        L.pre(K_TERS_GATHER); launch_tersoff_gather<T>(ls.atiles_ters, ls.n_ters, d, s);
+        L.post(K_TERS_GATHER);
+    }
+    if (ls.n_nep) {
         L.pre(K_TERS_GATHER); launch_tersoff_gather<T>(ls.atiles_nep, ls.n_nep, d, s);
         L.post(K_TERS_GATHER);
     }
-    L.pre(K_IMAGE_FINALIZE); launch_image_finalize<T>(ls.imgs, ls.nimg, d, s); L.post(K_IMAGE_FINALIZE);
+    if (fork) {
+        CK(cudaStreamWaitEvent(s, ls.fork->b, 0));
+    } else {
+        L.pre(K_IMAGE_FINALIZE); launch_image_finalize<T>(ls.imgs, ls.nimg, d, s);
+        L.post(K_IMAGE_FINALIZE);
+    }
 }
 
 template <typename T>
@@ -406,7 +452,7 @@ void enqueue_step_set(const LaunchSet &ls, Launcher &L) {
     enqueue_eval_set<T>(ls, L);
     L.pre(K_BAND_DOTS); launch_band_dots<T>(ls.rtiles, ls.n_rtiles, d, s); L.post(K_BAND_DOTS);
     L.pre(K_NEB_FORCE); launch_neb_force<T>(ls.rtiles, ls.n_rtiles, d, s); L.post(K_NEB_FORCE);
-    L.pre(K_FIRE_UPDATE); launch_fire_update<T>(ls.rtiles, ls.n_rtiles, d, s);
+    L.pre(K_FIRE_UPDATE); launch_fire_update<T>(ls.rtiles, ls.n_rtiles, ls.imgs, ls.nimg, d, s);
     L.post(K_FIRE_UPDATE);
 }
 
@@ -445,6 +491,7 @@ LaunchSet band_set(cfneb_band *b, const ImgRef *imgs, int nimg, const Tile *atil
     ls.nbands = 1;
     ls.max_bins = b->dv.nbins_cap;
     ls.s_body = b->s_body;
+    ls.fork = &b->fork;
     if (b->minb > 0) {
         if (b->kind == CFNEB_LJ) ls.lj_minb = b->minb;
         if (b->kind == CFNEB_TERSOFF) ls.ters_minb = b->minb;
@@ -510,6 +557,30 @@ cudaGraphExec_t capture(cudaStream_t s, F enq) {
     return ge;
 }
 
+// Steps per multi-step graph: n steps run as n / GRAPH_STEPS launches of a
+// graph of GRAPH_STEPS captured steps and n % GRAPH_STEPS of the one-step
+// graph, so that the gap between two graph launches is paid once per
+// GRAPH_STEPS steps.  Every step of a graph is the same captured sequence
+// (the kernels read the band's state from device memory).
+constexpr int GRAPH_STEPS = 8;
+
+void drop_graphs(cudaGraphExec_t &one, cudaGraphExec_t &many) {
+    if (one) CK(cudaGraphExecDestroy(one));
+    if (many) CK(cudaGraphExecDestroy(many));
+    one = many = nullptr;
+}
+
+template <typename F>
+void launch_steps(cudaGraphExec_t &one, cudaGraphExec_t &many, cudaStream_t s, int n, F enq) {
+    if (n >= GRAPH_STEPS && !many)
+        many = capture(s, [&](Launcher &L) {
+            for (int k = 0; k < GRAPH_STEPS; ++k) enq(L);
+        });
+    if (n % GRAPH_STEPS && !one) one = capture(s, enq);
+    for (int i = 0; i < n / GRAPH_STEPS; ++i) CK(cudaGraphLaunch(many, s));
+    for (int i = 0; i < n % GRAPH_STEPS; ++i) CK(cudaGraphLaunch(one, s));
+}
+
 void steps(cfneb_band *b, int n) {
     if (n <= 0 || b->N < 3) return;
     const LaunchSet ls = band_step_set(b);
@@ -521,15 +592,11 @@ void steps(cfneb_band *b, int n) {
         for (int i = 0; i < n; ++i) profiled(b->s, b->prof_ev, b->prof_ms, b->prof_n, enq);
         return;
     }
-    if (b->graph_dirty || !b->gexec) {
-        if (b->gexec) {
-            CK(cudaGraphExecDestroy(b->gexec));
-            b->gexec = nullptr;
-        }
-        b->gexec = capture(b->s, enq);
+    if (b->graph_dirty) {
+        drop_graphs(b->gexec, b->gexec_n);
         b->graph_dirty = false;
     }
-    for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(b->gexec, b->s));
+    launch_steps(b->gexec, b->gexec_n, b->s, n, enq);
 }
 
 // evaluate an arbitrary list of images of the band (endpoints, new images)
@@ -801,6 +868,7 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
         b->c = (double)b->n;
     CK(cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&b->s_body, cudaStreamNonBlocking));
+    b->fork.create();
     CK(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
     CK(cudaMallocHost((void **)&b->h_bp, sizeof(BandParams)));
@@ -1122,6 +1190,7 @@ double autotune_band(cfneb_band *b, int steps) {
 struct cfneb_batch {
     int precision = 0;
     cudaStream_t s_body = nullptr;   // captures the conditional list-rebuild body
+    Fork fork;                       // the finalize beside the force gather (graphs)
     int lj_minb = 0, ters_minb = 0;  // force kernel variants (0: the default)
     unsigned long long budget = 0, used = 0;
     cudaStream_t user = nullptr, s = nullptr;
@@ -1137,7 +1206,7 @@ struct cfneb_batch {
     size_t cap_bands = 0, cap_tiles = 0, cap_imgs = 0;
     LaunchSet ls;
     bool dirty = true;
-    cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t gexec = nullptr, gexec_n = nullptr;  // one step, GRAPH_STEPS steps
     bool prof = false;
     double prof_ms[K_COUNT]{};
     long long prof_n[K_COUNT]{};
@@ -1240,12 +1309,10 @@ void batch_rebuild(cfneb_batch *bt) {
     ls.nbands = (int)ids.size();
     ls.max_bins = max_bins;
     ls.s_body = bt->s_body;
+    ls.fork = &bt->fork;
     if (bt->lj_minb) ls.lj_minb = bt->lj_minb;
     if (bt->ters_minb) ls.ters_minb = bt->ters_minb;
-    if (bt->gexec) {
-        CK(cudaGraphExecDestroy(bt->gexec));
-        bt->gexec = nullptr;
-    }
+    drop_graphs(bt->gexec, bt->gexec_n);
     bt->dirty = false;
 }
 
@@ -1262,8 +1329,7 @@ void batch_steps(cfneb_batch *bt, int n) {
         for (int i = 0; i < n; ++i) profiled(bt->s, bt->prof_ev, bt->prof_ms, bt->prof_n, enq);
         return;
     }
-    if (!bt->gexec) bt->gexec = capture(bt->s, enq);
-    for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(bt->gexec, bt->s));
+    launch_steps(bt->gexec, bt->gexec_n, bt->s, n, enq);
 }
 
 // per-member (moves, converged, status, fmax, ci, N)
@@ -1325,6 +1391,7 @@ void batch_free(cfneb_batch *bt) {
         b->own_s = nullptr;
     }
     if (bt->gexec) cudaGraphExecDestroy(bt->gexec);
+    if (bt->gexec_n) cudaGraphExecDestroy(bt->gexec_n);
     if (bt->d_bands) cudaFree(bt->d_bands);
     if (bt->d_tiles) cudaFree(bt->d_tiles);
     if (bt->d_imgs) cudaFree(bt->d_imgs);
@@ -1336,6 +1403,7 @@ void batch_free(cfneb_batch *bt) {
     if (bt->ev_out) cudaEventDestroy(bt->ev_out);
     if (bt->s) cudaStreamDestroy(bt->s);
     if (bt->s_body) cudaStreamDestroy(bt->s_body);
+    bt->fork.destroy();
     delete bt;
 }
 
@@ -1916,9 +1984,11 @@ int cfneb_shard_move(cfneb_band *b, const double *sums) {
         enter(b);
         launch_shard_fire(b->d_self, sums[0], sums[1], sums[2], sums[3], b->s);
         if (b->precision == CFNEB_MIXED)
-            launch_fire_update<float>(b->d_rtiles, b->n_rtiles, b->d_self, b->s);
+            launch_fire_update<float>(b->d_rtiles, b->n_rtiles, b->d_imgs, b->n_imgs, b->d_self,
+                                      b->s);
         else
-            launch_fire_update<double>(b->d_rtiles, b->n_rtiles, b->d_self, b->s);
+            launch_fire_update<double>(b->d_rtiles, b->n_rtiles, b->d_imgs, b->n_imgs, b->d_self,
+                                       b->s);
         CK(cudaGetLastError());
         read_params(b);
         leave(b);
@@ -2028,6 +2098,7 @@ int cfneb_batch_create(int32_t precision, uint64_t budget_bytes, void *cuda_stre
     try {
         CK(cudaStreamCreateWithFlags(&bt->s, cudaStreamNonBlocking));
         CK(cudaStreamCreateWithFlags(&bt->s_body, cudaStreamNonBlocking));
+        bt->fork.create();
         CK(cudaEventCreateWithFlags(&bt->ev_in, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&bt->ev_out, cudaEventDisableTiming));
         bt->prof_ev.resize(2 * 64);

@@ -84,8 +84,8 @@ __device__ inline void lj_walk(const typename Vec4<T>::type *off, const int *sta
     using T4 = typename Vec4<T>::type;
     const int nb0 = s_nb[0], nb1 = s_nb[1], nb2 = s_nb[2];
     const int m0 = s_m[0], m1 = s_m[1], m2 = s_m[2];
-    const int b2 = (int)oi.w;
-    const int b0 = bin / (nb1 * nb2), b1 = (bin / nb2) % nb1;
+    int b0, b1, b2;
+    unpack_bin(bin, b0, b1, b2);
     const bool row_ok = (b2 - m2 >= 0) && (b2 + m2 < nb2);
     for (int d0 = -m0; d0 <= m0; ++d0) {
         int w0 = b0 + d0, t0 = 0;

@@ -226,7 +226,7 @@ extern "C" int cfneb_lj_evaluate_noalloc(const double *d_positions, int32_t n_at
     const double *d_h1 = (const double *)(base + O_H1);
     k_noalloc_init<<<32, 256, 0, s>>>(dv, bp, h1, dv.atpi);
     launch_setup<double>(d_positions, d_positions, nullptr, n, NA_IMAGES, d_band, s, d_h1);
-    launch_mapback<double>(d_img, 1, d_band, 0, s);
+    launch_mapback<double>(d_img, 1, d_band, 1, s);  // forced: the scratch record is reused
     launch_bin_assign<double>(d_tiles, dv.atpi, d_band, s);
     launch_bin_scan(d_img, 1, NA_MAX_BINS, d_band, s, 0);
     launch_bin_scan(d_img, 1, NA_MAX_BINS, d_band, s, 1);

@@ -233,9 +233,9 @@ __device__ inline int ters_collect_list(T rl2, const BandDev &b, int img, int t,
     int *nslot = b.nbr_slot + (size_t)img * MAXN_TERSOFF * n;
     int *ncode = b.nbr_code + (size_t)img * MAXN_TERSOFF * n;
     const T rc2_screen = rl2 * (T)1.00001;
-    const int bin = b.slot_bin[base + t];
     const int nb1 = s_nb[1], nb2 = s_nb[2];
-    const int b0 = bin / (nb1 * nb2), b1 = (bin / nb2) % nb1, b2 = bin % nb2;
+    int b0, b1, b2;
+    unpack_bin(b.slot_bin[base + t], b0, b1, b2);
     const T4 oi = off[t];
     int total = 0;
     for (int d0 = -s_m[0]; d0 <= s_m[0]; ++d0) {
@@ -447,8 +447,8 @@ __device__ inline void ters_load(const TP<T> &q, const BandDev &b, int img, int 
     const T4 *offl = (const T4 *)b.slot_off_lo + base;
     const int *nslot = b.nbr_slot + (size_t)img * MAXN_TERSOFF * n;
     const int *ncode = b.nbr_code + (size_t)img * MAXN_TERSOFF * n;
-    const int bin = b.slot_bin[base + t];
-    const int b0 = bin / (s_nb[1] * s_nb[2]), b1 = (bin / s_nb[2]) % s_nb[1], b2 = bin % s_nb[2];
+    int b0, b1, b2;
+    unpack_bin(b.slot_bin[base + t], b0, b1, b2);
     const T4 oi = off[t], oil = offl[t];
     for (int k = 0; k < cnt; ++k) {
         const int qs = nslot[(size_t)k * n + t];
@@ -488,10 +488,8 @@ __device__ inline void ters_load_reg(const TP<T> &q, const BandDev &b, int img, 
     const T4 *offl = (const T4 *)b.slot_off_lo + base;
     const int *nslot = b.nbr_slot + (size_t)img * MAXN_TERSOFF * n;
     const int *ncode = b.nbr_code + (size_t)img * MAXN_TERSOFF * n;
-    const int bin = b.slot_bin[base + t];
-    const int nb12 = s_nb[1] * s_nb[2];
-    const int b0 = bin / nb12, rem = bin - b0 * nb12;
-    const int b1 = rem / s_nb[2], b2 = rem - b1 * s_nb[2];
+    int b0, b1, b2;
+    unpack_bin(b.slot_bin[base + t], b0, b1, b2);
     const T4 oi = off[t], oil = offl[t];
     int qs[RMAX], code[RMAX];
 #pragma unroll
