@@ -41,23 +41,25 @@ constexpr int NEP_OCR = 0, NEP_OCA = NEP_NR * NEP_K, NEP_OW0 = NEP_OCA + NEP_NA 
               NEP_OB0 = NEP_OW0 + NEP_H * NEP_ND, NEP_OW1 = NEP_OB0 + NEP_H,
               NEP_OB1 = NEP_OW1 + NEP_H;
 constexpr int LJ_LIST_MAX_ATOMS = 1 << 17;  // LJ list entries index 17-bit slots
-// Grid of the kernels that only do work for images rebuilding their lists:
-// a fixed grid (8 blocks per SM of the current device) strides over the
-// tiles, so a step in which most images keep their lists costs a few reads
-// per block instead of a block per tile.
-inline int gated_grid() {
+// SMs of the current device (cached per device)
+inline int sm_count() {
     static int cached[64] = {0};
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152 * 8;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
     if (!cached[dev]) {
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
             sms <= 0)
             sms = 152;
-        cached[dev] = sms * 8;
+        cached[dev] = sms;
     }
     return cached[dev];
 }
+// Grid of the kernels that only do work for images rebuilding their lists:
+// a fixed grid (8 blocks per SM of the current device) strides over the
+// tiles, so a step in which most images keep their lists costs a few reads
+// per block instead of a block per tile.
+inline int gated_grid() { return sm_count() * 8; }
 
 // potential kinds of BandParams::kind (the values of include/cfneb.h)
 constexpr int KIND_LJ = 0, KIND_TERSOFF = 1, KIND_NEP = 2;
