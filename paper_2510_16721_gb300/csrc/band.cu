@@ -509,19 +509,29 @@ template <typename T>
 __device__ inline void lattice_move_warp(const ImgRef r, BandDev *bands) {
     BandDev &b = bands[r.band];
     const BandParams *bp = b.bp;
-    if (!bp->move) return;  // uniform over the warp
-    const int lane = threadIdx.x & 31;
+    ImgScalars &sc = b.sc[r.img];
+    const int lane = threadIdx.x & 31, l = lane % 9;
+    // every load first (one round trip, under the row tiles' traffic)
+    const int move = bp->move;
     const T cv = (T)bp->cv, cf = (T)bp->cf, dt = (T)bp->dt, ms = (T)bp->maxstep;
-    T x[3] = {0, 0, 0};
+    const double skin = bp->skin;
+    const CellIn k = cell_in(bp);
+    const int nba = sc.nb[l / 3];
+    float dbi[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) dbi[q] = lane == 0 ? sc.Dbif[q] : 0.0f;
+    T x[3] = {0, 0, 0}, v[3] = {0, 0, 0}, fn[3] = {0, 0, 0};
+    const size_t o = ((size_t)r.img * b.rows + b.n + (lane < 3 ? lane : 0)) * 3;
     if (lane < 3) {  // lane q moves lattice row n + q
-        const size_t o = ((size_t)r.img * b.rows + b.n + lane) * 3;
-        T v[3], fn[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             x[c] = ((const T *)b.X)[o + c];
             v[c] = ((const T *)b.v)[o + c];
             fn[c] = ((const T *)b.Fneb)[o + c];
         }
+    }
+    if (!move) return;  // uniform over the warp
+    if (lane < 3) {
         fire_row(x, v, fn, cv, cf, dt, ms);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -529,49 +539,45 @@ __device__ inline void lattice_move_warp(const ImgRef r, BandDev *bands) {
             ((T *)b.v)[o + c] = v[c];
         }
     }
-    // entry (l / 3, l % 3), l = lane % 9, of the moved lattice rows
-    const int l = lane % 9;
+    // entry (l / 3, l % 3) of the moved lattice rows
     const T a0 = __shfl_sync(0xffffffffu, x[0], l / 3);
     const T a1 = __shfl_sync(0xffffffffu, x[1], l / 3);
     const T a2 = __shfl_sync(0xffffffffu, x[2], l / 3);
     const T xl = l % 3 == 0 ? a0 : (l % 3 == 1 ? a1 : a2);
-    ImgScalars &sc = b.sc[r.img];
-    const bool ok = image_cell_warp(bp, (double)xl, sc);
+    double h;
+    const bool ok = image_cell_warp(k, (double)xl, sc, h);
     if (!ok && lane == 0) atomicOr(&b.bp->status, ST_NOT_SPD);
     __syncwarp();
-    bin_vectors_warp(sc);
+    bin_vectors_warp(sc, nba, h);
+    __syncwarp();
     if (lane == 0) {
-        if (bp->skin > 0.0) skin_terms(sc);  // for the next list decision
+        if (skin > 0.0) skin_terms(sc, dbi);  // for the next list decision
         sc.cell_fresh = 1;
     }
 }
 
-// Pass 3: blocks 0 .. nimg-1 move the lattice rows of imgs[block] (one warp
-// each, scheduled first so that their FP64 cell work overlaps the rest);
-// the other blocks move the atom rows of their row tile, 4 rows a thread,
-// and with a skin record the tile's largest displacement since the last
-// list build.
+// Pass 3 on one row tile: the atom rows move, 4 rows a thread (lattice
+// rows: lattice_move_warp; padding rows stay zero), and with a skin the
+// tile records its largest displacement since the last list build.
 template <typename T>
-__global__ void __launch_bounds__(RTHREADS, sizeof(T) == 4 ? 4 : 2)
-    k_fire_update(const Tile *tiles, const ImgRef *imgs, int nimg, BandDev *bands) {
-    using T4 = typename Vec4<T>::type;
-    if ((int)blockIdx.x < nimg) {
-        if (threadIdx.x < 32) lattice_move_warp<T>(imgs[blockIdx.x], bands);
-        return;
-    }
-    Tile tl = tiles[blockIdx.x - nimg];
+__device__ inline void move_tile(const Tile tl, BandDev *bands) {
     BandDev &b = bands[tl.band];
     const BandParams *bp = b.bp;
-    if (!bp->move) return;  // uniform over the block
-    // FIRE scalars in T, converted once per block
+    // FIRE scalars in T, converted once per tile
     __shared__ T s_k[4];
+    __shared__ int s_move;
     if (threadIdx.x == 0) {
+        s_move = bp->move;
         s_k[0] = (T)bp->cv;
         s_k[1] = (T)bp->cf;
         s_k[2] = (T)bp->dt;
         s_k[3] = (T)bp->maxstep;
     }
     __syncthreads();
+    if (!s_move) {  // uniform over the block
+        __syncthreads();
+        return;
+    }
     const T cv = s_k[0], cf = s_k[1], dt = s_k[2], ms = s_k[3];
     const int r0 = tl.t * RTILE + RPT * (int)threadIdx.x;
     const int n = b.n;
@@ -581,10 +587,11 @@ __global__ void __launch_bounds__(RTHREADS, sizeof(T) == 4 ? 4 : 2)
         // only atom rows move here (lattice rows: lattice_move_warp;
         // padding rows stay zero)
         const size_t o0 = (tl.img * (size_t)b.rows + (size_t)r0) * 3;
-        T x[12], v[12], fn[12];
+        T x[12], v[12], fn[12], rf[12];
         ld12((const T *)b.X + o0, x);
         ld12((const T *)b.v + o0, v);
         ld12((const T *)b.Fneb + o0, fn);
+        if (b.ref_X) ld12((const T *)b.ref_X + o0, rf);  // with the others: one round trip
 #pragma unroll
         for (int q = 0; q < RPT; ++q)
             if (r0 + q < n) fire_row(x + 3 * q, v + 3 * q, fn + 3 * q, cv, cf, dt, ms);
@@ -602,13 +609,11 @@ __global__ void __launch_bounds__(RTHREADS, sizeof(T) == 4 ? 4 : 2)
                     }
         }
         if (b.ref_X) {
-            const T4 *ref = (const T4 *)b.ref_X + (size_t)tl.img * n;
 #pragma unroll
             for (int q = 0; q < RPT; ++q) {
                 if (r0 + q < n) {
-                    const T4 rf = ref[r0 + q];
-                    const T ex = x[3 * q] - rf.x, ey = x[3 * q + 1] - rf.y,
-                            ez = x[3 * q + 2] - rf.z;
+                    const T ex = x[3 * q] - rf[3 * q], ey = x[3 * q + 1] - rf[3 * q + 1],
+                            ez = x[3 * q + 2] - rf[3 * q + 2];
                     d2 = fmax(d2, ex * ex + ey * ey + ez * ez);
                 }
             }
@@ -627,6 +632,24 @@ __global__ void __launch_bounds__(RTHREADS, sizeof(T) == 4 ? 4 : 2)
             b.skin_part[(size_t)tl.img * b.atpi + tl.t] = __fsqrt_ru(to_float_ru(m));
         }
     }
+    __syncthreads();  // the shared scalars are reused by the block's next tile
+}
+
+// Pass 3: blocks 0 .. nimg-1 move the lattice rows of imgs[block] (one warp
+// each, scheduled first so that their FP64 cell work overlaps the rest);
+// every other block moves the atom rows of FU_TILES consecutive row tiles
+// in turn (a grid that fits on the GPU at once: the tiles' loads are not
+// split into a second wave that starts behind the first one's stores).
+constexpr int FU_TILES = 2;
+template <typename T>
+__global__ void __launch_bounds__(RTHREADS, sizeof(T) == 4 ? 4 : 2)
+    k_fire_update(const Tile *tiles, int ntiles, const ImgRef *imgs, int nimg, BandDev *bands) {
+    if ((int)blockIdx.x < nimg) {
+        if (threadIdx.x < 32) lattice_move_warp<T>(imgs[blockIdx.x], bands);
+        return;
+    }
+    const int k0 = ((int)blockIdx.x - nimg) * FU_TILES;
+    for (int k = k0; k < k0 + FU_TILES && k < ntiles; ++k) move_tile<T>(tiles[k], bands);
 }
 
 // X_img <- 1/2 (X_{img-1} + X_{img+1}) (image insertion; all rows)
@@ -772,7 +795,8 @@ template <typename T>
 void launch_fire_update(const Tile *tiles, int ntiles, const ImgRef *imgs, int nimg,
                         BandDev *bands, cudaStream_t s) {
     if (ntiles + nimg <= 0) return;
-    k_fire_update<T><<<nimg + ntiles, RTHREADS, 0, s>>>(tiles, imgs, nimg, bands);
+    k_fire_update<T><<<nimg + (ntiles + FU_TILES - 1) / FU_TILES, RTHREADS, 0, s>>>(
+        tiles, ntiles, imgs, nimg, bands);
 }
 template <typename T>
 void launch_midpoint(BandDev *band, int img, int rows, cudaStream_t s) {

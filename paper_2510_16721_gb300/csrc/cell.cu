@@ -123,7 +123,7 @@ __device__ void skin_decide_one(const BandParams *bp, int nbins_cap, ImgScalars 
             Db[k] = (float)sc.D[k];
         }
         inv3f(Db, sc.Dbif);
-        skin_terms(sc);
+        skin_terms(sc, sc.Dbif);
         sc.builds += 1;
     }
     sc.rebuild = rebuild ? 1 : 0;
@@ -153,9 +153,10 @@ __global__ void __launch_bounds__(32) k_mapback(const ImgRef *imgs, int count, B
     ImgScalars &sc = s_sc;
     const int lane = threadIdx.x & 31;
     const bool fresh = !force && !bp->stale && sc.cell_fresh;
+    double h = 0.0;
     if (!fresh) {
         const T *Xl = (const T *)b.X + ((size_t)r.img * b.rows + b.n) * 3;
-        const bool ok = image_cell_warp(bp, (double)Xl[lane % 9], sc);
+        const bool ok = image_cell_warp(cell_in(bp), (double)Xl[lane % 9], sc, h);
         if (!ok && lane == 0) atomicOr(&b.bp->status, ST_NOT_SPD);
     }
     // largest displacement since the last build (skin > 0), in FP32 (a max
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(32) k_mapback(const ImgRef *imgs, int count, B
     __syncwarp();
     if (lane == 0) {
         sc.cell_fresh = 1;
-        if (!fresh && bp->skin > 0.0) skin_terms(sc);
+        if (!fresh && bp->skin > 0.0) skin_terms(sc, sc.Dbif);
         if (bp->skin <= 0.0) {
             // no skin: the cell list is rebuilt at every evaluation
             bin_grid(bp, b.nbins_cap, sc.h, sc.omega, sc);
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(32) k_mapback(const ImgRef *imgs, int count, B
     __syncwarp();
     // the grid (new or kept) follows the cell; a move that left the cell
     // also left the bin vectors of the kept grid
-    if (!fresh || sc.rebuild) bin_vectors_warp(sc);
+    if (!fresh || sc.rebuild) bin_vectors_warp(sc, sc.nb[(lane % 9) / 3], sc.h[lane % 9]);
     __syncwarp();
     stage_copy(&b.sc[r.img], &s_sc);
 }
@@ -366,13 +367,11 @@ __global__ void __launch_bounds__(TILE) k_bin_assign(const Tile *tiles, BandDev 
     refresh_offset(sc, bp, Xi, wrap, bi, o, lo);
     ((T4 *)b.atom_off)[ai] = o;
     ((T4 *)b.atom_off_lo)[ai] = lo;
-    if (b.ref_X) {  // a skin: reference state of the build
-        T4 x;
-        x.x = Xi[0];
-        x.y = Xi[1];
-        x.z = Xi[2];
-        x.w = (T)0;
-        ((T4 *)b.ref_X)[ai] = x;
+    if (b.ref_X) {  // a skin: reference state of the build (row layout of X)
+        T *ref = (T *)b.ref_X + ((size_t)tl.img * b.rows + i) * 3;
+        ref[0] = Xi[0];
+        ref[1] = Xi[1];
+        ref[2] = Xi[2];
         for (int a = 0; a < 3; ++a) b.atom_wrap[ai * 3 + a] = wrap[a];
     }
 }

@@ -221,7 +221,7 @@ struct BandDev {
     void *atom_off, *slot_off;   // [ncap][n] x 4 T (x, y, z, pad): offsets, leading part
     void *atom_off_lo, *slot_off_lo;  // [ncap][n] x 4 T: offset - leading part
     // neighbour-list reuse: positions and periodic wraps at the last build
-    void *ref_X;         // [ncap][n] x 4 T: R~ at the build (atom order)
+    void *ref_X;         // [ncap][rows][3] T: R~ at the build (the layout of X)
     int *atom_wrap;      // [ncap][n][3]: floor(s) at the build
     float *skin_part;    // [ncap][atpi]: per-row-tile max displacement (rtpi used)
     // per-slot neighbour lists: Tersoff (slot, code) pairs of MAXN_TERSOFF
@@ -370,14 +370,26 @@ __device__ inline double ldet(double a, double c) {
 // Omega = |det h|, written with D and D^-1 and their FP32 pairs into sc
 // (lanes 0..8; Omega by lane 0).  Returns false, with D = I, when B (or the
 // deformation gradient) is not positive definite.
-__device__ inline bool image_cell_warp(const BandParams *bp, double xlat, ImgScalars &sc) {
+// The band constants the cell needs, as one lane's share (entry l = lane %
+// 9 of h0 and h0^-1): loaded together, ahead of the FP64 work.
+struct CellIn {
+    int filter, variant;
+    double c, h0, h0inv;
+};
+__device__ inline CellIn cell_in(const BandParams *bp) {
+    const int l = (int)(threadIdx.x & 31) % 9;
+    return {bp->filter, bp->variant, bp->c, bp->h0[l], bp->h0inv[l]};
+}
+
+__device__ inline bool image_cell_warp(const CellIn &k, double xlat, ImgScalars &sc,
+                                       double &h_out) {
     const Lane3 p;
     const int lane = threadIdx.x & 31;
     double D = p.eye(), Di = p.eye();
     bool ok = true;
-    if (bp->filter) {
-        const double L = xlat * rcp64(bp->c);
-        if (bp->variant == 0) {
+    if (k.filter) {
+        const double L = xlat * rcp64(k.c);
+        if (k.variant == 0) {
             const double B = 0.5 * (L + ltrans(L, p));
             const double C = lcof(B, p);
             const double det = ldet(B, C);
@@ -417,8 +429,8 @@ __device__ inline bool image_cell_warp(const BandParams *bp, double xlat, ImgSca
         }
     }
     if (!ok) D = Di = p.eye();
-    const double h = lmul(bp->h0[p.l], D, p);
-    const double hinv = lmul(Di, bp->h0inv[p.l], p);  // (h0 D)^-1 = D^-1 h0^-1
+    const double h = lmul(k.h0, D, p);
+    const double hinv = lmul(Di, k.h0inv, p);  // (h0 D)^-1 = D^-1 h0^-1
     const double omega = fabs(ldet(h, lcof(h, p)));
     if (lane < 9) {
         sc.D[lane] = D;
@@ -431,9 +443,10 @@ __device__ inline bool image_cell_warp(const BandParams *bp, double xlat, ImgSca
         sc.dfl[9 + lane] = (float)(D - (double)Dh);
         sc.dfl[18 + lane] = hh;
         sc.dfl[27 + lane] = (float)(h - (double)hh);
-        sc.dfl[36 + lane] = (float)bp->h0inv[lane];
+        sc.dfl[36 + lane] = (float)k.h0inv;
     }
     if (lane == 0) sc.omega = omega;
+    h_out = h;
     return ok;
 }
 
@@ -444,12 +457,12 @@ __device__ inline bool image_cell_warp(const BandParams *bp, double xlat, ImgSca
 // quantisation to the periodic wrap.  Only the binade of max |h_a / nb_a|
 // matters; found in FP32 it can be one binade low by an ulp, and then
 // |bv| <= (2^19 + 1) q: three terms |delta| <= 7 still sum below 2^24 q.
-__device__ inline void bin_vectors_warp(ImgScalars &sc) {
+// nba = sc.nb[(lane % 9) / 3] and h = sc.h[lane % 9] are passed in (lanes
+// 9..31 mirror lane % 9; only lanes 0..8 store).
+__device__ inline void bin_vectors_warp(ImgScalars &sc, int nba, double h) {
     const int lane = threadIdx.x & 31;
-    const int l = lane < 9 ? lane : 0, a = l / 3;
-    const int nba = sc.nb[a];
-    const double h = sc.h[l];
-    float bmax = lane < 9 ? fabsf((float)h / (float)nba) : 0.0f;
+    const int l = lane % 9;
+    float bmax = fabsf((float)h / (float)nba);
     for (int o = 16; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
     const int e = ilogbf(bmax) + 1 - 19;
     const double q = ldexp(1.0, e), iq = ldexp(1.0, -e);  // exact powers of two
@@ -501,14 +514,14 @@ __device__ inline void inv3f(const float *m, float *o) {
 // FP32: M - I is small, so its FP32 rounding (~1e-7 absolute) moves the
 // bound by far less than the 1e-5 margins, which also cover the FP32 list
 // test and displacement.  D from its FP32 leading part, D_b^-1 from the
-// build (Dbif).
-__device__ inline void skin_terms(ImgScalars &sc) {
+// build (Dbi: sc.Dbif, or a copy of it loaded ahead).
+__device__ inline void skin_terms(ImgScalars &sc, const float *Dbi) {
     const float *D = sc.dfl;
     float M[9];
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j)
-            M[3 * i + j] = sc.Dbif[3 * i] * D[j] + sc.Dbif[3 * i + 1] * D[3 + j] +
-                           sc.Dbif[3 * i + 2] * D[6 + j] - (i == j ? 1.0f : 0.0f);
+            M[3 * i + j] = Dbi[3 * i] * D[j] + Dbi[3 * i + 1] * D[3 + j] +
+                           Dbi[3 * i + 2] * D[6 + j] - (i == j ? 1.0f : 0.0f);
     sc.skin_e = norm2_bound(M) * 1.00001f + 1e-6f;
     sc.skin_nD = norm2_bound(D);
 }

@@ -979,7 +979,7 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
     d.atom_off_lo = dalloc(b, na * 4 * b->ts);
     d.slot_off_lo = dalloc(b, na * 4 * b->ts);
     if (skin > 0.0) {
-        d.ref_X = dalloc(b, na * 4 * b->ts);
+        d.ref_X = dalloc(b, vec);  // the row layout of X (padding rows stay zero)
         d.atom_wrap = (int *)dalloc(b, na * 3 * sizeof(int));
         d.skin_part = (float *)dalloc(b, nc * d.atpi * sizeof(float));
     }
@@ -1026,6 +1026,7 @@ cfneb_band *create(const cfneb_structure *A, const cfneb_structure *B, int N,
     b->d_scratch_imgs = (ImgRef *)dalloc(b, nc * sizeof(ImgRef));
     CK(cudaMemsetAsync(d.bin_count, 0, nc * d.nbins_cap * sizeof(int), b->s));
     CK(cudaMemsetAsync(d.v, 0, vec, b->s));
+    if (d.ref_X) CK(cudaMemsetAsync(d.ref_X, 0, vec, b->s));
     CK(cudaMemsetAsync(d.Fneb, 0, vec, b->s));
     CK(cudaMemsetAsync(d.F, 0, vec, b->s));
     CK(cudaMemsetAsync(d.sc, 0, nc * sizeof(ImgScalars), b->s));
