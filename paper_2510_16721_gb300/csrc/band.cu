@@ -95,11 +95,11 @@ template <> struct Acc<float> {
         add(o.s);
         c = __fadd_rn(c, o.c);
     }
-    __device__ void shfl_xor(int o) {
+    __device__ Acc shfl(int o) const {  // the partner lane's pair
         Acc q;
         q.s = __shfl_xor_sync(0xffffffffu, s, o);
         q.c = __shfl_xor_sync(0xffffffffu, c, o);
-        add(q);
+        return q;
     }
     __device__ double value() const { return (double)s + (double)c; }
 };
@@ -107,27 +107,51 @@ template <> struct Acc<double> {
     double s = 0.0;
     __device__ void add(double p) { s += p; }
     __device__ void add(const Acc &o) { s += o.s; }
-    __device__ void shfl_xor(int o) { s += __shfl_xor_sync(0xffffffffu, s, o); }
+    __device__ Acc shfl(int o) const {
+        Acc q;
+        q.s = __shfl_xor_sync(0xffffffffu, s, o);
+        return q;
+    }
     __device__ double value() const { return s; }
 };
 
-// Block totals of K accumulators (fixed order: warp butterfly, then warps
-// 0..3 in turn); lane k < K of warp 0 stores total k to dst[k] in FP64.
+// Block totals of K accumulators in a fixed order: a transposing butterfly
+// within each warp (at each level a lane keeps half of its values and adds
+// its partner's copy of them, so 16 values take 31 exchanges instead of 80,
+// and lane 2j ends with value j), then warps 0..7 in turn.  Thread 0 stores
+// the totals to dst[0..K-1] in FP64 and fences them for the block that
+// finishes the image (one thread's stores: one fence).
 template <int K, typename T>
-__device__ inline void block_acc_store(Acc<T> (&a)[K], double *dst) {
-    static_assert(K <= 32, "one lane per value");
-    __shared__ Acc<T> red[RTHREADS / 32][K];
+__device__ inline void block_acc_store(Acc<T> (&v)[K], double *dst) {
+    static_assert(K <= 16, "values are padded to 16");
+    __shared__ Acc<T> red[RTHREADS / 32][16];
+    __shared__ double s_tot[16];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    Acc<T> a[16];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        for (int o = 16; o > 0; o >>= 1) a[k].shfl_xor(o);
-        if (lane == 0) red[w][k] = a[k];
+    for (int k = 0; k < 16; ++k) a[k] = k < K ? v[k] : Acc<T>();
+#pragma unroll
+    for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < h; ++k) {
+            const Acc<T> send = hi ? a[k] : a[k + h];
+            Acc<T> keep = hi ? a[k + h] : a[k];
+            keep.add(send.shfl(o));
+            a[k] = keep;
+        }
     }
+    a[0].add(a[0].shfl(1));
+    if ((lane & 1) == 0) red[w][lane >> 1] = a[0];
     __syncthreads();
     if (threadIdx.x < K) {
         Acc<T> t = red[0][threadIdx.x];
         for (int q = 1; q < RTHREADS / 32; ++q) t.add(red[q][threadIdx.x]);
-        dst[threadIdx.x] = t.value();
+        s_tot[threadIdx.x] = t.value();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < K; ++k) dst[k] = s_tot[k];
         __threadfence();  // visible to the block that finishes the image
     }
     __syncthreads();
