@@ -568,7 +568,7 @@ def run_ours(args, wl_name):
                                      else "Tersoff 1988 C"),
                        "cell_filter": "off (fixed cell)" if wl["kind"] == "lj_small"
                        else "rotation-free (B)",
-                       "l2": "working set > 129 MB L2, no flush", "graph": "CUDA graph per step",
+                       "l2": "working set > 129 MB L2, no flush", "graph": "CUDA graphs of 8 steps",
                        "parallelism": "replicas x%d" % ws},
             "roofline": roof, "kernel_share": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "fp64_plain": fp64, "lists": lists,
@@ -770,7 +770,7 @@ def batch_line(args, workload, nsteps, warmup, dist, with_fp64=True, with_cpu=Tr
                        "cell_filter": "rotation-free (B), lattice scale J",
                        "bin_width": "autotuned per class",
                        "l2": "working set > 129 MB L2, no flush",
-                       "graph": "one CUDA graph per batch step",
+                       "graph": "CUDA graphs of 8 batch steps",
                        "parallelism": "replicas x%d" % ws},
             "roofline": roof, "kernel_share": {k: round(v[0] / total, 4)
                                                for k, v in prof.items() if v[1]},
