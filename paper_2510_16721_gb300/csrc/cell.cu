@@ -327,13 +327,19 @@ __device__ inline void bin_of(const ImgScalars &sc, const BandParams *, const fl
     }
 }
 
+// In a graph (has_cond), the first tile of every image that rebuilds also
+// switches on the conditional node that holds the rebuild kernels (its
+// value is reset to 0 at every launch of the graph).
 template <typename T>
-__global__ void __launch_bounds__(TILE) k_bin_assign(const Tile *tiles, BandDev *bands) {
+__global__ void __launch_bounds__(TILE) k_bin_assign(const Tile *tiles, BandDev *bands,
+                                                     cudaGraphConditionalHandle cond,
+                                                     int has_cond) {
     using T4 = typename Vec4<T>::type;
     Tile tl = tiles[blockIdx.x];
     BandDev &b = bands[tl.band];
     const ImgScalars &sc = b.sc[tl.img];
     const BandParams *bp = b.bp;
+    if (has_cond && sc.rebuild && tl.t == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 1u);
     if (!sc.rebuild) {
         // keep the bins of the build: thread = slot, offset from the centre
         // of the slot's bin at the current position (unwrapped as at the build)
@@ -537,9 +543,10 @@ void launch_mapback(const ImgRef *imgs, int count, BandDev *bands, int force, cu
     k_mapback<T><<<count, 32, 0, s>>>(imgs, count, bands, force);
 }
 template <typename T>
-void launch_bin_assign(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s) {
+void launch_bin_assign(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s,
+                       cudaGraphConditionalHandle cond, int has_cond) {
     if (ntiles <= 0) return;
-    k_bin_assign<T><<<ntiles, TILE, 0, s>>>(tiles, bands);
+    k_bin_assign<T><<<ntiles, TILE, 0, s>>>(tiles, bands, cond, has_cond);
 }
 void launch_bin_scan(const ImgRef *imgs, int count, int max_bins, BandDev *bands,
                      cudaStream_t s, int part) {
@@ -569,30 +576,12 @@ void launch_cartesian(const ImgRef *imgs, int count, int max_n, BandDev *bands, 
 
 #define CFNEB_INST(T)                                                                     \
     template void launch_mapback<T>(const ImgRef *, int, BandDev *, int, cudaStream_t);  \
-    template void launch_bin_assign<T>(const Tile *, int, BandDev *, cudaStream_t);      \
+    template void launch_bin_assign<T>(const Tile *, int, BandDev *, cudaStream_t,       \
+                                       cudaGraphConditionalHandle, int);                 \
     template void launch_bin_order<T>(const ImgRef *, int, int, BandDev *, cudaStream_t); \
     template void launch_cartesian<T>(const ImgRef *, int, int, BandDev *, cudaStream_t);
 CFNEB_INST(float)
 CFNEB_INST(double)
 #undef CFNEB_INST
-
-// Whether any listed image rebuilds its cell list this step: switches the
-// conditional graph node that holds the rebuild kernels (one thread block;
-// the only setter of the condition)
-__global__ void k_any_rebuild(const ImgRef *imgs, int count, BandDev *bands,
-                              cudaGraphConditionalHandle cond) {
-    int any = 0;
-    for (int k = threadIdx.x; k < count; k += blockDim.x) {
-        const ImgRef r = imgs[k];
-        any |= bands[r.band].sc[r.img].rebuild;
-    }
-    any = __syncthreads_or(any);
-    if (threadIdx.x == 0) cudaGraphSetConditional(cond, any ? 1u : 0u);
-}
-
-void launch_any_rebuild(const ImgRef *imgs, int count, BandDev *bands,
-                        cudaGraphConditionalHandle cond, cudaStream_t s) {
-    k_any_rebuild<<<1, 256, 0, s>>>(imgs, count, bands, cond);
-}
 
 }  // namespace cfneb

@@ -794,12 +794,11 @@ __device__ inline void stage_copy(S *dst, const S *src) {
 // since the last build come from the last move, per row tile)
 template <typename T>
 void launch_mapback(const ImgRef *imgs, int count, BandDev *bands, int force, cudaStream_t s);
+// bins or offsets; with has_cond also sets `cond` (a conditional graph
+// node's handle, default 0) to 1 when a listed image rebuilds its cell list
 template <typename T>
-void launch_bin_assign(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
-// sets `cond` (a conditional graph node's handle) to whether any listed
-// image rebuilds its cell list in this step
-void launch_any_rebuild(const ImgRef *imgs, int count, BandDev *bands,
-                        cudaGraphConditionalHandle cond, cudaStream_t s);
+void launch_bin_assign(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s,
+                       cudaGraphConditionalHandle cond = 0, int has_cond = 0);
 // part 0: tile sums, 1: scan of the tile sums, 2: final per-bin scan
 void launch_bin_scan(const ImgRef *imgs, int count, int max_bins, BandDev *bands,
                      cudaStream_t s, int part);

@@ -356,21 +356,27 @@ void enqueue_eval_set(const LaunchSet &ls, Launcher &L, bool forces = true) {
     // (k_fire_update); then map-back and the list decision
     L.pre(K_MAPBACK); launch_mapback<T>(ls.imgs, ls.nimg, d, ls.force_rebuild, s);
     L.post(K_MAPBACK);
-    L.pre(K_BIN_ASSIGN); launch_bin_assign<T>(ls.atiles, ls.n_atiles, d, s); L.post(K_BIN_ASSIGN);
     // the cell-list and neighbour-list rebuild: inside a graph capture it
     // goes into the body of a conditional node that runs only in steps
-    // where some image rebuilds (most steps keep every list); outside a
-    // capture its kernels run and skip the images that keep their lists
+    // where some image rebuilds (most steps keep every list; bin_assign
+    // switches the node on); outside a capture its kernels run and skip the
+    // images that keep their lists
     cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(s, &cst));
-    if (cst == cudaStreamCaptureStatusActive && ls.s_body && !L.prof) {
+    const bool cond_node = cst == cudaStreamCaptureStatusActive && ls.s_body && !L.prof;
+    cudaGraphConditionalHandle cond = 0;
+    if (cond_node) {
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &graph, nullptr, nullptr, nullptr));
+        CK(cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault));
+    }
+    L.pre(K_BIN_ASSIGN);
+    launch_bin_assign<T>(ls.atiles, ls.n_atiles, d, s, cond, cond_node ? 1 : 0);
+    L.post(K_BIN_ASSIGN);
+    if (cond_node) {
         cudaGraph_t graph = nullptr;
         const cudaGraphNode_t *deps = nullptr;
         size_t nd = 0;
-        CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &graph, &deps, nullptr, &nd));
-        cudaGraphConditionalHandle cond;
-        CK(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
-        launch_any_rebuild(ls.imgs, ls.nimg, d, cond, s);
         CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &graph, &deps, nullptr, &nd));
         cudaGraphNodeParams cp = {};
         cp.type = cudaGraphNodeTypeConditional;
@@ -457,11 +463,12 @@ void enqueue_step_set(const LaunchSet &ls, Launcher &L) {
 }
 
 // launches of a step when it rebuilds lists (the graph's conditional node
-// skips the 5 cell-list and 1-2 neighbour-list kernels in other steps); the
-// +1 is the kernel that sets the condition
+// skips the 5 cell-list and 1-2 neighbour-list kernels in other steps):
+// map-back, bin_assign and the 5 list kernels, the force kernels, the
+// finalize and the three band passes
 int launches_in_set(const LaunchSet &ls) {
     return 7 + (ls.n_lj ? 2 : 0) + (ls.n_ljc ? 1 : 0) + (ls.n_ters ? 4 : 0) + (ls.n_nep ? 4 : 0) +
-           1 + 3 + 1;
+           1 + 3;
 }
 
 LaunchSet band_set(cfneb_band *b, const ImgRef *imgs, int nimg, const Tile *atiles, int nat) {

@@ -225,7 +225,7 @@ def test_large_lj_band_sampled_forces(g, oracle_mod, reps, lists):
     for prec, tol, nstep in ((g.MIXED, 1e-4, 6), (g.FP64, 1e-10, 0)):
         gb = gpu_band(g, R0, h0, R1, h1, 5, g.lj_potential(), k=1.0, dt=0.01,
                       cell_filter=False, precision=prec)
-        assert gb.launches_per_step() == (14 if lists else 13)
+        assert gb.launches_per_step() == (13 if lists else 12)
         gb.step(nstep)
         st = gb.get_state()
         gb.step(1)
