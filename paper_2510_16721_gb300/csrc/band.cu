@@ -27,9 +27,9 @@
 //                   the last list build (the next step's reuse test).  One
 //                   warp per image moves its lattice rows and computes the
 //                   new cell for the next map-back, beside the row tiles.
-// "Last" blocks are found with completion counters (a fence, then an atomic
-// increment); the sums they form read the other blocks' records in a fixed
-// order, so results do not depend on block scheduling.
+// "Last" blocks are found with completion counters (an acquire-release
+// atomic increment); the sums they form read the other blocks' records in a
+// fixed order, so results do not depend on block scheduling.
 #include "common.cuh"
 
 namespace cfneb {
@@ -119,8 +119,7 @@ template <> struct Acc<double> {
 // within each warp (at each level a lane keeps half of its values and adds
 // its partner's copy of them, so 16 values take 31 exchanges instead of 80,
 // and lane 2j ends with value j), then warps 0..7 in turn.  Thread 0 stores
-// the totals to dst[0..K-1] in FP64 and fences them for the block that
-// finishes the image (one thread's stores: one fence).
+// the totals to dst[0..K-1] in FP64.
 template <int K, typename T>
 __device__ inline void block_acc_store(Acc<T> (&v)[K], double *dst) {
     static_assert(K <= 16, "values are padded to 16");
@@ -150,26 +149,34 @@ __device__ inline void block_acc_store(Acc<T> (&v)[K], double *dst) {
         s_tot[threadIdx.x] = t.value();
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    // thread 0 stores the record: its increment of the image's counter
+    // (last_arrival) publishes it to the block that finishes the image
+    if (threadIdx.x == 0)
         for (int k = 0; k < K; ++k) dst[k] = s_tot[k];
-        __threadfence();  // visible to the block that finishes the image
-    }
     __syncthreads();
 }
 
 // true in every thread of the one block that arrives last (counter reaches
-// total); that block also resets the counter for the next launch
+// total); that block also resets the counter for the next launch.  Writes
+// the other blocks must see are thread 0's, made before the call
+// (thread 0's increment is an acquire-release atomic at GPU scope: its
+// release publishes the record thread 0 stored before it, its acquire in
+// the last block orders the reads of the other blocks' records after it,
+// and the barrier passes that order to the block's other threads)
+__device__ inline unsigned atom_add_acq_rel(unsigned int *p, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
 __device__ inline bool last_arrival(unsigned int *counter, unsigned int total) {
     __shared__ int s_last;
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned int prev = atomicAdd(counter, 1u);
+        const unsigned int prev = atom_add_acq_rel(counter, 1u);
         s_last = prev + 1u == total;
         if (s_last) *counter = 0u;
     }
     __syncthreads();
-    if (s_last) __threadfence();
     return s_last != 0;
 }
 
