@@ -724,44 +724,57 @@ __global__ void __launch_bounds__(TILE) k_ters_reverse(const Tile *tiles, int nt
 
 template <typename T>
 __global__ void __launch_bounds__(TILE) k_ters_gather(const Tile *tiles, BandDev *bands) {
-    Tile tl = tiles[blockIdx.x];
-    BandDev &b = bands[tl.band];
-    // D in T, converted once per block (a conversion from FP64 is an FP64
-    // instruction: per thread they would dominate this short kernel)
-    __shared__ T s_D[9];
-    if (threadIdx.x < 9) s_D[threadIdx.x] = (T)b.sc[tl.img].D[threadIdx.x];
-    __syncthreads();
+    using T4 = typename Vec4<T>::type;
+    const Tile tl = tiles[blockIdx.x];
+    const BandDev &b = bands[tl.band];
     const int n = b.n;
     const int t = tl.t * TILE + threadIdx.x;
     if (t >= n) return;
     const size_t base = (size_t)tl.img * n;
     const int *nslot = b.nbr_slot + (size_t)tl.img * MAXN_TERSOFF * n;
     const unsigned char *nrev = b.nbr_rev + (size_t)tl.img * MAXN_TERSOFF * n;
-    using T4 = typename Vec4<T>::type;
     const T4 *nP = (const T4 *)b.nbr_P + (size_t)tl.img * MAXN_TERSOFF * n;
-    T fx = 0, fy = 0, fz = 0;
     const int cnt = b.nbr_cnt[base + t];
-    // f^ij = P_ij - P_ji, in list order; the first GK entries with every
-    // index loaded before the partials they point to
-    constexpr int GK = 6;
+    const int atom = b.slot_atom[base + t];
+    // f^ij = P_ij - P_ji, in list order.  The first GK entries: their
+    // indices, then every partial they point to, are loaded before any is
+    // used (two round trips for the atom, not one per entry).
+    constexpr int GK = 4;
     int qs[GK], k2[GK];
 #pragma unroll
     for (int k = 0; k < GK; ++k) {
         qs[k] = k < cnt ? nslot[(size_t)k * n + t] : 0;
         k2[k] = k < cnt ? nrev[(size_t)k * n + t] : 255;
     }
+    T ax[GK], ay[GK], az[GK], rx[GK], ry[GK], rz[GK];
 #pragma unroll
     for (int k = 0; k < GK; ++k) {
-        if (k >= cnt) break;
-        const T4 a = nP[(size_t)k * n + t];
-        fx += a.x;
-        fy += a.y;
-        fz += a.z;
+        ax[k] = ay[k] = az[k] = rx[k] = ry[k] = rz[k] = (T)0;
+        if (k < cnt) {
+            const T4 a = nP[(size_t)k * n + t];
+            ax[k] = a.x;
+            ay[k] = a.y;
+            az[k] = a.z;
+        }
         if (k2[k] != 255) {
             const T4 r = nP[(size_t)k2[k] * n + qs[k]];
-            fx -= r.x;
-            fy -= r.y;
-            fz -= r.z;
+            rx[k] = r.x;
+            ry[k] = r.y;
+            rz[k] = r.z;
+        }
+    }
+    T fx = 0, fy = 0, fz = 0;
+#pragma unroll
+    for (int k = 0; k < GK; ++k) {
+        if (k < cnt) {
+            fx += ax[k];
+            fy += ay[k];
+            fz += az[k];
+            if (k2[k] != 255) {
+                fx -= rx[k];
+                fy -= ry[k];
+                fz -= rz[k];
+            }
         }
     }
     for (int k = GK; k < cnt; ++k) {
@@ -778,10 +791,15 @@ __global__ void __launch_bounds__(TILE) k_ters_gather(const Tile *tiles, BandDev
             fz -= p.z;
         }
     }
-    const T g0 = fx * s_D[0] + fy * s_D[1] + fz * s_D[2];
-    const T g1 = fx * s_D[3] + fy * s_D[4] + fz * s_D[5];
-    const T g2 = fx * s_D[6] + fy * s_D[7] + fz * s_D[8];
-    const int atom = b.slot_atom[base + t];
+    // D in T: the FP32 leading part k_mapback / the move stored (FP32
+    // bands), or D itself (FP64 bands); no conversion in this kernel
+    const ImgScalars &sc = b.sc[tl.img];
+    T D[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) D[k] = sizeof(T) == 4 ? (T)sc.dfl[k] : (T)sc.D[k];
+    const T g0 = fx * D[0] + fy * D[1] + fz * D[2];
+    const T g1 = fx * D[3] + fy * D[4] + fz * D[5];
+    const T g2 = fx * D[6] + fy * D[7] + fz * D[8];
     T *F = (T *)b.F + ((size_t)tl.img * b.rows + atom) * 3;
     F[0] = g0;
     F[1] = g1;
