@@ -301,7 +301,8 @@ int cfneb_evaluate(const cfneb_structure *structures, int32_t count,
 /* ---- batches: many bands, one launch per kernel --------------------------
  * A batch steps all its member bands together: every kernel of a step is
  * launched once over the tiles of all members (uneven atom and image counts
- * mixed), the whole step is one captured CUDA graph, and each band keeps its
+ * mixed), the steps run as captured CUDA graphs (eight steps per graph; a
+ * remainder as one-step graphs), and each band keeps its
  * own FIRE state, convergence test and refinement.  Results of a band do not
  * depend on the other members (reductions use fixed per-band slots).
  * Members must share the precision; LJ, Tersoff and NEP-style bands may be
