@@ -573,6 +573,8 @@ def run_ours(args, wl_name):
             "roofline": roof, "kernel_share": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "fp64_plain": fp64, "lists": lists,
             "rooflines": roofs, "tuning": tuning}
+    if not args.no_converged and wl_name == "tersoff_graphite_hexdiamond_98304":
+        line["converged_barrier"] = converged_line(g, torch, stream)
     if not args.no_batch and wl_name == "tersoff_graphite_hexdiamond_98304":
         # the batched workload (64 uneven LJ bands, one launch per kernel per
         # step), measured after the main line's numbers are taken
@@ -585,6 +587,42 @@ def run_ours(args, wl_name):
     if dist is not None:
         dist.barrier()
     return 0
+
+
+def converged_line(g, torch, stream):
+    """A band relaxed to convergence in both precisions: the Tersoff diamond
+    vacancy hop between relaxed endpoints in 98,303 atoms (16 x 24 x 32
+    cells), 11 images, adaptive refinement between 8 and 24 images, cell
+    filter on, fmax 0.05 eV/A.  Reports each precision's moves, final image
+    count, converged barrier (FP64 energies) and the time from the relax call
+    to its return with the band resident, and the barrier gap."""
+    import numpy as np
+    import cfneb_inputs as ci
+    R0, h0, R1, h1 = ci.diamond_vacancy_hop_relaxed((16, 24, 32))
+    out = {"workload": "tersoff_diamond_vacancy_98303", "atoms": len(R0), "images": 11,
+           "adaptive": [8, 24], "cell_filter": "rotation-free (B)", "fmax": 0.05,
+           "fire": {"dt": 0.05, "dt_max": 0.2, "maxstep": 0.1}, "k_spring": 0.1}
+    for prec in ("mixed", "fp64"):
+        opt = g.default_options()
+        opt.k_spring, opt.climb = 0.1, 1
+        opt.precision = g.MIXED if prec == "mixed" else g.FP64
+        opt.dt, opt.dt_max, opt.maxstep = 0.05, 0.2, 0.1
+        opt.adaptive, opt.n_min, opt.n_max = 1, 8, 24
+        cf = g.CellFilter(1, g.ROTFREE_B, 0.0, 0.0)
+        b = g.create_band((R0, h0), (R1, h1), 11, g.tersoff_potential(), cf, opt,
+                          stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps, conv = b.relax(0.05, 6000)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        E = b.get_path()["energies"]
+        out[prec] = {"moves": steps, "converged": bool(conv), "final_images": b.n_images,
+                     "barrier_eV": float(np.max(E) - E[0]), "seconds": sec}
+        b.destroy()
+    out["barrier_gap_eV"] = abs(out["mixed"]["barrier_eV"] - out["fp64"]["barrier_eV"])
+    out["time_ratio_fp64_over_mixed"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    return out
 
 
 def make_lj_band(g, bc, precision, stream, skin=None):
@@ -784,8 +822,8 @@ def _serve_options(g, spec, precision):
     opt.climb = 1
     opt.precision = precision
     opt.dt = spec["dt"]
-    opt.dt_max = 10 * spec["dt"]
-    opt.maxstep = 0.2
+    opt.dt_max = spec.get("dt_max", 10 * spec["dt"])
+    opt.maxstep = spec.get("maxstep", 0.2)
     opt.n_max = spec["n_images"]
     opt.bin_scale = 0.0
     return opt
@@ -894,8 +932,8 @@ def run_serve(args):
             "config": {"workload": args.workload, "rate_per_s": wl["rate"],
                        "window_s": args.serve_window, "budget_gb": wl["budget_gb"],
                        "atoms": "log-uniform 500-50,000", "images": "uniform 7-16",
-                       "mix": "LJ FCC vacancy 50%, Tersoff C graphite->hex-diamond 25%, "
-                              "Tersoff C diamond vacancy 25%",
+                       "mix": "LJ FCC vacancy 50% (strained end cell), Tersoff C diamond "
+                              "vacancy between relaxed endpoints 50% (odd image counts)",
                        "fmax": 0.05, "max_steps": args.serve_max_steps, "precision": "mixed",
                        "cell_filter": "rotation-free (B)",
                        "steps": "not applicable: a request stream, value = served "
@@ -925,6 +963,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batch", action="store_true",
                     help="leave the batched LJ workload out of the default line")
+    ap.add_argument("--no-converged", action="store_true",
+                    help="leave the band relaxed to convergence out of the default line")
     ap.add_argument("--skin", type=float, default=None,
                     help="neighbour-list skin of the LJ batch bands (default: the library's)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

@@ -98,6 +98,54 @@ def diamond_vacancy_hop(a=DIAMOND_A, reps=(2, 2, 2)):
     return R0, h.copy(), R1, h.copy()
 
 
+def diamond_vacancy_hop_relaxed(reps=(4, 4, 4)):
+    """Vacancy hop in cubic diamond (Tersoff carbon) between relaxed
+    endpoints, in an n1 x n2 x n3 conventional supercell (each n >= 4).
+
+    The displacement field of both endpoints, relaxed around the vacancy in
+    a 4 x 4 x 4 cell by oracle/make_diamond_vacancy_endpoints.py, is placed
+    around site 0 of the supercell: every atom within the 4 x 4 x 4 box
+    centred on the vacancy (boundary included) takes the stored displacement
+    of its site, atoms farther out stay on their ideal sites.  At 4 x 4 x 4
+    the endpoints are the stored relaxed ones.  Atom order: the supercell's
+    sites in lattice order without site 0; the hopping atom is the nearest
+    neighbour the stored hop names.  Returns (R0, h, R1, h).
+    """
+    with open(os.path.join(_DATA, "tersoff_c_diamond_vacancy_4x4x4.json")) as f:
+        d = json.load(f)
+    a = d["a"]
+    small = np.array(d["reps"]) * 4  # box side in units of a/4
+    half = small // 2
+    off_s = np.array(d["offset"])
+    key = lambda u: tuple(int(x) for x in (np.asarray(u) + half) % small - half)
+    field = {key(u): (np.array(p0), np.array(p1))
+             for u, p0, p1 in zip(off_s, d["d0"], d["d1"])}
+    hop_key = key(off_s[d["hop"]])
+    R, h = diamond(a, *reps)
+    if any(r < s // 4 for r, s in zip(reps, small)):
+        raise ValueError("supercell smaller than the stored relaxed cell")
+    site = R[0]
+    s = (R - site) @ np.linalg.inv(h)
+    s -= np.round(s)
+    off = np.rint(s @ h / (a / 4.0)).astype(int)
+    off = off[1:]
+    R0 = R[1:].copy()
+    R1 = R0.copy()
+    hop = None
+    for m in np.flatnonzero(np.all(np.abs(off) <= half, axis=1)):
+        ku = key(off[m])
+        d0, d1 = field[ku]
+        R0[m] += d0
+        if ku == hop_key and hop is None:
+            hop = m
+            R1[m] = site + d1
+        else:
+            R1[m] += d1
+    if hop is None:
+        raise ValueError("hopping atom not found")
+    return R0, h.copy(), R1, h.copy()
+
+
 def strained_cell(h, seed, amplitude=0.02):
     """h (I + eps) with eps symmetric, entries uniform in [-amplitude, amplitude]."""
     rng = np.random.default_rng(seed)
@@ -297,10 +345,13 @@ def serve_requests(seed=5, rate=20.0, window=60.0, n_lo=500, n_hi=50000, img_lo=
     """Request stream for the serving loop: Poisson arrivals at `rate` per
     second over `window` seconds; each request is an LJ or a Tersoff carbon
     band (even odds).  LJ: FCC vacancy hop, end cell strained by up to
-    lj_strain.  Tersoff: graphite -> hexagonal diamond tiled, or a cubic
-    diamond vacancy hop (even odds).  Atom counts log-uniform in
-    [n_lo, n_hi], image counts (endpoints included) uniform in
-    [img_lo, img_hi].  Returns specs; build_request() makes the structures.
+    lj_strain, image counts (endpoints included) uniform in [img_lo, img_hi].
+    Tersoff: cubic-diamond vacancy hop between relaxed endpoints
+    (diamond_vacancy_hop_relaxed, at least 4 x 4 x 4 cells), an odd image
+    count in the same range (the hop is mirror-symmetric: an odd count puts
+    one image on the saddle), FIRE dt 0.05, dt_max 0.2, maxstep 0.1.  Atom
+    counts log-uniform in [n_lo, n_hi].  Returns specs; build_request()
+    makes the structures.
     """
     rng = np.random.default_rng(seed)
     arrivals = poisson_arrivals(seed, rate, window)
@@ -317,18 +368,17 @@ def serve_requests(seed=5, rate=20.0, window=60.0, n_lo=500, n_hi=50000, img_lo=
             specs.append(dict(id=q, arrival=float(t), kind="lj_vacancy", reps=reps,
                               n_images=n_images, k=1.0, dt=0.01, fmax=fmax,
                               strain_seed=seed * 100000 + q, strain=lj_strain))
-        elif rng.integers(0, 2) == 0:
-            specs.append(dict(id=q, arrival=float(t), kind="tersoff_graphite_hexdiamond",
-                              reps=_orthohex_reps(target), n_images=n_images, k=0.1, dt=0.1,
-                              fmax=fmax))
         else:
-            m = max(8, int(round(target / 8.0)))
+            m = max(64, int(round(target / 8.0)))
             reps = near_cubic_factors(m)
-            while min(reps) < 2:
+            while min(reps) < 4:
                 m += 1
                 reps = near_cubic_factors(m)
+            if n_images % 2 == 0:
+                n_images = n_images + 1 if n_images < img_hi else n_images - 1
             specs.append(dict(id=q, arrival=float(t), kind="tersoff_diamond_vacancy", reps=reps,
-                              n_images=n_images, k=0.1, dt=0.1, fmax=fmax))
+                              n_images=n_images, k=0.1, dt=0.05, dt_max=0.2, maxstep=0.1,
+                              fmax=fmax))
     return specs
 
 
@@ -340,6 +390,8 @@ def build_request(spec):
         return (R0, h0, affine(R1, h1, h1s), h1s), "lj"
     if spec["kind"] == "tersoff_graphite_hexdiamond":
         return graphite_hexdiamond_path(spec["reps"]), "tersoff"
+    if spec["kind"] == "tersoff_diamond_vacancy":
+        return diamond_vacancy_hop_relaxed(spec["reps"]), "tersoff"
     return diamond_vacancy_hop(DIAMOND_A, spec["reps"]), "tersoff"
 
 

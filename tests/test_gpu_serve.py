@@ -144,3 +144,56 @@ def test_served_mixed_equal_alone_and_oracle_barriers(g, oracle_mod):
         assert oconv
         assert abs(r["barrier"] - ob.barrier()) <= 1e-3, (r["barrier"], ob.barrier())
     sv.destroy()
+
+
+def test_served_mixed_carbon_vacancy_equal_alone_and_oracle(g, oracle_mod):
+    """Mixed precision, Tersoff carbon: diamond vacancy hops between relaxed
+    endpoints (511 atoms at fixed cell, 5 images, fmax 1e-3; 999 atoms with
+    the cell filter, 7 images, fmax 0.05) served beside an LJ request.  Each
+    served result equals the band relaxed alone (bitwise), and the 511-atom
+    barrier is within 1 meV of the oracle's band relaxed to the same
+    tolerance."""
+    from _cases import oracle_band
+    vac = dict(k=0.1, dt=0.05, dt_max=0.2, maxstep=0.1)
+    reqs = []
+    R0, h0, R1, h1 = ci.diamond_vacancy_hop_relaxed((4, 4, 4))
+    reqs.append(((R0, h0, R1, h1), 5, False, 1e-3))
+    R0, h0, R1, h1 = ci.diamond_vacancy_hop_relaxed((5, 5, 5))
+    reqs.append(((R0, h0, R1, h1), 7, True, 5e-2))
+
+    def opts(N):
+        o = g.default_options()
+        o.k_spring, o.dt, o.dt_max, o.maxstep = vac["k"], vac["dt"], vac["dt_max"], vac["maxstep"]
+        o.precision, o.n_max = g.MIXED, N
+        return o
+
+    sv = g.Server(g.MIXED)
+    ids = []
+    lj = _requests()[2]
+    o_lj = _opts(g, lj[4])
+    o_lj.precision = g.MIXED
+    ids.append(sv.submit(lj[:2], lj[2:4], lj[4], g.lj_potential(),
+                         g.CellFilter(1, g.ROTFREE_B, g.CELL_FACTOR_J, 0.0), o_lj, 5e-2, 4000,
+                         arrival_s=0.0))
+    for k, (ends, N, cf, fmax) in enumerate(reqs):
+        ids.append(sv.submit(ends[:2], ends[2:], N, g.tersoff_potential(),
+                             g.CellFilter(int(cf), g.ROTFREE_B, 0.0, 0.0), opts(N), fmax, 6000,
+                             arrival_s=0.005 * (k + 1)))
+    assert sv.run(until_s=120.0)
+    res = [sv.result(i) for i in ids]
+    assert all(r["state"] == 2 and r["status"] == 0 and r["converged"] for r in res), \
+        [(r["state"], r["status"], r["converged"], r["steps"]) for r in res]
+    for (ends, N, cf, fmax), r in zip(reqs, res[1:]):
+        b = gpu_band(g, *ends, N, g.tersoff_potential(), cell_filter=cf, precision=g.MIXED,
+                     **vac)
+        done, conv = b.relax(fmax, 6000)
+        E = b.get_path()["energies"]
+        assert conv and done == r["steps"]
+        assert E.max() - E[0] == r["barrier"]
+        b.destroy()
+    ends, N, cf, fmax = reqs[0]
+    ob = oracle_band(oracle_mod, oracle_mod.Tersoff(), *ends, N, cell_filter=False, **vac)
+    _, oconv = ob.relax(fmax, 20000)
+    assert oconv
+    assert abs(res[1]["barrier"] - ob.barrier()) <= 1e-3, (res[1]["barrier"], ob.barrier())
+    sv.destroy()
