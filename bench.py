@@ -855,6 +855,7 @@ def serve_once(g, stream, specs, built, budget, max_steps, lead, drain, window):
     sv.destroy()
     done = [r for r in res if r["state"] == 2]
     lat = np.array([r["latency_s"] for r in done])
+    lat_conv = np.array([r["latency_s"] for r in done if r["converged"]])
     work = [len(b[0][0]) * (sp["n_images"] - 2) * r["steps"]
             for sp, b, r in zip(specs, built, res) if r["state"] == 2]
     t_end = max(sp["arrival"] + r["latency_s"] for sp, r in zip(specs, res) if r["state"] == 2)
@@ -879,6 +880,9 @@ def serve_once(g, stream, specs, built, budget, max_steps, lead, drain, window):
             "errors": sum(int(r["status"] != 0) for r in res),
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "mean_s": float(lat.mean()),
+            # time to convergence: latencies of the requests that converged
+            "converged_p50_s": float(np.percentile(lat_conv, 50)) if len(lat_conv) else None,
+            "converged_p99_s": float(np.percentile(lat_conv, 99)) if len(lat_conv) else None,
             "offered_rate_per_s": len(specs) / window,
             "offered_atom_images_per_s": atom_images / window,
             "offered_atom_steps_per_s": sum(work) / window,
