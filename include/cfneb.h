@@ -427,7 +427,7 @@ int cfneb_get_work(const cfneb_band *band, double *pairs, double *triples);
 
 /* The band's tuning: *bin_scale = cell-list bin width / list cutoff and
  * *blocks_per_sm = resident blocks per SM of the force kernel variant it
- * launches (FP32 LJ with lists: 5-8, FP32 Tersoff: 4-6; 0 where the
+ * launches (FP32 LJ with lists: 5-8, FP32 Tersoff: 4-8; 0 where the
  * potential or precision has one variant).  cfneb_autotune picks both: the
  * bin width from timed evaluations with forced rebuilds, then the variant
  * at that width.  Any output pointer may be NULL.  Reads host state only. */

@@ -811,7 +811,7 @@ void launch_lj(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 template <typename T>
 void launch_lj_list(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s);
 // minb: resident blocks per SM of the force kernel variant (FP32: 5-8 for
-// LJ, 4-6 for Tersoff; the autotuner picks it)
+// LJ, 4-8 for Tersoff; the autotuner picks it)
 template <typename T>
 void launch_lj_nbr(const Tile *tiles, int ntiles, BandDev *bands, cudaStream_t s, int minb);
 template <typename T>

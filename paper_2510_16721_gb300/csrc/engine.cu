@@ -71,7 +71,7 @@ const double kTuneScales[4] = {0.5, 0.75, 1.0, 1.3};
 // kernel variant launched): defaults and the autotuner's candidates
 constexpr int kLjMinb = 7, kTersMinb = 5;
 const int kLjMinbs[4] = {5, 6, 7, 8};
-const int kTersMinbs[3] = {4, 5, 6};
+const int kTersMinbs[5] = {4, 5, 6, 7, 8};
 
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, double> g_tune;  // class -> bin width / rc
@@ -1167,7 +1167,7 @@ double autotune_band(cfneb_band *b, int steps) {
     const bool lj_list = b->kind == CFNEB_LJ && b->dv.lj_cap > 0;
     if (b->precision == CFNEB_MIXED && (lj_list || b->kind == CFNEB_TERSOFF)) {
         const int *cand = lj_list ? kLjMinbs : kTersMinbs;
-        const int nc = lj_list ? 4 : 3;
+        const int nc = lj_list ? 4 : 5;
         double bm = 1e300;
         for (int q = 0; q < nc; ++q) {
             b->minb = cand[q];

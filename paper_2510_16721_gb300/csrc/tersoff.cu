@@ -1123,6 +1123,8 @@ void launch_tersoff_partials(const Tile *tiles, int ntiles, BandDev *bands, cuda
     switch (minb) {
         case 4: k_ters_partials<T, 4><<<ntiles, TILE, 0, s>>>(tiles, bands); break;
         case 6: k_ters_partials<T, 6><<<ntiles, TILE, 0, s>>>(tiles, bands); break;
+        case 7: k_ters_partials<T, 7><<<ntiles, TILE, 0, s>>>(tiles, bands); break;
+        case 8: k_ters_partials<T, 8><<<ntiles, TILE, 0, s>>>(tiles, bands); break;
         default: k_ters_partials<T, 5><<<ntiles, TILE, 0, s>>>(tiles, bands); break;
     }
 }

@@ -232,7 +232,7 @@ def test_batch_autotune_sets_variants(g):
         bt.add(b)
     bt.autotune(2)
     assert bands[0].tuning()[1] in (5, 6, 7, 8)
-    assert bands[1].tuning()[1] in (4, 5, 6)
+    assert bands[1].tuning()[1] in (4, 5, 6, 7, 8)
     bt.step(3)
     assert all(s["status"] == 0 for s in bt.status())
     bt.destroy()
