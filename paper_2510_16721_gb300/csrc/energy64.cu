@@ -82,11 +82,14 @@ __device__ inline void for_neighbours64(const BandDev &b, int img, int t, const 
 }
 
 // sin a on [0, pi/2] in FP64 by its Taylor series to the a^25 term in
-// nested form (truncation below 2e-23 at pi/2)
+// nested form (truncation below 2e-23 at pi/2); the coefficients
+// 1 / ((2k)(2k + 1)) are compile-time constants (an FP64 divide is a long
+// dependent sequence on this GPU)
 __device__ inline double sin_quarter64(double a) {
     const double a2 = a * a;
     double p = 1.0;
-    for (int k = 12; k >= 1; --k) p = 1.0 - a2 / (double)((2 * k) * (2 * k + 1)) * p;
+#pragma unroll
+    for (int k = 12; k >= 1; --k) p = 1.0 - a2 * (1.0 / (double)((2 * k) * (2 * k + 1))) * p;
     return a * p;
 }
 
