@@ -2,8 +2,9 @@
 
 The Mueller-Brown surface (published stationary points and an independent
 Newton solve) pins the tangent/projection/CI/FIRE chain; the LJ vacancy hop
-pins symmetry and the saddle energy (constrained minimisation of the
-midpoint image with scipy); rotating both endpoints must leave the
+and the Tersoff carbon vacancy hop pin symmetry and the saddle energy
+(constrained minimisation of the midpoint image with scipy); rotating both
+endpoints must leave the
 converged path unchanged; insertion/deletion must keep the endpoints.
 """
 import json
@@ -148,6 +149,42 @@ def test_lj_vacancy_hop_symmetric_and_saddle(oracle_mod):
                    options=dict(gtol=1e-11, ftol=1e-15, maxiter=5000))
     e0 = np.sum(pot.evaluate(R0, h0)[0])
     assert abs((res.fun - e0) - band.barrier()) < 1e-6
+
+
+def test_tersoff_vacancy_hop_symmetric_and_saddle(oracle_mod):
+    """Tersoff carbon diamond vacancy hop between relaxed endpoints (511
+    atoms, fixed cell, 5 images, k = 0.1 eV/A^2, FIRE dt 0.05 / dt_max 0.2 /
+    maxstep 0.1): the converged profile is symmetric, the climbing image is
+    the centre image with the hopping atom at the midpoint of its two sites,
+    and the barrier equals the constrained minimum of the energy with the
+    hopping atom held at that midpoint (scipy L-BFGS from the symmetric
+    midpoint configuration, on the oracle energy): the split-vacancy saddle."""
+    R0, h0, R1, h1 = ci.diamond_vacancy_hop_relaxed((4, 4, 4))
+    pot = oracle_mod.Tersoff()
+    band = oracle_mod.make_band(pot, R0, h0, R1, h1, 5, k=0.1, climb=True, cell_filter=False,
+                                fire=oracle_mod.Fire(dt=0.05, dt_max=0.2, maxstep=0.1))
+    steps, conv = band.relax(1e-3, 20000)
+    assert conv
+    E = np.array(band.E)
+    np.testing.assert_allclose(E, E[::-1], atol=1e-6)
+    assert band.ci == 2
+    hop = int(np.argmax(np.linalg.norm(R1 - R0, axis=1)))
+    mid = 0.5 * (R0[hop] + R1[hop])
+    np.testing.assert_allclose(band.info[2]["R"][hop], mid, atol=1e-5)
+    base = 0.5 * (R0 + R1)
+    others = [i for i in range(len(R0)) if i != hop]
+
+    def f(x):
+        R = base.copy()
+        R[others] = x.reshape(-1, 3)
+        e, F, _ = pot.evaluate(R, h0)
+        return np.sum(e), -F[others].ravel()
+
+    res = minimize(f, base[others].ravel(), jac=True, method="L-BFGS-B",
+                   options=dict(gtol=1e-9, ftol=1e-15, maxiter=5000))
+    e0 = np.sum(pot.evaluate(R0, h0)[0])
+    assert abs((res.fun - e0) - band.barrier()) < 1e-6
+    assert 5.0 < band.barrier() < 15.0
 
 
 def _rot(a, b):
