@@ -236,3 +236,43 @@ def test_batch_autotune_sets_variants(g):
     bt.step(3)
     assert all(s["status"] == 0 for s in bt.status())
     bt.destroy()
+
+
+def test_full_lj_batch_sampled_forces_mixed(g, oracle_mod):
+    """The 64-band LJ batch as the benchmark steps it (vacancy and divacancy
+    hops of 270-30,346 atoms, 5-15 images, +-2% end-cell strain, cell filter
+    with the lattice scale J, mixed precision, one batch): after three batch
+    steps, the atom rows of the generalised force (F D^T) of the middle image
+    of the smallest, a median and the largest band, at the stored
+    configuration, against the brute-force oracle on 32 sampled atoms each
+    (1e-4 eps/sigma, or 2e-6 of the largest force on close contacts)."""
+    bcs = ci.lj_batch(seed=4)
+    bands = []
+    for bc in bcs:
+        R0, h0, R1, h1 = bc["endpoints"]
+        bands.append(gpu_band(g, R0, h0, R1, h1, bc["n_images"], g.lj_potential(), k=bc["k"],
+                              dt=bc["dt"], cell_filter=True, precision=g.MIXED,
+                              cell_factor=g.CELL_FACTOR_J))
+    bt = g.Batch(g.MIXED)
+    for b in bands:
+        bt.add(b)
+    bt.step(3)
+    order = np.argsort([len(bc["endpoints"][0]) for bc in bcs])
+    picks = [int(order[0]), int(order[len(order) // 2]), int(order[-1])]
+    states = {q: bands[q].get_state() for q in picks}
+    bt.step(1)  # forces of the stored configurations come from this evaluation
+    rng = np.random.default_rng(11)
+    for q in picks:
+        R0, h0, _, _ = bcs[q]["endpoints"]
+        n = len(R0)
+        i = bcs[q]["n_images"] // 2
+        c = abs(np.linalg.det(h0)) ** (1.0 / 3.0) * n ** (1.0 / 6.0)
+        R, h, D = oracle_mod.from_generalized(states[q]["X"][i], h0, c)
+        idx = rng.choice(n, 32, replace=False)
+        Fo = oracle_mod.LJ().forces_sampled(R, h, idx) @ D.T
+        F = bands[q].get_state()["F"][i][:n]
+        err = np.max(np.abs(F[idx] - Fo))
+        assert err <= max(1e-4, 2e-6 * np.max(np.abs(Fo))), (q, n, err)
+    bt.destroy()
+    for b in bands:
+        b.destroy()
