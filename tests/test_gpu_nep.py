@@ -111,3 +111,37 @@ def test_nep_invalid_weights_are_rejected(g):
     assert e.value.status == g.ERR_INVALID_ARG
     with pytest.raises(g.CfnebError):
         gpu_band(g, R0, h0, R1, h1, 5, g.nep_potential(_weights(), -1.0), k=0.1, dt=0.05)
+
+
+def test_large_nep_band_image_properties(g):
+    """Full size: a 98,304-atom image of the graphite -> hexagonal-diamond
+    path (the middle of the linear interpolation in the 32 x 24 x 16 tiling,
+    seeded 0.02 A jitter) under the NEP-style potential, where the oracle's
+    whole-structure autograd does not reach.  Properties that hold at any
+    size: the forces sum to zero (translation invariance); a central
+    difference of the FP64 energy along a random direction of all atoms
+    matches -F.d; the mixed forces match the FP64 ones on 64 sampled atoms
+    at the FP32-rounded configuration (1e-4 eV/A)."""
+    R0, h0, R1, h1 = ci.graphite_hexdiamond_path(ci.TERSOFF_LARGE_REPS)
+    s0 = R0 @ np.linalg.inv(h0)
+    s1 = R1 @ np.linalg.inv(h1)
+    h = 0.5 * (h0 + h1)
+    rng = np.random.default_rng(21)
+    R = (0.5 * (s0 + s1)) @ h + rng.normal(0.0, 0.02, R0.shape)
+    R, h = f32_structure(R, h)
+    pot = g.nep_potential(_weights(), RC)
+    E, F, _ = g.evaluate([(R, h)], pot, g.FP64)
+    F = F[0]
+    assert len(R) == 98304
+    assert np.all(np.abs(F.sum(axis=0)) <= 1e-9 * len(R) * max(1.0, np.max(np.abs(F))))
+    d = rng.normal(size=R.shape)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    s = 1e-4
+    Ep, _, _ = g.evaluate([(R + s * d, h)], pot, g.FP64)
+    Em, _, _ = g.evaluate([(R - s * d, h)], pot, g.FP64)
+    fd = -(Ep[0] - Em[0]) / (2.0 * s)
+    fd_ref = np.sum(F * d)
+    assert abs(fd - fd_ref) <= 1e-3 * max(1.0, np.sqrt(np.sum(F * F))), (fd, fd_ref)
+    _, Fm, _ = g.evaluate([(R, h)], pot, g.MIXED)
+    idx = rng.choice(len(R), 64, replace=False)
+    assert np.max(np.abs(Fm[0][idx] - F[idx])) <= 1e-4
