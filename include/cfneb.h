@@ -176,7 +176,11 @@ int cfneb_default_options(cfneb_options *opt);
  *   plus `interior_noise`.  Endpoint energies are evaluated once.
  * n_images >= 3.  cuda_stream is a cudaStream_t (NULL = legacy default).
  * On success *out owns the band; destroy it with cfneb_destroy_band.
- * Errors: INVALID_ARG, SHAPE_MISMATCH, OUT_OF_MEMORY, CUDA, NOT_SPD. */
+ * Errors: INVALID_ARG (also for coincident endpoints -- every atom on the
+ * same periodic site to 1e-12 in fractional coordinates and, with the cell
+ * filter on, the same cell -- which leave no path: every tangent would
+ * vanish), SHAPE_MISMATCH, OUT_OF_MEMORY, CUDA, NOT_SPD.  Arguments are
+ * checked on the host before any CUDA call. */
 int cfneb_create_band(const cfneb_structure *initial, const cfneb_structure *final,
                       int32_t n_images, const cfneb_potential *potential,
                       const cfneb_cell_filter *cell_filter, const cfneb_options *options,

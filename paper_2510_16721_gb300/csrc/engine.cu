@@ -1604,10 +1604,13 @@ int cfneb_default_options(cfneb_options *o) {
     return CFNEB_OK;
 }
 
-int cfneb_create_band(const cfneb_structure *initial, const cfneb_structure *final_,
-                      int32_t n_images, const cfneb_potential *potential,
-                      const cfneb_cell_filter *cell_filter, const cfneb_options *options,
-                      void *cuda_stream, cfneb_band **out) {
+namespace {
+// cfneb_create_band with the argument checks; need_path: refuse coincident
+// endpoints (single-point evaluations build a band of one structure)
+int create_band_checked(const cfneb_structure *initial, const cfneb_structure *final_,
+                        int32_t n_images, const cfneb_potential *potential,
+                        const cfneb_cell_filter *cell_filter, const cfneb_options *options,
+                        void *cuda_stream, cfneb_band **out, bool need_path) {
     if (!initial || !final_ || !potential || !out || n_images < 3) return CFNEB_ERR_INVALID_ARG;
     *out = nullptr;
     if (!initial->positions || !final_->positions || initial->n_atoms <= 0)
@@ -1642,6 +1645,34 @@ int cfneb_create_band(const cfneb_structure *initial, const cfneb_structure *fin
             if (!std::isfinite(S->cell[k])) return CFNEB_ERR_INVALID_ARG;
         for (long long k = 0; k < 3LL * S->n_atoms; ++k)
             if (!std::isfinite(S->positions[k])) return CFNEB_ERR_INVALID_ARG;
+    }
+    // coincident endpoints (every atom on the same periodic site, the same
+    // cell where the filter is on) leave no path: every tangent of the
+    // band would vanish (Sec. II.A's projection is undefined)
+    if (need_path) {
+        const bool filter = cell_filter && cell_filter->enabled;
+        bool same_cell = true;
+        for (int k = 0; k < 9 && filter; ++k)
+            same_cell = same_cell && std::fabs(final_->cell[k] - initial->cell[k]) <=
+                                         1e-12 * (1.0 + std::fabs(initial->cell[k]));
+        double hi0[9], hi1[9];
+        inv3(initial->cell, hi0);
+        inv3(filter ? final_->cell : initial->cell, hi1);
+        bool same_sites = same_cell;
+        for (int i = 0; i < initial->n_atoms && same_sites; ++i) {
+            const double *p0 = initial->positions + 3 * (size_t)i;
+            const double *p1 = final_->positions + 3 * (size_t)i;
+            for (int a = 0; a < 3; ++a) {
+                const double s0 = p0[0] * hi0[a] + p0[1] * hi0[3 + a] + p0[2] * hi0[6 + a];
+                const double s1 = p1[0] * hi1[a] + p1[1] * hi1[3 + a] + p1[2] * hi1[6 + a];
+                const double d = (s1 - s0) - std::nearbyint(s1 - s0);
+                if (!(std::fabs(d) <= 1e-12)) {
+                    same_sites = false;
+                    break;
+                }
+            }
+        }
+        if (same_sites) return CFNEB_ERR_INVALID_ARG;
     }
     cfneb_options opt;
     if (options) opt = *options;
@@ -1679,6 +1710,16 @@ int cfneb_create_band(const cfneb_structure *initial, const cfneb_structure *fin
     }
     *out = b;
     return CFNEB_OK;
+}
+
+}  // namespace
+
+int cfneb_create_band(const cfneb_structure *initial, const cfneb_structure *final_,
+                      int32_t n_images, const cfneb_potential *potential,
+                      const cfneb_cell_filter *cell_filter, const cfneb_options *options,
+                      void *cuda_stream, cfneb_band **out) {
+    return create_band_checked(initial, final_, n_images, potential, cell_filter, options,
+                               cuda_stream, out, true);
 }
 
 int cfneb_step(cfneb_band *b, int32_t n_steps) {
@@ -2058,7 +2099,7 @@ int cfneb_evaluate(const cfneb_structure *structures, int32_t count,
         opt.skin = 0.0;  // one evaluation: nothing to reuse
         cfneb_cell_filter cf{1, CFNEB_ROTFREE_B, 0.0, 0.0};
         cfneb_band *b = nullptr;
-        int st = cfneb_create_band(&S, &S, 3, potential, &cf, &opt, cuda_stream, &b);
+        int st = create_band_checked(&S, &S, 3, potential, &cf, &opt, cuda_stream, &b, false);
         if (st != CFNEB_OK) return st;
         try {
             enter(b);

@@ -125,3 +125,42 @@ def test_noalloc_rejects_invalid_input_before_gpu_work(libmod, case):
         h[2] = h[1]
     st = libmod.lj_evaluate_noalloc(16, 4, h, eps, sigma, rc, 1, 0, 0, 0)
     assert st == libmod.ERR_INVALID_ARG
+
+
+def test_coincident_endpoints_are_rejected_on_the_host(libmod):
+    """Endpoints with every atom on the same periodic site (here: the final
+    structure is the initial one with a few atoms shifted by whole lattice
+    vectors), and the same cell, leave no path: cfneb_create_band returns
+    INVALID_ARG before any CUDA call, with the cell filter on or off."""
+    import ctypes
+
+    import numpy as np
+
+    import cfneb_inputs as ci
+    g = libmod
+    R0, h0, _, _ = ci.lj_vacancy_hop(ci.LJ_A, (2, 2, 2))
+    R1 = R0.copy()
+    R1[:5] += h0[0]
+    R1[7] -= h0[2]
+    keep = []
+    A = g.make_structure(R0, h0, keep)
+    B = g.make_structure(R1, h0, keep)
+    opt = g.default_options()
+    pot = g.lj_potential()
+    out = ctypes.c_void_p()
+    for enabled in (0, 1):
+        cf = g.CellFilter(enabled, g.ROTFREE_B, 0.0, 0.0)
+        st = g.lib().cfneb_create_band(ctypes.byref(A), ctypes.byref(B), 5, ctypes.byref(pot),
+                                       ctypes.byref(cf), ctypes.byref(opt), None,
+                                       ctypes.byref(out))
+        assert st == g.ERR_INVALID_ARG
+    # control: one atom off its site passes the host checks (and then needs
+    # a device)
+    import torch
+    if not torch.cuda.is_available():
+        R2 = R1.copy()
+        R2[3] += 0.1
+        C = g.make_structure(R2, h0, keep)
+        st = g.lib().cfneb_create_band(ctypes.byref(A), ctypes.byref(C), 5, ctypes.byref(pot),
+                                       None, ctypes.byref(opt), None, ctypes.byref(out))
+        assert st != g.ERR_INVALID_ARG and st < 0
