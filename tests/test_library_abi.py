@@ -164,3 +164,30 @@ def test_coincident_endpoints_are_rejected_on_the_host(libmod):
         st = g.lib().cfneb_create_band(ctypes.byref(A), ctypes.byref(C), 5, ctypes.byref(pot),
                                        None, ctypes.byref(opt), None, ctypes.byref(out))
         assert st != g.ERR_INVALID_ARG and st < 0
+
+
+def test_empty_and_short_bands_are_rejected_on_the_host(libmod):
+    """A structure without atoms, endpoints of different sizes, and a band
+    of fewer than three images (no moving image) are refused before any
+    CUDA call."""
+    import ctypes
+
+    import numpy as np
+
+    import cfneb_inputs as ci
+    g = libmod
+    R0, h0, R1, h1 = ci.lj_vacancy_hop(ci.LJ_A, (2, 2, 2))
+    keep = []
+    A = g.make_structure(R0, h0, keep)
+    B = g.make_structure(R1, h1, keep)
+    E = g.make_structure(np.zeros((0, 3)), h0, keep)
+    S = g.make_structure(R1[:-1], h1, keep)
+    opt = g.default_options()
+    pot = g.lj_potential()
+    out = ctypes.c_void_p()
+    create = g.lib().cfneb_create_band
+    for (a, b, n, want) in ((E, E, 5, g.ERR_INVALID_ARG), (A, B, 2, g.ERR_INVALID_ARG),
+                            (A, S, 5, g.ERR_SHAPE_MISMATCH)):
+        st = create(ctypes.byref(a), ctypes.byref(b), n, ctypes.byref(pot), None,
+                    ctypes.byref(opt), None, ctypes.byref(out))
+        assert st == want, (n, st)
