@@ -8,8 +8,11 @@ imports the product.
 Parity status: every function is pinned by ``tests/test_oracle_*.py``
 (finite differences, closed-form lattice sums, published equilibrium values,
 the Mueller-Brown saddle, symmetry and invariance checks).  The converged
-barriers of the synthetic workloads have no published value: beyond the pins
-of their ingredients they are "parity unpinned".
+barriers of the synthetic workloads have no published value.  The LJ and
+Tersoff vacancy-hop barriers are pinned by a constrained minimisation of the
+symmetric midpoint image (an independent route to the same saddle); the
+graphite -> hexagonal-diamond barriers are pinned only through their
+ingredients: for them parity is "parity unpinned".
 """
 from . import _native  # noqa: F401
 from .cfneb import (LJ, Tersoff, TERSOFF_C1988, ROTFREE_B, DEFGRAD_D, NotSPD,  # noqa: F401

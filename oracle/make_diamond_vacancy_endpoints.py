@@ -1,4 +1,6 @@
-"""Relax the endpoints of a vacancy hop in Tersoff carbon diamond with the
+"""TEST INFRASTRUCTURE (an input generator run by hand, never by the product).
+
+Relax the endpoints of a vacancy hop in Tersoff carbon diamond with the
 oracle, in a 4 x 4 x 4 conventional cell (511 atoms), at the fixed lattice
 constant of the diamond workloads.
 

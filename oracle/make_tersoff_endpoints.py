@@ -1,4 +1,6 @@
-"""Relax the 8-atom graphite and hexagonal-diamond cells with the oracle.
+"""TEST INFRASTRUCTURE (an input generator run by hand, never by the product).
+
+Relax the 8-atom graphite and hexagonal-diamond cells with the oracle.
 
 Writes cfneb_inputs/data/tersoff_c_endpoints_8atom.json, the endpoints every
 Tersoff workload is tiled from.  Runs the FP64 CPU reference only:
