@@ -85,7 +85,7 @@ BAND_PHASE_BYTES = lambda w: w["atoms"] * 108.0 * (w["ts"] / 4)
 # the force kernel's useful work by the per-entry / per-triple model of the
 # method's arithmetic: 30 flops and 2 exponentials per neighbour entry,
 # 60 flops per ordered triple (zeta and its derivatives)
-SURVEY_FLOPS = {"tersoff_partials": lambda w: 32.0 * w["pairs"] + 60.0 * w["triples"]}
+METHOD_FLOPS = {"tersoff_partials": lambda w: 32.0 * w["pairs"] + 60.0 * w["triples"]}
 
 
 def kernel_rooflines(prof, w, peaks, peak_src, sm_max):
@@ -491,8 +491,8 @@ def run_ours(args, wl_name):
                 "frac": achieved / peak,
                 "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 (FMA) x %.0f MHz"
                                % (sm_count(), sm_max)}
-        if dom in SURVEY_FLOPS:
-            a2 = SURVEY_FLOPS[dom](w) / (dom_ms * 1e-3) / 1e12
+        if dom in METHOD_FLOPS:
+            a2 = METHOD_FLOPS[dom](w) / (dom_ms * 1e-3) / 1e12
             roof["frac_method_model"] = {"achieved": a2, "frac": a2 / peak,
                                          "model": "32 flops per neighbour entry (2 exp as 1 "
                                                   "each) + 60 per ordered triple"}
