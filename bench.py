@@ -936,8 +936,9 @@ def run_serve(args):
             "config": {"workload": args.workload, "rate_per_s": wl["rate"],
                        "window_s": args.serve_window, "budget_gb": wl["budget_gb"],
                        "atoms": "log-uniform 500-50,000", "images": "uniform 7-16",
-                       "mix": "LJ FCC vacancy 50% (strained end cell), Tersoff C diamond "
-                              "vacancy between relaxed endpoints 50% (odd image counts)",
+                       "mix": "LJ FCC vacancy 50% (strained end cell, FIRE dt_max 3 dt), "
+                              "Tersoff C diamond vacancy between relaxed endpoints 50% (odd "
+                              "image counts)",
                        "fmax": 0.05, "max_steps": args.serve_max_steps, "precision": "mixed",
                        "cell_filter": "rotation-free (B)",
                        "steps": "not applicable: a request stream, value = served "

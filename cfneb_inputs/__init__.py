@@ -345,7 +345,9 @@ def serve_requests(seed=5, rate=20.0, window=60.0, n_lo=500, n_hi=50000, img_lo=
     """Request stream for the serving loop: Poisson arrivals at `rate` per
     second over `window` seconds; each request is an LJ or a Tersoff carbon
     band (even odds).  LJ: FCC vacancy hop, end cell strained by up to
-    lj_strain, image counts (endpoints included) uniform in [img_lo, img_hi].
+    lj_strain, image counts (endpoints included) uniform in [img_lo, img_hi],
+    FIRE dt 0.01 with dt_max 0.03 (3 dt: the large strained bands overshoot
+    into atom overlaps more often at 10 dt).
     Tersoff: cubic-diamond vacancy hop between relaxed endpoints
     (diamond_vacancy_hop_relaxed, at least 4 x 4 x 4 cells), an odd image
     count in the same range (the hop is mirror-symmetric: an odd count puts
@@ -366,7 +368,7 @@ def serve_requests(seed=5, rate=20.0, window=60.0, n_lo=500, n_hi=50000, img_lo=
                 m += 1
                 reps = near_cubic_factors(m)
             specs.append(dict(id=q, arrival=float(t), kind="lj_vacancy", reps=reps,
-                              n_images=n_images, k=1.0, dt=0.01, fmax=fmax,
+                              n_images=n_images, k=1.0, dt=0.01, dt_max=0.03, fmax=fmax,
                               strain_seed=seed * 100000 + q, strain=lj_strain))
         else:
             m = max(64, int(round(target / 8.0)))
