@@ -221,18 +221,23 @@ __device__ inline int climbing_image_warp(const BandDev &b, int N, double e0) {
 //   F_NEB.v = F.v + a dX+.v + b dX-.v,
 //   |F_NEB|^2 = F.F + a^2 |dX+|^2 + b^2 |dX-|^2 + 2a F.dX+ + 2b F.dX-
 //               + 2ab dX+.dX-.
+// etol: energy differences up to etol count as ties (0 in FP64 bands: the
+// rule exactly as stated; mixed bands: the error bound of their step
+// energies, FP32 site energies summed in FP64, so that the upwind branch is
+// not chosen by rounding between nearly equal images -- those take the
+// equal-weight tangent dX+ + dX-).
 __device__ inline void image_coef(BandDev &b, int i, int ci, const double *d, double Em,
-                                  double E0, double Ep, double kspring) {
+                                  double E0, double Ep, double kspring, double etol) {
     ImgScalars &sc = b.sc[i];
     double wp, wm;
-    if (Ep > E0 && E0 > Em) {
+    if (Ep - E0 > etol && E0 - Em > etol) {
         wp = 1.0; wm = 0.0;
-    } else if (Ep < E0 && E0 < Em) {
+    } else if (E0 - Ep > etol && Em - E0 > etol) {
         wp = 0.0; wm = 1.0;
     } else {
         const double a = fabs(Ep - E0), c = fabs(Em - E0);
         const double dmax = fmax(a, c), dmin = fmin(a, c);
-        if (dmax == 0.0) {
+        if (dmax <= etol) {
             wp = 1.0; wm = 1.0;
         } else if (Ep > Em) {
             wp = dmax; wm = dmin;
@@ -361,7 +366,10 @@ __global__ void __launch_bounds__(RTHREADS, sizeof(T) == 4 ? 4 : 2) k_band_dots(
         const int ci = shard ? ci_ext : (climb ? climbing_image_warp(b, N, e0) : -1);
         if (threadIdx.x == 0) {
             if (tl.img == 1) bp->ci = ci;
-            image_coef(b, tl.img, ci, s_d, Em, E0, Ep, kspring);
+            // mixed bands: 2 x 4e-6 energy units per atom, twice the bound
+            // on the error of a step energy
+            image_coef(b, tl.img, ci, s_d, Em, E0, Ep, kspring,
+                       sizeof(T) == 4 ? 8e-6 * (double)b.n : 0.0);
         }
     }
 }
