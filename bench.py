@@ -592,36 +592,48 @@ def run_ours(args, wl_name):
 def converged_line(g, torch, stream):
     """A band relaxed to convergence in both precisions: the Tersoff diamond
     vacancy hop between relaxed endpoints in 98,303 atoms (16 x 24 x 32
-    cells), 11 images, adaptive refinement between 8 and 24 images, cell
-    filter on, fmax 0.05 eV/A.  Reports each precision's moves, final image
-    count, converged barrier (FP64 energies) and the time from the relax call
-    to its return with the band resident, and the barrier gap."""
+    cells), 11 images, cell filter on; fmax 0.05 eV/A with adaptive
+    refinement between 8 and 24 images, and fmax 0.01 eV/A with the 11
+    images kept ("tight").  Reports each precision's moves, final image
+    count, converged barrier (FP64 energies) and the time from the relax
+    call to its return with the band resident, and the barrier gap."""
     import numpy as np
     import cfneb_inputs as ci
     R0, h0, R1, h1 = ci.diamond_vacancy_hop_relaxed((16, 24, 32))
-    out = {"workload": "tersoff_diamond_vacancy_98303", "atoms": len(R0), "images": 11,
-           "adaptive": [8, 24], "cell_filter": "rotation-free (B)", "fmax": 0.05,
-           "fire": {"dt": 0.05, "dt_max": 0.2, "maxstep": 0.1}, "k_spring": 0.1}
-    for prec in ("mixed", "fp64"):
+
+    def one(prec, fmax, adaptive):
         opt = g.default_options()
         opt.k_spring, opt.climb = 0.1, 1
         opt.precision = g.MIXED if prec == "mixed" else g.FP64
         opt.dt, opt.dt_max, opt.maxstep = 0.05, 0.2, 0.1
-        opt.adaptive, opt.n_min, opt.n_max = 1, 8, 24
+        opt.adaptive, opt.n_min, opt.n_max = int(adaptive), 8, 24 if adaptive else 11
         cf = g.CellFilter(1, g.ROTFREE_B, 0.0, 0.0)
         b = g.create_band((R0, h0), (R1, h1), 11, g.tersoff_potential(), cf, opt,
                           stream=stream)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        steps, conv = b.relax(0.05, 6000)
+        steps, conv = b.relax(fmax, 6000)
         torch.cuda.synchronize()
         sec = time.perf_counter() - t0
         E = b.get_path()["energies"]
-        out[prec] = {"moves": steps, "converged": bool(conv), "final_images": b.n_images,
-                     "barrier_eV": float(np.max(E) - E[0]), "seconds": sec}
+        r = {"moves": steps, "converged": bool(conv), "final_images": b.n_images,
+             "barrier_eV": float(np.max(E) - E[0]), "seconds": sec}
         b.destroy()
+        return r
+
+    out = {"workload": "tersoff_diamond_vacancy_98303", "atoms": len(R0), "images": 11,
+           "adaptive": [8, 24], "cell_filter": "rotation-free (B)", "fmax": 0.05,
+           "fire": {"dt": 0.05, "dt_max": 0.2, "maxstep": 0.1}, "k_spring": 0.1}
+    for prec in ("mixed", "fp64"):
+        out[prec] = one(prec, 0.05, True)
     out["barrier_gap_eV"] = abs(out["mixed"]["barrier_eV"] - out["fp64"]["barrier_eV"])
     out["time_ratio_fp64_over_mixed"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    tight = {"fmax": 0.01, "adaptive": None}
+    for prec in ("mixed", "fp64"):
+        tight[prec] = one(prec, 0.01, False)
+    tight["barrier_gap_eV"] = abs(tight["mixed"]["barrier_eV"] - tight["fp64"]["barrier_eV"])
+    tight["time_ratio_fp64_over_mixed"] = tight["fp64"]["seconds"] / tight["mixed"]["seconds"]
+    out["tight"] = tight
     return out
 
 
