@@ -128,3 +128,62 @@ def test_mixed_matches_fp64_at_same_x(large_pair):
     print("step-energy error: max |dE| %.3e eV (%.2e per atom), max |d(E_i+1 - E_i)| %.3e eV"
           % (np.max(np.abs(dE)), np.max(np.abs(dE)) / n, np.max(np.abs(dd))))
     assert np.max(np.abs(dE)) <= 4e-6 * n
+
+
+def _coefs(E, dots, ci, k, etol):
+    """The f_NEB coefficients (a, b) of every interior image from the step
+    energies and the ten dots, by the tangent rule with ties up to etol
+    (Sec. II.A, upwind tangent; equal-weight tangent when both energy
+    differences are within etol)."""
+    out = {}
+    for i in range(1, len(E) - 1):
+        Em, E0, Ep = E[i - 1], E[i], E[i + 1]
+        if Ep - E0 > etol and E0 - Em > etol:
+            wp, wm = 1.0, 0.0
+        elif E0 - Ep > etol and Em - E0 > etol:
+            wp, wm = 0.0, 1.0
+        else:
+            a, c = abs(Ep - E0), abs(Em - E0)
+            dmax, dmin = max(a, c), min(a, c)
+            if dmax <= etol:
+                wp, wm = 1.0, 1.0
+            elif Ep > Em:
+                wp, wm = dmax, dmin
+            else:
+                wp, wm = dmin, dmax
+        pp, mm, pm, fp, fm = dots[i][:5]
+        itn = 1.0 / np.sqrt(wp * wp * pp + 2.0 * wp * wm * pm + wm * wm * mm)
+        ft = (wp * fp + wm * fm) * itn
+        gamma = -2.0 * ft if i == ci else k * (np.sqrt(pp) - np.sqrt(mm)) - ft
+        out[i] = (gamma * wp * itn, gamma * wm * itn, wp, wm)
+    return out
+
+
+def test_mixed_tangent_ties_within_energy_error():
+    """The mixed path's tangent rule on a 98,303-atom Tersoff vacancy-hop
+    band (linear interpolation between relaxed endpoints, 11 images): energy
+    differences up to 8e-6 eV per atom (twice the step energies' error
+    bound) count as ties, so the nearly flat images beside the endpoints
+    take the equal-weight tangent, the others their upwind branch.  The NEB
+    coefficients the step used match the rule applied to the step's own
+    energies and dots (1e-9 relative)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2510_16721_gb300 as g
+    g.build()
+    R0, h0, R1, h1 = ci.diamond_vacancy_hop_relaxed((16, 24, 32))
+    b = gpu_band(g, R0, h0, R1, h1, 11, g.tersoff_potential(), k=0.1, dt=0.05, dt_max=0.2,
+                 maxstep=0.1, cell_filter=True, precision=g.MIXED)
+    b.step(40)  # the images beside the endpoints have relaxed to nearly equal energies
+    sc = b.image_scalars()
+    ci_ = b.get_state()["ci"]
+    etol = 8e-6 * len(R0)
+    want = _coefs(sc["E"], sc["dots"], ci_, 0.1, etol)
+    kinds = set()
+    for i, (a, bb, wp, wm) in want.items():
+        kinds.add((wp, wm) if wp in (0.0, 1.0) and wm in (0.0, 1.0) else "weighted")
+        np.testing.assert_allclose(sc["coef"][i], [a, bb], rtol=1e-9, atol=1e-12, err_msg=str(i))
+    # the flat ends tie, the slopes are upwind
+    assert (1.0, 1.0) in kinds and ((1.0, 0.0) in kinds or (0.0, 1.0) in kinds), kinds
+    b.destroy()
