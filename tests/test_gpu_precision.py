@@ -16,6 +16,9 @@ every image, the NEB coefficients, f_NEB and fmax.  The FP64 path is the
 oracle's stand-in at this size (it matches the oracle at 1e-10 on the
 smaller bands of test_gpu_parity.py; the brute-force oracle needs hours per
 evaluation of 98,304 atoms).
+
+Last, the mixed path's tangent rule (energy differences within the step
+energies' error bound count as ties) on a 98,303-atom carbon vacancy band.
 """
 import numpy as np
 import pytest
