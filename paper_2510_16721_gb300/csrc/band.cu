@@ -762,11 +762,15 @@ __global__ void k_setup(const double *R0, const double *R1, const double *noise,
         } else {
             for (int k = 0; k < 9; ++k) { L0[k] = D0[k]; L1[k] = D1[k]; }
         }
+        // stored relative to the reference cell, c (L - I): the rows keep
+        // their precision in FP32 when the cell changes little along the
+        // band (c = n makes c B large next to its differences)
         for (int k = 0; k < N; ++k) {
             const double t = (double)k / (double)(N - 1);
             T *x = (T *)b.X + k * stride + (size_t)n * 3;
             for (int e = 0; e < 9; ++e) {
-                double a = bp->c * L0[e], c = bp->c * L1[e];
+                const double one = e % 4 == 0 ? 1.0 : 0.0;
+                double a = bp->c * (L0[e] - one), c = bp->c * (L1[e] - one);
                 x[e] = (T)(a + t * (c - a));
             }
         }

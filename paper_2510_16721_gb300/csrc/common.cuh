@@ -388,7 +388,8 @@ __device__ inline bool image_cell_warp(const CellIn &k, double xlat, ImgScalars 
     double D = p.eye(), Di = p.eye();
     bool ok = true;
     if (k.filter) {
-        const double L = xlat * rcp64(k.c);
+        // lattice rows are stored as c (B - I) (or c (D - I)): B = X / c + I
+        const double L = xlat * rcp64(k.c) + p.eye();
         if (k.variant == 0) {
             const double B = 0.5 * (L + ltrans(L, p));
             const double C = lcof(B, p);

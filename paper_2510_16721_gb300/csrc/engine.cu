@@ -666,6 +666,14 @@ int status_from_bits(int bits) {
     return CFNEB_OK;
 }
 
+// The lattice rows of X are stored as c (B - I) (c (D - I) for the
+// deformation-gradient filter); the C ABI exchanges X = (R~, c B).  sign +1
+// turns stored rows into the ABI's, -1 the other way (one image of n + 3
+// rows at x).
+void lattice_rows_public(const cfneb_band *b, double *x, double sign) {
+    for (int e = 0; e < 9; e += 4) x[(size_t)b->n * 3 + e] += sign * b->c;
+}
+
 // write FIRE reset values into the device params and zero velocities
 void fire_reset(cfneb_band *b) {
     read_params(b);
@@ -1847,6 +1855,8 @@ int cfneb_get_state(const cfneb_band *cb, double *X, double *F, double *Fneb, do
                                                    : ((const double *)tmp.data())[im * stride + i];
         };
         fetch(b->dv.X, X);
+        if (X)
+            for (int im = 0; im < b->N; ++im) lattice_rows_public(b, X + im * per, 1.0);
         fetch(b->dv.F, F);
         fetch(b->dv.Fneb, Fneb);
         if (Fneb) {  // endpoints carry no NEB force
@@ -1883,8 +1893,10 @@ int cfneb_set_state(cfneb_band *b, const double *X) {
         // n + 3 rows per image into the padded row stride (padding stays 0)
         const size_t cnt = (size_t)b->N * stride;
         std::vector<double> pad(cnt, 0.0);
-        for (int im = 0; im < b->N; ++im)
+        for (int im = 0; im < b->N; ++im) {
             std::memcpy(pad.data() + im * stride, X + im * per, per * sizeof(double));
+            lattice_rows_public(b, pad.data() + im * stride, -1.0);
+        }
         if (b->ts == 4) {
             std::vector<float> tmp(cnt);
             for (size_t i = 0; i < cnt; ++i) tmp[i] = (float)pad[i];
@@ -1957,13 +1969,16 @@ int cfneb_shard_set_ghost(cfneb_band *b, int32_t side, const double *X, double e
         enter(b);
         const int img = side == 0 ? 0 : b->N - 1;
         char *dst = (char *)b->dv.X + (size_t)img * b->dv.rows * 3 * b->ts;
+        std::vector<double> xs(X, X + per);
+        lattice_rows_public(b, xs.data(), -1.0);
         std::vector<float> f;
         if (b->ts == 4) {
             f.resize(per);
-            for (size_t i = 0; i < per; ++i) f[i] = (float)X[i];
+            for (size_t i = 0; i < per; ++i) f[i] = (float)xs[i];
             CK(cudaMemcpyAsync(dst, f.data(), per * sizeof(float), cudaMemcpyHostToDevice, b->s));
         } else {
-            CK(cudaMemcpyAsync(dst, X, per * sizeof(double), cudaMemcpyHostToDevice, b->s));
+            CK(cudaMemcpyAsync(dst, xs.data(), per * sizeof(double), cudaMemcpyHostToDevice,
+                               b->s));
         }
         CK(cudaMemcpyAsync(&b->dv.sc[img].E, &energy, sizeof(double), cudaMemcpyHostToDevice,
                            b->s));
@@ -1987,9 +2002,11 @@ int cfneb_shard_get_image(const cfneb_band *cb, int32_t index, double *X, double
         CK(cudaMemcpyAsync(tmp.data(), src, tmp.size(), cudaMemcpyDeviceToHost, b->s));
         CK(cudaMemcpyAsync(&e, &b->dv.sc[index].E, sizeof(double), cudaMemcpyDeviceToHost, b->s));
         CK(cudaStreamSynchronize(b->s));
-        if (X)
+        if (X) {
             for (size_t i = 0; i < per; ++i)
                 X[i] = b->ts == 4 ? ((const float *)tmp.data())[i] : ((const double *)tmp.data())[i];
+            lattice_rows_public(b, X, 1.0);
+        }
         if (energy) *energy = e;
         leave(b);
         return CFNEB_OK;
