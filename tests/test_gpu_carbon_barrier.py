@@ -13,8 +13,10 @@ image, Sec. II.C cell filter).
      within 1 meV of the FP64 path, both within 0.01 eV of the 511-atom
      oracle barrier (the finite-size and cell-relaxation effect is ~2 meV).
    Symmetric hops use an odd image count so that one image starts on the
-   saddle: with an even count the climbing image starts beside it and, on
-   Tersoff's rough surface, often stops on another stationary point.
+   saddle: with an even count the climbing image is one of the two images
+   flanking it, which the mixed path's step energies cannot order, and from
+   the other one its climb can end on another stationary point of Tersoff's
+   rough surface (FP64 bands converge either way).
 
 2. Graphite -> hexagonal diamond, the 2 x 2 x 2 tiling of the 8-atom cells
    (64 atoms), 9 images, interior jitter N(0, 0.01 A) from seed 2510,
